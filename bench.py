@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark of the FE-4DGS differentiable rasterization pass on one GB300.
+
+Workload (default): 200,000 deforming Gaussians, 640x512 frame (fx=fy=560),
+D=32 features, HexPlane 6x64^2x32 + MLP deformation at t=0.5, L1 loss to
+random RGB / feature targets.  A step is one pass of the whole hot path:
+deformation query, projection, SH colour, binning and sort, compositing,
+L1 loss and the full reverse pass.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N>1 (torchrun) every rank renders its own timestamp of the same scene
+(independent replicas, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd FPS & fwd+bwd it/s @640x512, 200k Gaussians, D=32; % of HBM/FP32 roofline"
+WORKLOAD = "endonerf_200k_640x512"
+SMS = 152
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--t", type=float, default=0.5)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic work per kernel (flop counts stated in the design notes)
+# ---------------------------------------------------------------------------
+def flops_gauss_fwd(P, C, deform=True):
+    mlp = 2 * (64 * C + 64 * 64 + 11 * 64) if deform else 0
+    grid = 6 * C * 9 if deform else 0          # 4-tap bilinear (8) + product (1)
+    return P * (mlp + grid + 450)              # projection + EWA + SH-3 colour
+
+
+def flops_gauss_bwd(Pvis, P, C, deform=True):
+    recompute = flops_gauss_fwd(1, C, deform)
+    mlp_b = 2 * (64 * C + 64 * 64 + 11 * 64 + 64 * 64 + 64 * C) if deform else 0
+    grid_b = 6 * C * 24 if deform else 0
+    return Pvis * (recompute + mlp_b + grid_b + 600)
+
+
+def flops_composite_fwd(visits, contribs, D):
+    return 14 * visits + (2 * (4 + D) + 4) * contribs
+
+
+def flops_composite_bwd(visits, contribs, D):
+    # replay (14 per visit), per blended pair: the s dot (2(4+D)), dalpha and
+    # conic/mean terms (~35), and the tile sums of 10+D terms (2 each).
+    return 14 * visits + (2 * (4 + D) + 35 + 2 * (10 + D)) * contribs
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2503_06161_gb300 import _lib, synth
+    from paper_2503_06161_gb300.raster import DeformField, GaussianScene, Rasterizer, camera_struct
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = synth.CONFIGS[args.workload]
+    sc, cam_np, df_np = synth.config_inputs(args.workload)
+    t = (args.t + rank / max(world, 1)) % 1.0 if world > 1 else args.t
+    P, D, W, H = sc.P, sc.D, cam_np.width, cam_np.height
+    HW = W * H
+    bf16 = bool(cfg.get("bf16", False))
+    scene = GaussianScene.from_numpy(sc, dev, bf16=bf16)
+    deform = DeformField.from_numpy(df_np, dev) if df_np is not None else None
+    C = df_np.C if df_np is not None else 0
+    cam = camera_struct(cam_np)
+    rgb_t_np, feat_t_np = synth.make_targets(H, W, D, seed=2)
+    tgt_rgb = torch.as_tensor(rgb_t_np, device=dev)
+    tgt_feat = torch.as_tensor(feat_t_np, device=dev)
+
+    # Capacity: size the duplicate list from a probe forward (+25%).
+    probe = Rasterizer(P, D, W, H, device=dev)
+    probe.forward(scene, cam, deform, t)
+    K0 = probe.stats()["num_dups"]
+    del probe
+    torch.cuda.empty_cache()
+    rast = Rasterizer(P, D, W, H, max_dups=int(K0 * 1.25) + 4096, device=dev)
+    kw = dict(dtype=torch.float32, device=dev)
+    out = (torch.empty(3, H, W, **kw), torch.empty(H, W, **kw), torch.empty(H, W, **kw), torch.empty(HW, D, **kw))
+    g_rgb = torch.empty(3, H, W, **kw)
+    g_feat = torch.empty(HW, D, **kw)
+    losses = torch.zeros(2, **kw)
+    scratch = torch.empty(2048, **kw)
+    grads = dict(means=torch.empty(P, 3, **kw), log_scales=torch.empty(P, 3, **kw), quats=torch.empty(P, 4, **kw),
+                 opacity_logits=torch.empty(P, **kw), sh=torch.empty(P, 16, 3, **kw), feat=torch.empty(P, D, **kw))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, **kw)
+
+    def step(sc_obj=scene, df_obj=deform):
+        rast.forward(sc_obj, cam, df_obj, t, out=out)
+        _lib.fe_l1_loss_grad(out[0], tgt_rgb, HW, g_rgb, losses[0:1], scratch[:1024])
+        _lib.fe_l1_loss_grad(out[3], tgt_feat, HW, g_feat, losses[1:2], scratch[1024:])
+        rast.backward(sc_obj, cam, df_obj, t, g_rgb, None, None, g_feat, grads=grads)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = rast.stats()
+    K = st["num_dups"]
+    counts = torch.zeros(2, dtype=torch.int64, device=dev)
+    _lib.fe_count_pairs(scene.struct(), cam, rast.opts, rast.workspace, counts)
+    visits, contribs = (int(x) for x in counts.cpu())
+
+    # ---- timed fwd+bwd loop: L2 flushed before every step, events per step
+    K_steps = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(K_steps)]
+    stream = torch.cuda.current_stream()
+    for row in ev:
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for i in range(K_steps):
+        flush.zero_()
+        _lib.set_events(rast.opts, ev[i][1:9])
+        ev[i][0].record(stream)
+        step()
+        ev[i][9].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    _lib.set_events(rast.opts, None)
+    step_ms = [ev[i][0].elapsed_time(ev[i][9]) for i in range(K_steps)]
+    stage_names = ["deform_project", "binning", "composite_fwd", "loss", "composite_bwd", "feat_grad", "gauss_bwd"]
+    bounds = [(1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 7), (7, 8)]
+    stages = {n: statistics.mean(ev[i][a].elapsed_time(ev[i][b]) for i in range(K_steps))
+              for n, (a, b) in zip(stage_names, bounds)}
+    fwd_ms = statistics.mean(ev[i][1].elapsed_time(ev[i][4]) for i in range(K_steps))
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # ---- forward-only FPS (rendering, the paper's speed metric)
+    fwd_only = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(max(3, K_steps)):
+        flush.zero_()
+        e0.record(stream)
+        rast.forward(scene, cam, deform, t, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fwd_only.append(e0.elapsed_time(e1))
+    fwd_only_ms = statistics.mean(fwd_only)
+
+    # ---- roofline of the dominant kernel
+    clock_mhz = clk.get("sm_mhz") or 2070.0
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12   # TFLOP/s at the sampled clock
+    alu_peak_max = SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    probe_tflops = _lib.fe_probe_fp32_peak(4096) / 1e12
+    nvis = int(st["num_visible"])
+    work = {
+        "composite_fwd": flops_composite_fwd(visits, contribs, D),
+        "composite_bwd": flops_composite_bwd(visits, contribs, D),
+        "deform_project": flops_gauss_fwd(P, C, deform is not None),
+        "gauss_bwd": flops_gauss_bwd(nvis, P, C, deform is not None),
+    }
+    kern = {}
+    for n, fl in work.items():
+        a = fl / (stages[n] * 1e-3) / 1e12
+        kern[n] = {"ms": round(stages[n], 4), "tflops": round(a, 3), "frac_of_alu_peak": round(a / alu_peak, 4)}
+    for n in ("binning", "loss", "feat_grad"):
+        kern[n] = {"ms": round(stages[n], 4)}
+    dom = max(work, key=lambda n: stages[n])
+    ach = work[dom] / (stages[dom] * 1e-3) / 1e12
+    roofline = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
+                "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4), "traffic": None,
+                "peak_basis": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz "
+                              f"(median SM clock sampled in the timed region; {alu_peak_max:.1f} at 2070 MHz max)",
+                "fma_probe_tflops": round(probe_tflops, 2)}
+
+    # ---- end to end through host buffers (pinned), copies inside the region
+    e2e = None
+    if not args.no_e2e:
+        host = {k: v.detach().cpu().pin_memory() for k, v in dict(
+            means=scene.means, log_scales=scene.log_scales, quats=scene.quats, opacity_logits=scene.opacity_logits,
+            sh=scene.sh, feat=scene.feat, tgt_rgb=tgt_rgb, tgt_feat=tgt_feat).items()}
+        if deform is not None:
+            for k in ("planes", "w1", "b1", "w2", "b2", "wh", "bh", "noise"):
+                host["df_" + k] = getattr(deform, k).detach().cpu().pin_memory()
+        dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+        host_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in grads.items()}
+        host_loss = torch.empty(2).pin_memory()
+        sc_e = GaussianScene(dev_in["means"], dev_in["log_scales"], dev_in["quats"], dev_in["opacity_logits"],
+                             dev_in["sh"], dev_in["feat"], scene.sh_degree)
+        df_e = None
+        if deform is not None:
+            df_e = DeformField(dev_in["df_planes"], dev_in["df_w1"], dev_in["df_b1"], dev_in["df_w2"],
+                               dev_in["df_b2"], dev_in["df_wh"], dev_in["df_bh"], deform.bbox_min, deform.bbox_max,
+                               dev_in["df_noise"], deform.noise_scale)
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + 8
+
+        def e2e_step():
+            for k, v in host.items():
+                dev_in[k].copy_(v, non_blocking=True)
+            rast.forward(sc_e, cam, df_e, t, out=out)
+            _lib.fe_l1_loss_grad(out[0], dev_in["tgt_rgb"], HW, g_rgb, losses[0:1], scratch[:1024])
+            _lib.fe_l1_loss_grad(out[3], dev_in["tgt_feat"], HW, g_feat, losses[1:2], scratch[1024:])
+            rast.backward(sc_e, cam, df_e, t, g_rgb, None, None, g_feat, grads=grads)
+            for k, v in grads.items():
+                host_out[k].copy_(v, non_blocking=True)
+            host_loss.copy_(losses, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        for _ in range(K_steps):
+            e2e_step()
+        x1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = x0.elapsed_time(x1) / K_steps
+        e2e = {"value": round(world * 1000.0 / e2e_ms, 3), "unit": "it/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4)}
+
+    launches_per_step = 1 + 1 + 4 + 1 + rast_tile_passes(W, H) + 1 + 1 + 4 + 3
+    result = {
+        "metric": METRIC, "value": round(world * 1000.0 / ms, 3), "unit": "it/s", "n_gpus": world,
+        "steps": K_steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "gaussians": P, "width": W, "height": H, "D": D,
+                   "storage": "bf16 sh/feat" if bf16 else "f32",
+                   "deform": f"hexplane 6x{df_np.R}^2x{C} + MLP {C}-64-64-11" if df_np is not None else "static",
+                   "t": t, "step": "deform+project+bin+sort+composite fwd, L1 rgb+feat, full reverse",
+                   "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
+        "fwd_fps": round(world * 1000.0 / fwd_only_ms, 2), "fwd_ms": round(fwd_only_ms, 4),
+        "fwd_ms_in_step": round(fwd_ms, 4),
+        "K": int(K), "visible": nvis, "pairs": {"visits": visits, "blended": contribs,
+                                                  "visits_per_pixel": round(visits / HW, 1)},
+        "kernels": kern, "roofline": roofline, "gpu_launches": launches_per_step * K_steps,
+        "clocks": clk, "wall_s_timed_loop": round(wall, 4),
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.workload, budget_s=20.0)
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def rast_tile_passes(W, H, tile=16):
+    n = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)
+    bits = 1
+    while (1 << bits) < n:
+        bits += 1
+    return (bits + 7) // 8
+
+
+# ---------------------------------------------------------------------------
+# FP64 oracle on the host cores (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_sample(O, sc, cam, df, t, npix, seed):
+    rng = np.random.default_rng(seed)
+    pix = np.c_[rng.integers(0, cam.width, npix), rng.integers(0, cam.height, npix)].astype(np.int32)
+    G = dict(g_rgb=rng.normal(size=(npix, 3)), g_feat=rng.normal(size=(npix, sc.D)))
+    t0 = time.perf_counter()
+    O.backward(sc, cam, df, t, (0, 0, 0), pix, G["g_rgb"], None, None, G["g_feat"])
+    return time.perf_counter() - t0
+
+
+def oracle_rate(workload: str, budget_s: float):
+    """Fwd+bwd it/s of the FP64 oracle for a full frame, extrapolated from
+    timed samples: fixed per-call cost (per-Gaussian deformation, projection
+    and reverse chain for every Gaussian) from a 1-pixel call, per-pixel cost
+    from an n-pixel call (n sized to the budget)."""
+    from oracle import oracle as O
+    from paper_2503_06161_gb300 import synth
+    sc, cam, df = synth.config_inputs(workload)
+    t = 0.5
+    fixed = _oracle_sample(O, sc, cam, df, t, 1, 0)
+    n = 64
+    tn = _oracle_sample(O, sc, cam, df, t, n, 1)
+    per_pix = max(tn - fixed, 1e-9) / (n - 1)
+    n2 = int(max(64, min(cam.width * cam.height, (budget_s - fixed - tn) / max(per_pix, 1e-9) * 0.5)))
+    tn2 = _oracle_sample(O, sc, cam, df, t, n2, 2)
+    per_pix = max(tn2 - fixed, 1e-9) / (n2 - 1)
+    full = fixed + per_pix * cam.width * cam.height
+    return 1.0 / full, O.num_threads(), n2, fixed, per_pix
+
+
+def cpu_baseline(workload: str, budget_s: float = 20.0) -> dict:
+    rate, cores, n2, fixed, per_pix = oracle_rate(workload, budget_s)
+    return {"value": rate, "unit": "it/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle fwd+bwd on {n2} random pixels of the full scene (all Gaussians deformed, "
+                      f"projected and back-propagated: {fixed:.2f} s fixed) + {per_pix * 1e3:.2f} ms/pixel, "
+                      f"extrapolated to one full frame"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2503_06161_gb300 import synth
+    sc, cam, df = synth.config_inputs(args.workload)
+    t = args.t
+    fixed = _oracle_sample(O, sc, cam, df, t, 1, 0)
+    n = 64
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt = _oracle_sample(O, sc, cam, df, t, n, 10 + i)
+        if i >= args.warmup:
+            times.append(dt)
+    per_pix = max(statistics.mean(times) - fixed, 1e-9) / (n - 1)
+    full = fixed + per_pix * cam.width * cam.height
+    value = 1.0 / full
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "gaussians": sc.P, "width": cam.width, "height": cam.height,
+                      "D": sc.D, "t": t},
+           "cpu_baseline": {"value": value, "unit": "it/s", "cores": O.num_threads(), "kind": "oracle",
+                            "sample": f"each step: FP64 oracle fwd+bwd on {n} random pixels of the full scene; "
+                                      f"{fixed:.2f} s fixed per-Gaussian cost + {per_pix * 1e3:.2f} ms/pixel "
+                                      f"extrapolated to one full frame"},
+           "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * fe4dgs.h -- C ABI of the GB300 (sm_103a) FE-4DGS rasterization library.
+ *
+ * One differentiable tile-rasterization pass of FeatureEndo-4DGS
+ * (arXiv 2503.06161): per-Gaussian deformation query (Sec. 3.2, Eq. 4-6),
+ * EWA projection (Sec. 3.3, Sigma' = J W Sigma W^T J^T), SH colour
+ * (Sec. 3.1), (tile, depth) binning and sort (the tile-based rasterization
+ * of 3DGS the paper builds on, Sec. 2.1), and front-to-back blending of
+ * colour, a D-channel semantic feature and depth in one pass (Sec. 3.3,
+ * Eq. 7-8), plus the reverse pass of all of it.
+ *
+ * Conventions shared by every entry point:
+ *  - Every array pointer is a DEVICE pointer owned by the caller, except
+ *    where "host" is written.  The library never frees caller memory and
+ *    allocates no device memory: scratch space is the caller's workspace.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream).  A return of FE_OK means the work was enqueued;
+ *    device-side conditions (duplicate-list overflow, a bounded wait that
+ *    gave up, non-finite input) are recorded in the workspace and read
+ *    back with fe_read_stats().
+ *  - Arrays are row-major and densely packed, float32 unless stated;
+ *    bfloat16 arrays hold raw 16-bit patterns.
+ *  - Pixel (x, y) covers [x, x+1) x [y, y+1); its centre is (x+0.5, y+0.5).
+ *  - No entry point throws; each returns an fe_status.
+ */
+#ifndef FE4DGS_H
+#define FE4DGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FE_OK = 0,
+  FE_ERR_INVALID_ARG = 1,   /* NULL pointer, negative size, bad tile shape, ... */
+  FE_ERR_CUDA = 2,          /* a CUDA runtime call failed (launch, memset, ...) */
+  FE_ERR_WORKSPACE = 3,     /* workspace too small, or (stats) duplicate capacity exceeded */
+  FE_ERR_UNSUPPORTED = 4,   /* D, plane channels, SH degree or tile shape not compiled in */
+  FE_ERR_NONFINITE = 5,     /* (stats) a non-finite Gaussian parameter was seen */
+  FE_ERR_TIMEOUT = 6,       /* (stats) a bounded device-side wait gave up */
+  FE_ERR_STATE = 7          /* backward called on a workspace without a matching forward */
+} fe_status;
+
+/* Pinhole camera (Sec. 3.3).  u = fx * x/z + cx, v = fy * y/z + cy for the
+ * camera-space point (x, y, z) = world_to_cam * (X, Y, Z, 1).  Gaussians
+ * with z <= znear are culled. */
+typedef struct {
+  int width, height;        /* image size in pixels, both >= 1 */
+  float fx, fy, cx, cy;
+  float world_to_cam[16];   /* host array, row-major 4x4 rigid transform */
+  float campos[3];          /* host array, camera centre in world space (SH view direction) */
+  float znear;
+} fe_camera;
+
+/* Canonical Gaussians (Sec. 3.1, Eq. 1-2) with a D-channel semantic
+ * feature z (Sec. 3.2-3.3).  Opacity o = sigmoid(logit); scale s = exp(log_scale);
+ * rotation from the quaternion (w, x, y, z) after normalisation. */
+typedef struct {
+  int P;                    /* number of Gaussians, >= 0 */
+  int D;                    /* feature channels: 16, 32, 64 or 128 */
+  int sh_degree;            /* 0..3; sh always holds 16 coefficients per channel */
+  int sh_bf16;              /* 1: sh holds bfloat16, else float32 */
+  int feat_bf16;            /* 1: feat holds bfloat16, else float32 */
+  const float *means;       /* [P,3] */
+  const float *log_scales;  /* [P,3] */
+  const float *quats;       /* [P,4] (w, x, y, z), any non-zero length */
+  const float *opacity_logits; /* [P] */
+  const void *sh;           /* [P,16,3] coefficient-major: sh[g][k][channel] */
+  const void *feat;         /* [P,D] */
+} fe_gaussians;
+
+/* FST deformation field (Sec. 3.2, Eq. 4 and 6; Appendix A), single
+ * resolution: six planes xy, xz, yz, xt, yt, zt sampled bilinearly at the
+ * Gaussian's normalised (x, y, z, t) (grid corners at -1 and +1, positions
+ * clamped to the border), multiplied elementwise into f[C], then
+ * h1 = relu(W1 f + b1), h2 = relu(W2 h1 + b2), delta = Wh h2 + bh with
+ * delta = (d_mu[3], d_q[4], d_s[3], d_o[1]) applied as
+ * mu + d_mu (+ noise_scale * t * noise), normalise(q + d_q), log_s + d_s,
+ * logit + d_o. */
+typedef struct {
+  int C;                    /* plane channels: 32 or 64 */
+  int R;                    /* plane resolution (R x R), >= 2 */
+  const float *planes;      /* [6,R,R,C] channels-last; plane k index [i][j] with i along
+                               the first coordinate of the pair, j along the second */
+  const float *w1, *b1;     /* [64,C], [64] */
+  const float *w2, *b2;     /* [64,64], [64] */
+  const float *wh, *bh;     /* [11,64], [11] */
+  float bbox_min[3], bbox_max[3]; /* host arrays: scene box mapped to [-1,1]^3 */
+  const float *noise;       /* [P,3] or NULL */
+  float noise_scale;
+} fe_deform;
+
+typedef struct {
+  int tile_w, tile_h;       /* tile shape; tile_w * tile_h == 256, each in {8,16,32} */
+  float bg[3];              /* background colour added as bg * T_final */
+  int64_t max_dups;         /* capacity of the (Gaussian, tile) list; 0 = 16 * P + 4096 */
+  int forward_only;         /* 1: workspace without backward storage */
+  void *const *events;      /* profiling: NULL, or host array of 8 cudaEvent_t (NULL entries
+                               skipped) recorded on the stream at stage boundaries:
+                               forward [0] start [1] after deform+projection [2] after
+                               binning [3] after compositing; backward [4] start [5] after
+                               the compositing reverse [6] after the feature-gradient sum
+                               [7] after the per-Gaussian reverse */
+} fe_opts;
+
+/* Render outputs (Eq. 7-8 plus depth): rgb [3,H,W] planar = sum w c + bg T;
+ * depth [H,W] = sum w z_cam (not normalised); alpha [H,W] = 1 - T_final;
+ * feat [H*W, D] channels-last = sum w z. */
+typedef struct {
+  float *rgb, *depth, *alpha, *feat;
+} fe_outputs;
+
+/* Upstream gradients, same shapes as fe_outputs; any may be NULL (= zero). */
+typedef struct {
+  const float *rgb, *depth, *alpha, *feat;
+} fe_output_grads;
+
+/* Parameter gradients (overwritten, float32 even for bfloat16 storage):
+ * means [P,3], log_scales [P,3], quats [P,4], opacity_logits [P],
+ * sh [P,16,3], feat [P,D].  Deformation-network weight gradients are not
+ * produced (the canonical mean receives the gradient through the grid). */
+typedef struct {
+  float *means, *log_scales, *quats, *opacity_logits, *sh, *feat;
+} fe_grads;
+
+/* Host-side view of the workspace header, filled by fe_read_stats(). */
+typedef struct {
+  int64_t num_dups;         /* K: (Gaussian, tile) pairs of the last forward */
+  int64_t capacity;         /* duplicate capacity of this workspace */
+  int64_t num_visible;      /* Gaussians in front of znear with a non-empty rect */
+  uint32_t device_errors;   /* bit 0 overflow, bit 1 timeout, bit 2 non-finite */
+  int32_t has_forward;      /* 1 after a forward on this workspace */
+} fe_stats;
+
+/* Bytes of workspace for P Gaussians, D channels, a width x height image
+ * and opts (NULL = defaults).  Returns FE_ERR_UNSUPPORTED for a tile shape
+ * or D that is not compiled in. */
+fe_status fe_workspace_size(int P, int D, int width, int height, const fe_opts *opts, size_t *bytes);
+
+/* Forward pass (Sec. 3.2-3.3): deform (deform may be NULL: static scene)
+ * at time t, project, colour, bin, sort and composite.  The workspace (at
+ * least fe_workspace_size bytes, 256-byte aligned, device memory) receives
+ * the state the backward pass needs; it must not be modified in between.
+ * All output pointers are required. */
+fe_status fe_render_forward(const fe_gaussians *g, const fe_deform *deform, const fe_camera *cam, float t,
+                            const fe_opts *opts, void *workspace, size_t workspace_bytes,
+                            const fe_outputs *out, void *stream);
+
+/* Reverse pass of fe_render_forward: same g, deform, cam, t, opts and
+ * workspace as the forward that preceded it on this stream.  Replays
+ * transmittance from T_final (no per-pixel lists), reduces per tile in a
+ * fixed order and sums per-(tile, Gaussian) partials in a fixed order:
+ * deterministic, no floating-point atomics. */
+fe_status fe_render_backward(const fe_gaussians *g, const fe_deform *deform, const fe_camera *cam, float t,
+                             const fe_opts *opts, void *workspace, size_t workspace_bytes,
+                             const fe_output_grads *grad_out, const fe_grads *grads, void *stream);
+
+/* Integer stage alone (tile-based binning of 3DGS, Sec. 2.1): given
+ * projected centres uv [P,2], integer radii [P] (<= 0: culled) and depths
+ * [P] (float32), build the tile lists sorted by (tile, depth), ties by
+ * index, in the workspace.  A Gaussian covers the pixels whose centre lies
+ * in the square of half-side r around (u, v); its pixel rect is
+ * [ceil(u-(r+0.5)), floor(u+(r-0.5))] x [ceil(v-(r+0.5)), floor(v+(r-0.5))]
+ * in binary32, clamped to the image.  Read the result with fe_debug_dump. */
+fe_status fe_tile_bin(int P, const float *uv, const int *radius, const float *depth, int width, int height,
+                      const fe_opts *opts, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Synchronous: wait for `stream`, then copy the workspace header to host. */
+fe_status fe_read_stats(const void *workspace, size_t workspace_bytes, int P, int D, int width, int height,
+                        const fe_opts *opts, fe_stats *stats, void *stream);
+
+/* Pair counts of the last forward's compositing, for the roofline: visits
+ * (pixel, list entry) pairs a pixel evaluated before stopping, contrib the
+ * pairs that were blended.  counts: device array of 2 uint64 (overwritten).
+ * Re-runs the compositing on the same workspace (outputs are not written). */
+fe_status fe_count_pairs(const fe_gaussians *g, const fe_camera *cam, const fe_opts *opts, void *workspace,
+                         size_t workspace_bytes, uint64_t *counts, void *stream);
+
+/* Copy forward state out for parity tests; any pointer may be NULL.
+ * keys [cap] u64 = (tile << 32) | bits(depth), gauss [cap] u32 (sorted
+ * Gaussian index per list entry), ranges [tiles,2] u32 (start, end),
+ * n_contrib [H*W] u32, t_final [H*W] f32, uv [P,2], conic [P,3]
+ * (inverse of the dilated 2D covariance), opacity [P], depth [P],
+ * rgb [P,3] (clamped), radius [P] i32, touched [P] u32.  Entries past the
+ * last forward's K are left untouched. */
+fe_status fe_debug_dump(const void *workspace, size_t workspace_bytes, int P, int D, int width, int height,
+                        const fe_opts *opts, uint64_t *keys, uint32_t *gauss, uint32_t *ranges,
+                        uint32_t *n_contrib, float *t_final, float *uv, float *conic, float *opacity,
+                        float *depth, float *rgb, int32_t *radius, uint32_t *touched, void *stream);
+
+/* Per-pixel L1 loss (Sec. 3.3, Eq. 10 form: mean over `rows` pixels of the
+ * L1 norm over the channels) of pred against target, both [n] float32 with
+ * n = rows * channels in any layout.  Writes grad [n] = sign(pred - target)
+ * / rows (sign(0) = 0) and *loss (one device float) = sum |pred - target|
+ * / rows.  scratch: device array of at least 1024 floats for the per-block
+ * partial sums; summation order is fixed, so the result is deterministic. */
+fe_status fe_l1_loss_grad(const float *pred, const float *target, int64_t n, int64_t rows, float *grad,
+                          float *loss, float *scratch, void *stream);
+
+/* Measured single-precision FMA throughput: runs an FMA-chain kernel over
+ * the whole GPU for `iters` iterations per thread and writes FLOP/s
+ * (2 per FMA) to *flops (host).  Synchronous; used for the FP32 roofline. */
+fe_status fe_probe_fp32_peak(int iters, double *flops, void *stream);
+
+const char *fe_status_string(fe_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FE4DGS_H */

@@ -1,0 +1,254 @@
+"""ctypes binding of ``libfe4dgs.so`` (the C ABI in ``include/fe4dgs.h``).
+
+Argument marshalling only: every function here has the name of its C entry
+point, turns torch tensors into raw device pointers and the current CUDA
+stream into a ``cudaStream_t`` handle, and raises on a non-zero status.
+There is no fallback: if the library is missing the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfe4dgs.so")
+
+c_int, c_float, c_void_p, c_int64 = ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_int64
+
+FE_OK = 0
+STATUS = {0: "FE_OK", 1: "FE_ERR_INVALID_ARG", 2: "FE_ERR_CUDA", 3: "FE_ERR_WORKSPACE", 4: "FE_ERR_UNSUPPORTED",
+          5: "FE_ERR_NONFINITE", 6: "FE_ERR_TIMEOUT", 7: "FE_ERR_STATE"}
+
+
+class FeError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        self.code = code
+        super().__init__(f"{fn} returned {STATUS.get(code, code)}: {status_string(code)}")
+
+
+class fe_camera(ctypes.Structure):
+    _fields_ = [("width", c_int), ("height", c_int), ("fx", c_float), ("fy", c_float), ("cx", c_float),
+                ("cy", c_float), ("world_to_cam", c_float * 16), ("campos", c_float * 3), ("znear", c_float)]
+
+
+class fe_gaussians(ctypes.Structure):
+    _fields_ = [("P", c_int), ("D", c_int), ("sh_degree", c_int), ("sh_bf16", c_int), ("feat_bf16", c_int),
+                ("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p), ("opacity_logits", c_void_p),
+                ("sh", c_void_p), ("feat", c_void_p)]
+
+
+class fe_deform(ctypes.Structure):
+    _fields_ = [("C", c_int), ("R", c_int), ("planes", c_void_p), ("w1", c_void_p), ("b1", c_void_p),
+                ("w2", c_void_p), ("b2", c_void_p), ("wh", c_void_p), ("bh", c_void_p),
+                ("bbox_min", c_float * 3), ("bbox_max", c_float * 3), ("noise", c_void_p),
+                ("noise_scale", c_float)]
+
+
+class fe_opts(ctypes.Structure):
+    _fields_ = [("tile_w", c_int), ("tile_h", c_int), ("bg", c_float * 3), ("max_dups", c_int64),
+                ("forward_only", c_int), ("events", ctypes.POINTER(c_void_p))]
+
+
+class fe_outputs(ctypes.Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("alpha", c_void_p), ("feat", c_void_p)]
+
+
+class fe_output_grads(ctypes.Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("alpha", c_void_p), ("feat", c_void_p)]
+
+
+class fe_grads(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p), ("opacity_logits", c_void_p),
+                ("sh", c_void_p), ("feat", c_void_p)]
+
+
+class fe_stats(ctypes.Structure):
+    _fields_ = [("num_dups", c_int64), ("capacity", c_int64), ("num_visible", c_int64),
+                ("device_errors", ctypes.c_uint32), ("has_forward", ctypes.c_int32)]
+
+
+_P = ctypes.POINTER
+_SIGNATURES = {
+    "fe_workspace_size": [c_int, c_int, c_int, c_int, _P(fe_opts), _P(ctypes.c_size_t)],
+    "fe_render_forward": [_P(fe_gaussians), _P(fe_deform), _P(fe_camera), c_float, _P(fe_opts), c_void_p,
+                          ctypes.c_size_t, _P(fe_outputs), c_void_p],
+    "fe_render_backward": [_P(fe_gaussians), _P(fe_deform), _P(fe_camera), c_float, _P(fe_opts), c_void_p,
+                           ctypes.c_size_t, _P(fe_output_grads), _P(fe_grads), c_void_p],
+    "fe_tile_bin": [c_int, c_void_p, c_void_p, c_void_p, c_int, c_int, _P(fe_opts), c_void_p, ctypes.c_size_t,
+                    c_void_p],
+    "fe_read_stats": [c_void_p, ctypes.c_size_t, c_int, c_int, c_int, c_int, _P(fe_opts), _P(fe_stats), c_void_p],
+    "fe_debug_dump": [c_void_p, ctypes.c_size_t, c_int, c_int, c_int, c_int, _P(fe_opts)] + [c_void_p] * 13
+                     + [c_void_p],
+    "fe_probe_fp32_peak": [c_int, _P(ctypes.c_double), c_void_p],
+    "fe_l1_loss_grad": [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p, c_void_p, c_void_p],
+    "fe_count_pairs": [_P(fe_gaussians), _P(fe_camera), _P(fe_opts), c_void_p, ctypes.c_size_t, c_void_p,
+                       c_void_p],
+}
+
+_lib = None
+
+
+def load():
+    """Load the in-tree shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2503_06161_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = c_int
+        L.fe_status_string.argtypes = [c_int]
+        L.fe_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return load().fe_status_string(int(code)).decode()
+
+
+def _check(fn: str, rc: int):
+    if rc != FE_OK:
+        raise FeError(fn, rc)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def make_opts(tile=(16, 16), bg=(0.0, 0.0, 0.0), max_dups=0, forward_only=False) -> fe_opts:
+    o = fe_opts()
+    o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
+    o.bg[:] = [float(x) for x in bg]
+    o.max_dups = int(max_dups)
+    o.forward_only = 1 if forward_only else 0
+    return o
+
+
+def make_camera(width, height, fx, fy, cx, cy, world_to_cam, campos, znear=0.2) -> fe_camera:
+    c = fe_camera()
+    c.width, c.height = int(width), int(height)
+    c.fx, c.fy, c.cx, c.cy = float(fx), float(fy), float(cx), float(cy)
+    c.world_to_cam[:] = [float(v) for v in list(world_to_cam)]
+    c.campos[:] = [float(v) for v in list(campos)]
+    c.znear = float(znear)
+    return c
+
+
+def make_gaussians(means, log_scales, quats, opacity_logits, sh, feat, sh_degree=3) -> fe_gaussians:
+    import torch
+    g = fe_gaussians()
+    g.P = int(means.shape[0])
+    g.D = int(feat.shape[1])
+    g.sh_degree = int(sh_degree)
+    g.sh_bf16 = int(sh.dtype == torch.bfloat16)
+    g.feat_bf16 = int(feat.dtype == torch.bfloat16)
+    g.means, g.log_scales, g.quats = _ptr(means), _ptr(log_scales), _ptr(quats)
+    g.opacity_logits, g.sh, g.feat = _ptr(opacity_logits), _ptr(sh), _ptr(feat)
+    return g
+
+
+def make_deform(planes, w1, b1, w2, b2, wh, bh, bbox_min, bbox_max, noise=None, noise_scale=0.01) -> fe_deform:
+    d = fe_deform()
+    d.C = int(planes.shape[3])
+    d.R = int(planes.shape[1])
+    d.planes, d.w1, d.b1, d.w2, d.b2, d.wh, d.bh = (_ptr(x) for x in (planes, w1, b1, w2, b2, wh, bh))
+    d.bbox_min[:] = [float(v) for v in bbox_min]
+    d.bbox_max[:] = [float(v) for v in bbox_max]
+    d.noise = _ptr(noise)
+    d.noise_scale = float(noise_scale)
+    return d
+
+
+def fe_workspace_size(P: int, D: int, width: int, height: int, opts: fe_opts) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_workspace_size", load().fe_workspace_size(P, D, width, height, ctypes.byref(opts), ctypes.byref(n)))
+    return int(n.value)
+
+
+def fe_render_forward(g: fe_gaussians, deform, cam: fe_camera, t: float, opts: fe_opts, workspace, rgb, depth,
+                      alpha, feat, stream=None):
+    out = fe_outputs(_ptr(rgb), _ptr(depth), _ptr(alpha), _ptr(feat))
+    rc = load().fe_render_forward(ctypes.byref(g), ctypes.byref(deform) if deform is not None else None,
+                                  ctypes.byref(cam), float(t), ctypes.byref(opts), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), ctypes.byref(out), _stream(stream))
+    _check("fe_render_forward", rc)
+
+
+def fe_render_backward(g: fe_gaussians, deform, cam: fe_camera, t: float, opts: fe_opts, workspace, g_rgb, g_depth,
+                       g_alpha, g_feat, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_feat, stream=None):
+    go = fe_output_grads(_ptr(g_rgb), _ptr(g_depth), _ptr(g_alpha), _ptr(g_feat))
+    gr = fe_grads(_ptr(d_means), _ptr(d_log_scales), _ptr(d_quats), _ptr(d_opacity_logits), _ptr(d_sh),
+                  _ptr(d_feat))
+    rc = load().fe_render_backward(ctypes.byref(g), ctypes.byref(deform) if deform is not None else None,
+                                   ctypes.byref(cam), float(t), ctypes.byref(opts), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), ctypes.byref(go), ctypes.byref(gr),
+                                   _stream(stream))
+    _check("fe_render_backward", rc)
+
+
+def fe_tile_bin(uv, radius, depth, width: int, height: int, opts: fe_opts, workspace, stream=None):
+    P = int(radius.shape[0])
+    rc = load().fe_tile_bin(P, _ptr(uv), _ptr(radius), _ptr(depth), int(width), int(height), ctypes.byref(opts),
+                            _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check("fe_tile_bin", rc)
+
+
+def fe_read_stats(workspace, P: int, D: int, width: int, height: int, opts: fe_opts, stream=None,
+                  raise_on_error: bool = True) -> dict:
+    s = fe_stats()
+    rc = load().fe_read_stats(_ptr(workspace), workspace.numel() * workspace.element_size(), P, D, width, height,
+                              ctypes.byref(opts), ctypes.byref(s), _stream(stream))
+    if raise_on_error:
+        _check("fe_read_stats", rc)
+    return dict(status=rc, num_dups=s.num_dups, capacity=s.capacity, num_visible=s.num_visible,
+                device_errors=s.device_errors, has_forward=s.has_forward)
+
+
+def fe_debug_dump(workspace, P: int, D: int, width: int, height: int, opts: fe_opts, keys=None, gauss=None,
+                  ranges=None, n_contrib=None, t_final=None, uv=None, conic=None, opacity=None, depth=None,
+                  rgb=None, radius=None, touched=None, stream=None):
+    rc = load().fe_debug_dump(_ptr(workspace), workspace.numel() * workspace.element_size(), P, D, width, height,
+                              ctypes.byref(opts), _ptr(keys), _ptr(gauss), _ptr(ranges), _ptr(n_contrib),
+                              _ptr(t_final), _ptr(uv), _ptr(conic), _ptr(opacity), _ptr(depth), _ptr(rgb),
+                              _ptr(radius), _ptr(touched), _stream(stream))
+    _check("fe_debug_dump", rc)
+
+
+def set_events(opts: fe_opts, events):
+    """Attach 8 stage-boundary events (torch.cuda.Event, recorded once so
+    their handles exist) to opts; None detaches.  Keeps the array alive."""
+    if events is None:
+        opts.events = None
+        opts._event_array = None
+        return
+    arr = (c_void_p * 8)(*[c_void_p(e.cuda_event) if e is not None else None for e in events])
+    opts._event_array = arr
+    opts.events = ctypes.cast(arr, ctypes.POINTER(c_void_p))
+
+
+def fe_l1_loss_grad(pred, target, rows: int, grad, loss, scratch, stream=None):
+    rc = load().fe_l1_loss_grad(_ptr(pred), _ptr(target), int(pred.numel()), int(rows), _ptr(grad), _ptr(loss),
+                                _ptr(scratch), _stream(stream))
+    _check("fe_l1_loss_grad", rc)
+
+
+def fe_count_pairs(g: fe_gaussians, cam: fe_camera, opts: fe_opts, workspace, counts, stream=None):
+    rc = load().fe_count_pairs(ctypes.byref(g), ctypes.byref(cam), ctypes.byref(opts), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), _ptr(counts), _stream(stream))
+    _check("fe_count_pairs", rc)
+
+
+def fe_probe_fp32_peak(iters: int = 4096, stream=None) -> float:
+    f = ctypes.c_double(0.0)
+    _check("fe_probe_fp32_peak", load().fe_probe_fp32_peak(int(iters), ctypes.byref(f), _stream(stream)))
+    return float(f.value)

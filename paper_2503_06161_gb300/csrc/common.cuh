@@ -1,0 +1,181 @@
+// Shared definitions of the sm_103a FE-4DGS kernels: constants of the
+// compositing recurrence, the workspace layout and small device helpers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fe4dgs.h"
+
+namespace fe {
+
+constexpr int kHidden = 64;   // MLP width W (Appendix A)
+constexpr int kHeads = 11;    // d_mu(3) d_q(4) d_s(3) d_o(1) (Eq. 4)
+constexpr int kThreads = 256; // one pixel per thread in a 256-pixel tile
+
+// Compositing thresholds (readings; the paper gives none): alpha clamp,
+// skip below 1/255, stop before T would drop under 1e-4, EWA dilation.
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kDilation = 0.3f;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// Packed per-Gaussian render record (48 bytes, 16-byte aligned):
+//  [0] u  [1] v  [2] A  [3] B  [4] Cc  [5] opacity  [6] depth
+//  [7] r  [8] g  [9] b  [10] radius (float)  [11] 0
+// with power2 = A dx^2 + B dx dy + Cc dy^2 = log2(e) * power, i.e.
+// A = -0.5 log2(e) a, B = -log2(e) b, Cc = -0.5 log2(e) c for the conic
+// (a, b, c) = inverse of the dilated 2D covariance.
+constexpr int kRec = 12;
+
+// Device-side error bits, sticky within one call.
+enum : uint32_t { kErrOverflow = 1u, kErrTimeout = 2u, kErrNonFinite = 4u };
+
+// Partial-gradient row per (tile, Gaussian) entry, length 10 + D:
+//  [0] du [1] dv [2] dA [3] dB [4] dCc [5] dopacity [6..8] drgb [9] ddepth [10..] dfeat
+constexpr int kPartialScalars = 10;
+
+struct Header {           // first 256 bytes of every workspace
+  uint32_t err;           // error bits
+  uint32_t num_dups;      // K written by keygen (may exceed capacity)
+  uint32_t num_visible;
+  uint32_t has_forward;
+  uint32_t ticket[24];    // per-kernel block tickets (decoupled look-back)
+  uint32_t pad[36];
+};
+static_assert(sizeof(Header) == 256, "header is 256 bytes");
+
+// Radix / scan chunking: 256 threads x 16 items.
+constexpr int kSortItems = 16;
+constexpr int kSortChunk = kThreads * kSortItems;
+
+// Ticket slots in the header.
+enum : int {
+  kTicketDepth0 = 0,  // 4 depth passes
+  kTicketScan = 4,
+  kTicketTile0 = 5,   // up to 3 tile passes
+  kNumTickets = 8,
+};
+
+struct Layout {
+  int P, D, W, H, tw, th, tiles_x, tiles_y, ntiles, tile_passes;
+  int64_t cap;
+  bool with_backward;
+  size_t hdr, rec, rect, touched, dkey[2], dval[2], offs, offs_by_gid, tkey[2], tval[2], gid_of_emit;
+  size_t status, hist, ranges, tfinal, ncontrib, partials, pflags;
+  size_t status_words, scan_blocks_p, sort_blocks_k;
+  size_t total;
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Host-side layout of a workspace; every region 256-byte aligned.
+inline Layout make_layout(int P, int D, int W, int H, int tw, int th, int64_t cap, bool with_backward) {
+  Layout L{};
+  L.P = P; L.D = D; L.W = W; L.H = H; L.tw = tw; L.th = th;
+  L.tiles_x = (W + tw - 1) / tw;
+  L.tiles_y = (H + th - 1) / th;
+  L.ntiles = L.tiles_x * L.tiles_y;
+  int bits = 1;
+  while ((1 << bits) < L.ntiles) ++bits;
+  L.tile_passes = (bits + 7) / 8;
+  L.cap = cap;
+  L.with_backward = with_backward;
+  const size_t Pn = (size_t)(P > 0 ? P : 1);
+  const size_t Kn = (size_t)(cap > 0 ? cap : 1);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  L.hdr = take(sizeof(Header));
+  L.rec = take(Pn * kRec * 4);
+  L.rect = take(Pn * 8);
+  L.touched = take(Pn * 4);
+  for (int i = 0; i < 2; ++i) L.dkey[i] = take(Pn * 4);
+  for (int i = 0; i < 2; ++i) L.dval[i] = take(Pn * 4);
+  L.offs = take((Pn + 1) * 4);
+  L.offs_by_gid = take(Pn * 4);
+  for (int i = 0; i < 2; ++i) L.tkey[i] = take(Kn * 4);
+  for (int i = 0; i < 2; ++i) L.tval[i] = take(Kn * 4);
+  L.gid_of_emit = take(Kn * 4);
+  L.scan_blocks_p = (size_t)ceil_div((int64_t)Pn, kSortChunk);
+  L.sort_blocks_k = (size_t)ceil_div((int64_t)Kn, kSortChunk);
+  // Look-back status words: 4 depth passes (u32 per digit per block), up to 3
+  // tile passes, then one u64 per block of the tiles_touched scan.
+  L.status_words = L.scan_blocks_p * 256 * 4 + L.sort_blocks_k * 256 * 3 + 2 * L.scan_blocks_p;
+  L.status = take(L.status_words * 4);
+  L.hist = take((4 + 3) * 256 * 4);
+  L.ranges = take((size_t)L.ntiles * 8);
+  L.tfinal = take((size_t)W * H * 4);
+  L.ncontrib = take((size_t)W * H * 4);
+  if (with_backward) {
+    L.partials = take(Kn * (size_t)(kPartialScalars + D) * 4);
+    L.pflags = take(Kn);
+  }
+  L.total = off;
+  return L;
+}
+
+template <typename T>
+__host__ __device__ inline T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float(((uint32_t)b) << 16); }
+
+// Tile rect of the pixels whose centre lies in the square of half-side r
+// around (u, v), in binary32 with one rounding per add (no contraction).
+// Returns false when empty.
+__host__ __device__ inline bool pixel_rect(float u, float v, int r, int W, int H, int& x0, int& y0, int& x1, int& y1) {
+#ifdef __CUDA_ARCH__
+  const float rf = (float)r;
+  const float rp = __fadd_rn(rf, 0.5f), rm = __fsub_rn(rf, 0.5f);
+  float fx0 = ceilf(__fsub_rn(u, rp)), fx1 = floorf(__fadd_rn(u, rm));
+  float fy0 = ceilf(__fsub_rn(v, rp)), fy1 = floorf(__fadd_rn(v, rm));
+#else
+  const float rf = (float)r;
+  const float rp = rf + 0.5f, rm = rf - 0.5f;
+  float fx0 = ceilf(u - rp), fx1 = floorf(u + rm);
+  float fy0 = ceilf(v - rp), fy1 = floorf(v + rm);
+#endif
+  fx0 = fmaxf(fx0, 0.0f);
+  fy0 = fmaxf(fy0, 0.0f);
+  fx1 = fminf(fx1, (float)(W - 1));
+  fy1 = fminf(fy1, (float)(H - 1));
+  if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
+  x0 = (int)fx0; x1 = (int)fx1; y0 = (int)fy0; y1 = (int)fy1;
+  return true;
+}
+
+// alpha of record `rec` at pixel centre (pxc, pyc); one evaluation order,
+// shared by the forward and reverse kernels so both take the same skip,
+// clamp and inclusion decisions.  Returns false when the pair is skipped.
+struct PairEval {
+  float dx, dy, G, alpha;
+  bool clamped;
+};
+
+__device__ __forceinline__ bool eval_pair(const float* rec, float pxc, float pyc, PairEval& e) {
+  const float r = rec[10];
+  e.dx = __fsub_rn(pxc, rec[0]);
+  e.dy = __fsub_rn(pyc, rec[1]);
+  if (fabsf(e.dx) > r || fabsf(e.dy) > r) return false;
+  const float p2 = __fadd_rn(__fadd_rn(__fmul_rn(rec[2], __fmul_rn(e.dx, e.dx)), __fmul_rn(rec[4], __fmul_rn(e.dy, e.dy))),
+                             __fmul_rn(rec[3], __fmul_rn(e.dx, e.dy)));
+  if (p2 > 0.0f) return false;
+  e.G = exp2f(p2);
+  const float oG = __fmul_rn(rec[5], e.G);
+  e.clamped = oG > kAlphaMax;
+  e.alpha = e.clamped ? kAlphaMax : oG;
+  return e.alpha >= kAlphaMin;
+}
+
+__device__ __forceinline__ void set_err(uint32_t* err, uint32_t bits) { atomicOr(err, bits); }
+
+}  // namespace fe

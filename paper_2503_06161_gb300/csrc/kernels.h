@@ -1,0 +1,109 @@
+// Internal launcher interface between the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fe {
+
+struct GaussArgs {
+  int P, sh_degree, sh_bf16;
+  const float *means, *log_scales, *quats, *logits;
+  const void* sh;
+  // deformation
+  int has_deform, C, R;
+  const float *planes, *w1, *b1, *w2, *b2, *wh, *bh;
+  float bmin[3], bscale[3];  // coordinate = (mu - bmin) * bscale - 1
+  const float* noise;
+  float noise_scale, t;
+  // camera
+  int W, H, tw, th;
+  float fx, fy, cx, cy, znear, limx, limy;
+  float V[12];
+  float campos[3];
+  // outputs
+  float4* rec;
+  ushort4* rect;
+  uint32_t *touched, *dkey;
+  uint32_t *err, *num_visible;
+};
+
+struct GaussBwdArgs {
+  int D;
+  int64_t cap;
+  const uint32_t *touched, *offs_by_gid;
+  const float* partials;
+  const uint8_t* pflags;
+  float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh, *d_feat;
+};
+
+cudaError_t launch_gauss_fwd(const GaussArgs& a, cudaStream_t st);
+cudaError_t launch_gauss_bwd(const GaussArgs& a, const GaussBwdArgs& b, cudaStream_t st, cudaEvent_t mid);
+
+// Integer stage: binning of projected Gaussians into tile lists.
+struct BinArgs {
+  int P, ntiles, tiles_x, tile_passes;
+  int64_t cap;
+  const ushort4* rect;
+  const uint32_t* touched;
+  uint32_t *dkey[2], *dval[2];  // depth-sort ping-pong
+  uint32_t *offs, *offs_by_gid;
+  uint32_t *tkey[2], *tval[2];  // tile-sort ping-pong
+  uint32_t* gid_of_emit;
+  uint32_t* status;             // decoupled look-back words
+  uint32_t* hist;               // global digit histograms [7][256]
+  uint2* ranges;
+  void* hdr;                    // fe::Header*
+  // results (which ping-pong buffer holds the final data)
+  int depth_final, tile_final;
+};
+
+// Rect / touched / depth key from given (u, v, r, depth) (fe_tile_bin).
+cudaError_t launch_bin_prep(int P, const float* uv, const int* radius, const float* depth, int W, int H, int tw,
+                            int th, ushort4* rect, uint32_t* touched, uint32_t* dkey, uint32_t* num_visible,
+                            cudaStream_t st);
+cudaError_t launch_binning(BinArgs& b, cudaStream_t st);
+
+struct CompositeArgs {
+  int W, H, tw, th, tiles_x, D, feat_bf16;
+  float bg[3];
+  const uint2* ranges;
+  const uint32_t *sorted_e, *gid_of_emit;
+  const float4* rec;
+  const void* feat;
+  float *out_rgb, *out_depth, *out_alpha, *out_feat;
+  float* t_final;
+  uint32_t* n_contrib;
+  // backward
+  const float *g_rgb, *g_depth, *g_alpha, *g_feat;
+  float* partials;
+  uint8_t* pflags;
+  int ntiles;
+  uint64_t* counts;  // non-NULL: counting variant of the forward (no outputs)
+};
+
+cudaError_t launch_composite_fwd(const CompositeArgs& a, cudaStream_t st);
+cudaError_t launch_composite_bwd(const CompositeArgs& a, cudaStream_t st);
+
+struct DumpArgs {
+  int64_t cap;
+  int P, ntiles, HW;
+  const void* hdr;
+  const uint32_t *sorted_tile, *sorted_e, *gid_of_emit, *dkey_by_gid;
+  const uint2* ranges;
+  const uint32_t* ncontrib;
+  const float* tfinal;
+  const float4* rec;
+  const uint32_t* touched;
+  uint64_t* keys;
+  uint32_t *gauss, *ranges_out, *ncontrib_out, *touched_out;
+  float *tfinal_out, *uv, *conic, *opacity, *depth, *rgb;
+  int32_t* radius;
+};
+cudaError_t launch_dump(const DumpArgs& d, cudaStream_t st);
+
+cudaError_t probe_fp32(int iters, double* flops, cudaStream_t st);
+cudaError_t launch_l1(const float* pred, const float* target, int64_t n, int64_t rows, float* grad, float* loss,
+                      float* scratch, cudaStream_t st);
+
+}  // namespace fe

@@ -1,0 +1,80 @@
+// Per-pixel L1 loss and its gradient (Sec. 3.3, Eq. 10 form: mean over
+// pixels of the L1 norm over channels), with a fixed-order two-level sum so
+// the loss value is bitwise deterministic.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace fe {
+
+namespace {
+
+constexpr int kL1Blocks = 1024;
+
+__device__ __forceinline__ float block_sum(float v, float* s_warp) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s_warp[warp] = v;
+  __syncthreads();
+  float t = 0.0f;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_warp[w];
+  return t;
+}
+
+// Grid-stride over float4 groups when aligned, scalars for the tail; each
+// block writes one partial sum.
+__global__ void __launch_bounds__(256) l1_grad_kernel(const float* __restrict__ pred, const float* __restrict__ target,
+                                                       int64_t n, float inv_rows, float* __restrict__ grad,
+                                                       float* __restrict__ partial) {
+  __shared__ float s_warp[8];
+  float acc = 0.0f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(pred) | reinterpret_cast<uintptr_t>(target) |
+                     reinterpret_cast<uintptr_t>(grad)) & 15u) == 0;
+  int64_t done = 0;
+  if (vec) {
+    const int64_t n4 = n / 4;
+    for (int64_t i = i0; i < n4; i += stride) {
+      const float4 p = reinterpret_cast<const float4*>(pred)[i];
+      const float4 t = reinterpret_cast<const float4*>(target)[i];
+      const float d0 = p.x - t.x, d1 = p.y - t.y, d2 = p.z - t.z, d3 = p.w - t.w;
+      acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+      auto sg = [&](float d) { return d > 0.0f ? inv_rows : (d < 0.0f ? -inv_rows : 0.0f); };
+      reinterpret_cast<float4*>(grad)[i] = make_float4(sg(d0), sg(d1), sg(d2), sg(d3));
+    }
+    done = n4 * 4;
+  }
+  for (int64_t i = done + i0; i < n; i += stride) {
+    const float d = pred[i] - target[i];
+    acc += fabsf(d);
+    grad[i] = d > 0.0f ? inv_rows : (d < 0.0f ? -inv_rows : 0.0f);
+  }
+  const float b = block_sum(acc, s_warp);
+  if (threadIdx.x == 0) partial[blockIdx.x] = b;
+}
+
+__global__ void __launch_bounds__(256) l1_finish_kernel(const float* __restrict__ partial, int nparts, float inv_rows,
+                                                         float* loss) {
+  __shared__ float s_warp[8];
+  float acc = 0.0f;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partial[i];
+  const float b = block_sum(acc, s_warp);
+  if (threadIdx.x == 0) *loss = b * inv_rows;
+}
+
+}  // namespace
+
+cudaError_t launch_l1(const float* pred, const float* target, int64_t n, int64_t rows, float* grad, float* loss,
+                      float* scratch, cudaStream_t st) {
+  const float inv = rows > 0 ? 1.0f / (float)rows : 0.0f;
+  int blocks = (int)((n + 1023) / 1024);
+  if (blocks > kL1Blocks) blocks = kL1Blocks;
+  if (blocks < 1) blocks = 1;
+  l1_grad_kernel<<<blocks, 256, 0, st>>>(pred, target, n, inv, grad, scratch);
+  l1_finish_kernel<<<1, 256, 0, st>>>(scratch, blocks, inv, loss);
+  return cudaGetLastError();
+}
+
+}  // namespace fe

@@ -1,0 +1,80 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU, exports
+every entry point that include/fe4dgs.h declares, its structs match the
+ctypes mirrors byte for byte, and host-side argument checks return the
+documented status codes (no CUDA call is made by these)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2503_06161_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fe4dgs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fe_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "fe_render_forward" in names and "fe_render_backward" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (fe_[a-z0-9_]+)\b", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert getattr(lib, n) is not None
+
+
+def test_struct_layouts_match_header(tmp_path):
+    structs = ["fe_camera", "fe_gaussians", "fe_deform", "fe_opts", "fe_outputs", "fe_output_grads", "fe_grads",
+               "fe_stats"]
+    c = "#include <stdio.h>\n#include <stddef.h>\n#include \"fe4dgs.h\"\nint main(void){\n"
+    for s in structs:
+        c += f'printf("{s} %zu\\n", sizeof({s}));\n'
+    c += 'printf("fe_opts.max_dups %zu\\n", offsetof(fe_opts, max_dups));\n'
+    c += 'printf("fe_deform.bbox_min %zu\\n", offsetof(fe_deform, bbox_min));\n'
+    c += "return 0;}\n"
+    (tmp_path / "t.c").write_text(c)
+    exe = tmp_path / "t"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(tmp_path / "t.c"), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    for s in structs:
+        assert int(got[s]) == ctypes.sizeof(getattr(_lib, s)), s
+    assert int(got["fe_opts.max_dups"]) == _lib.fe_opts.max_dups.offset
+    assert int(got["fe_deform.bbox_min"]) == _lib.fe_deform.bbox_min.offset
+
+
+def test_host_side_status_codes(lib):
+    o = _lib.make_opts()
+    n = ctypes.c_size_t(0)
+    assert lib.fe_workspace_size(1000, 16, 64, 64, ctypes.byref(o), ctypes.byref(n)) == 0 and n.value > 0
+    assert lib.fe_workspace_size(1000, 24, 64, 64, ctypes.byref(o), ctypes.byref(n)) == 4   # D not compiled in
+    bad = _lib.make_opts(tile=(12, 12))
+    assert lib.fe_workspace_size(1000, 16, 64, 64, ctypes.byref(bad), ctypes.byref(n)) == 4
+    assert lib.fe_workspace_size(-1, 16, 64, 64, ctypes.byref(o), ctypes.byref(n)) == 1
+    assert lib.fe_workspace_size(10, 16, 0, 64, ctypes.byref(o), ctypes.byref(n)) == 1
+    huge = _lib.make_opts(max_dups=1 << 31)
+    assert lib.fe_workspace_size(10, 16, 64, 64, ctypes.byref(huge), ctypes.byref(n)) == 1
+    assert lib.fe_render_forward(None, None, None, 0.0, None, None, 0, None, None) == 1
+    assert lib.fe_render_backward(None, None, None, 0.0, None, None, 0, None, None, None) == 1
+    assert _lib.status_string(3).startswith("workspace")
+
+
+def test_workspace_grows_with_capacity_and_backward(lib):
+    a = _lib.fe_workspace_size(5000, 32, 320, 256, _lib.make_opts(max_dups=100000))
+    b = _lib.fe_workspace_size(5000, 32, 320, 256, _lib.make_opts(max_dups=200000))
+    c = _lib.fe_workspace_size(5000, 32, 320, 256, _lib.make_opts(max_dups=200000, forward_only=True))
+    assert b > a > c
