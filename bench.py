@@ -151,13 +151,14 @@ def run_ours(args, world, rank, local):
     tgt_rgb = torch.as_tensor(rgb_t_np, device=dev)
     tgt_feat = torch.as_tensor(feat_t_np, device=dev)
 
-    # Capacity: size the duplicate list from a probe forward (+25%).
-    probe = Rasterizer(P, D, W, H, device=dev)
+    # Capacity: size the duplicate list from a probe forward (+25%); the
+    # timed loop then runs without any host synchronisation.
+    probe = Rasterizer(P, D, W, H, device=dev, max_dups=64 * P + 4096, forward_only=True)
     probe.forward(scene, cam, deform, t)
     K0 = probe.stats()["num_dups"]
     del probe
     torch.cuda.empty_cache()
-    rast = Rasterizer(P, D, W, H, max_dups=int(K0 * 1.25) + 4096, device=dev)
+    rast = Rasterizer(P, D, W, H, max_dups=int(K0 * 1.25) + 4096, device=dev, auto_grow=False)
     kw = dict(dtype=torch.float32, device=dev)
     out = (torch.empty(3, H, W, **kw), torch.empty(H, W, **kw), torch.empty(H, W, **kw), torch.empty(HW, D, **kw))
     g_rgb = torch.empty(3, H, W, **kw)

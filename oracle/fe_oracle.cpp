@@ -424,8 +424,11 @@ void gaussian_forward(const or_scene& sc, const or_deform* df, const or_camera& 
     rms1 = std::sqrt(rms1 / kHidden) + 1e-30; rms2 = std::sqrt(rms2 / kHidden) + 1e-30;
     for (int o = 0; o < kHidden; ++o)
       if (std::fabs(st.ds.pre1[o]) < geps[2] * rms1 || std::fabs(st.ds.pre2[o]) < geps[2] * rms2) st.gflags |= 4;
+    // Only the spatial coordinates carry a gradient (to the canonical mean);
+    // the time coordinate of the xt, yt, zt planes does not.
     for (int k = 0; k < 6; ++k)
       for (int e = 0; e < 2; ++e) {
+        if (kPair[k][e] == 3) continue;
         const double gp = st.ds.pos[k][e];
         if (std::fabs(gp - std::nearbyint(gp)) < geps[3] * (df->R - 1)) st.gflags |= 8;
       }

@@ -35,7 +35,7 @@ _lib = None
 # take the other branch in binary32; such pixels are flagged, counted and
 # masked.  Order: inclusion, radius ceil, alpha skip, termination, depth tie,
 # alpha clamp.
-DEFAULT_EPS = (1e-5, 1e-5, 2e-4, 2e-4, 2e-6, 2e-4)
+DEFAULT_EPS = (1e-5, 1e-5, 2e-4, 2e-4, 1e-6, 2e-4)
 # Gradient-only decisions per Gaussian: rgb clamp |raw|, J clamp (relative),
 # relu (relative to rms), grid cell (relative to R-1).
 DEFAULT_GEPS = (1e-5, 1e-5, 1e-5, 1e-6)

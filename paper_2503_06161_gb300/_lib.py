@@ -77,7 +77,7 @@ _SIGNATURES = {
     "fe_tile_bin": [c_int, c_void_p, c_void_p, c_void_p, c_int, c_int, _P(fe_opts), c_void_p, ctypes.c_size_t,
                     c_void_p],
     "fe_read_stats": [c_void_p, ctypes.c_size_t, c_int, c_int, c_int, c_int, _P(fe_opts), _P(fe_stats), c_void_p],
-    "fe_debug_dump": [c_void_p, ctypes.c_size_t, c_int, c_int, c_int, c_int, _P(fe_opts)] + [c_void_p] * 13
+    "fe_debug_dump": [c_void_p, ctypes.c_size_t, c_int, c_int, c_int, c_int, _P(fe_opts)] + [c_void_p] * 12
                      + [c_void_p],
     "fe_probe_fp32_peak": [c_int, _P(ctypes.c_double), c_void_p],
     "fe_l1_loss_grad": [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p, c_void_p, c_void_p],

@@ -96,12 +96,24 @@ class Rasterizer:
     the same Rasterizer before the next forward."""
 
     def __init__(self, P: int, D: int, width: int, height: int, tile=(16, 16), bg=(0.0, 0.0, 0.0),
-                 max_dups: int = 0, forward_only: bool = False, device="cuda"):
+                 max_dups: int = 0, forward_only: bool = False, device="cuda", auto_grow: bool | None = None):
         self.P, self.D, self.width, self.height = int(P), int(D), int(width), int(height)
-        self.opts = _lib.make_opts(tile, bg, max_dups, forward_only)
+        self.tile, self.bg, self.forward_only = tuple(tile), tuple(bg), bool(forward_only)
+        self.device = torch.device(device)
+        # Without an explicit capacity, check each forward for overflow (one
+        # host sync) and grow the duplicate list when needed.
+        self.auto_grow = (max_dups == 0) if auto_grow is None else bool(auto_grow)
+        self._alloc(int(max_dups))
+
+    def _alloc(self, max_dups: int):
+        self.opts = _lib.make_opts(self.tile, self.bg, max_dups, self.forward_only)
         self.nbytes = _lib.fe_workspace_size(self.P, self.D, self.width, self.height, self.opts)
-        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
-        self.device = self.workspace.device
+        self.workspace = None
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+
+    @property
+    def capacity(self) -> int:
+        return int(self.opts.max_dups) if self.opts.max_dups > 0 else 16 * self.P + 4096
 
     def forward(self, scene: GaussianScene, cam: _lib.fe_camera, deform: DeformField | None = None, t: float = 0.0,
                 out=None):
@@ -111,8 +123,15 @@ class Rasterizer:
             out = (torch.empty(3, H, W, **kw), torch.empty(H, W, **kw), torch.empty(H, W, **kw),
                    torch.empty(H * W, D, **kw))
         rgb, depth, alpha, feat = out
-        _lib.fe_render_forward(scene.struct(), deform.struct() if deform is not None else None, cam, t, self.opts,
-                               self.workspace, rgb, depth, alpha, feat)
+        for _ in range(4):
+            _lib.fe_render_forward(scene.struct(), deform.struct() if deform is not None else None, cam, t,
+                                   self.opts, self.workspace, rgb, depth, alpha, feat)
+            if not self.auto_grow:
+                break
+            st = self.stats(raise_on_error=False)
+            if not (st["device_errors"] & 1):
+                break
+            self._alloc(int(st["num_dups"] * 1.25) + 4096)
         return rgb, depth, alpha, feat
 
     def backward(self, scene: GaussianScene, cam: _lib.fe_camera, deform: DeformField | None, t: float,

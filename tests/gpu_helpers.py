@@ -42,7 +42,8 @@ class GpuRun:
 def gpu_forward(sc, cam, df=None, t=0.0, tile=(16, 16), bg=(0.0, 0.0, 0.0), bf16=False, max_dups=0):
     scene = GaussianScene.from_numpy(sc, "cuda", bf16=bf16)
     deform = DeformField.from_numpy(df, "cuda") if df is not None else None
-    rast = Rasterizer(sc.P, sc.D, cam.width, cam.height, tile=tile, bg=bg, max_dups=max_dups)
+    rast = Rasterizer(sc.P, sc.D, cam.width, cam.height, tile=tile, bg=bg, max_dups=max_dups,
+                      auto_grow=(max_dups == 0))
     c = camera_struct(cam)
     rgb, depth, alpha, feat = rast.forward(scene, c, deform, t)
     torch.cuda.synchronize()

@@ -85,7 +85,7 @@ def test_forward_static_1k_64x64():
     ref = O.render(sc, cam)
     e, flagged = masked_forward_errors(run, ref)
     print("static_1k_64x64 errors", e, "flagged", flagged)
-    assert flagged <= 0.01 * cam.width * cam.height
+    assert flagged <= 0.02 * cam.width * cam.height
     assert e["rgb"] < TOL_RGB_ABS and e["depth"] < TOL_DEPTH_ABS and e["alpha"] < TOL_RGB_ABS
     assert e["feat"] < TOL_FEAT_REL
 
