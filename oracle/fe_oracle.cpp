@@ -300,6 +300,7 @@ struct GState {
   int radius;
   int rect[4];
   double rmargin;
+  double zerr;         // bound on the binary32 error of the camera-space depth
   int gflags;
   int visible;
 };
@@ -345,6 +346,30 @@ void gaussian_forward(const or_scene& sc, const or_deform* df, const or_camera& 
   const double* V = cam.view;
   for (int i = 0; i < 3; ++i)
     st.p[i] = V[4 * i + 0] * st.mu[0] + V[4 * i + 1] * st.mu[1] + V[4 * i + 2] * st.mu[2] + V[4 * i + 3];
+  {
+    // Standard rounding-error bound of the binary32 depth z = V2 . (mu + dmu) + V23,
+    // unit roundoff u = 2^-24: the rounding of each mu + dmu (propagated by
+    // |V2a|), a generous bound for the binary32 offsets themselves, one u per
+    // product whose factor is not a power of two and per addition of
+    // non-zero terms.  Exact operations (factor 0, +-1, additions of zero)
+    // contribute nothing.
+    const double u = std::ldexp(1.0, -24);
+    double prop = 0, sum = 0;
+    int inexact = 0, nz = 0;
+    for (int a = 0; a < 4; ++a) {
+      const double va = V[8 + a];
+      const double term = a < 3 ? va * st.mu[a] : va;
+      if (term != 0) ++nz;
+      sum += std::fabs(term);
+      if (a < 3) {
+        prop += std::fabs(va) * (std::fabs(st.mu[a]) + 64.0 * std::fabs(delta[a]));
+        int ex;
+        const double m = std::frexp(std::fabs(va), &ex);
+        if (va != 0 && m != 0.5) ++inexact;
+      }
+    }
+    st.zerr = u * (prop + (inexact + std::max(nz - 1, 0)) * sum);
+  }
   st.visible = 0;
   st.radius = 0;
   st.rect[0] = 0; st.rect[1] = 0; st.rect[2] = -1; st.rect[3] = -1;
@@ -513,8 +538,10 @@ void composite_pixel(const or_scene& sc, const std::vector<GState>& gs, const or
     if (Tn < kTMin) break;
     if (eps && std::fabs(oG - kAlphaMax) < eps[5] * kAlphaMax) flags |= kFlagClamp;
     if (eps && prev_contrib >= 0) {
+      // Two depths closer than their binary32 error bounds (times eps[4]) may
+      // be ordered either way.
       const double d0 = gs[prev_contrib].p[2], d1 = s.p[2];
-      if (std::fabs(d1 - d0) <= eps[4] * std::fabs(d1)) flags |= kFlagDepth;
+      if (std::fabs(d1 - d0) <= eps[4] * (gs[prev_contrib].zerr + s.zerr)) flags |= kFlagDepth;
     }
     prev_contrib = g;
     const double w = alpha * T;
@@ -708,7 +735,8 @@ int or_preprocess(const or_scene* sc, const or_deform* df, const or_camera* cam,
 // Composite the listed pixels (pix = npix (x,y) pairs).  eps (may be NULL):
 // decision thresholds {inclusion (relative to |u|+|v|+r), radius ceil
 // (relative), alpha skip (relative), termination (relative), depth tie
-// (relative), alpha clamp (relative)}.  Outputs per pixel: rgb[3]
+// (safety factor on the two depths' binary32 error bounds), alpha clamp
+// (relative)}.  Outputs per pixel: rgb[3]
 // (with bg*T), depth, alpha = 1-T, feat[D], sumw (sum of blend weights),
 // ncontrib, flags, sig (hash of the contributor sequence).
 int or_render(const or_scene* sc, const or_deform* df, const or_camera* cam, double t, const double* bg,

@@ -30,12 +30,13 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-# Decision thresholds of the comparison protocol (relative margins).  A pixel
-# whose FP64 decision lies closer than this to its threshold may legitimately
-# take the other branch in binary32; such pixels are flagged, counted and
-# masked.  Order: inclusion, radius ceil, alpha skip, termination, depth tie,
-# alpha clamp.
-DEFAULT_EPS = (1e-5, 1e-5, 2e-4, 2e-4, 1e-6, 2e-4)
+# Decision thresholds of the comparison protocol.  A pixel whose FP64
+# decision lies closer than this to its threshold may legitimately take the
+# other branch in binary32; such pixels are flagged, counted and masked.
+# Order: inclusion (relative to |u|+|v|+r), radius ceil (relative), alpha
+# skip (relative), termination (relative), depth tie (factor on the binary32
+# depth error bounds), alpha clamp (relative).
+DEFAULT_EPS = (1e-6, 5e-6, 1e-4, 1e-4, 2.0, 1e-4)
 # Gradient-only decisions per Gaussian: rgb clamp |raw|, J clamp (relative),
 # relu (relative to rms), grid cell (relative to R-1).
 DEFAULT_GEPS = (1e-5, 1e-5, 1e-5, 1e-6)
