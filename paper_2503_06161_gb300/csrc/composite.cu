@@ -139,28 +139,45 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
 }
 
 // ---------------------------------------------------------------------------
-constexpr int kBwdBatch = 8;
-constexpr int kPairStride = kThreads + 1;  // padded row of per-pixel terms
-
+// Reverse pass.  Per batch of B list entries (walked backwards), each pixel
+// thread replays its recurrence and forms, per (pixel, entry): the blend
+// weight w and six geometric terms (du, dv, dA, dB, dCc, dopacity).  Then:
+//  * geometric terms: a shuffle reduce-scatter over the warp's 32 pixels,
+//    only for entries where some lane of the warp contributed;
+//  * linear terms sum_p w_p G_p with G_p = (g_rgb, g_depth, g_feat): a
+//    register-blocked (entries x channels) product over the warp's pixels;
+//  * a fixed-order sum of the 8 warp partials per entry.
 template <int D>
-constexpr size_t bwd_smem_floats() {
-  return (size_t)kBwdBatch * kRec + (size_t)kBwdBatch * D + (size_t)kThreads * (4 + D + 1) +
-         (size_t)7 * kBwdBatch * kPairStride + kBwdBatch + 4;
-}
+struct BwdCfg {
+  static constexpr int NC = 4 + D;                  // linear channels
+  static constexpr int B = D <= 64 ? 32 : 16;       // entries per batch
+  static constexpr int JG = 8, CG = 4;              // lane grid of the per-warp product
+  static constexpr int JPL = B / JG;                // entries per lane
+  static constexpr int CPL = NC / CG;               // channels per lane
+  static constexpr bool GREG = D <= 32;             // upstream gradients kept in registers
+  static constexpr int GS = NC + 1;                 // per-pixel gradient row stride (odd)
+  static constexpr int WS = B + 4;                  // w row stride (16-byte rows)
+  static constexpr int SLICE = (32 * WS > B * NC) ? 32 * WS : B * NC;
+  static constexpr size_t smem_floats() {
+    return (size_t)B * kRec + (size_t)B * NC + (size_t)kThreads * GS + (size_t)8 * SLICE + (size_t)8 * B * 8 + B +
+           8 + 4;
+  }
+};
 
 template <int D>
 __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const CompositeArgs a) {
-  constexpr int B = kBwdBatch;
-  constexpr int GS = 4 + D + 1;  // row stride of the per-pixel upstream gradients
-  constexpr int NP = kPartialScalars + D;
+  using K = BwdCfg<D>;
+  constexpr int B = K::B, NC = K::NC, GS = K::GS, WS = K::WS, NP = kPartialScalars + D;
   extern __shared__ __align__(16) float smem[];
-  float* s_rec = smem;
-  float* s_feat = s_rec + B * kRec;
-  float* s_G = s_feat + B * D;
-  float* s_pair = s_G + kThreads * GS;
-  uint32_t* s_e = reinterpret_cast<uint32_t*>(s_pair + 7 * B * kPairStride);
-  uint32_t* s_maxn = s_e + B;
-  const int tid = threadIdx.x;
+  float* s_rec = smem;                       // [B][12]
+  float* s_x = s_rec + B * kRec;             // [B][NC]: rgb, depth, z
+  float* s_G = s_x + B * NC;                 // [256][GS]
+  float* s_slice = s_G + kThreads * GS;      // [8][SLICE]: w[p][j], then P[j][c]
+  float* s_geo = s_slice + 8 * K::SLICE;     // [8][B][8]
+  uint32_t* s_e = reinterpret_cast<uint32_t*>(s_geo + 8 * B * 8);
+  uint32_t* s_jact = s_e + B;
+  uint32_t* s_maxn = s_jact + 8;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
   const int px = tx * a.tw + tid % a.tw, py = ty * a.th + tid / a.tw;
@@ -168,37 +185,44 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
   const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
   const size_t HW = (size_t)a.W * a.H, pix = inside ? (size_t)py * a.W + px : 0;
   const uint2 rg = a.ranges[tile];
-  float gr0 = 0.f, gr1 = 0.f, gr2 = 0.f, gz = 0.f, ga = 0.f;
-  float* gF = s_G + tid * GS + 4;
-  if (inside) {
-    if (a.g_rgb) { gr0 = a.g_rgb[pix]; gr1 = a.g_rgb[HW + pix]; gr2 = a.g_rgb[2 * HW + pix]; }
-    if (a.g_depth) gz = a.g_depth[pix];
-    if (a.g_alpha) ga = a.g_alpha[pix];
-  }
-  s_G[tid * GS + 0] = gr0;
-  s_G[tid * GS + 1] = gr1;
-  s_G[tid * GS + 2] = gr2;
-  s_G[tid * GS + 3] = gz;
-  if (inside && a.g_feat) {
-    const float4* src = reinterpret_cast<const float4*>(a.g_feat + pix * D);
-#pragma unroll
-    for (int d4 = 0; d4 < D / 4; ++d4) {
-      const float4 v = __ldg(src + d4);
-      gF[4 * d4] = v.x; gF[4 * d4 + 1] = v.y; gF[4 * d4 + 2] = v.z; gF[4 * d4 + 3] = v.w;
+  float* grow = s_G + tid * GS;
+  float ga = 0.f;
+  {
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, gz = 0.f;
+    if (inside) {
+      if (a.g_rgb) { g0 = a.g_rgb[pix]; g1 = a.g_rgb[HW + pix]; g2 = a.g_rgb[2 * HW + pix]; }
+      if (a.g_depth) gz = a.g_depth[pix];
+      if (a.g_alpha) ga = a.g_alpha[pix];
     }
-  } else {
+    grow[0] = g0; grow[1] = g1; grow[2] = g2; grow[3] = gz;
+    if (inside && a.g_feat) {
+      const float4* src = reinterpret_cast<const float4*>(a.g_feat + pix * D);
 #pragma unroll
-    for (int d = 0; d < D; ++d) gF[d] = 0.0f;
+      for (int d4 = 0; d4 < D / 4; ++d4) {
+        const float4 v = __ldg(src + d4);
+        grow[4 + 4 * d4] = v.x; grow[5 + 4 * d4] = v.y; grow[6 + 4 * d4] = v.z; grow[7 + 4 * d4] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int d = 0; d < D; ++d) grow[4 + d] = 0.0f;
+    }
+  }
+  float G[K::GREG ? NC : 1];
+  if (K::GREG) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) G[c] = grow[c];
   }
   const float Tf = inside ? a.t_final[pix] : 1.0f;
   const uint32_t nc = inside ? a.n_contrib[pix] : 0u;
   float T = Tf;
-  float Q = (gr0 * a.bg[0] + gr1 * a.bg[1] + gr2 * a.bg[2]) * Tf;
+  float Q = (grow[0] * a.bg[0] + grow[1] * a.bg[1] + grow[2] * a.bg[2]) * Tf;
+  const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, nc);
   if (tid == 0) *s_maxn = 0u;
   __syncthreads();
-  if (nc) atomicMax(s_maxn, nc);
+  if (lane == 0 && wmax) atomicMax(s_maxn, wmax);
   __syncthreads();
   const uint32_t end = rg.x + *s_maxn;
+  float* slice = s_slice + warp * K::SLICE;
   for (uint32_t be = end; be > rg.x;) {
     const uint32_t bs = be - rg.x > (uint32_t)B ? be - B : rg.x;
     const int nb = (int)(be - bs);
@@ -208,63 +232,133 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
       const uint32_t g = a.gid_of_emit[e];
       s_e[tid] = e;
       const float4* r = a.rec + 3 * (size_t)g;
+      const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2);
       float4* d = reinterpret_cast<float4*>(s_rec + tid * kRec);
-      d[0] = __ldg(r);
-      d[1] = __ldg(r + 1);
-      d[2] = __ldg(r + 2);
-      load_feat_row<D>(a.feat, a.feat_bf16, g, s_feat + tid * D);
+      d[0] = r0; d[1] = r1; d[2] = r2;
+      float* x = s_x + tid * NC;
+      x[0] = r1.w; x[1] = r2.x; x[2] = r2.y; x[3] = r1.z;  // rgb, depth
+      load_feat_row<D>(a.feat, a.feat_bf16, g, x + 4);
     }
     __syncthreads();
-    for (int j = nb - 1; j >= 0; --j) {
-      const uint32_t rel = bs - rg.x + (uint32_t)j;
-      float du = 0.f, dv = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dop = 0.f, w = 0.f;
-      if (rel < nc) {
-        const float* rec = s_rec + j * kRec;
-        PairEval pe;
-        if (eval_pair(rec, pxc, pyc, pe)) {
-          const float one_m = 1.0f - pe.alpha;
-          T = T / one_m;  // transmittance before this Gaussian
-          w = pe.alpha * T;
-          const float* fj = s_feat + j * D;
-          float s = gr0 * rec[7] + gr1 * rec[8] + gr2 * rec[9] + gz * rec[6];
+    const uint32_t rel0 = bs - rg.x;
+    uint32_t jact = 0;
+    if (rel0 < wmax) {
+      for (int j = nb - 1; j >= 0; --j) {
+        float v[8];
 #pragma unroll
-          for (int d = 0; d < D; ++d) s = fmaf(gF[d], fj[d], s);
-          const float dalpha = T * s - (Q - ga * Tf) / one_m;
-          Q = fmaf(w, s, Q);
-          if (!pe.clamped) {
-            const float dp2 = dalpha * pe.alpha * kLn2;
-            du = -dp2 * (2.0f * rec[2] * pe.dx + rec[3] * pe.dy);
-            dv = -dp2 * (2.0f * rec[4] * pe.dy + rec[3] * pe.dx);
-            dA = dp2 * pe.dx * pe.dx;
-            dB = dp2 * pe.dx * pe.dy;
-            dC = dp2 * pe.dy * pe.dy;
-            dop = dalpha * pe.G;
+        for (int k = 0; k < 8; ++k) v[k] = 0.0f;
+        float w = 0.0f;
+        bool contrib = false;
+        if (rel0 + (uint32_t)j < nc) {
+          const float* rec = s_rec + j * kRec;
+          PairEval pe;
+          if (eval_pair(rec, pxc, pyc, pe)) {
+            contrib = true;
+            const float one_m = 1.0f - pe.alpha;
+            T = T / one_m;  // transmittance before this Gaussian
+            w = pe.alpha * T;
+            const float4* x4 = reinterpret_cast<const float4*>(s_x + j * NC);
+            float s = 0.0f;
+#pragma unroll
+            for (int c4 = 0; c4 < NC / 4; ++c4) {
+              const float4 xv = x4[c4];
+              if (K::GREG) {
+                s = fmaf(G[4 * c4], xv.x, s);
+                s = fmaf(G[4 * c4 + 1], xv.y, s);
+                s = fmaf(G[4 * c4 + 2], xv.z, s);
+                s = fmaf(G[4 * c4 + 3], xv.w, s);
+              } else {
+                s = fmaf(grow[4 * c4], xv.x, s);
+                s = fmaf(grow[4 * c4 + 1], xv.y, s);
+                s = fmaf(grow[4 * c4 + 2], xv.z, s);
+                s = fmaf(grow[4 * c4 + 3], xv.w, s);
+              }
+            }
+            const float dalpha = T * s - (Q - ga * Tf) / one_m;
+            Q = fmaf(w, s, Q);
+            if (!pe.clamped) {
+              const float dp2 = dalpha * pe.alpha * kLn2;
+              v[0] = -dp2 * (2.0f * rec[2] * pe.dx + rec[3] * pe.dy);
+              v[1] = -dp2 * (2.0f * rec[4] * pe.dy + rec[3] * pe.dx);
+              v[2] = dp2 * pe.dx * pe.dx;
+              v[3] = dp2 * pe.dx * pe.dy;
+              v[4] = dp2 * pe.dy * pe.dy;
+              v[5] = dalpha * pe.G;
+            }
           }
         }
+        slice[lane * WS + j] = w;
+        if (__ballot_sync(0xFFFFFFFFu, contrib)) {
+          jact |= 1u << j;
+          // Reduce-scatter of v[0..7] over the warp: lane 4m ends with index m.
+          const int b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float send = b16 ? v[i] : v[i + 4];
+            const float keep = b16 ? v[i + 4] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+          }
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const float send = b8 ? v[i] : v[i + 2];
+            const float keep = b8 ? v[i + 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+          }
+          {
+            const float send = b4 ? v[0] : v[1];
+            const float keep = b4 ? v[1] : v[0];
+            v[0] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
+          }
+          v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 2);
+          v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 1);
+          const int m = lane >> 2;
+          if ((lane & 3) == 0 && m < 6) s_geo[(warp * B + j) * 8 + m] = v[0];
+        }
       }
-      float* sp = s_pair + j * kPairStride + tid;
-      sp[0 * B * kPairStride] = du;
-      sp[1 * B * kPairStride] = dv;
-      sp[2 * B * kPairStride] = dA;
-      sp[3 * B * kPairStride] = dB;
-      sp[4 * B * kPairStride] = dC;
-      sp[5 * B * kPairStride] = dop;
-      sp[6 * B * kPairStride] = w;
+      __syncwarp();
+      if (jact) {
+        // P[j][c] = sum over the warp's pixels of w[p][j] * G[p][c].
+        const int jg = lane >> 2, cg = lane & 3;
+        float acc[K::JPL][K::CPL];
+#pragma unroll
+        for (int jj = 0; jj < K::JPL; ++jj)
+#pragma unroll
+          for (int c = 0; c < K::CPL; ++c) acc[jj][c] = 0.0f;
+#pragma unroll 4
+        for (int p = 0; p < 32; ++p) {
+          float wv[K::JPL];
+          if (K::JPL == 4) {
+            const float4 t4 = *reinterpret_cast<const float4*>(slice + p * WS + jg * 4);
+            wv[0] = t4.x; wv[1] = t4.y; wv[2] = t4.z; wv[3] = t4.w;
+          } else {
+            const float2 t2 = *reinterpret_cast<const float2*>(slice + p * WS + jg * 2);
+            wv[0] = t2.x; wv[1] = t2.y;
+          }
+          const float* gr = s_G + (warp * 32 + p) * GS + cg * K::CPL;
+#pragma unroll
+          for (int c = 0; c < K::CPL; ++c) {
+            const float gv = gr[c];
+#pragma unroll
+            for (int jj = 0; jj < K::JPL; ++jj) acc[jj][c] = fmaf(wv[jj], gv, acc[jj][c]);
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int jj = 0; jj < K::JPL; ++jj)
+#pragma unroll
+          for (int c = 0; c < K::CPL; ++c) slice[(jg * K::JPL + jj) * NC + cg * K::CPL + c] = acc[jj][c];
+      }
     }
+    if (lane == 0) s_jact[warp] = jact;
     __syncthreads();
-    // Fixed-order sums over the tile's 256 pixels.
+    // Fixed-order sum of the warp partials: one row per (tile, entry).
     for (int item = tid; item < nb * NP; item += kThreads) {
       const int j = item / NP, k = item - j * NP;
       float acc = 0.0f;
-      if (k < 6) {
-        const float* row = s_pair + (k * B + j) * kPairStride;
-#pragma unroll 8
-        for (int p = 0; p < kThreads; ++p) acc += row[p];
-      } else {
-        const float* wr = s_pair + (6 * B + j) * kPairStride;
-        const float* gc = s_G + (k - 6);
-#pragma unroll 8
-        for (int p = 0; p < kThreads; ++p) acc = fmaf(wr[p], gc[p * GS], acc);
+#pragma unroll
+      for (int w8 = 0; w8 < 8; ++w8) {
+        if ((s_jact[w8] >> j) & 1u)
+          acc += k < 6 ? s_geo[(w8 * B + j) * 8 + k] : s_slice[w8 * K::SLICE + j * NC + (k - 6)];
       }
       a.partials[(size_t)s_e[j] * NP + k] = acc;
     }
@@ -285,7 +379,7 @@ cudaError_t launch_fwd_t(const CompositeArgs& a, cudaStream_t st) {
 
 template <int D>
 cudaError_t launch_bwd_t(const CompositeArgs& a, cudaStream_t st) {
-  const size_t smem = bwd_smem_floats<D>() * sizeof(float);
+  const size_t smem = BwdCfg<D>::smem_floats() * sizeof(float);
   auto k = composite_bwd_kernel<D>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<a.ntiles, kThreads, smem, st>>>(a);
