@@ -105,6 +105,7 @@ fe_status fill_gauss_args(const fe_gaussians* g, const fe_deform* df, const fe_c
   a.dkey = at<uint32_t>(ws, L.dkey[0]);
   a.err = &hdr->err;
   a.num_visible = &hdr->num_visible;
+  if (L.with_backward) a.dstate = at<float>(ws, L.dstate);
   return FE_OK;
 }
 
@@ -264,6 +265,7 @@ fe_status fe_render_backward(const fe_gaussians* g, const fe_deform* deform, con
   gb.d_logits = grads->opacity_logits;
   gb.d_sh = grads->sh;
   gb.d_feat = grads->feat;
+  gb.ddstate = at<float>(workspace, L.ddstate);
   FE_TRY_CUDA(launch_gauss_bwd(ga, gb, st, opts && opts->events ? static_cast<cudaEvent_t>(opts->events[6]) : nullptr));
   FE_TRY_CUDA(mark(opts, 7, st));
   return FE_OK;

@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(kThreads) depth_hist_kernel(const uint32_t* __
   __shared__ uint32_t s[4][256];
   for (int i = threadIdx.x; i < 4 * 256; i += kThreads) (&s[0][0])[i] = 0;
   __syncthreads();
-  const int start = blockIdx.x * kSortChunk;
-  const int end = min(n, start + kSortChunk);
+  const int start = blockIdx.x * kPChunk;
+  const int end = min(n, start + kPChunk);
   for (int i = start + threadIdx.x; i < end; i += kThreads) {
     const uint32_t k = keys[i];
 #pragma unroll
@@ -83,17 +83,18 @@ __global__ void __launch_bounds__(kThreads) depth_hist_kernel(const uint32_t* __
 // Block b (taken from an atomic ticket so predecessors are always running)
 // handles elements [b*4096, b*4096+4096); warp w its sub-chunk of 512.
 // ---------------------------------------------------------------------------
+template <int ITEMS>
 struct PassSmem {
   uint32_t wcnt[8][256];
   uint32_t gbase[256];
   uint32_t bstart[256];
-  uint32_t keys[kSortChunk];
-  uint32_t vals[kSortChunk];
+  uint32_t keys[kThreads * ITEMS];
+  uint32_t vals[kThreads * ITEMS];
   uint32_t scan[8];
   uint32_t ticket;
 };
 
-template <bool kIdentVals>
+template <bool kIdentVals, int ITEMS>
 __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint32_t* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out,
@@ -101,23 +102,24 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint32_t* __re
                                                             const uint32_t* n_dev, int64_t n_cap, int shift,
                                                             const uint32_t* __restrict__ hist, uint32_t* status,
                                                             uint32_t* ticket, uint32_t* err) {
+  constexpr int CHUNK = kThreads * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
+  PassSmem<ITEMS>& sm = *reinterpret_cast<PassSmem<ITEMS>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < 8 * 256; i += kThreads) (&sm.wcnt[0][0])[i] = 0;
   if (tid == 0) sm.ticket = atomicAdd(ticket, 1u);
   __syncthreads();
   const uint32_t b = sm.ticket;
   const uint64_t n = n_dev ? min((uint64_t)*n_dev, (uint64_t)n_cap) : (uint64_t)n_cap;
-  const uint64_t start = (uint64_t)b * kSortChunk;
+  const uint64_t start = (uint64_t)b * CHUNK;
   if (start >= n) return;
-  const uint32_t cnt = (uint32_t)min((uint64_t)kSortChunk, n - start);
+  const uint32_t cnt = (uint32_t)min((uint64_t)CHUNK, n - start);
 
-  uint32_t k[kSortItems], v[kSortItems], rk[kSortItems];
-  int dg[kSortItems];
-  const uint64_t wbase = start + (uint64_t)warp * (kSortChunk / 8);
+  uint32_t k[ITEMS], v[ITEMS], rk[ITEMS];
+  int dg[ITEMS];
+  const uint64_t wbase = start + (uint64_t)warp * (CHUNK / 8);
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
+  for (int r = 0; r < ITEMS; ++r) {
     const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
     const bool valid = idx < n;
     const uint32_t key = valid ? keys_in[idx] : 0u;
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint32_t* __re
   sm.bstart[tid] = bst;
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
+  for (int r = 0; r < ITEMS; ++r) {
     if (dg[r] < 256) {
       const uint32_t lp = sm.bstart[dg[r]] + sm.wcnt[warp][dg[r]] + rk[r];
       sm.keys[lp] = k[r];
@@ -193,8 +195,11 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint32_t* __re
 
 // ---------------------------------------------------------------------------
 // Exclusive scan of tiles_touched in depth order + tile emission + tile
-// digit histograms.  Thread t owns ranks [start + 16t, start + 16t + 16).
-// ---------------------------------------------------------------------------
+// digit histograms.  Block b owns depth ranks [1024 b, 1024 b + 1024);
+// thread t scans ranks 4t..4t+3 of it.  Emission is load balanced: each
+// thread writes whole output entries, finding the owning Gaussian by a
+// binary search over the block's offsets in shared memory, so the writes
+// are coalesced and no thread walks a long rect alone.
 struct KeygenArgs {
   int P, tiles_x, tile_passes;
   int64_t cap;
@@ -210,6 +215,9 @@ struct KeygenArgs {
 
 __global__ void __launch_bounds__(kThreads) scan_keygen_kernel(const KeygenArgs a) {
   __shared__ uint32_t s_hist[3][256];
+  __shared__ uint32_t s_off[kPChunk];
+  __shared__ uint32_t s_gid[kPChunk];
+  __shared__ ushort4 s_rect[kPChunk];
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_ticket;
   __shared__ uint64_t s_prefix;
@@ -218,18 +226,26 @@ __global__ void __launch_bounds__(kThreads) scan_keygen_kernel(const KeygenArgs 
   if (tid == 0) s_ticket = atomicAdd(a.ticket, 1u);
   __syncthreads();
   const uint32_t b = s_ticket;
-  const int64_t start = (int64_t)b * kSortChunk;
+  const int64_t start = (int64_t)b * kPChunk;
   if (start >= a.P) return;
-  uint32_t gid[kSortItems], cnt[kSortItems];
+  uint32_t cnt[kPItems];
   uint32_t tsum = 0;
 #pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    const int64_t r = start + (int64_t)tid * kSortItems + i;
-    gid[i] = r < a.P ? a.order[r] : 0u;
-    cnt[i] = r < a.P ? a.touched[gid[i]] : 0u;
-    tsum += cnt[i];
+  for (int i = 0; i < kPItems; ++i) {
+    const int li = tid * kPItems + i;
+    const int64_t r = start + li;
+    uint32_t g = 0, c = 0;
+    ushort4 rc = make_ushort4(1, 1, 0, 0);
+    if (r < a.P) {
+      g = a.order[r];
+      c = a.touched[g];
+      if (c) rc = a.rect[g];
+    }
+    s_gid[li] = g;
+    s_rect[li] = rc;
+    cnt[i] = c;
+    tsum += c;
   }
-  // Counts of one block stay below 2^32 (4096 Gaussians x 65536 tiles).
   uint32_t btot;
   const uint32_t texcl = block_excl_scan(tsum, s_scan, btot);
   if (tid == 0) {
@@ -257,38 +273,53 @@ __global__ void __launch_bounds__(kThreads) scan_keygen_kernel(const KeygenArgs 
     }
     s_prefix = excl;
   }
-  __syncthreads();
-  uint64_t run = s_prefix + texcl;
-  const uint64_t cap = (uint64_t)a.cap;
-#pragma unroll 1
-  for (int i = 0; i < kSortItems; ++i) {
-    const int64_t r = start + (int64_t)tid * kSortItems + i;
-    if (r >= a.P) break;
-    const uint32_t o32 = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
-    a.offs[r] = o32;
-    a.offs_by_gid[gid[i]] = o32;
-    if (cnt[i]) {
-      const ushort4 rc = a.rect[gid[i]];
-      uint64_t e = run;
-      for (int ty = rc.y; ty <= rc.w; ++ty) {
-        for (int tx = rc.x; tx <= rc.z; ++tx, ++e) {
-          if (e >= cap) continue;
-          const uint32_t tile = (uint32_t)(ty * a.tiles_x + tx);
-          a.tile_out[e] = tile;
-          a.gid_of_emit[e] = gid[i];
-          atomicAdd(&s_hist[0][tile & 255u], 1u);
-          if (a.tile_passes > 1) atomicAdd(&s_hist[1][(tile >> 8) & 255u], 1u);
-          if (a.tile_passes > 2) atomicAdd(&s_hist[2][(tile >> 16) & 255u], 1u);
-        }
-      }
-    }
+  // Local offsets of this thread's ranks.
+  uint32_t run = texcl;
+#pragma unroll
+  for (int i = 0; i < kPItems; ++i) {
+    s_off[tid * kPItems + i] = run;
     run += cnt[i];
   }
-  if (start + kSortChunk >= a.P && tid == kThreads - 1) {
+  __syncthreads();
+  const uint64_t base = s_prefix;
+#pragma unroll
+  for (int i = 0; i < kPItems; ++i) {
+    const int li = tid * kPItems + i;
+    const int64_t r = start + li;
+    if (r < a.P) {
+      const uint32_t o32 = (uint32_t)min(base + s_off[li], (uint64_t)0xFFFFFFFFu);
+      a.offs[r] = o32;
+      a.offs_by_gid[s_gid[li]] = o32;
+    }
+  }
+  const uint64_t cap = (uint64_t)a.cap;
+  const int nloc = (int)min((int64_t)kPChunk, (int64_t)a.P - start);
+  for (uint32_t i = tid; i < btot; i += kThreads) {
+    const uint64_t e = base + i;
+    if (e >= cap) break;
+    // Owner: last local Gaussian whose offset is <= i.
+    int lo = 0, hi = nloc;  // invariant: s_off[lo] <= i < s_off[hi] (s_off[nloc] = btot)
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    const ushort4 rc = s_rect[lo];
+    const uint32_t loc = i - s_off[lo];
+    const uint32_t wdt = (uint32_t)(rc.z - rc.x + 1);
+    const uint32_t ty = rc.y + loc / wdt, tx = rc.x + loc % wdt;
+    const uint32_t tile = ty * (uint32_t)a.tiles_x + tx;
+    a.tile_out[e] = tile;
+    a.gid_of_emit[e] = s_gid[lo];
+    atomicAdd(&s_hist[0][tile & 255u], 1u);
+    if (a.tile_passes > 1) atomicAdd(&s_hist[1][(tile >> 8) & 255u], 1u);
+    if (a.tile_passes > 2) atomicAdd(&s_hist[2][(tile >> 16) & 255u], 1u);
+  }
+  if (start + kPChunk >= a.P && tid == 0) {
     // Last block: total K.
-    a.offs[a.P] = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
-    a.hdr->num_dups = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
-    if (run > cap) set_err(&a.hdr->err, kErrOverflow);
+    const uint64_t total = base + btot;
+    a.offs[a.P] = (uint32_t)min(total, (uint64_t)0xFFFFFFFFu);
+    a.hdr->num_dups = (uint32_t)min(total, (uint64_t)0xFFFFFFFFu);
+    if (total > cap) set_err(&a.hdr->err, kErrOverflow);
   }
   __syncthreads();
   for (int i = tid; i < a.tile_passes * 256; i += kThreads) {
@@ -353,16 +384,19 @@ cudaError_t launch_bin_prep(int P, const float* uv, const int* radius, const flo
 
 cudaError_t launch_binning(BinArgs& b, cudaStream_t st) {
   Header* hdr = static_cast<Header*>(b.hdr);
-  const size_t pass_smem = sizeof(PassSmem);
+  const size_t pass_smem = sizeof(PassSmem<kSortItems>);
+  const size_t ppass_smem = sizeof(PassSmem<kPItems>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem);
-    cudaFuncSetAttribute(onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem);
+    cudaFuncSetAttribute(onesweep_kernel<true, kSortItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pass_smem);
+    cudaFuncSetAttribute(onesweep_kernel<false, kSortItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pass_smem);
     attr_set = true;
   }
   cudaError_t e;
   const int P = b.P;
-  const int pblocks = ceil_div(P > 0 ? P : 1, kSortChunk);
+  const int pblocks = ceil_div(P > 0 ? P : 1, kPChunk);
   uint32_t* status_depth = b.status;
   uint32_t* status_tile = b.status + (size_t)pblocks * 256 * 4;
   const int kblocks = ceil_div(b.cap > 0 ? b.cap : 1, kSortChunk);
@@ -373,11 +407,11 @@ cudaError_t launch_binning(BinArgs& b, cudaStream_t st) {
     int cur = 0;
     for (int p = 0; p < 4; ++p) {
       if (p == 0)
-        onesweep_kernel<true><<<pblocks, kThreads, pass_smem, st>>>(
+        onesweep_kernel<true, kPItems><<<pblocks, kThreads, ppass_smem, st>>>(
             b.dkey[cur], nullptr, b.dkey[cur ^ 1], b.dval[cur ^ 1], nullptr, P, 8 * p, b.hist + 256 * p,
             status_depth + (size_t)p * pblocks * 256, hdr->ticket + kTicketDepth0 + p, &hdr->err);
       else
-        onesweep_kernel<false><<<pblocks, kThreads, pass_smem, st>>>(
+        onesweep_kernel<false, kPItems><<<pblocks, kThreads, ppass_smem, st>>>(
             b.dkey[cur], b.dval[cur], b.dkey[cur ^ 1], b.dval[cur ^ 1], nullptr, P, 8 * p, b.hist + 256 * p,
             status_depth + (size_t)p * pblocks * 256, hdr->ticket + kTicketDepth0 + p, &hdr->err);
       cur ^= 1;
@@ -408,11 +442,11 @@ cudaError_t launch_binning(BinArgs& b, cudaStream_t st) {
   int cur = 0;
   for (int p = 0; p < b.tile_passes; ++p) {
     if (p == 0)
-      onesweep_kernel<true><<<kblocks, kThreads, pass_smem, st>>>(
+      onesweep_kernel<true, kSortItems><<<kblocks, kThreads, pass_smem, st>>>(
           b.tkey[cur], nullptr, b.tkey[cur ^ 1], b.tval[cur ^ 1], &hdr->num_dups, b.cap, 8 * p,
           b.hist + (4 + p) * 256, status_tile + (size_t)p * kblocks * 256, hdr->ticket + kTicketTile0 + p, &hdr->err);
     else
-      onesweep_kernel<false><<<kblocks, kThreads, pass_smem, st>>>(
+      onesweep_kernel<false, kSortItems><<<kblocks, kThreads, pass_smem, st>>>(
           b.tkey[cur], b.tval[cur], b.tkey[cur ^ 1], b.tval[cur ^ 1], &hdr->num_dups, b.cap, 8 * p,
           b.hist + (4 + p) * 256, status_tile + (size_t)p * kblocks * 256, hdr->ticket + kTicketTile0 + p, &hdr->err);
     cur ^= 1;

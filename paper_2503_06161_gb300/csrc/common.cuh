@@ -48,9 +48,13 @@ struct Header {           // first 256 bytes of every workspace
 };
 static_assert(sizeof(Header) == 256, "header is 256 bytes");
 
-// Radix / scan chunking: 256 threads x 16 items.
+// Radix / scan chunking: 256 threads x 16 items over the K list entries,
+// 256 threads x 4 items over the P Gaussians (so P-sized passes still fill
+// all SMs).
 constexpr int kSortItems = 16;
 constexpr int kSortChunk = kThreads * kSortItems;
+constexpr int kPItems = 4;
+constexpr int kPChunk = kThreads * kPItems;
 
 // Ticket slots in the header.
 enum : int {
@@ -65,7 +69,7 @@ struct Layout {
   int64_t cap;
   bool with_backward;
   size_t hdr, rec, rect, touched, dkey[2], dval[2], offs, offs_by_gid, tkey[2], tval[2], gid_of_emit;
-  size_t status, hist, ranges, tfinal, ncontrib, partials, pflags;
+  size_t status, hist, ranges, tfinal, ncontrib, partials, pflags, dstate, ddstate;
   size_t status_words, scan_blocks_p, sort_blocks_k;
   size_t total;
 };
@@ -101,7 +105,7 @@ inline Layout make_layout(int P, int D, int W, int H, int tw, int th, int64_t ca
   for (int i = 0; i < 2; ++i) L.tkey[i] = take(Kn * 4);
   for (int i = 0; i < 2; ++i) L.tval[i] = take(Kn * 4);
   L.gid_of_emit = take(Kn * 4);
-  L.scan_blocks_p = (size_t)ceil_div((int64_t)Pn, kSortChunk);
+  L.scan_blocks_p = (size_t)ceil_div((int64_t)Pn, kPChunk);
   L.sort_blocks_k = (size_t)ceil_div((int64_t)Kn, kSortChunk);
   // Look-back status words: 4 depth passes (u32 per digit per block), up to 3
   // tile passes, then one u64 per block of the tiles_touched scan.
@@ -114,6 +118,8 @@ inline Layout make_layout(int P, int D, int W, int H, int tw, int th, int64_t ca
   if (with_backward) {
     L.partials = take(Kn * (size_t)(kPartialScalars + D) * 4);
     L.pflags = take(Kn);
+    L.dstate = take(Pn * 16 * 4);
+    L.ddstate = take(Pn * 12 * 4);
   }
   L.total = off;
   return L;

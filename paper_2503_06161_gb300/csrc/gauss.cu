@@ -155,91 +155,144 @@ __device__ __forceinline__ void hexplane_sample(const GaussArgs& a, const float 
   }
 }
 
-// Shared-memory weight block: w1[64*C] b1[64] w2[64*64] b2[64] wh[11*64] bh[12].
+// Shared-memory weights, laid out so every inner loop reads 16-byte
+// broadcast rows: w1[64][C], b1[64], w2t[64][64] with w2t[i][o] = W2[o][i],
+// b2[64], wh[11][64], wht[64][12] with wht[o][k] = Wh[k][o], bh[12].
 template <int C>
-constexpr int mlp_floats() { return kHidden * C + kHidden + kHidden * kHidden + kHidden + kHeads * kHidden + 12; }
+struct Mlp {
+  static constexpr int kW1 = 0, kB1 = kHidden * C, kW2t = kB1 + kHidden, kB2 = kW2t + kHidden * kHidden,
+                       kWh = kB2 + kHidden, kWht = kWh + kHeads * kHidden, kBh = kWht + kHidden * 12,
+                       kFloats = kBh + 12;
+};
+template <int C>
+constexpr int mlp_floats() { return Mlp<C>::kFloats; }
 
 template <int C>
 __device__ __forceinline__ void load_mlp(const GaussArgs& a, float* sw) {
-  float* w1 = sw;
-  float* b1 = w1 + kHidden * C;
-  float* w2 = b1 + kHidden;
-  float* b2 = w2 + kHidden * kHidden;
-  float* wh = b2 + kHidden;
-  float* bh = wh + kHeads * kHidden;
-  for (int i = threadIdx.x; i < kHidden * C; i += blockDim.x) w1[i] = a.w1[i];
-  for (int i = threadIdx.x; i < kHidden * kHidden; i += blockDim.x) w2[i] = a.w2[i];
-  for (int i = threadIdx.x; i < kHeads * kHidden; i += blockDim.x) wh[i] = a.wh[i];
-  for (int i = threadIdx.x; i < kHidden; i += blockDim.x) { b1[i] = a.b1[i]; b2[i] = a.b2[i]; }
-  if (threadIdx.x < 12) bh[threadIdx.x] = threadIdx.x < kHeads ? a.bh[threadIdx.x] : 0.0f;
+  using L = Mlp<C>;
+  for (int i = threadIdx.x; i < kHidden * C; i += blockDim.x) sw[L::kW1 + i] = a.w1[i];
+  for (int i = threadIdx.x; i < kHidden * kHidden; i += blockDim.x) {
+    const int o = i / kHidden, in = i % kHidden;  // W2[o][in]
+    sw[L::kW2t + in * kHidden + o] = a.w2[i];
+  }
+  for (int i = threadIdx.x; i < kHeads * kHidden; i += blockDim.x) {
+    const int k = i / kHidden, o = i % kHidden;   // Wh[k][o]
+    sw[L::kWh + i] = a.wh[i];
+    sw[L::kWht + o * 12 + k] = a.wh[i];
+  }
+  for (int i = threadIdx.x; i < kHidden; i += blockDim.x) {
+    sw[L::kB1 + i] = a.b1[i];
+    sw[L::kB2 + i] = a.b2[i];
+    sw[L::kWht + i * 12 + 11] = 0.0f;
+  }
+  if (threadIdx.x < 12) sw[L::kBh + threadIdx.x] = threadIdx.x < kHeads ? a.bh[threadIdx.x] : 0.0f;
 }
 
 // h2pre = W2 relu(W1 f + b1) + b2, streamed over the first-layer units so
-// only f and the 64 second-layer accumulators live in registers.
+// only f and the 64 second-layer accumulators live in registers; m1 gets
+// bit i set where first-layer unit i is active.
 template <int C>
-__device__ __forceinline__ void mlp_hidden2(const float* sw, const float f[C], float h2[kHidden]) {
-  const float* w1 = sw;
-  const float* b1 = w1 + kHidden * C;
-  const float* w2 = b1 + kHidden;
-  const float* b2 = w2 + kHidden * kHidden;
+__device__ __forceinline__ void mlp_hidden2(const float* sw, const float f[C], float h2[kHidden], uint64_t& m1) {
+  using L = Mlp<C>;
 #pragma unroll
-  for (int o = 0; o < kHidden; ++o) h2[o] = b2[o];
+  for (int o = 0; o < kHidden; ++o) h2[o] = sw[L::kB2 + o];
+  m1 = 0;
 #pragma unroll 1
   for (int o1 = 0; o1 < kHidden; ++o1) {
-    float acc = b1[o1];
+    const float4* w1r = reinterpret_cast<const float4*>(sw + L::kW1 + o1 * C);
+    float acc = sw[L::kB1 + o1];
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc = fmaf(w1[o1 * C + c], f[c], acc);
+    for (int c4 = 0; c4 < C / 4; ++c4) {
+      const float4 w = w1r[c4];
+      acc = fmaf(w.x, f[4 * c4], acc);
+      acc = fmaf(w.y, f[4 * c4 + 1], acc);
+      acc = fmaf(w.z, f[4 * c4 + 2], acc);
+      acc = fmaf(w.w, f[4 * c4 + 3], acc);
+    }
+    m1 |= (uint64_t)(acc > 0.0f) << o1;
     const float h = fmaxf(acc, 0.0f);
+    const float4* w2r = reinterpret_cast<const float4*>(sw + L::kW2t + o1 * kHidden);
 #pragma unroll
-    for (int o = 0; o < kHidden; ++o) h2[o] = fmaf(w2[o * kHidden + o1], h, h2[o]);
+    for (int o4 = 0; o4 < kHidden / 4; ++o4) {
+      const float4 w = w2r[o4];
+      h2[4 * o4] = fmaf(w.x, h, h2[4 * o4]);
+      h2[4 * o4 + 1] = fmaf(w.y, h, h2[4 * o4 + 1]);
+      h2[4 * o4 + 2] = fmaf(w.z, h, h2[4 * o4 + 2]);
+      h2[4 * o4 + 3] = fmaf(w.w, h, h2[4 * o4 + 3]);
+    }
   }
 }
 
-// delta = Wh relu(h2pre) + bh.
+// delta = Wh relu(h2pre) + bh; m1 / m2: active units of the two layers.
 template <int C>
-__device__ __forceinline__ void mlp_forward(const float* sw, const float f[C], float delta[kHeads]) {
-  const float* wh = sw + kHidden * C + kHidden + kHidden * kHidden + kHidden;
-  const float* bh = wh + kHeads * kHidden;
+__device__ __forceinline__ void mlp_forward(const float* sw, const float f[C], float delta[kHeads], uint64_t& m1,
+                                            uint64_t& m2) {
+  using L = Mlp<C>;
   float h2[kHidden];
-  mlp_hidden2<C>(sw, f, h2);
+  mlp_hidden2<C>(sw, f, h2, m1);
+  m2 = 0;
+#pragma unroll
+  for (int o = 0; o < kHidden; ++o) {
+    m2 |= (uint64_t)(h2[o] > 0.0f) << o;
+    h2[o] = fmaxf(h2[o], 0.0f);
+  }
 #pragma unroll
   for (int k = 0; k < kHeads; ++k) {
-    float acc = bh[k];
+    const float4* wr = reinterpret_cast<const float4*>(sw + L::kWh + k * kHidden);
+    float acc = sw[L::kBh + k];
 #pragma unroll
-    for (int o = 0; o < kHidden; ++o) acc = fmaf(wh[k * kHidden + o], fmaxf(h2[o], 0.0f), acc);
+    for (int o4 = 0; o4 < kHidden / 4; ++o4) {
+      const float4 w = wr[o4];
+      acc = fmaf(w.x, h2[4 * o4], acc);
+      acc = fmaf(w.y, h2[4 * o4 + 1], acc);
+      acc = fmaf(w.z, h2[4 * o4 + 2], acc);
+      acc = fmaf(w.w, h2[4 * o4 + 3], acc);
+    }
     delta[k] = acc;
   }
 }
 
-// df = (d delta / d f)^T dd, recomputing the activations.
+// df = (d delta / d f)^T dd from the forward's unit masks: no activation is
+// recomputed.  g2 = m2 (Wh^T dd), d1 = m1 (W2^T g2), df = W1^T d1.
 template <int C>
-__device__ __forceinline__ void mlp_backward(const float* sw, const float f[C], const float dd[kHeads], float df[C]) {
-  const float* w1 = sw;
-  const float* b1 = w1 + kHidden * C;
-  const float* w2 = b1 + kHidden;
-  const float* wh = w2 + kHidden * kHidden + kHidden;
+__device__ __forceinline__ void mlp_backward(const float* sw, uint64_t m1, uint64_t m2, const float dd[kHeads],
+                                             float df[C]) {
+  using L = Mlp<C>;
   float g2[kHidden];
-  mlp_hidden2<C>(sw, f, g2);
 #pragma unroll
   for (int o = 0; o < kHidden; ++o) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int k = 0; k < kHeads; ++k) acc = fmaf(wh[k * kHidden + o], dd[k], acc);
-    g2[o] = g2[o] > 0.0f ? acc : 0.0f;
+    const float4* wr = reinterpret_cast<const float4*>(sw + L::kWht + o * 12);
+    const float4 a0 = wr[0], a1 = wr[1], a2 = wr[2];
+    float acc = a0.x * dd[0];
+    acc = fmaf(a0.y, dd[1], acc); acc = fmaf(a0.z, dd[2], acc); acc = fmaf(a0.w, dd[3], acc);
+    acc = fmaf(a1.x, dd[4], acc); acc = fmaf(a1.y, dd[5], acc); acc = fmaf(a1.z, dd[6], acc);
+    acc = fmaf(a1.w, dd[7], acc); acc = fmaf(a2.x, dd[8], acc); acc = fmaf(a2.y, dd[9], acc);
+    acc = fmaf(a2.z, dd[10], acc);
+    g2[o] = ((m2 >> o) & 1ull) ? acc : 0.0f;
   }
 #pragma unroll
   for (int c = 0; c < C; ++c) df[c] = 0.0f;
 #pragma unroll 1
   for (int o1 = 0; o1 < kHidden; ++o1) {
-    float acc = b1[o1];
+    if (!((m1 >> o1) & 1ull)) continue;
+    const float4* w2r = reinterpret_cast<const float4*>(sw + L::kW2t + o1 * kHidden);
+    float d1 = 0.0f;
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc = fmaf(w1[o1 * C + c], f[c], acc);
-    if (acc > 0.0f) {
-      float d1 = 0.0f;
+    for (int o4 = 0; o4 < kHidden / 4; ++o4) {
+      const float4 w = w2r[o4];
+      d1 = fmaf(w.x, g2[4 * o4], d1);
+      d1 = fmaf(w.y, g2[4 * o4 + 1], d1);
+      d1 = fmaf(w.z, g2[4 * o4 + 2], d1);
+      d1 = fmaf(w.w, g2[4 * o4 + 3], d1);
+    }
+    const float4* w1r = reinterpret_cast<const float4*>(sw + L::kW1 + o1 * C);
 #pragma unroll
-      for (int o = 0; o < kHidden; ++o) d1 = fmaf(w2[o * kHidden + o1], g2[o], d1);
-#pragma unroll
-      for (int c = 0; c < C; ++c) df[c] = fmaf(w1[o1 * C + c], d1, df[c]);
+    for (int c4 = 0; c4 < C / 4; ++c4) {
+      const float4 w = w1r[c4];
+      df[4 * c4] = fmaf(w.x, d1, df[4 * c4]);
+      df[4 * c4 + 1] = fmaf(w.y, d1, df[4 * c4 + 1]);
+      df[4 * c4 + 2] = fmaf(w.z, d1, df[4 * c4 + 2]);
+      df[4 * c4 + 3] = fmaf(w.w, d1, df[4 * c4 + 3]);
     }
   }
 }
@@ -447,25 +500,37 @@ __device__ __forceinline__ void project(const GaussArgs& a, int g, const float d
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Deformation offsets of Gaussian g (zero for a static scene).
+// Deformation offsets of Gaussian g (zero for a static scene).  When
+// dstate is given, the reverse pass's state is stored there: the offsets
+// (11 floats) and the two MLP unit masks (words 12..15).
 template <int C>
-__device__ __forceinline__ void deform_delta(const GaussArgs& a, const float* sw, int g, float delta[kHeads]) {
+__device__ __forceinline__ void deform_delta(const GaussArgs& a, const float* sw, int g, float delta[kHeads],
+                                             float* dstate) {
 #pragma unroll
   for (int k = 0; k < kHeads; ++k) delta[k] = 0.0f;
   if (!a.has_deform) return;
   const float mu[3] = {a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2]};
   float f[C];
   hexplane_sample<C>(a, mu, f);
-  mlp_forward<C>(sw, f, delta);
+  uint64_t m1, m2;
+  mlp_forward<C>(sw, f, delta, m1, m2);
   if (a.noise) {
     const float nt = a.noise_scale * a.t;
 #pragma unroll
     for (int k = 0; k < 3; ++k) delta[k] = fmaf(nt, a.noise[3 * g + k], delta[k]);
   }
+  if (dstate) {
+    float4* d = reinterpret_cast<float4*>(dstate);
+    d[0] = make_float4(delta[0], delta[1], delta[2], delta[3]);
+    d[1] = make_float4(delta[4], delta[5], delta[6], delta[7]);
+    d[2] = make_float4(delta[8], delta[9], delta[10], 0.0f);
+    reinterpret_cast<uint4*>(dstate)[3] = make_uint4((uint32_t)m1, (uint32_t)(m1 >> 32), (uint32_t)m2,
+                                                     (uint32_t)(m2 >> 32));
+  }
 }
 
 template <int C>
-__global__ void __launch_bounds__(kThreads) gauss_fwd_kernel(const GaussArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) gauss_fwd_kernel(const GaussArgs a) {
   extern __shared__ __align__(16) float sw[];
   if (a.has_deform) load_mlp<C>(a, sw);
   __syncthreads();
@@ -473,7 +538,7 @@ __global__ void __launch_bounds__(kThreads) gauss_fwd_kernel(const GaussArgs a) 
   bool vis = false;
   if (g < a.P) {
     float delta[kHeads];
-    deform_delta<C>(a, sw, g, delta);
+    deform_delta<C>(a, sw, g, delta, a.dstate ? a.dstate + (size_t)g * kDStride : nullptr);
     float sh[48];
     load_sh(a.sh, a.sh_bf16, g, sh);
     Proj s;
@@ -527,16 +592,16 @@ __global__ void feat_grad_kernel(const GaussBwdArgs b, int P) {
 }
 
 // ---------------------------------------------------------------------------
-template <int C>
-__global__ void __launch_bounds__(kThreads) gauss_bwd_kernel(const GaussArgs a, const GaussBwdArgs b) {
-  extern __shared__ __align__(16) float sw[];
-  float* s_df = sw + mlp_floats<C>();  // [kThreads][C] thread-private slices
-  if (a.has_deform) load_mlp<C>(a, sw);
-  __syncthreads();
+// Reverse of projection and colour, per Gaussian: sums the partial rows,
+// recomputes the projection from the stored deformation offsets and writes
+// the gradients of the deformed parameters, which are also the canonical
+// gradients of log-scale, quaternion, opacity logit and SH; the mean's
+// path through the HexPlane grid is added by gauss_bwd_deform_kernel from
+// dd = d L / d delta stored per Gaussian.
+__global__ void __launch_bounds__(kThreads) gauss_bwd_proj_kernel(const GaussArgs a, const GaussBwdArgs b) {
   const int g = blockIdx.x * kThreads + threadIdx.x;
   if (g >= a.P) return;
   const int NP = kPartialScalars + b.D;
-  // 1. Fixed-order sum of this Gaussian's per-tile partials (emission order).
   float acc[kPartialScalars];
 #pragma unroll
   for (int k = 0; k < kPartialScalars; ++k) acc[k] = 0.0f;
@@ -553,14 +618,21 @@ __global__ void __launch_bounds__(kThreads) gauss_bwd_kernel(const GaussArgs a, 
       acc[2 * k + 1] += v.y;
     }
   }
-  // 2. Recompute the forward state.
   float delta[kHeads];
-  deform_delta<C>(a, sw, g, delta);
+  if (a.has_deform) {
+    const float4* d = reinterpret_cast<const float4*>(a.dstate + (size_t)g * kDStride);
+    const float4 d0 = d[0], d1 = d[1], d2 = d[2];
+    delta[0] = d0.x; delta[1] = d0.y; delta[2] = d0.z; delta[3] = d0.w;
+    delta[4] = d1.x; delta[5] = d1.y; delta[6] = d1.z; delta[7] = d1.w;
+    delta[8] = d2.x; delta[9] = d2.y; delta[10] = d2.z;
+  } else {
+#pragma unroll
+    for (int k = 0; k < kHeads; ++k) delta[k] = 0.0f;
+  }
   float sh[48];
   load_sh(a.sh, a.sh_bf16, g, sh);
   Proj s;
   project(a, g, delta, sh, s);
-  // 3. Screen-space gradients -> deformed parameters.
   const float du = acc[0], dv = acc[1];
   // Scaled conic back to (a, b, c) of the conic: A = -0.5 log2e a, B = -log2e b.
   const float dca = -0.5f * kLog2e * acc[2], dcb = -kLog2e * acc[3], dcc = -0.5f * kLog2e * acc[4];
@@ -598,7 +670,8 @@ __global__ void __launch_bounds__(kThreads) gauss_bwd_kernel(const GaussArgs a, 
   const float dlogit = dop * s.o * (1.0f - s.o);
   float dlogs[3] = {0.f, 0.f, 0.f};
   float dqt[4] = {0.f, 0.f, 0.f, 0.f};
-  if (s.visible && nt > 0) {
+  const bool active = s.visible && nt > 0;
+  if (active) {
     const float* V = a.V;
     const float zc = s.p[2], iz = 1.0f / zc;
     // Conic M = inverse of [[a,b],[b,c]]: Gs = -M Gm M with Gm = [[da, db/2],[db/2, dc]].
@@ -676,33 +749,54 @@ __global__ void __launch_bounds__(kThreads) gauss_bwd_kernel(const GaussArgs a, 
 #pragma unroll
     for (int i = 0; i < 4; ++i) dqt[i] = (dq[i] - s.q[i] * qd) * s.qinv;
   }
-  // 4. Deformation: canonical = deformed gradient + path through the grid.
-  float dmu_c[3] = {dmu[0], dmu[1], dmu[2]};
-  if (a.has_deform && nt > 0) {
-    const float dd[kHeads] = {dmu[0], dmu[1], dmu[2], dqt[0], dqt[1], dqt[2], dqt[3], dlogs[0], dlogs[1], dlogs[2], dlogit};
-    const float mu0[3] = {a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2]};
-    float* my_df = s_df + (size_t)threadIdx.x * C;
-    {
-      float f[C], df[C];
-      hexplane_sample<C>(a, mu0, f);
-      mlp_backward<C>(sw, f, dd, df);
-#pragma unroll
-      for (int c4 = 0; c4 < C / 4; ++c4)
-        reinterpret_cast<float4*>(my_df)[c4] = make_float4(df[4 * c4], df[4 * c4 + 1], df[4 * c4 + 2], df[4 * c4 + 3]);
-    }
-    float dg[3];
-    hexplane_backward<C>(a, mu0, my_df, dg);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) dmu_c[i] += dg[i];
-  }
-  b.d_means[3 * g] = dmu_c[0];
-  b.d_means[3 * g + 1] = dmu_c[1];
-  b.d_means[3 * g + 2] = dmu_c[2];
+  b.d_means[3 * g] = dmu[0];
+  b.d_means[3 * g + 1] = dmu[1];
+  b.d_means[3 * g + 2] = dmu[2];
   b.d_log_scales[3 * g] = dlogs[0];
   b.d_log_scales[3 * g + 1] = dlogs[1];
   b.d_log_scales[3 * g + 2] = dlogs[2];
   reinterpret_cast<float4*>(b.d_quats)[g] = make_float4(dqt[0], dqt[1], dqt[2], dqt[3]);
   b.d_logits[g] = dlogit;
+  if (a.has_deform) {
+    // dd = dL/d delta: d_mu, d_q (pre-normalisation), d_log_s, d_logit; [11] = active flag.
+    float4* o = reinterpret_cast<float4*>(b.ddstate + (size_t)g * 12);
+    o[0] = make_float4(dmu[0], dmu[1], dmu[2], dqt[0]);
+    o[1] = make_float4(dqt[1], dqt[2], dqt[3], dlogs[0]);
+    o[2] = make_float4(dlogs[1], dlogs[2], dlogit, active ? 1.0f : 0.0f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mean gradient through the deformation: MLP reverse from the stored
+// HexPlane feature, then the six bilinear samples (Sec. 3.2, Eq. 4-6).
+template <int C>
+__global__ void __launch_bounds__(kThreads, 2) gauss_bwd_deform_kernel(const GaussArgs a, const GaussBwdArgs b) {
+  extern __shared__ __align__(16) float sw[];
+  float* s_df = sw + mlp_floats<C>();  // [kThreads][C] thread-private slices
+  load_mlp<C>(a, sw);
+  __syncthreads();
+  const int g = blockIdx.x * kThreads + threadIdx.x;
+  if (g >= a.P) return;
+  const float4* dd4 = reinterpret_cast<const float4*>(b.ddstate + (size_t)g * 12);
+  const float4 q0 = dd4[0], q1 = dd4[1], q2 = dd4[2];
+  if (q2.w == 0.0f) return;
+  const float dd[kHeads] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z};
+  const uint4 mk = reinterpret_cast<const uint4*>(a.dstate + (size_t)g * kDStride)[3];
+  const uint64_t m1 = (uint64_t)mk.x | ((uint64_t)mk.y << 32), m2 = (uint64_t)mk.z | ((uint64_t)mk.w << 32);
+  float* my_df = s_df + (size_t)threadIdx.x * C;
+  {
+    float df[C];
+    mlp_backward<C>(sw, m1, m2, dd, df);
+#pragma unroll
+    for (int c4 = 0; c4 < C / 4; ++c4)
+      reinterpret_cast<float4*>(my_df)[c4] = make_float4(df[4 * c4], df[4 * c4 + 1], df[4 * c4 + 2], df[4 * c4 + 3]);
+  }
+  const float mu0[3] = {a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2]};
+  float dg[3];
+  hexplane_backward<C>(a, mu0, my_df, dg);
+  b.d_means[3 * g] += dg[0];
+  b.d_means[3 * g + 1] += dg[1];
+  b.d_means[3 * g + 2] += dg[2];
 }
 
 // ---------------------------------------------------------------------------
@@ -726,11 +820,10 @@ cudaError_t launch_gauss_fwd(const GaussArgs& a, cudaStream_t st) {
 }
 
 template <int C>
-static cudaError_t launch_bwd_t(const GaussArgs& a, const GaussBwdArgs& b, cudaStream_t st) {
-  const size_t full = (mlp_floats<C>() + (size_t)kThreads * C) * sizeof(float);
-  const size_t smem = a.has_deform ? full : 0;
-  auto k = gauss_bwd_kernel<C>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
+static cudaError_t launch_bwd_deform_t(const GaussArgs& a, const GaussBwdArgs& b, cudaStream_t st) {
+  const size_t smem = (mlp_floats<C>() + (size_t)kThreads * C) * sizeof(float);
+  auto k = gauss_bwd_deform_kernel<C>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<ceil_div(a.P, kThreads), kThreads, smem, st>>>(a, b);
   return cudaGetLastError();
 }
@@ -742,9 +835,11 @@ cudaError_t launch_gauss_bwd(const GaussArgs& a, const GaussBwdArgs& b, cudaStre
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mid && (e = cudaEventRecord(mid, st)) != cudaSuccess) return e;
-  const int C = a.has_deform ? a.C : 32;
-  if (C == 32) return launch_bwd_t<32>(a, b, st);
-  if (C == 64) return launch_bwd_t<64>(a, b, st);
+  gauss_bwd_proj_kernel<<<ceil_div(a.P, kThreads), kThreads, 0, st>>>(a, b);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!a.has_deform) return cudaSuccess;
+  if (a.C == 32) return launch_bwd_deform_t<32>(a, b, st);
+  if (a.C == 64) return launch_bwd_deform_t<64>(a, b, st);
   return cudaErrorInvalidValue;
 }
 

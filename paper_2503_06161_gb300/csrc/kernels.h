@@ -6,6 +6,8 @@
 
 namespace fe {
 
+constexpr int kDStride = 16;  // floats per Gaussian of reverse-pass state: offsets[11], pad, unit masks[4]
+
 struct GaussArgs {
   int P, sh_degree, sh_bf16;
   const float *means, *log_scales, *quats, *logits;
@@ -21,6 +23,9 @@ struct GaussArgs {
   float fx, fy, cx, cy, znear, limx, limy;
   float V[12];
   float campos[3];
+  // state kept for the reverse pass (NULL when the workspace has none):
+  // [P][kDStride] deformation offsets and MLP unit masks
+  float* dstate;
   // outputs
   float4* rec;
   ushort4* rect;
@@ -35,6 +40,7 @@ struct GaussBwdArgs {
   const float* partials;
   const uint8_t* pflags;
   float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh, *d_feat;
+  float* ddstate;  // [P][12] dL/d delta, [11] = active flag
 };
 
 cudaError_t launch_gauss_fwd(const GaussArgs& a, cudaStream_t st);
