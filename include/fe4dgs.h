@@ -137,7 +137,7 @@ typedef struct {
 
 /* Bytes of workspace for P Gaussians, D channels, a width x height image
  * and opts (NULL = defaults).  Returns FE_ERR_UNSUPPORTED for a tile shape
- * or D that is not compiled in. */
+ * or D that is not compiled in, or for more than 8192 tiles. */
 fe_status fe_workspace_size(int P, int D, int width, int height, const fe_opts *opts, size_t *bytes);
 
 /* Forward pass (Sec. 3.2-3.3): deform (deform may be NULL: static scene)

@@ -37,7 +37,7 @@ fe_status layout_for(int P, int D, int W, int H, const fe_opts* opts, Layout& L,
   fe_status s = resolve_opts(opts, P, tw, th, cap, wb, bg);
   if (s != FE_OK) return s;
   const int tiles_x = (W + tw - 1) / tw, tiles_y = (H + th - 1) / th;
-  if (tiles_x > 65535 || tiles_y > 65535 || (int64_t)tiles_x * tiles_y > (1 << 24)) return FE_ERR_UNSUPPORTED;
+  if ((int64_t)tiles_x * tiles_y > kMaxTiles) return FE_ERR_UNSUPPORTED;
   L = make_layout(P, D, W, H, tw, th, cap, wb);
   return FE_OK;
 }
@@ -114,25 +114,24 @@ BinArgs bin_args(const Layout& L, void* ws) {
   b.P = L.P;
   b.ntiles = L.ntiles;
   b.tiles_x = L.tiles_x;
-  b.tile_passes = L.tile_passes;
+  b.pblocks = L.pblocks;
+  b.bblocks = L.bblocks;
   b.cap = L.cap;
   b.rect = at<ushort4>(ws, L.rect);
   b.touched = at<uint32_t>(ws, L.touched);
   for (int i = 0; i < 2; ++i) {
     b.dkey[i] = at<uint32_t>(ws, L.dkey[i]);
     b.dval[i] = at<uint32_t>(ws, L.dval[i]);
-    b.tkey[i] = at<uint32_t>(ws, L.tkey[i]);
-    b.tval[i] = at<uint32_t>(ws, L.tval[i]);
   }
   b.offs = at<uint32_t>(ws, L.offs);
   b.offs_by_gid = at<uint32_t>(ws, L.offs_by_gid);
+  b.sorted_e = at<uint32_t>(ws, L.sorted_e);
   b.gid_of_emit = at<uint32_t>(ws, L.gid_of_emit);
+  b.table = at<uint32_t>(ws, L.table);
   b.status = at<uint32_t>(ws, L.status);
   b.hist = at<uint32_t>(ws, L.hist);
   b.ranges = at<uint2>(ws, L.ranges);
   b.hdr = at<Header>(ws, L.hdr);
-  b.depth_final = 0;
-  b.tile_final = L.tile_passes % 2;
   return b;
 }
 
@@ -151,17 +150,17 @@ CompositeArgs composite_args(const Layout& L, void* ws, int feat_bf16, const voi
   c.feat_bf16 = feat_bf16;
   for (int i = 0; i < 3; ++i) c.bg[i] = bg[i];
   c.ranges = at<uint2>(ws, L.ranges);
-  const int tf = L.tile_passes % 2;
-  c.sorted_e = at<uint32_t>(ws, L.tval[tf]);
+  c.sorted_e = at<uint32_t>(ws, L.sorted_e);
   c.gid_of_emit = at<uint32_t>(ws, L.gid_of_emit);
   c.rec = at<float4>(ws, L.rec);
   c.feat = feat;
   c.t_final = at<float>(ws, L.tfinal);
   c.n_contrib = at<uint32_t>(ws, L.ncontrib);
   c.ntiles = L.ntiles;
+  c.cap = L.cap;
   if (L.with_backward) {
     c.partials = at<float>(ws, L.partials);
-    c.pflags = at<uint8_t>(ws, L.pflags);
+    c.pflags = at<uint32_t>(ws, L.pflags);
   }
   return c;
 }
@@ -243,7 +242,7 @@ fe_status fe_render_backward(const fe_gaussians* g, const fe_deform* deform, con
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GaussArgs ga;
   if ((s = fill_gauss_args(g, deform, cam, t, L, workspace, ga)) != FE_OK) return s;
-  FE_TRY_CUDA(cudaMemsetAsync(at<char>(workspace, L.pflags), 0, (size_t)L.cap, st));
+  FE_TRY_CUDA(cudaMemsetAsync(at<char>(workspace, L.pflags), 0, ((size_t)L.cap + 31) / 32 * 4, st));
   FE_TRY_CUDA(mark(opts, 4, st));
   CompositeArgs c = composite_args(L, workspace, g->feat_bf16, g->feat, bg);
   c.g_rgb = grad_out->rgb;
@@ -258,7 +257,7 @@ fe_status fe_render_backward(const fe_gaussians* g, const fe_deform* deform, con
   gb.touched = at<uint32_t>(workspace, L.touched);
   gb.offs_by_gid = at<uint32_t>(workspace, L.offs_by_gid);
   gb.partials = at<float>(workspace, L.partials);
-  gb.pflags = at<uint8_t>(workspace, L.pflags);
+  gb.pflags = at<uint32_t>(workspace, L.pflags);
   gb.d_means = grads->means;
   gb.d_log_scales = grads->log_scales;
   gb.d_quats = grads->quats;
@@ -266,6 +265,7 @@ fe_status fe_render_backward(const fe_gaussians* g, const fe_deform* deform, con
   gb.d_sh = grads->sh;
   gb.d_feat = grads->feat;
   gb.ddstate = at<float>(workspace, L.ddstate);
+  gb.psum = at<float>(workspace, L.psum);
   FE_TRY_CUDA(launch_gauss_bwd(ga, gb, st, opts && opts->events ? static_cast<cudaEvent_t>(opts->events[6]) : nullptr));
   FE_TRY_CUDA(mark(opts, 7, st));
   return FE_OK;
@@ -335,9 +335,7 @@ fe_status fe_debug_dump(const void* workspace, size_t workspace_bytes, int P, in
   d.ntiles = L.ntiles;
   d.HW = width * height;
   d.hdr = at<Header>(ws, L.hdr);
-  const int tf = L.tile_passes % 2;
-  d.sorted_tile = at<uint32_t>(ws, L.tkey[tf]);
-  d.sorted_e = at<uint32_t>(ws, L.tval[tf]);
+  d.sorted_e = at<uint32_t>(ws, L.sorted_e);
   d.gid_of_emit = at<uint32_t>(ws, L.gid_of_emit);
   d.ranges = at<uint2>(ws, L.ranges);
   d.ncontrib = at<uint32_t>(ws, L.ncontrib);

@@ -1,17 +1,17 @@
 // Integer stage of the pass: the tile-based binning of 3DGS that the paper
-// builds on (Sec. 2.1), reorganised for one GPU with large HBM:
+// builds on (Sec. 2.1), reorganised for one GPU:
 //   1. stable LSD radix sort of the P depth keys (4 x 8-bit passes);
-//   2. one fused kernel: exclusive scan of tiles_touched in depth order
-//      (decoupled look-back), emission of each Gaussian's tiles row-major,
-//      and the digit histograms of the tile ids;
-//   3. stable LSD radix sort of the K tile ids (1-2 x 8-bit passes) whose
-//      payload is the emission index;
-//   4. tile ranges from the sorted tile ids.
-// Emitting in depth order and sorting stably by tile gives exactly the order
-// of a stable sort on (tile << 32 | depth bits) with ties by index, while
-// moving 32-bit keys through 2 passes instead of 64-bit keys through 6.
-// Every inter-block wait is a bounded spin that records kErrTimeout and
-// carries on, so no launch can hang.
+//   2. exclusive scan of tiles_touched in depth order (decoupled look-back)
+//      and, per block of 1024 depth-ordered Gaussians, its count of
+//      entries per tile (a tile-major (tile, block) table);
+//   3. exclusive scan of that table: the start of every (tile, block)
+//      segment of the final list, and the tile ranges;
+//   4. a scatter in which each warp walks its Gaussians in depth order with
+//      per-warp tile counters, so every entry lands at its final position.
+// The result is the order of a stable sort on (tile << 32 | depth bits) with
+// ties by index, built with one write per entry instead of radix passes over
+// 64-bit keys.  Every inter-block wait is a bounded spin that records
+// kErrTimeout and carries on, so no launch can hang.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -194,148 +194,224 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint32_t* __re
 }
 
 // ---------------------------------------------------------------------------
-// Exclusive scan of tiles_touched in depth order + tile emission + tile
-// digit histograms.  Block b owns depth ranks [1024 b, 1024 b + 1024);
-// thread t scans ranks 4t..4t+3 of it.  Emission is load balanced: each
-// thread writes whole output entries, finding the owning Gaussian by a
-// binary search over the block's offsets in shared memory, so the writes
-// are coalesced and no thread walks a long rect alone.
-struct KeygenArgs {
-  int P, tiles_x, tile_passes;
+// Decoupled look-back over a 64-bit running total: block b publishes its
+// aggregate, then sums its predecessors back to the first inclusive prefix.
+__device__ __forceinline__ uint64_t lookback64(uint64_t* status, uint32_t b, uint64_t aggregate, uint32_t* err) {
+  if (b == 0) {
+    st_vol64(status, kFlagPre64 | aggregate);
+    return 0;
+  }
+  st_vol64(status + b, kFlagAgg64 | aggregate);
+  uint64_t excl = 0;
+  for (int64_t j = (int64_t)b - 1; j >= 0; --j) {
+    uint64_t s = ld_vol64(status + j);
+    int spins = 0;
+    while ((s & ~kValMask64) == 0ull) {
+      if (++spins > kSpinLimit) {
+        set_err(err, kErrTimeout);
+        s = kFlagPre64;
+        break;
+      }
+      __nanosleep(32);
+      s = ld_vol64(status + j);
+    }
+    excl += s & kValMask64;
+    if (s & kFlagPre64) break;
+  }
+  st_vol64(status + b, kFlagPre64 | (excl + aggregate));
+  return excl;
+}
+
+// Step 2: block b (ticket) owns depth ranks [512 b, 512 b + 512); thread t
+// scans ranks 2t..2t+1.  Writes offs / offs_by_gid and column b of the
+// tile-major count table.
+struct CountArgs {
+  int P, tiles_x, ntiles, nblocks;
   int64_t cap;
-  const uint32_t* order;     // depth-sorted Gaussian ids
+  const uint32_t* order;  // depth-sorted Gaussian ids
   const uint32_t* touched;
   const ushort4* rect;
-  uint32_t *offs, *offs_by_gid, *tile_out, *gid_of_emit;
-  uint32_t* hist;            // [3][256] tile digit histograms
+  uint32_t *offs, *offs_by_gid, *table;
   uint64_t* status;
   uint32_t* ticket;
   Header* hdr;
 };
 
-__global__ void __launch_bounds__(kThreads) scan_keygen_kernel(const KeygenArgs a) {
-  __shared__ uint32_t s_hist[3][256];
-  __shared__ uint32_t s_off[kPChunk];
-  __shared__ uint32_t s_gid[kPChunk];
-  __shared__ ushort4 s_rect[kPChunk];
+__global__ void __launch_bounds__(kThreads) bin_count_kernel(const CountArgs a) {
+  extern __shared__ uint32_t s_cnt[];  // [ntiles]
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_ticket;
   __shared__ uint64_t s_prefix;
   const int tid = threadIdx.x;
-  for (int i = tid; i < 3 * 256; i += kThreads) (&s_hist[0][0])[i] = 0;
+  for (int i = tid; i < a.ntiles; i += kThreads) s_cnt[i] = 0;
   if (tid == 0) s_ticket = atomicAdd(a.ticket, 1u);
   __syncthreads();
   const uint32_t b = s_ticket;
-  const int64_t start = (int64_t)b * kPChunk;
+  const int64_t start = (int64_t)b * kBinChunk;
   if (start >= a.P) return;
-  uint32_t cnt[kPItems];
+  uint32_t gid[kBinItems], cnt[kBinItems];
   uint32_t tsum = 0;
 #pragma unroll
-  for (int i = 0; i < kPItems; ++i) {
-    const int li = tid * kPItems + i;
-    const int64_t r = start + li;
-    uint32_t g = 0, c = 0;
-    ushort4 rc = make_ushort4(1, 1, 0, 0);
-    if (r < a.P) {
-      g = a.order[r];
-      c = a.touched[g];
-      if (c) rc = a.rect[g];
-    }
-    s_gid[li] = g;
-    s_rect[li] = rc;
-    cnt[i] = c;
-    tsum += c;
+  for (int i = 0; i < kBinItems; ++i) {
+    const int64_t r = start + tid * kBinItems + i;
+    gid[i] = r < a.P ? a.order[r] : 0u;
+    cnt[i] = r < a.P ? a.touched[gid[i]] : 0u;
+    tsum += cnt[i];
   }
   uint32_t btot;
   const uint32_t texcl = block_excl_scan(tsum, s_scan, btot);
-  if (tid == 0) {
-    uint64_t excl = 0;
-    if (b == 0) {
-      st_vol64(a.status, kFlagPre64 | (uint64_t)btot);
-    } else {
-      st_vol64(a.status + b, kFlagAgg64 | (uint64_t)btot);
-      for (int64_t j = (int64_t)b - 1; j >= 0; --j) {
-        uint64_t s = ld_vol64(a.status + j);
-        int spins = 0;
-        while ((s & ~kValMask64) == 0ull) {
-          if (++spins > kSpinLimit) {
-            set_err(&a.hdr->err, kErrTimeout);
-            s = kFlagPre64;
-            break;
-          }
-          __nanosleep(32);
-          s = ld_vol64(a.status + j);
-        }
-        excl += s & kValMask64;
-        if (s & kFlagPre64) break;
-      }
-      st_vol64(a.status + b, kFlagPre64 | (excl + btot));
-    }
-    s_prefix = excl;
-  }
-  // Local offsets of this thread's ranks.
-  uint32_t run = texcl;
+  if (tid == 0) s_prefix = lookback64(a.status, b, btot, &a.hdr->err);
+  __syncthreads();
+  uint64_t run = s_prefix + texcl;
 #pragma unroll
-  for (int i = 0; i < kPItems; ++i) {
-    s_off[tid * kPItems + i] = run;
+  for (int i = 0; i < kBinItems; ++i) {
+    const int64_t r = start + tid * kBinItems + i;
+    if (r < a.P) {
+      const uint32_t o32 = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
+      a.offs[r] = o32;
+      a.offs_by_gid[gid[i]] = o32;
+      if (cnt[i]) {
+        const ushort4 rc = a.rect[gid[i]];
+        for (int ty = rc.y; ty <= rc.w; ++ty)
+          for (int tx = rc.x; tx <= rc.z; ++tx) atomicAdd(&s_cnt[ty * a.tiles_x + tx], 1u);
+      }
+    }
     run += cnt[i];
   }
+  if (start + kBinChunk >= a.P && tid == kThreads - 1) {
+    a.offs[a.P] = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
+    a.hdr->num_dups = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
+    if (run > (uint64_t)a.cap) set_err(&a.hdr->err, kErrOverflow);
+  }
   __syncthreads();
-  const uint64_t base = s_prefix;
+  for (int t = tid; t < a.ntiles; t += kThreads) a.table[(size_t)t * a.nblocks + b] = s_cnt[t];
+}
+
+// Step 3: in-place exclusive scan of the (tile, block) table, tile-major.
+__global__ void __launch_bounds__(kThreads) table_scan_kernel(uint32_t* table, int64_t n, uint64_t* status,
+                                                             uint32_t* ticket, uint32_t* err) {
+  __shared__ uint32_t s_scan[8];
+  __shared__ uint32_t s_ticket;
+  __shared__ uint64_t s_prefix;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_ticket = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const uint32_t b = s_ticket;
+  const int64_t start = (int64_t)b * kPChunk;
+  if (start >= n) return;
+  uint32_t v[kPItems], tsum = 0;
 #pragma unroll
   for (int i = 0; i < kPItems; ++i) {
-    const int li = tid * kPItems + i;
-    const int64_t r = start + li;
-    if (r < a.P) {
-      const uint32_t o32 = (uint32_t)min(base + s_off[li], (uint64_t)0xFFFFFFFFu);
-      a.offs[r] = o32;
-      a.offs_by_gid[s_gid[li]] = o32;
-    }
+    const int64_t r = start + tid * kPItems + i;
+    v[i] = r < n ? table[r] : 0u;
+    tsum += v[i];
   }
-  const uint64_t cap = (uint64_t)a.cap;
-  const int nloc = (int)min((int64_t)kPChunk, (int64_t)a.P - start);
-  for (uint32_t i = tid; i < btot; i += kThreads) {
-    const uint64_t e = base + i;
-    if (e >= cap) break;
-    // Owner: last local Gaussian whose offset is <= i.
-    int lo = 0, hi = nloc;  // invariant: s_off[lo] <= i < s_off[hi] (s_off[nloc] = btot)
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (s_off[mid] <= i) lo = mid; else hi = mid;
-    }
-    const ushort4 rc = s_rect[lo];
-    const uint32_t loc = i - s_off[lo];
-    const uint32_t wdt = (uint32_t)(rc.z - rc.x + 1);
-    const uint32_t ty = rc.y + loc / wdt, tx = rc.x + loc % wdt;
-    const uint32_t tile = ty * (uint32_t)a.tiles_x + tx;
-    a.tile_out[e] = tile;
-    a.gid_of_emit[e] = s_gid[lo];
-    atomicAdd(&s_hist[0][tile & 255u], 1u);
-    if (a.tile_passes > 1) atomicAdd(&s_hist[1][(tile >> 8) & 255u], 1u);
-    if (a.tile_passes > 2) atomicAdd(&s_hist[2][(tile >> 16) & 255u], 1u);
-  }
-  if (start + kPChunk >= a.P && tid == 0) {
-    // Last block: total K.
-    const uint64_t total = base + btot;
-    a.offs[a.P] = (uint32_t)min(total, (uint64_t)0xFFFFFFFFu);
-    a.hdr->num_dups = (uint32_t)min(total, (uint64_t)0xFFFFFFFFu);
-    if (total > cap) set_err(&a.hdr->err, kErrOverflow);
-  }
+  uint32_t btot;
+  const uint32_t texcl = block_excl_scan(tsum, s_scan, btot);
+  if (tid == 0) s_prefix = lookback64(status, b, btot, err);
   __syncthreads();
-  for (int i = tid; i < a.tile_passes * 256; i += kThreads) {
-    const uint32_t v = (&s_hist[0][0])[i];
-    if (v) atomicAdd(a.hist + i, v);
+  uint64_t run = s_prefix + texcl;
+#pragma unroll
+  for (int i = 0; i < kPItems; ++i) {
+    const int64_t r = start + tid * kPItems + i;
+    if (r < n) table[r] = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
+    run += v[i];
   }
 }
 
-__global__ void ranges_kernel(const uint32_t* __restrict__ tiles, const Header* hdr, int64_t cap, uint2* ranges,
-                              uint32_t* has_forward) {
-  const uint64_t n = min((uint64_t)hdr->num_dups, (uint64_t)cap);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && has_forward) *has_forward = 1u;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t t = tiles[i];
-    if (i == 0 || tiles[i - 1] != t) ranges[t].x = (uint32_t)i;
-    if (i + 1 == n || tiles[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+// Step 4: block b (= blockIdx.x) re-walks the ranks of count block b.  Each
+// warp takes 64 consecutive Gaussians; its lanes cover one Gaussian's tiles
+// at a time (all distinct), so per-warp tile counters give stable ranks.
+// Block 0 also writes the tile ranges and marks the workspace as holding a
+// forward's state.
+struct ScatterArgs {
+  int P, tiles_x, ntiles, nblocks;
+  int64_t cap;
+  const uint32_t *order, *touched, *offs, *table;
+  const ushort4* rect;
+  uint32_t *sorted_e, *gid_of_emit;
+  uint2* ranges;
+  Header* hdr;
+};
+
+__global__ void __launch_bounds__(kThreads) bin_scatter_kernel(const ScatterArgs a) {
+  extern __shared__ __align__(16) uint32_t s_dyn[];
+  uint32_t* s_base = s_dyn;                                        // [ntiles]
+  uint16_t* s_wc = reinterpret_cast<uint16_t*>(s_dyn + a.ntiles);  // [8][ntiles]
+  __shared__ uint32_t s_gid[kBinChunk], s_cnt[kBinChunk], s_off[kBinChunk];
+  __shared__ ushort4 s_rect[kBinChunk];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.x;
+  const int64_t start = (int64_t)b * kBinChunk;
+  const int nloc = (int)min((int64_t)kBinChunk, (int64_t)a.P - start);
+  const uint64_t cap = (uint64_t)a.cap;
+  // Past capacity the list is incomplete (and flagged): every range is
+  // published empty so no later kernel follows an index beyond capacity.
+  const bool overflow = (uint64_t)a.hdr->num_dups > cap;
+  const uint64_t K = overflow ? 0 : (uint64_t)a.hdr->num_dups;
+  for (int t = tid; t < a.ntiles; t += kThreads) {
+    s_base[t] = a.table[(size_t)t * a.nblocks + b];
+    if (b == 0) {
+      const uint64_t lo = min((uint64_t)a.table[(size_t)t * a.nblocks], K);
+      const uint64_t hi = t + 1 < a.ntiles ? min((uint64_t)a.table[(size_t)(t + 1) * a.nblocks], K) : K;
+      a.ranges[t] = make_uint2((uint32_t)lo, (uint32_t)hi);
+    }
+  }
+  if (b == 0 && tid == 0) a.hdr->has_forward = 1u;
+  for (int i = tid; i < 8 * a.ntiles; i += kThreads) s_wc[i] = 0;
+  for (int i = tid; i < nloc; i += kThreads) {
+    const uint32_t g = a.order[start + i];
+    const uint32_t c = a.touched[g];
+    s_gid[i] = g;
+    s_cnt[i] = c;
+    s_off[i] = a.offs[start + i];
+    s_rect[i] = c ? a.rect[g] : make_ushort4(1, 1, 0, 0);
+  }
+  __syncthreads();
+  uint16_t* wc = s_wc + (size_t)warp * a.ntiles;
+  const int i0 = warp * (kBinChunk / 8), i1 = min(nloc, i0 + kBinChunk / 8);
+  for (int i = i0; i < i1; ++i) {
+    const uint32_t c = s_cnt[i];
+    if (!c) continue;
+    const ushort4 rc = s_rect[i];
+    const uint32_t wdt = rc.z - rc.x + 1u;
+    const float iw = 1.0f / (float)wdt;
+    for (uint32_t k = lane; k < c; k += 32) {
+      const uint32_t dy = (uint32_t)(((float)k + 0.5f) * iw), dx = k - dy * wdt;  // exact for k < 2^20
+      const uint32_t tile = (rc.y + dy) * (uint32_t)a.tiles_x + rc.x + dx;
+      wc[tile] = (uint16_t)(wc[tile] + 1u);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int t = tid; t < a.ntiles; t += kThreads) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const uint32_t c = s_wc[w * a.ntiles + t];
+      s_wc[w * a.ntiles + t] = (uint16_t)run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int i = i0; i < i1; ++i) {
+    const uint32_t c = s_cnt[i];
+    if (!c) continue;
+    const ushort4 rc = s_rect[i];
+    const uint32_t wdt = rc.z - rc.x + 1u;
+    const float iw = 1.0f / (float)wdt;
+    const uint32_t g = s_gid[i], e0 = s_off[i];
+    for (uint32_t k = lane; k < c; k += 32) {
+      const uint32_t dy = (uint32_t)(((float)k + 0.5f) * iw), dx = k - dy * wdt;
+      const uint32_t tile = (rc.y + dy) * (uint32_t)a.tiles_x + rc.x + dx;
+      const uint32_t r = wc[tile];
+      wc[tile] = (uint16_t)(r + 1u);
+      const uint64_t pos = (uint64_t)s_base[tile] + r;
+      const uint64_t e = (uint64_t)e0 + k;
+      if (pos < cap) a.sorted_e[pos] = (uint32_t)e;
+      if (e < cap) a.gid_of_emit[e] = g;
+    }
+    __syncwarp();
   }
 }
 
@@ -384,76 +460,74 @@ cudaError_t launch_bin_prep(int P, const float* uv, const int* radius, const flo
 
 cudaError_t launch_binning(BinArgs& b, cudaStream_t st) {
   Header* hdr = static_cast<Header*>(b.hdr);
-  const size_t pass_smem = sizeof(PassSmem<kSortItems>);
   const size_t ppass_smem = sizeof(PassSmem<kPItems>);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(onesweep_kernel<true, kSortItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)pass_smem);
-    cudaFuncSetAttribute(onesweep_kernel<false, kSortItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)pass_smem);
-    attr_set = true;
-  }
-  cudaError_t e;
   const int P = b.P;
-  const int pblocks = ceil_div(P > 0 ? P : 1, kPChunk);
+  if (P <= 0) return cudaSuccess;  // K = 0: the cleared header and ranges already say so
+  cudaError_t e;
+  const int pblocks = b.pblocks;
   uint32_t* status_depth = b.status;
-  uint32_t* status_tile = b.status + (size_t)pblocks * 256 * 4;
-  const int kblocks = ceil_div(b.cap > 0 ? b.cap : 1, kSortChunk);
-  uint64_t* status_scan = reinterpret_cast<uint64_t*>(status_tile + (size_t)kblocks * 256 * 3);
-  if (P > 0) {
-    // 1. depth sort (values: Gaussian ids)
-    depth_hist_kernel<<<pblocks, kThreads, 0, st>>>(b.dkey[0], P, b.hist);
-    int cur = 0;
-    for (int p = 0; p < 4; ++p) {
-      if (p == 0)
-        onesweep_kernel<true, kPItems><<<pblocks, kThreads, ppass_smem, st>>>(
-            b.dkey[cur], nullptr, b.dkey[cur ^ 1], b.dval[cur ^ 1], nullptr, P, 8 * p, b.hist + 256 * p,
-            status_depth + (size_t)p * pblocks * 256, hdr->ticket + kTicketDepth0 + p, &hdr->err);
-      else
-        onesweep_kernel<false, kPItems><<<pblocks, kThreads, ppass_smem, st>>>(
-            b.dkey[cur], b.dval[cur], b.dkey[cur ^ 1], b.dval[cur ^ 1], nullptr, P, 8 * p, b.hist + 256 * p,
-            status_depth + (size_t)p * pblocks * 256, hdr->ticket + kTicketDepth0 + p, &hdr->err);
-      cur ^= 1;
-    }
-    b.depth_final = cur;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // 2. scan + emission
-    KeygenArgs ka;
-    ka.P = P;
-    ka.tiles_x = b.tiles_x;
-    ka.tile_passes = b.tile_passes;
-    ka.cap = b.cap;
-    ka.order = b.dval[cur];
-    ka.touched = b.touched;
-    ka.rect = b.rect;
-    ka.offs = b.offs;
-    ka.offs_by_gid = b.offs_by_gid;
-    ka.tile_out = b.tkey[0];
-    ka.gid_of_emit = b.gid_of_emit;
-    ka.hist = b.hist + 4 * 256;
-    ka.status = status_scan;
-    ka.ticket = hdr->ticket + kTicketScan;
-    ka.hdr = hdr;
-    scan_keygen_kernel<<<pblocks, kThreads, 0, st>>>(ka);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  // 3. tile sort (values: emission index)
+  const int bblocks = b.bblocks;
+  uint64_t* status_count = reinterpret_cast<uint64_t*>(b.status + (size_t)pblocks * 256 * 4);
+  uint64_t* status_table = status_count + bblocks;
+  // 1. depth sort (values: Gaussian ids)
+  depth_hist_kernel<<<pblocks, kThreads, 0, st>>>(b.dkey[0], P, b.hist);
   int cur = 0;
-  for (int p = 0; p < b.tile_passes; ++p) {
+  for (int p = 0; p < 4; ++p) {
     if (p == 0)
-      onesweep_kernel<true, kSortItems><<<kblocks, kThreads, pass_smem, st>>>(
-          b.tkey[cur], nullptr, b.tkey[cur ^ 1], b.tval[cur ^ 1], &hdr->num_dups, b.cap, 8 * p,
-          b.hist + (4 + p) * 256, status_tile + (size_t)p * kblocks * 256, hdr->ticket + kTicketTile0 + p, &hdr->err);
+      onesweep_kernel<true, kPItems><<<pblocks, kThreads, ppass_smem, st>>>(
+          b.dkey[cur], nullptr, b.dkey[cur ^ 1], b.dval[cur ^ 1], nullptr, P, 8 * p, b.hist + 256 * p,
+          status_depth + (size_t)p * pblocks * 256, hdr->ticket + kTicketDepth0 + p, &hdr->err);
     else
-      onesweep_kernel<false, kSortItems><<<kblocks, kThreads, pass_smem, st>>>(
-          b.tkey[cur], b.tval[cur], b.tkey[cur ^ 1], b.tval[cur ^ 1], &hdr->num_dups, b.cap, 8 * p,
-          b.hist + (4 + p) * 256, status_tile + (size_t)p * kblocks * 256, hdr->ticket + kTicketTile0 + p, &hdr->err);
+      onesweep_kernel<false, kPItems><<<pblocks, kThreads, ppass_smem, st>>>(
+          b.dkey[cur], b.dval[cur], b.dkey[cur ^ 1], b.dval[cur ^ 1], nullptr, P, 8 * p, b.hist + 256 * p,
+          status_depth + (size_t)p * pblocks * 256, hdr->ticket + kTicketDepth0 + p, &hdr->err);
     cur ^= 1;
   }
-  b.tile_final = cur;
-  // 4. ranges
-  ranges_kernel<<<grid_for(b.cap, 256), 256, 0, st>>>(b.tkey[cur], hdr, b.cap, b.ranges, &hdr->has_forward);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // 2. tiles_touched scan + per-block tile counts
+  CountArgs ca;
+  ca.P = P;
+  ca.tiles_x = b.tiles_x;
+  ca.ntiles = b.ntiles;
+  ca.nblocks = bblocks;
+  ca.cap = b.cap;
+  ca.order = b.dval[cur];
+  ca.touched = b.touched;
+  ca.rect = b.rect;
+  ca.offs = b.offs;
+  ca.offs_by_gid = b.offs_by_gid;
+  ca.table = b.table;
+  ca.status = status_count;
+  ca.ticket = hdr->ticket + kTicketScan;
+  ca.hdr = hdr;
+  const size_t count_smem = (size_t)b.ntiles * 4;
+  cudaFuncSetAttribute(bin_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)count_smem);
+  bin_count_kernel<<<bblocks, kThreads, count_smem, st>>>(ca);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // 3. scan of the (tile, block) table
+  const int64_t tn = (int64_t)b.ntiles * bblocks;
+  table_scan_kernel<<<ceil_div(tn, kPChunk), kThreads, 0, st>>>(b.table, tn, status_table,
+                                                                hdr->ticket + kTicketTable, &hdr->err);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // 4. scatter into the final list
+  ScatterArgs sa;
+  sa.P = P;
+  sa.tiles_x = b.tiles_x;
+  sa.ntiles = b.ntiles;
+  sa.nblocks = bblocks;
+  sa.cap = b.cap;
+  sa.order = b.dval[cur];
+  sa.touched = b.touched;
+  sa.offs = b.offs;
+  sa.table = b.table;
+  sa.rect = b.rect;
+  sa.sorted_e = b.sorted_e;
+  sa.gid_of_emit = b.gid_of_emit;
+  sa.ranges = b.ranges;
+  sa.hdr = hdr;
+  const size_t scat_smem = (size_t)b.ntiles * 4 + (size_t)8 * b.ntiles * 2;
+  cudaFuncSetAttribute(bin_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scat_smem);
+  bin_scatter_kernel<<<bblocks, kThreads, scat_smem, st>>>(sa);
   return cudaGetLastError();
 }
 
@@ -467,10 +541,18 @@ __global__ void dump_kernel(const DumpArgs d) {
   const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (uint64_t i = i0; i < K; i += stride) {
     const uint32_t e = d.sorted_e[i];
+    if ((uint64_t)e >= (uint64_t)d.cap) continue;  // only after an overflow
     const uint32_t g = d.gid_of_emit[e];
     if (d.keys) {
+      // Tile of list position i: the last tile whose range starts at or
+      // before i (empty tiles share the start of the next tile).
+      int lo = 0, hi = d.ntiles;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (d.ranges[mid].x <= i) lo = mid; else hi = mid;
+      }
       const float dep = d.rec[3 * (size_t)g + 1].z;
-      d.keys[i] = ((uint64_t)d.sorted_tile[i] << 32) | __float_as_uint(dep);
+      d.keys[i] = ((uint64_t)(uint32_t)lo << 32) | __float_as_uint(dep);
     }
     if (d.gauss) d.gauss[i] = g;
   }

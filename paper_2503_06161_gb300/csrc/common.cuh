@@ -34,9 +34,12 @@ constexpr int kRec = 12;
 // Device-side error bits, sticky within one call.
 enum : uint32_t { kErrOverflow = 1u, kErrTimeout = 2u, kErrNonFinite = 4u };
 
-// Partial-gradient row per (tile, Gaussian) entry, length 10 + D:
-//  [0] du [1] dv [2] dA [3] dB [4] dCc [5] dopacity [6..8] drgb [9] ddepth [10..] dfeat
+// Partial-gradient row per (tile, Gaussian) entry, D + 12 floats (16-byte
+// rows): [0, D) dfeat, then du dv dA dB dCc dopacity, drgb[3], ddepth, 2 pad.
+// Written only for the entries the reverse pass reached, which set their
+// bit in a bitmask over the emission index.
 constexpr int kPartialScalars = 10;
+__host__ __device__ constexpr int partial_stride(int D) { return D + 12; }
 
 struct Header {           // first 256 bytes of every workspace
   uint32_t err;           // error bits
@@ -55,22 +58,30 @@ constexpr int kSortItems = 16;
 constexpr int kSortChunk = kThreads * kSortItems;
 constexpr int kPItems = 4;
 constexpr int kPChunk = kThreads * kPItems;
+// Depth-ordered Gaussians per block of the tile count / scatter kernels
+// (each of the 8 warps walks 64 of them in order).
+constexpr int kBinItems = 2;
+constexpr int kBinChunk = kThreads * kBinItems;
 
 // Ticket slots in the header.
 enum : int {
   kTicketDepth0 = 0,  // 4 depth passes
-  kTicketScan = 4,
-  kTicketTile0 = 5,   // up to 3 tile passes
+  kTicketScan = 4,    // tiles_touched scan + per-block tile counts
+  kTicketTable = 5,   // scan of the (tile, block) count table
   kNumTickets = 8,
 };
 
+// Largest tile count of the counting scatter (its per-warp counters live in
+// shared memory).
+constexpr int kMaxTiles = 8192;
+
 struct Layout {
-  int P, D, W, H, tw, th, tiles_x, tiles_y, ntiles, tile_passes;
+  int P, D, W, H, tw, th, tiles_x, tiles_y, ntiles, pblocks, bblocks;
   int64_t cap;
   bool with_backward;
-  size_t hdr, rec, rect, touched, dkey[2], dval[2], offs, offs_by_gid, tkey[2], tval[2], gid_of_emit;
-  size_t status, hist, ranges, tfinal, ncontrib, partials, pflags, dstate, ddstate;
-  size_t status_words, scan_blocks_p, sort_blocks_k;
+  size_t hdr, rec, rect, touched, dkey[2], dval[2], offs, offs_by_gid, sorted_e, gid_of_emit, table;
+  size_t status, hist, ranges, tfinal, ncontrib, partials, pflags, dstate, ddstate, psum;
+  size_t status_words, table_blocks;
   size_t total;
 };
 
@@ -85,13 +96,12 @@ inline Layout make_layout(int P, int D, int W, int H, int tw, int th, int64_t ca
   L.tiles_x = (W + tw - 1) / tw;
   L.tiles_y = (H + th - 1) / th;
   L.ntiles = L.tiles_x * L.tiles_y;
-  int bits = 1;
-  while ((1 << bits) < L.ntiles) ++bits;
-  L.tile_passes = (bits + 7) / 8;
   L.cap = cap;
   L.with_backward = with_backward;
   const size_t Pn = (size_t)(P > 0 ? P : 1);
   const size_t Kn = (size_t)(cap > 0 ? cap : 1);
+  L.pblocks = ceil_div((int64_t)Pn, kPChunk);
+  L.bblocks = ceil_div((int64_t)Pn, kBinChunk);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   L.hdr = take(sizeof(Header));
@@ -102,24 +112,25 @@ inline Layout make_layout(int P, int D, int W, int H, int tw, int th, int64_t ca
   for (int i = 0; i < 2; ++i) L.dval[i] = take(Pn * 4);
   L.offs = take((Pn + 1) * 4);
   L.offs_by_gid = take(Pn * 4);
-  for (int i = 0; i < 2; ++i) L.tkey[i] = take(Kn * 4);
-  for (int i = 0; i < 2; ++i) L.tval[i] = take(Kn * 4);
+  L.sorted_e = take(Kn * 4);
   L.gid_of_emit = take(Kn * 4);
-  L.scan_blocks_p = (size_t)ceil_div((int64_t)Pn, kPChunk);
-  L.sort_blocks_k = (size_t)ceil_div((int64_t)Kn, kSortChunk);
-  // Look-back status words: 4 depth passes (u32 per digit per block), up to 3
-  // tile passes, then one u64 per block of the tiles_touched scan.
-  L.status_words = L.scan_blocks_p * 256 * 4 + L.sort_blocks_k * 256 * 3 + 2 * L.scan_blocks_p;
+  const size_t table_n = (size_t)L.ntiles * L.bblocks;
+  L.table = take(table_n * 4);
+  L.table_blocks = (size_t)ceil_div((int64_t)(table_n > 0 ? table_n : 1), kPChunk);
+  // Look-back words: 4 depth passes (u32 per digit per block), then u64 per
+  // block of the tiles_touched scan and of the table scan.
+  L.status_words = (size_t)L.pblocks * 256 * 4 + 2 * (size_t)L.bblocks + 2 * L.table_blocks;
   L.status = take(L.status_words * 4);
   L.hist = take((4 + 3) * 256 * 4);
   L.ranges = take((size_t)L.ntiles * 8);
   L.tfinal = take((size_t)W * H * 4);
   L.ncontrib = take((size_t)W * H * 4);
   if (with_backward) {
-    L.partials = take(Kn * (size_t)(kPartialScalars + D) * 4);
-    L.pflags = take(Kn);
+    L.partials = take(Kn * (size_t)partial_stride(D) * 4);
+    L.pflags = take((Kn + 31) / 32 * 4);
     L.dstate = take(Pn * 16 * 4);
     L.ddstate = take(Pn * 12 * 4);
+    L.psum = take(Pn * 12 * 4);
   }
   L.total = off;
   return L;

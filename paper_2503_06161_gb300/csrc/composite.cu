@@ -68,13 +68,17 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
     if (__syncthreads_count(done) == kThreads) break;
     if (tid < B && bs + tid < rg.y) {
       const uint32_t e = a.sorted_e[bs + tid];
-      const uint32_t g = a.gid_of_emit[e];
-      const float4* r = a.rec + 3 * (size_t)g;
       float4* d = reinterpret_cast<float4*>(s_rec + tid * kRec);
-      d[0] = __ldg(r);
-      d[1] = __ldg(r + 1);
-      d[2] = __ldg(r + 2);
-      load_feat_row<D>(a.feat, a.feat_bf16, g, s_feat + tid * D);
+      if ((int64_t)e < a.cap) {
+        const uint32_t g = a.gid_of_emit[e];
+        const float4* r = a.rec + 3 * (size_t)g;
+        d[0] = __ldg(r);
+        d[1] = __ldg(r + 1);
+        d[2] = __ldg(r + 2);
+        load_feat_row<D>(a.feat, a.feat_bf16, g, s_feat + tid * D);
+      } else {
+        d[2] = make_float4(0.f, 0.f, -1.0f, 0.f);  // radius -1: never included
+      }
     }
     __syncthreads();
     const int nb = (int)min((uint32_t)B, rg.y - bs);
@@ -167,7 +171,8 @@ struct BwdCfg {
 template <int D>
 __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const CompositeArgs a) {
   using K = BwdCfg<D>;
-  constexpr int B = K::B, NC = K::NC, GS = K::GS, WS = K::WS, NP = kPartialScalars + D;
+  constexpr int B = K::B, NC = K::NC, GS = K::GS, WS = K::WS, NP = partial_stride(D);
+  constexpr int NV = kPartialScalars + D;  // values per row
   extern __shared__ __align__(16) float smem[];
   float* s_rec = smem;                       // [B][12]
   float* s_x = s_rec + B * kRec;             // [B][NC]: rgb, depth, z
@@ -229,15 +234,19 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
     __syncthreads();
     if (tid < nb) {
       const uint32_t e = a.sorted_e[bs + tid];
-      const uint32_t g = a.gid_of_emit[e];
-      s_e[tid] = e;
-      const float4* r = a.rec + 3 * (size_t)g;
-      const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2);
       float4* d = reinterpret_cast<float4*>(s_rec + tid * kRec);
-      d[0] = r0; d[1] = r1; d[2] = r2;
-      float* x = s_x + tid * NC;
-      x[0] = r1.w; x[1] = r2.x; x[2] = r2.y; x[3] = r1.z;  // rgb, depth
-      load_feat_row<D>(a.feat, a.feat_bf16, g, x + 4);
+      s_e[tid] = e;
+      if ((int64_t)e < a.cap) {
+        const uint32_t g = a.gid_of_emit[e];
+        const float4* r = a.rec + 3 * (size_t)g;
+        const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2);
+        d[0] = r0; d[1] = r1; d[2] = r2;
+        float* x = s_x + tid * NC;
+        x[0] = r1.w; x[1] = r2.x; x[2] = r2.y; x[3] = r1.z;  // rgb, depth
+        load_feat_row<D>(a.feat, a.feat_bf16, g, x + 4);
+      } else {
+        d[2] = make_float4(0.f, 0.f, -1.0f, 0.f);  // radius -1: never included
+      }
     }
     __syncthreads();
     const uint32_t rel0 = bs - rg.x;
@@ -352,17 +361,20 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
     if (lane == 0) s_jact[warp] = jact;
     __syncthreads();
     // Fixed-order sum of the warp partials: one row per (tile, entry).
-    for (int item = tid; item < nb * NP; item += kThreads) {
-      const int j = item / NP, k = item - j * NP;
+    for (int item = tid; item < nb * NV; item += kThreads) {
+      // k: 0..5 geometric terms, 6..9 rgb/depth, 10.. features; row index
+      // puts the features first.
+      const int j = item / NV, k = item - j * NV;
       float acc = 0.0f;
 #pragma unroll
       for (int w8 = 0; w8 < 8; ++w8) {
         if ((s_jact[w8] >> j) & 1u)
           acc += k < 6 ? s_geo[(w8 * B + j) * 8 + k] : s_slice[w8 * K::SLICE + j * NC + (k - 6)];
       }
-      a.partials[(size_t)s_e[j] * NP + k] = acc;
+      const int col = k < kPartialScalars ? D + k : k - kPartialScalars;
+      if ((int64_t)s_e[j] < a.cap) a.partials[(size_t)s_e[j] * NP + col] = acc;
     }
-    if (tid < nb) a.pflags[s_e[tid]] = 1;
+    if (tid < nb && (int64_t)s_e[tid] < a.cap) atomicOr(a.pflags + (s_e[tid] >> 5), 1u << (s_e[tid] & 31u));
     be = bs;
   }
 }

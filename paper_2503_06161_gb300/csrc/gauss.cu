@@ -571,24 +571,47 @@ __global__ void __launch_bounds__(kThreads, 2) gauss_fwd_kernel(const GaussArgs 
 }
 
 // ---------------------------------------------------------------------------
-// Feature gradient: fixed-order sum of the partial rows' feature part.
-// Thread (g, c4) sums channels 4*c4..4*c4+3 of Gaussian g.
-__global__ void feat_grad_kernel(const GaussBwdArgs b, int P) {
-  const int nq = b.D / 4;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)P * nq) return;
-  const int g = (int)(i / nq), c4 = (int)(i - (int64_t)g * nq);
+// Iterates the written partial rows of emission range [e0, e1) in increasing
+// order (fixed summation order), reading the bitmask a word at a time.
+template <typename F>
+__device__ __forceinline__ void for_each_row(const uint32_t* bits, uint32_t e0, uint32_t e1, F&& f) {
+  if (e0 >= e1) return;
+  for (uint32_t w = e0 >> 5; w <= (e1 - 1) >> 5; ++w) {
+    uint32_t m = bits[w];
+    const uint32_t lo = w << 5;
+    if (lo < e0) m &= ~0u << (e0 - lo);
+    if (e1 - lo < 32) m &= (1u << (e1 - lo)) - 1u;
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      f(lo + (uint32_t)b);
+    }
+  }
+}
+
+// Sum of each Gaussian's partial rows, one warp per Gaussian: lane c adds
+// column c of every written row (fixed increasing order), so each row is a
+// coalesced read.  Writes d_feat[g] and the ten scalar sums to psum[g].
+__global__ void __launch_bounds__(kThreads) partial_reduce_kernel(const GaussBwdArgs b, int P) {
+  const int lane = threadIdx.x & 31;
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (g >= P) return;
+  const int D = b.D, NP = partial_stride(D);
   const uint32_t e0 = b.offs_by_gid[g];
   const uint32_t e1 = (uint32_t)min((uint64_t)e0 + b.touched[g], (uint64_t)b.cap);  // e0 >= e1 past capacity
-  const int NP = kPartialScalars + b.D;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (uint32_t e = e0; e < e1; ++e) {
-    if (!b.pflags[e]) continue;
-    const float* row = b.partials + (size_t)e * NP + kPartialScalars + 4 * c4;
-    const float2 x0 = *reinterpret_cast<const float2*>(row), x1 = *reinterpret_cast<const float2*>(row + 2);
-    acc.x += x0.x; acc.y += x0.y; acc.z += x1.x; acc.w += x1.y;
+  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // columns lane, lane+32, ... (NP <= 140)
+  for_each_row(b.pflags, e0, e1, [&](uint32_t e) {
+    const float* row = b.partials + (size_t)e * NP;
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+      if (lane + 32 * q < NP) acc[q] += row[lane + 32 * q];
+  });
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int col = lane + 32 * q;
+    if (col < D) b.d_feat[g * D + col] = acc[q];
+    else if (col < NP) b.psum[g * 12 + (col - D)] = acc[q];
   }
-  reinterpret_cast<float4*>(b.d_feat + (size_t)g * b.D)[c4] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -601,23 +624,16 @@ __global__ void feat_grad_kernel(const GaussBwdArgs b, int P) {
 __global__ void __launch_bounds__(kThreads) gauss_bwd_proj_kernel(const GaussArgs a, const GaussBwdArgs b) {
   const int g = blockIdx.x * kThreads + threadIdx.x;
   if (g >= a.P) return;
-  const int NP = kPartialScalars + b.D;
-  float acc[kPartialScalars];
+  float acc[kPartialScalars + 2];
+  {
+    const float4* ps = reinterpret_cast<const float4*>(b.psum + (size_t)g * 12);
 #pragma unroll
-  for (int k = 0; k < kPartialScalars; ++k) acc[k] = 0.0f;
-  const uint32_t nt = b.touched[g];
-  const uint32_t e0 = b.offs_by_gid[g];
-  const uint32_t e1 = (uint32_t)min((uint64_t)e0 + nt, (uint64_t)b.cap);  // e0 >= e1 past capacity
-  for (uint32_t e = e0; e < e1; ++e) {
-    if (!b.pflags[e]) continue;
-    const float2* row = reinterpret_cast<const float2*>(b.partials + (size_t)e * NP);
-#pragma unroll
-    for (int k = 0; k < kPartialScalars / 2; ++k) {
-      const float2 v = row[k];
-      acc[2 * k] += v.x;
-      acc[2 * k + 1] += v.y;
+    for (int k = 0; k < 3; ++k) {
+      const float4 v = ps[k];
+      acc[4 * k] = v.x; acc[4 * k + 1] = v.y; acc[4 * k + 2] = v.z; acc[4 * k + 3] = v.w;
     }
   }
+  const uint32_t nt = b.touched[g];
   float delta[kHeads];
   if (a.has_deform) {
     const float4* d = reinterpret_cast<const float4*>(a.dstate + (size_t)g * kDStride);
@@ -830,8 +846,8 @@ static cudaError_t launch_bwd_deform_t(const GaussArgs& a, const GaussBwdArgs& b
 
 cudaError_t launch_gauss_bwd(const GaussArgs& a, const GaussBwdArgs& b, cudaStream_t st, cudaEvent_t mid) {
   if (a.P <= 0) return mid ? cudaEventRecord(mid, st) : cudaSuccess;
-  const int64_t nthreads = (int64_t)a.P * (b.D / 4);
-  feat_grad_kernel<<<(int)((nthreads + 255) / 256), 256, 0, st>>>(b, a.P);
+  const int64_t nthreads = (int64_t)a.P * 32;
+  partial_reduce_kernel<<<(int)((nthreads + kThreads - 1) / kThreads), kThreads, 0, st>>>(b, a.P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mid && (e = cudaEventRecord(mid, st)) != cudaSuccess) return e;

@@ -38,9 +38,10 @@ struct GaussBwdArgs {
   int64_t cap;
   const uint32_t *touched, *offs_by_gid;
   const float* partials;
-  const uint8_t* pflags;
+  const uint32_t* pflags;  // bit e set: partial row e was written
   float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh, *d_feat;
   float* ddstate;  // [P][12] dL/d delta, [11] = active flag
+  float* psum;     // [P][12] sums of the partial rows' scalars
 };
 
 cudaError_t launch_gauss_fwd(const GaussArgs& a, cudaStream_t st);
@@ -48,20 +49,19 @@ cudaError_t launch_gauss_bwd(const GaussArgs& a, const GaussBwdArgs& b, cudaStre
 
 // Integer stage: binning of projected Gaussians into tile lists.
 struct BinArgs {
-  int P, ntiles, tiles_x, tile_passes;
+  int P, ntiles, tiles_x, pblocks, bblocks;
   int64_t cap;
   const ushort4* rect;
   const uint32_t* touched;
-  uint32_t *dkey[2], *dval[2];  // depth-sort ping-pong
+  uint32_t *dkey[2], *dval[2];  // depth-sort ping-pong (final: index 0)
   uint32_t *offs, *offs_by_gid;
-  uint32_t *tkey[2], *tval[2];  // tile-sort ping-pong
-  uint32_t* gid_of_emit;
+  uint32_t* sorted_e;           // [cap] emission index per list position
+  uint32_t* gid_of_emit;        // [cap] Gaussian of each emission index
+  uint32_t* table;              // [ntiles][bblocks] counts, then segment starts
   uint32_t* status;             // decoupled look-back words
-  uint32_t* hist;               // global digit histograms [7][256]
+  uint32_t* hist;               // depth digit histograms [4][256]
   uint2* ranges;
   void* hdr;                    // fe::Header*
-  // results (which ping-pong buffer holds the final data)
-  int depth_final, tile_final;
 };
 
 // Rect / touched / depth key from given (u, v, r, depth) (fe_tile_bin).
@@ -83,8 +83,9 @@ struct CompositeArgs {
   // backward
   const float *g_rgb, *g_depth, *g_alpha, *g_feat;
   float* partials;
-  uint8_t* pflags;
+  uint32_t* pflags;
   int ntiles;
+  int64_t cap;       // list capacity: emission indices at or past it are skipped
   uint64_t* counts;  // non-NULL: counting variant of the forward (no outputs)
 };
 
@@ -95,7 +96,7 @@ struct DumpArgs {
   int64_t cap;
   int P, ntiles, HW;
   const void* hdr;
-  const uint32_t *sorted_tile, *sorted_e, *gid_of_emit, *dkey_by_gid;
+  const uint32_t *sorted_e, *gid_of_emit;
   const uint2* ranges;
   const uint32_t* ncontrib;
   const float* tfinal;
