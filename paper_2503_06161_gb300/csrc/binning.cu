@@ -242,7 +242,9 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const CountArgs a) 
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_ticket;
   __shared__ uint64_t s_prefix;
-  const int tid = threadIdx.x;
+  __shared__ uint32_t s_c[kBinChunk];
+  __shared__ ushort4 s_rect[kBinChunk];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < a.ntiles; i += kThreads) s_cnt[i] = 0;
   if (tid == 0) s_ticket = atomicAdd(a.ticket, 1u);
   __syncthreads();
@@ -253,9 +255,12 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const CountArgs a) 
   uint32_t tsum = 0;
 #pragma unroll
   for (int i = 0; i < kBinItems; ++i) {
-    const int64_t r = start + tid * kBinItems + i;
+    const int li = tid * kBinItems + i;
+    const int64_t r = start + li;
     gid[i] = r < a.P ? a.order[r] : 0u;
     cnt[i] = r < a.P ? a.touched[gid[i]] : 0u;
+    s_c[li] = cnt[i];
+    s_rect[li] = cnt[i] ? a.rect[gid[i]] : make_ushort4(1, 1, 0, 0);
     tsum += cnt[i];
   }
   uint32_t btot;
@@ -270,11 +275,6 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const CountArgs a) 
       const uint32_t o32 = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
       a.offs[r] = o32;
       a.offs_by_gid[gid[i]] = o32;
-      if (cnt[i]) {
-        const ushort4 rc = a.rect[gid[i]];
-        for (int ty = rc.y; ty <= rc.w; ++ty)
-          for (int tx = rc.x; tx <= rc.z; ++tx) atomicAdd(&s_cnt[ty * a.tiles_x + tx], 1u);
-      }
     }
     run += cnt[i];
   }
@@ -282,6 +282,20 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const CountArgs a) 
     a.offs[a.P] = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
     a.hdr->num_dups = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
     if (run > (uint64_t)a.cap) set_err(&a.hdr->err, kErrOverflow);
+  }
+  // Tile counts: each warp walks its Gaussians, lanes over one rect's tiles.
+  const int nloc = (int)min((int64_t)kBinChunk, (int64_t)a.P - start);
+  const int i0 = warp * (kBinChunk / 8), i1 = min(nloc, i0 + kBinChunk / 8);
+  for (int i = i0; i < i1; ++i) {
+    const uint32_t c = s_c[i];
+    if (!c) continue;
+    const ushort4 rc = s_rect[i];
+    const uint32_t wdt = rc.z - rc.x + 1u;
+    const float iw = 1.0f / (float)wdt;
+    for (uint32_t k = lane; k < c; k += 32) {
+      const uint32_t dy = (uint32_t)(((float)k + 0.5f) * iw), dx = k - dy * wdt;  // exact for these sizes
+      atomicAdd(&s_cnt[(rc.y + dy) * (uint32_t)a.tiles_x + rc.x + dx], 1u);
+    }
   }
   __syncthreads();
   for (int t = tid; t < a.ntiles; t += kThreads) a.table[(size_t)t * a.nblocks + b] = s_cnt[t];

@@ -589,23 +589,105 @@ __device__ __forceinline__ void for_each_row(const uint32_t* bits, uint32_t e0, 
   }
 }
 
-// Sum of each Gaussian's partial rows, one warp per Gaussian: lane c adds
-// column c of every written row (fixed increasing order), so each row is a
-// coalesced read.  Writes d_feat[g] and the ten scalar sums to psum[g].
+// Sum of each Gaussian's partial rows, one warp per Gaussian, in a fixed
+// order, writing d_feat[g] and the ten scalar sums to psum[g].
+//  * short ranges (<= 64 emission entries): lane c adds column c of every
+//    written row in increasing order, loading four rows before adding;
+//  * long ranges (a large Gaussian near the camera can sit at the front of
+//    a thousand tile lists): lane L walks bitmask words L, L+32, ... and adds
+//    whole rows 16 columns at a time, then a fixed shuffle tree adds the
+//    lanes.  The mode depends only on the range length, so the result is
+//    bitwise reproducible.
+template <int NP>
+__device__ __forceinline__ void reduce_rows_short(const GaussBwdArgs& b, uint32_t e0, uint32_t e1, int lane,
+                                                  float acc[5]) {
+  const uint32_t w0 = e0 >> 5, w1 = (e1 - 1) >> 5;
+  for (uint32_t w = w0; w <= w1; ++w) {
+    uint32_t m = b.pflags[w];
+    const uint32_t lo = w << 5;
+    if (lo < e0) m &= ~0u << (e0 - lo);
+    if (e1 - lo < 32) m &= (1u << (e1 - lo)) - 1u;
+    while (m) {
+      uint32_t e[4];
+      bool v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v[u] = m != 0u;
+        e[u] = lo + (v[u] ? (uint32_t)(__ffs(m) - 1) : 0u);
+        m = v[u] ? (m & (m - 1u)) : 0u;
+      }
+      float x[4][5];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float* row = b.partials + (size_t)e[u] * NP;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) x[u][q] = (v[u] && lane + 32 * q < NP) ? row[lane + 32 * q] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+          if (v[u]) acc[q] += x[u][q];
+    }
+  }
+}
+
+template <int NP>
+__device__ __forceinline__ void reduce_rows_long(const GaussBwdArgs& b, uint32_t e0, uint32_t e1, int lane,
+                                                 float acc[5]) {
+  const uint32_t w0 = e0 >> 5, w1 = (e1 - 1) >> 5;
+#pragma unroll 1
+  for (int c0 = 0; c0 < NP; c0 += 16) {
+    float part[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) part[i] = 0.0f;
+    for (uint32_t w = w0 + lane; w <= w1; w += 32) {
+      uint32_t m = b.pflags[w];
+      const uint32_t lo = w << 5;
+      if (lo < e0) m &= ~0u << (e0 - lo);
+      if (e1 - lo < 32) m &= (1u << (e1 - lo)) - 1u;
+      while (m) {
+        const uint32_t e = lo + (uint32_t)(__ffs(m) - 1);
+        m &= m - 1u;
+        const float4* row = reinterpret_cast<const float4*>(b.partials + (size_t)e * NP + c0);
+#pragma unroll
+        for (int i4 = 0; i4 < 4; ++i4) {
+          if (c0 + 4 * i4 < NP) {
+            const float4 v = row[i4];
+            part[4 * i4] += v.x; part[4 * i4 + 1] += v.y; part[4 * i4 + 2] += v.z; part[4 * i4 + 3] += v.w;
+          }
+        }
+      }
+    }
+    // Fixed-order tree over the 32 lanes; lane 0 ends with the sums.
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part[i] += __shfl_down_sync(0xFFFFFFFFu, part[i], o);
+    }
+    // Columns c0..c0+15 go to the lanes that own them in the column layout.
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float v = __shfl_sync(0xFFFFFFFFu, part[i], 0);
+      const int col = c0 + i;
+      if (col < NP && (col & 31) == lane) acc[col >> 5] = v;
+    }
+  }
+}
+
+template <int D>
 __global__ void __launch_bounds__(kThreads) partial_reduce_kernel(const GaussBwdArgs b, int P) {
+  constexpr int NP = partial_stride(D);
   const int lane = threadIdx.x & 31;
   const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (g >= P) return;
-  const int D = b.D, NP = partial_stride(D);
   const uint32_t e0 = b.offs_by_gid[g];
   const uint32_t e1 = (uint32_t)min((uint64_t)e0 + b.touched[g], (uint64_t)b.cap);  // e0 >= e1 past capacity
   float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // columns lane, lane+32, ... (NP <= 140)
-  for_each_row(b.pflags, e0, e1, [&](uint32_t e) {
-    const float* row = b.partials + (size_t)e * NP;
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-      if (lane + 32 * q < NP) acc[q] += row[lane + 32 * q];
-  });
+  if (e0 < e1) {
+    if (e1 - e0 <= 64) reduce_rows_short<NP>(b, e0, e1, lane, acc);
+    else reduce_rows_long<NP>(b, e0, e1, lane, acc);
+  }
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     const int col = lane + 32 * q;
@@ -847,7 +929,14 @@ static cudaError_t launch_bwd_deform_t(const GaussArgs& a, const GaussBwdArgs& b
 cudaError_t launch_gauss_bwd(const GaussArgs& a, const GaussBwdArgs& b, cudaStream_t st, cudaEvent_t mid) {
   if (a.P <= 0) return mid ? cudaEventRecord(mid, st) : cudaSuccess;
   const int64_t nthreads = (int64_t)a.P * 32;
-  partial_reduce_kernel<<<(int)((nthreads + kThreads - 1) / kThreads), kThreads, 0, st>>>(b, a.P);
+  const int nblk = (int)((nthreads + kThreads - 1) / kThreads);
+  switch (b.D) {
+    case 16: partial_reduce_kernel<16><<<nblk, kThreads, 0, st>>>(b, a.P); break;
+    case 32: partial_reduce_kernel<32><<<nblk, kThreads, 0, st>>>(b, a.P); break;
+    case 64: partial_reduce_kernel<64><<<nblk, kThreads, 0, st>>>(b, a.P); break;
+    case 128: partial_reduce_kernel<128><<<nblk, kThreads, 0, st>>>(b, a.P); break;
+    default: return cudaErrorInvalidValue;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mid && (e = cudaEventRecord(mid, st)) != cudaSuccess) return e;
