@@ -155,6 +155,72 @@ __device__ __forceinline__ void hexplane_sample(const GaussArgs& a, const float 
   }
 }
 
+// Warp-cooperative HexPlane sample.  For each active Gaussian j of the warp
+// in turn, lane c handles channel c (and c+32 when C = 64): its texel loads
+// for a fixed j are one coalesced line per texel instead of 32 scattered
+// lines per load instruction.  The products are transposed through the
+// warp's shared slice sfw[32][C+1] into each Gaussian's own thread.
+struct PlaneParams {
+  uint32_t base[6];   // float offset of texel (i0, j0) of each plane
+  float w[6][4];      // bilinear weights w00 w10 w01 w11
+};
+
+template <int C>
+__device__ __forceinline__ PlaneParams plane_params(const GaussArgs& a, const float mu[3]) {
+  PlaneParams pp;
+  float coord[4];
+  grid_coords(a, mu, coord);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const GridPos gp = grid_pos(a, coord[pair_a(k)], coord[pair_b(k)]);
+    pp.base[k] = (uint32_t)(((k * a.R + gp.i0) * a.R + gp.j0) * C);
+    pp.w[k][0] = (1.f - gp.f0) * (1.f - gp.f1);
+    pp.w[k][1] = gp.f0 * (1.f - gp.f1);
+    pp.w[k][2] = (1.f - gp.f0) * gp.f1;
+    pp.w[k][3] = gp.f0 * gp.f1;
+  }
+  return pp;
+}
+
+template <int C>
+__device__ __forceinline__ void hexplane_sample_warp(const GaussArgs& a, const float mu[3], bool active, float* sfw,
+                                                     float f[C]) {
+  constexpr int CPL = C / 32;
+  const int lane = threadIdx.x & 31;
+  PlaneParams pp{};
+  if (active) pp = plane_params<C>(a, mu);
+  const unsigned act = __ballot_sync(0xFFFFFFFFu, active);
+  const size_t RC = (size_t)a.R * C;
+  for (int j = 0; j < 32; ++j) {
+    if (!((act >> j) & 1u)) continue;
+    float prod[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) prod[q] = 1.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const uint32_t bj = __shfl_sync(0xFFFFFFFFu, pp.base[k], j);
+      const float w00 = __shfl_sync(0xFFFFFFFFu, pp.w[k][0], j), w10 = __shfl_sync(0xFFFFFFFFu, pp.w[k][1], j);
+      const float w01 = __shfl_sync(0xFFFFFFFFu, pp.w[k][2], j), w11 = __shfl_sync(0xFFFFFFFFu, pp.w[k][3], j);
+      const float* p00 = a.planes + bj;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const int c = lane + 32 * q;
+        const float x00 = __ldg(p00 + c), x01 = __ldg(p00 + C + c), x10 = __ldg(p00 + RC + c),
+                    x11 = __ldg(p00 + RC + C + c);
+        prod[q] *= w00 * x00 + w10 * x10 + w01 * x01 + w11 * x11;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) sfw[j * (C + 1) + lane + 32 * q] = prod[q];
+  }
+  __syncwarp();
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) f[c] = sfw[lane * (C + 1) + c];
+  }
+  __syncwarp();
+}
+
 // Shared-memory weights, laid out so every inner loop reads 16-byte
 // broadcast rows: w1[64][C], b1[64], w2t[64][64] with w2t[i][o] = W2[o][i],
 // b2[64], wh[11][64], wht[64][12] with wht[o][k] = Wh[k][o], bh[12].
@@ -363,6 +429,114 @@ __device__ __forceinline__ void hexplane_backward(const GaussArgs& a, const floa
   for (int i = 0; i < 3; ++i) dmu[i] = dcoord[i] * a.bscale[i];
 }
 
+// Warp-cooperative reverse of the HexPlane sample: for each active Gaussian
+// j of the warp, lane c takes channel c of its six planes (coalesced texel
+// loads), forms d f_c / d(grid position) by prefix/suffix products, weights
+// it by df_j[c] (thread j's slice of dfs), and the warp reduces the twelve
+// (plane, axis) sums.  Returns dmu of this thread's own Gaussian.
+template <int C>
+__device__ __forceinline__ void hexplane_backward_warp(const GaussArgs& a, const float mu[3], bool active,
+                                                       const float* dfs, float* sred, float dmu[3]) {
+  constexpr int CPL = C / 32;
+  const int lane = threadIdx.x & 31;
+  PlaneParams pp{};
+  float fr[6][2];
+  bool clamp[6][2];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) { fr[k][0] = fr[k][1] = 0.f; clamp[k][0] = clamp[k][1] = true; }
+  if (active) {
+    float coord[4];
+    grid_coords(a, mu, coord);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const GridPos gp = grid_pos(a, coord[pair_a(k)], coord[pair_b(k)]);
+      pp.base[k] = (uint32_t)(((k * a.R + gp.i0) * a.R + gp.j0) * C);
+      fr[k][0] = gp.f0;
+      fr[k][1] = gp.f1;
+      clamp[k][0] = gp.c0;
+      clamp[k][1] = gp.c1;
+      pp.w[k][0] = (1.f - gp.f0) * (1.f - gp.f1);
+      pp.w[k][1] = gp.f0 * (1.f - gp.f1);
+      pp.w[k][2] = (1.f - gp.f0) * gp.f1;
+      pp.w[k][3] = gp.f0 * gp.f1;
+    }
+  }
+  const unsigned act = __ballot_sync(0xFFFFFFFFu, active);
+  const size_t RC = (size_t)a.R * C;
+  for (int j = 0; j < 32; ++j) {
+    if (!((act >> j) & 1u)) continue;
+    float v[16];  // dg[k][0], dg[k][1] for k < 6 (lane-partial), 4 pad
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      const int c = lane + 32 * q;
+      float sv[6], d0[6], d1[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const uint32_t bj = __shfl_sync(0xFFFFFFFFu, pp.base[k], j);
+        const float f0 = __shfl_sync(0xFFFFFFFFu, fr[k][0], j), f1 = __shfl_sync(0xFFFFFFFFu, fr[k][1], j);
+        const float* p00 = a.planes + bj;
+        const float x00 = __ldg(p00 + c), x01 = __ldg(p00 + C + c), x10 = __ldg(p00 + RC + c),
+                    x11 = __ldg(p00 + RC + C + c);
+        sv[k] = (1.f - f0) * (1.f - f1) * x00 + f0 * (1.f - f1) * x10 + (1.f - f0) * f1 * x01 + f0 * f1 * x11;
+        d0[k] = (1.f - f1) * (x10 - x00) + f1 * (x11 - x01);
+        d1[k] = (1.f - f0) * (x01 - x00) + f0 * (x11 - x10);
+      }
+      const float dfc = dfs[j * C + c];
+      float pre[6], suf = 1.0f;
+      pre[0] = 1.0f;
+#pragma unroll
+      for (int k = 1; k < 6; ++k) pre[k] = pre[k - 1] * sv[k - 1];
+#pragma unroll
+      for (int k = 5; k >= 0; --k) {
+        const float ds = dfc * pre[k] * suf;
+        v[2 * k] = fmaf(ds, d0[k], v[2 * k]);
+        v[2 * k + 1] = fmaf(ds, d1[k], v[2 * k + 1]);
+        suf *= sv[k];
+      }
+    }
+    // Reduce-scatter of v[0..15] over the warp: lane 2m ends with index m.
+    const int b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1, b2 = (lane >> 1) & 1;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float send = b16 ? v[i] : v[i + 8], keep = b16 ? v[i + 8] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float send = b8 ? v[i] : v[i + 4], keep = b8 ? v[i + 4] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float send = b4 ? v[i] : v[i + 2], keep = b4 ? v[i + 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
+    }
+    {
+      const float send = b2 ? v[0] : v[1], keep = b2 ? v[1] : v[0];
+      v[0] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 2);
+    }
+    v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 1);
+    const int m = b2 + 2 * b4 + 4 * b8 + 8 * b16;
+    if ((lane & 1) == 0 && m < 12) sred[j * 12 + m] = v[0];
+  }
+  __syncwarp();
+  dmu[0] = dmu[1] = dmu[2] = 0.0f;
+  if (active) {
+    float dcoord[4] = {0.f, 0.f, 0.f, 0.f};
+    const float half = 0.5f * (float)(a.R - 1);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      if (!clamp[k][0]) dcoord[pair_a(k)] += sred[lane * 12 + 2 * k] * half;
+      if (!clamp[k][1]) dcoord[pair_b(k)] += sred[lane * 12 + 2 * k + 1] * half;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dmu[i] = dcoord[i] * a.bscale[i];
+  }
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // Projection state of one deformed Gaussian.
 // ---------------------------------------------------------------------------
@@ -504,14 +678,16 @@ __device__ __forceinline__ void project(const GaussArgs& a, int g, const float d
 // dstate is given, the reverse pass's state is stored there: the offsets
 // (11 floats) and the two MLP unit masks (words 12..15).
 template <int C>
-__device__ __forceinline__ void deform_delta(const GaussArgs& a, const float* sw, int g, float delta[kHeads],
-                                             float* dstate) {
+__device__ __forceinline__ void deform_delta(const GaussArgs& a, const float* sw, float* sfw, int g, bool active,
+                                             float delta[kHeads], float* dstate) {
 #pragma unroll
   for (int k = 0; k < kHeads; ++k) delta[k] = 0.0f;
-  if (!a.has_deform) return;
-  const float mu[3] = {a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2]};
+  if (!a.has_deform) return;  // uniform over the launch
+  float mu[3] = {0.f, 0.f, 0.f};
+  if (active) { mu[0] = a.means[3 * g]; mu[1] = a.means[3 * g + 1]; mu[2] = a.means[3 * g + 2]; }
   float f[C];
-  hexplane_sample<C>(a, mu, f);
+  hexplane_sample_warp<C>(a, mu, active, sfw, f);
+  if (!active) return;
   uint64_t m1, m2;
   mlp_forward<C>(sw, f, delta, m1, m2);
   if (a.noise) {
@@ -532,13 +708,14 @@ __device__ __forceinline__ void deform_delta(const GaussArgs& a, const float* sw
 template <int C>
 __global__ void __launch_bounds__(kThreads, 2) gauss_fwd_kernel(const GaussArgs a) {
   extern __shared__ __align__(16) float sw[];
+  float* sfw = sw + mlp_floats<C>() + (threadIdx.x >> 5) * 32 * (C + 1);  // this warp's transpose slice
   if (a.has_deform) load_mlp<C>(a, sw);
   __syncthreads();
   const int g = blockIdx.x * kThreads + threadIdx.x;
   bool vis = false;
+  float delta[kHeads];
+  deform_delta<C>(a, sw, sfw, g, g < a.P, delta, (a.dstate && g < a.P) ? a.dstate + (size_t)g * kDStride : nullptr);
   if (g < a.P) {
-    float delta[kHeads];
-    deform_delta<C>(a, sw, g, delta, a.dstate ? a.dstate + (size_t)g * kDStride : nullptr);
     float sh[48];
     load_sh(a.sh, a.sh_bf16, g, sh);
     Proj s;
@@ -870,31 +1047,43 @@ __global__ void __launch_bounds__(kThreads) gauss_bwd_proj_kernel(const GaussArg
 template <int C>
 __global__ void __launch_bounds__(kThreads, 2) gauss_bwd_deform_kernel(const GaussArgs a, const GaussBwdArgs b) {
   extern __shared__ __align__(16) float sw[];
-  float* s_df = sw + mlp_floats<C>();  // [kThreads][C] thread-private slices
+  float* s_df = sw + mlp_floats<C>();                               // [kThreads][C]
+  float* s_red = s_df + (size_t)kThreads * C + (threadIdx.x >> 5) * 32 * 12;  // this warp's [32][12]
   load_mlp<C>(a, sw);
   __syncthreads();
   const int g = blockIdx.x * kThreads + threadIdx.x;
-  if (g >= a.P) return;
-  const float4* dd4 = reinterpret_cast<const float4*>(b.ddstate + (size_t)g * 12);
-  const float4 q0 = dd4[0], q1 = dd4[1], q2 = dd4[2];
-  if (q2.w == 0.0f) return;
-  const float dd[kHeads] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z};
-  const uint4 mk = reinterpret_cast<const uint4*>(a.dstate + (size_t)g * kDStride)[3];
-  const uint64_t m1 = (uint64_t)mk.x | ((uint64_t)mk.y << 32), m2 = (uint64_t)mk.z | ((uint64_t)mk.w << 32);
+  bool active = false;
+  float dd[kHeads];
+  uint64_t m1 = 0, m2 = 0;
+  if (g < a.P) {
+    const float4* dd4 = reinterpret_cast<const float4*>(b.ddstate + (size_t)g * 12);
+    const float4 q0 = dd4[0], q1 = dd4[1], q2 = dd4[2];
+    active = q2.w != 0.0f;
+    dd[0] = q0.x; dd[1] = q0.y; dd[2] = q0.z; dd[3] = q0.w; dd[4] = q1.x; dd[5] = q1.y;
+    dd[6] = q1.z; dd[7] = q1.w; dd[8] = q2.x; dd[9] = q2.y; dd[10] = q2.z;
+    const uint4 mk = reinterpret_cast<const uint4*>(a.dstate + (size_t)g * kDStride)[3];
+    m1 = (uint64_t)mk.x | ((uint64_t)mk.y << 32);
+    m2 = (uint64_t)mk.z | ((uint64_t)mk.w << 32);
+  }
+  if (!__any_sync(0xFFFFFFFFu, active)) return;  // whole warp idle
   float* my_df = s_df + (size_t)threadIdx.x * C;
-  {
+  if (active) {
     float df[C];
     mlp_backward<C>(sw, m1, m2, dd, df);
 #pragma unroll
     for (int c4 = 0; c4 < C / 4; ++c4)
       reinterpret_cast<float4*>(my_df)[c4] = make_float4(df[4 * c4], df[4 * c4 + 1], df[4 * c4 + 2], df[4 * c4 + 3]);
   }
-  const float mu0[3] = {a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2]};
+  __syncwarp();
+  float mu0[3] = {0.f, 0.f, 0.f};
+  if (active) { mu0[0] = a.means[3 * g]; mu0[1] = a.means[3 * g + 1]; mu0[2] = a.means[3 * g + 2]; }
   float dg[3];
-  hexplane_backward<C>(a, mu0, my_df, dg);
-  b.d_means[3 * g] += dg[0];
-  b.d_means[3 * g + 1] += dg[1];
-  b.d_means[3 * g + 2] += dg[2];
+  hexplane_backward_warp<C>(a, mu0, active, s_df + (size_t)(threadIdx.x & ~31) * C, s_red, dg);
+  if (active) {
+    b.d_means[3 * g] += dg[0];
+    b.d_means[3 * g + 1] += dg[1];
+    b.d_means[3 * g + 2] += dg[2];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -902,9 +1091,10 @@ __global__ void __launch_bounds__(kThreads, 2) gauss_bwd_deform_kernel(const Gau
 // ---------------------------------------------------------------------------
 template <int C>
 static cudaError_t launch_fwd_t(const GaussArgs& a, cudaStream_t st) {
-  const size_t smem = a.has_deform ? mlp_floats<C>() * sizeof(float) : 0;
+  const size_t full = (mlp_floats<C>() + (size_t)8 * 32 * (C + 1)) * sizeof(float);
+  const size_t smem = a.has_deform ? full : 0;
   auto k = gauss_fwd_kernel<C>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(mlp_floats<C>() * sizeof(float)));
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
   k<<<ceil_div(a.P, kThreads), kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -919,7 +1109,7 @@ cudaError_t launch_gauss_fwd(const GaussArgs& a, cudaStream_t st) {
 
 template <int C>
 static cudaError_t launch_bwd_deform_t(const GaussArgs& a, const GaussBwdArgs& b, cudaStream_t st) {
-  const size_t smem = (mlp_floats<C>() + (size_t)kThreads * C) * sizeof(float);
+  const size_t smem = (mlp_floats<C>() + (size_t)kThreads * C + (size_t)8 * 32 * 12) * sizeof(float);
   auto k = gauss_bwd_deform_kernel<C>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<ceil_div(a.P, kThreads), kThreads, smem, st>>>(a, b);
