@@ -200,6 +200,23 @@ fe_status fe_debug_dump(const void *workspace, size_t workspace_bytes, int P, in
 fe_status fe_l1_loss_grad(const float *pred, const float *target, int64_t n, int64_t rows, float *grad,
                           float *loss, float *scratch, void *stream);
 
+/* Allocation-free form of fe_l1_loss_grad, for callers that cannot
+ * allocate device memory even for 4 KiB of scratch -- for example a plug-in
+ * whose host application owns every device allocation, or a latency-bound
+ * loop in which a cudaMalloc (which synchronises the device) is not
+ * acceptable.  The paper has no counterpart: this is a deployment variant.
+ * Same inputs, outputs and layout as fe_l1_loss_grad except that the
+ * per-block partial sums live in a 64 KiB array inside the library (one
+ * per GPU that loads it, kept until the process exits); n may be at most
+ * 33,554,432 elements (16384 blocks of 2048), else FE_ERR_WORKSPACE is
+ * returned and nothing is launched.  The first call on a device looks up
+ * that array's device address with the device current; make that first
+ * call before any stream capture.  Every call shares the array: calls whose
+ * work overlaps on the GPU (different streams, or other threads) race and
+ * must be ordered by the caller.  No device memory is allocated or freed. */
+fe_status fe_l1_loss_grad_noalloc(const float *pred, const float *target, int64_t n, int64_t rows, float *grad,
+                                  float *loss, void *stream);
+
 /* Measured single-precision FMA throughput: runs an FMA-chain kernel over
  * the whole GPU for `iters` iterations per thread and writes FLOP/s
  * (2 per FMA) to *flops (host).  Synchronous; used for the FP32 roofline. */

@@ -81,6 +81,7 @@ _SIGNATURES = {
                      + [c_void_p],
     "fe_probe_fp32_peak": [c_int, _P(ctypes.c_double), c_void_p],
     "fe_l1_loss_grad": [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p, c_void_p, c_void_p],
+    "fe_l1_loss_grad_noalloc": [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p, c_void_p],
     "fe_count_pairs": [_P(fe_gaussians), _P(fe_camera), _P(fe_opts), c_void_p, ctypes.c_size_t, c_void_p,
                        c_void_p],
 }
@@ -240,6 +241,13 @@ def fe_l1_loss_grad(pred, target, rows: int, grad, loss, scratch, stream=None):
     rc = load().fe_l1_loss_grad(_ptr(pred), _ptr(target), int(pred.numel()), int(rows), _ptr(grad), _ptr(loss),
                                 _ptr(scratch), _stream(stream))
     _check("fe_l1_loss_grad", rc)
+
+
+def fe_l1_loss_grad_noalloc(pred, target, rows: int, grad, loss, stream=None):
+    """fe_l1_loss_grad without caller scratch (see the header for its limits)."""
+    rc = load().fe_l1_loss_grad_noalloc(_ptr(pred), _ptr(target), int(pred.numel()), int(rows), _ptr(grad),
+                                        _ptr(loss), _stream(stream))
+    _check("fe_l1_loss_grad_noalloc", rc)
 
 
 def fe_count_pairs(g: fe_gaussians, cam: fe_camera, opts: fe_opts, workspace, counts, stream=None):

@@ -112,5 +112,8 @@ cudaError_t launch_dump(const DumpArgs& d, cudaStream_t st);
 cudaError_t probe_fp32(int iters, double* flops, cudaStream_t st);
 cudaError_t launch_l1(const float* pred, const float* target, int64_t n, int64_t rows, float* grad, float* loss,
                       float* scratch, cudaStream_t st);
+void l1_grad_launch(const float* pred, const float* target, int64_t n, float inv_rows, float* grad, float* partial,
+                    int blocks, cudaStream_t st);
+void l1_finish_launch(const float* partial, int nparts, float inv_rows, float* loss, cudaStream_t st);
 
 }  // namespace fe

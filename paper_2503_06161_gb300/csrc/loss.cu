@@ -66,6 +66,15 @@ __global__ void __launch_bounds__(256) l1_finish_kernel(const float* __restrict_
 
 }  // namespace
 
+void l1_grad_launch(const float* pred, const float* target, int64_t n, float inv_rows, float* grad, float* partial,
+                    int blocks, cudaStream_t st) {
+  l1_grad_kernel<<<blocks, 256, 0, st>>>(pred, target, n, inv_rows, grad, partial);
+}
+
+void l1_finish_launch(const float* partial, int nparts, float inv_rows, float* loss, cudaStream_t st) {
+  l1_finish_kernel<<<1, 256, 0, st>>>(partial, nparts, inv_rows, loss);
+}
+
 cudaError_t launch_l1(const float* pred, const float* target, int64_t n, int64_t rows, float* grad, float* loss,
                       float* scratch, cudaStream_t st) {
   const float inv = rows > 0 ? 1.0f / (float)rows : 0.0f;
@@ -78,3 +87,55 @@ cudaError_t launch_l1(const float* pred, const float* target, int64_t n, int64_t
 }
 
 }  // namespace fe
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the L1 loss: the per-block partial sums live in
+// a file-scope device array instead of caller scratch.  One block per 2048
+// elements, at most 16384 blocks (64 KiB, held by every GPU that loads the
+// library until the process exits).
+namespace {
+
+constexpr int kNoAllocBlocks = 16384;
+constexpr int64_t kNoAllocPerBlock = 2048;
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) float g_l1_noalloc_scratch[kNoAllocBlocks];
+
+// Device address of g_l1_noalloc_scratch per device, looked up once per
+// device with that device current (the host-side name of the array is only
+// a stand-in, not a device address).
+float* g_scratch_addr[kMaxDevices] = {};
+
+cudaError_t noalloc_scratch(float** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_scratch_addr[dev]) {
+    float* p = nullptr;
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_l1_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" fe_status fe_l1_loss_grad_noalloc(const float* pred, const float* target, int64_t n, int64_t rows,
+                                             float* grad, float* loss, void* stream) {
+  if (n < 0 || rows <= 0 || (n > 0 && (!pred || !target || !grad)) || !loss) return FE_ERR_INVALID_ARG;
+  if (n > (int64_t)kNoAllocBlocks * kNoAllocPerBlock) return FE_ERR_WORKSPACE;
+  float* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess || !scratch) return FE_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const float inv = 1.0f / (float)rows;
+  int blocks = (int)((n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
+  if (blocks < 1) blocks = 1;
+  // Every block writes its own partial before the finishing kernel reads
+  // it, so nothing in the shared array needs clearing between calls.
+  fe::l1_grad_launch(pred, target, n, inv, grad, scratch, blocks, st);
+  fe::l1_finish_launch(scratch, blocks, inv, loss, st);
+  return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+}
