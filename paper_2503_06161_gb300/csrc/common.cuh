@@ -178,15 +178,26 @@ struct PairEval {
   bool clamped;
 };
 
+// 2^x by the hardware approximation (ex2.approx.ftz: about 2 ulp; results
+// below the normal range flush to 0, which the alpha >= 1/255 test rejects
+// either way).
+__device__ __forceinline__ float fast_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ bool eval_pair(const float* rec, float pxc, float pyc, PairEval& e) {
   const float r = rec[10];
   e.dx = __fsub_rn(pxc, rec[0]);
   e.dy = __fsub_rn(pyc, rec[1]);
   if (fabsf(e.dx) > r || fabsf(e.dy) > r) return false;
-  const float p2 = __fadd_rn(__fadd_rn(__fmul_rn(rec[2], __fmul_rn(e.dx, e.dx)), __fmul_rn(rec[4], __fmul_rn(e.dy, e.dy))),
-                             __fmul_rn(rec[3], __fmul_rn(e.dx, e.dy)));
+  // power2 = A dx^2 + B dx dy + Cc dy^2 = (A dx + B dy) dx + Cc dy dy, with
+  // explicit FMAs so the forward and reverse kernels round identically.
+  const float t = __fmaf_rn(rec[2], e.dx, __fmul_rn(rec[3], e.dy));
+  const float p2 = __fmaf_rn(t, e.dx, __fmul_rn(__fmul_rn(rec[4], e.dy), e.dy));
   if (p2 > 0.0f) return false;
-  e.G = exp2f(p2);
+  e.G = fast_exp2(p2);
   const float oG = __fmul_rn(rec[5], e.G);
   e.clamped = oG > kAlphaMax;
   e.alpha = e.clamped ? kAlphaMax : oG;

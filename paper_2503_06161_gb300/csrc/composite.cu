@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
           if (eval_pair(rec, pxc, pyc, pe)) {
             contrib = true;
             const float one_m = 1.0f - pe.alpha;
-            T = T / one_m;  // transmittance before this Gaussian
+            const float inv = __fdividef(1.0f, one_m);  // one_m >= 0.01
+            T = T * inv;  // transmittance before this Gaussian
             w = pe.alpha * T;
             const float4* x4 = reinterpret_cast<const float4*>(s_x + j * NC);
             float s = 0.0f;
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
                 s = fmaf(grow[4 * c4 + 3], xv.w, s);
               }
             }
-            const float dalpha = T * s - (Q - ga * Tf) / one_m;
+            const float dalpha = T * s - (Q - ga * Tf) * inv;
             Q = fmaf(w, s, Q);
             if (!pe.clamped) {
               const float dp2 = dalpha * pe.alpha * kLn2;
