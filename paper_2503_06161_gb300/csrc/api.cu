@@ -126,7 +126,7 @@ BinArgs bin_args(const Layout& L, void* ws) {
   b.offs = at<uint32_t>(ws, L.offs);
   b.offs_by_gid = at<uint32_t>(ws, L.offs_by_gid);
   b.sorted_e = at<uint32_t>(ws, L.sorted_e);
-  b.gid_of_emit = at<uint32_t>(ws, L.gid_of_emit);
+  b.sorted_g = at<uint32_t>(ws, L.sorted_g);
   b.table = at<uint32_t>(ws, L.table);
   b.status = at<uint32_t>(ws, L.status);
   b.hist = at<uint32_t>(ws, L.hist);
@@ -151,13 +151,14 @@ CompositeArgs composite_args(const Layout& L, void* ws, int feat_bf16, const voi
   for (int i = 0; i < 3; ++i) c.bg[i] = bg[i];
   c.ranges = at<uint2>(ws, L.ranges);
   c.sorted_e = at<uint32_t>(ws, L.sorted_e);
-  c.gid_of_emit = at<uint32_t>(ws, L.gid_of_emit);
+  c.sorted_g = at<uint32_t>(ws, L.sorted_g);
   c.rec = at<float4>(ws, L.rec);
   c.feat = feat;
   c.t_final = at<float>(ws, L.tfinal);
   c.n_contrib = at<uint32_t>(ws, L.ncontrib);
   c.ntiles = L.ntiles;
   c.cap = L.cap;
+  c.err = &at<Header>(ws, L.hdr)->err;
   if (L.with_backward) {
     c.partials = at<float>(ws, L.partials);
     c.pflags = at<uint32_t>(ws, L.pflags);
@@ -336,7 +337,7 @@ fe_status fe_debug_dump(const void* workspace, size_t workspace_bytes, int P, in
   d.HW = width * height;
   d.hdr = at<Header>(ws, L.hdr);
   d.sorted_e = at<uint32_t>(ws, L.sorted_e);
-  d.gid_of_emit = at<uint32_t>(ws, L.gid_of_emit);
+  d.sorted_g = at<uint32_t>(ws, L.sorted_g);
   d.ranges = at<uint2>(ws, L.ranges);
   d.ncontrib = at<uint32_t>(ws, L.ncontrib);
   d.tfinal = at<float>(ws, L.tfinal);

@@ -343,7 +343,7 @@ struct ScatterArgs {
   int64_t cap;
   const uint32_t *order, *touched, *offs, *table;
   const ushort4* rect;
-  uint32_t *sorted_e, *gid_of_emit;
+  uint32_t *sorted_e, *sorted_g;
   uint2* ranges;
   Header* hdr;
 };
@@ -422,8 +422,10 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(const ScatterArgs
       wc[tile] = (uint16_t)(r + 1u);
       const uint64_t pos = (uint64_t)s_base[tile] + r;
       const uint64_t e = (uint64_t)e0 + k;
-      if (pos < cap) a.sorted_e[pos] = (uint32_t)e;
-      if (e < cap) a.gid_of_emit[e] = g;
+      if (pos < cap) {
+        a.sorted_e[pos] = (uint32_t)e;
+        a.sorted_g[pos] = g;
+      }
     }
     __syncwarp();
   }
@@ -536,7 +538,7 @@ cudaError_t launch_binning(BinArgs& b, cudaStream_t st) {
   sa.table = b.table;
   sa.rect = b.rect;
   sa.sorted_e = b.sorted_e;
-  sa.gid_of_emit = b.gid_of_emit;
+  sa.sorted_g = b.sorted_g;
   sa.ranges = b.ranges;
   sa.hdr = hdr;
   const size_t scat_smem = (size_t)b.ntiles * 4 + (size_t)8 * b.ntiles * 2;
@@ -554,9 +556,7 @@ __global__ void dump_kernel(const DumpArgs d) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (uint64_t i = i0; i < K; i += stride) {
-    const uint32_t e = d.sorted_e[i];
-    if ((uint64_t)e >= (uint64_t)d.cap) continue;  // only after an overflow
-    const uint32_t g = d.gid_of_emit[e];
+    const uint32_t g = d.sorted_g[i];
     if (d.keys) {
       // Tile of list position i: the last tile whose range starts at or
       // before i (empty tiles share the start of the next tile).

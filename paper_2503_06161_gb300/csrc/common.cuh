@@ -79,7 +79,7 @@ struct Layout {
   int P, D, W, H, tw, th, tiles_x, tiles_y, ntiles, pblocks, bblocks;
   int64_t cap;
   bool with_backward;
-  size_t hdr, rec, rect, touched, dkey[2], dval[2], offs, offs_by_gid, sorted_e, gid_of_emit, table;
+  size_t hdr, rec, rect, touched, dkey[2], dval[2], offs, offs_by_gid, sorted_e, sorted_g, table;
   size_t status, hist, ranges, tfinal, ncontrib, partials, pflags, dstate, ddstate, psum;
   size_t status_words, table_blocks;
   size_t total;
@@ -113,7 +113,7 @@ inline Layout make_layout(int P, int D, int W, int H, int tw, int th, int64_t ca
   L.offs = take((Pn + 1) * 4);
   L.offs_by_gid = take(Pn * 4);
   L.sorted_e = take(Kn * 4);
-  L.gid_of_emit = take(Kn * 4);
+  L.sorted_g = take(Kn * 4);
   const size_t table_n = (size_t)L.ntiles * L.bblocks;
   L.table = take(table_n * 4);
   L.table_blocks = (size_t)ceil_div((int64_t)(table_n > 0 ? table_n : 1), kPChunk);
@@ -205,5 +205,53 @@ __device__ __forceinline__ bool eval_pair(const float* rec, float pxc, float pyc
 }
 
 __device__ __forceinline__ void set_err(uint32_t* err, uint32_t bits) { atomicOr(err, bits); }
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies into shared memory with mbarrier completion.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One arrival that also announces `bytes` of incoming transactions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Generic-proxy accesses of a buffer before it is overwritten by the async proxy.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 1-D bulk copy global -> shared (addresses and size multiples of 16 bytes).
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity; false after `limit`
+// polls (each poll may suspend the thread for a short time).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = 1 << 20) {
+  for (int i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
 
 }  // namespace fe

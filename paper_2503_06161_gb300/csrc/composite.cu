@@ -20,43 +20,89 @@ namespace fe {
 
 namespace {
 
+// Gaussians per staged batch of the forward; two batches are in flight.
 template <int D>
-constexpr int fwd_batch() { return D <= 32 ? 256 : (D <= 64 ? 128 : 64); }
+constexpr int fwd_batch() { return D <= 32 ? 128 : (D <= 64 ? 64 : 32); }
 
+// Bytes of one staged batch: B render records (48 bytes each), then B
+// feature rows in their stored format (fp32 or bf16).
+__host__ __device__ constexpr uint32_t stage_bytes(int B, int D, int bf16) {
+  return (uint32_t)B * (uint32_t)(kRec * 4 + D * (bf16 ? 2 : 4));
+}
+
+// Bulk copies of one batch into a staging buffer, completing on `bar`:
+// thread 0 arms the barrier with the batch's byte count, thread t < nb copies
+// the record and the feature row of its Gaussian g.  Sources start at
+// 48 g and g * row bytes of 16-byte aligned arrays, destinations at
+// multiples of 16 bytes, and every size is a multiple of 16 bytes.
 template <int D>
-__device__ __forceinline__ void load_feat_row(const void* feat, int bf16, uint32_t g, float* dst) {
-  if (bf16) {
-    const uint4* src = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(feat) + (size_t)g * D);
-#pragma unroll
-    for (int i = 0; i < D / 8; ++i) {
-      const uint4 q = __ldg(src + i);
-      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        dst[8 * i + 2 * j] = __uint_as_float(w[j] << 16);
-        dst[8 * i + 2 * j + 1] = __uint_as_float(w[j] & 0xFFFF0000u);
-      }
-    }
-  } else {
-    const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(feat) + (size_t)g * D);
-#pragma unroll
-    for (int i = 0; i < D / 4; ++i) reinterpret_cast<float4*>(dst)[i] = __ldg(src + i);
+__device__ __forceinline__ void stage_issue(const CompositeArgs& a, unsigned char* buf, int B, int nb, uint32_t g,
+                                            uint64_t* bar) {
+  const int tid = threadIdx.x;
+  const uint32_t rowb = (uint32_t)D * (a.feat_bf16 ? 2u : 4u);
+  if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)nb * ((uint32_t)kRec * 4u + rowb));
+  if (tid < nb) {
+    fence_proxy_async();  // earlier generic reads of this buffer come first
+    tma_load_1d(buf + (size_t)tid * kRec * 4, a.rec + 3 * (size_t)g, (uint32_t)kRec * 4u, bar);
+    tma_load_1d(buf + (size_t)B * kRec * 4 + (size_t)tid * rowb,
+                static_cast<const unsigned char*>(a.feat) + (size_t)g * rowb, rowb, bar);
   }
+}
+
+// bf16 feature rows of a landed batch -> fp32 rows (whole block).
+template <int D>
+__device__ __forceinline__ void widen_bf16(const unsigned char* raw, float* dst, int nb) {
+  const uint4* src = reinterpret_cast<const uint4*>(raw);
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  for (int i = threadIdx.x; i < nb * (D / 8); i += kThreads) {
+    const uint4 q = src[i];
+    d4[2 * i] = make_float4(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xFFFF0000u),
+                            __uint_as_float(q.y << 16), __uint_as_float(q.y & 0xFFFF0000u));
+    d4[2 * i + 1] = make_float4(__uint_as_float(q.z << 16), __uint_as_float(q.z & 0xFFFF0000u),
+                                __uint_as_float(q.w << 16), __uint_as_float(q.w & 0xFFFF0000u));
+  }
+}
+
+// Shared memory of the forward: two staging buffers, then (bf16 features)
+// one fp32 copy of the current batch's rows.
+template <int D>
+__host__ __device__ constexpr size_t fwd_smem_bytes(int bf16) {
+  return 2 * (size_t)stage_bytes(fwd_batch<D>(), D, bf16) + (bf16 ? (size_t)fwd_batch<D>() * D * 4 : 0);
 }
 
 template <int D, bool kCount>
 __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const CompositeArgs a) {
   constexpr int B = fwd_batch<D>();
-  extern __shared__ __align__(16) float smem[];
-  float* s_rec = smem;                 // [B][12]
-  float* s_feat = smem + B * kRec;     // [B][D]
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_abort;
   const int tid = threadIdx.x;
+  const bool bf16 = a.feat_bf16 != 0;
+  const uint32_t sbytes = stage_bytes(B, D, a.feat_bf16);
+  float* s_wide = reinterpret_cast<float*>(smem + 2 * (size_t)sbytes);
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
   const int px = tx * a.tw + tid % a.tw, py = ty * a.th + tid / a.tw;
   const bool inside = px < a.W && py < a.H;
   const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
   const uint2 rg = a.ranges[tile];
+  const uint32_t n = rg.y - rg.x;
+  const uint32_t nbatch = (n + B - 1) / B;
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_init_fence();
+    s_abort = 0;
+  }
+  __syncthreads();
+  // Gaussian of this thread's slot in batch k (prefetched a batch ahead).
+  auto slot_gid = [&](uint32_t k) -> uint32_t {
+    const uint32_t p = k * B + (uint32_t)tid;
+    return (k < nbatch && tid < B && p < n) ? __ldg(a.sorted_g + rg.x + p) : 0u;
+  };
+  auto batch_len = [&](uint32_t k) -> int { return (int)min((uint32_t)B, n - k * B); };
+  if (nbatch > 0) stage_issue<D>(a, smem, B, batch_len(0), slot_gid(0), &s_bar[0]);
+  uint32_t g_next = slot_gid(1);
   float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Z = 0.f;
   float F[D];
 #pragma unroll
@@ -64,24 +110,30 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
   uint32_t last = 0;
   uint32_t visits = 0, contribs = 0;  // only used by the counting variant
   bool done = !inside;
-  for (uint32_t bs = rg.x; bs < rg.y; bs += B) {
+  uint32_t k = 0;
+  for (; k < nbatch; ++k) {
+    // Every thread is past batch k-1 here, so its buffer may be refilled.
     if (__syncthreads_count(done) == kThreads) break;
-    if (tid < B && bs + tid < rg.y) {
-      const uint32_t e = a.sorted_e[bs + tid];
-      float4* d = reinterpret_cast<float4*>(s_rec + tid * kRec);
-      if ((int64_t)e < a.cap) {
-        const uint32_t g = a.gid_of_emit[e];
-        const float4* r = a.rec + 3 * (size_t)g;
-        d[0] = __ldg(r);
-        d[1] = __ldg(r + 1);
-        d[2] = __ldg(r + 2);
-        load_feat_row<D>(a.feat, a.feat_bf16, g, s_feat + tid * D);
-      } else {
-        d[2] = make_float4(0.f, 0.f, -1.0f, 0.f);  // radius -1: never included
-      }
+    if (k + 1 < nbatch) {
+      stage_issue<D>(a, smem + ((k + 1) & 1) * (size_t)sbytes, B, batch_len(k + 1), g_next, &s_bar[(k + 1) & 1]);
+      g_next = slot_gid(k + 2);
     }
-    __syncthreads();
-    const int nb = (int)min((uint32_t)B, rg.y - bs);
+    const unsigned char* buf = smem + (k & 1) * (size_t)sbytes;
+    if (*(volatile int*)&s_abort || !mbar_wait(&s_bar[k & 1], (k >> 1) & 1)) {
+      if (!*(volatile int*)&s_abort) {
+        *(volatile int*)&s_abort = 1;
+        set_err(a.err, kErrTimeout);
+      }
+      done = true;
+    }
+    const int nb = batch_len(k);
+    const float* s_rec = reinterpret_cast<const float*>(buf);
+    const float* s_feat = reinterpret_cast<const float*>(buf + (size_t)B * kRec * 4);
+    if (bf16) {
+      widen_bf16<D>(buf + (size_t)B * kRec * 4, s_wide, nb);
+      __syncthreads();
+      s_feat = s_wide;
+    }
     if (!done) {
       for (int j = 0; j < nb; ++j) {
         const float* rec = s_rec + j * kRec;
@@ -109,12 +161,16 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
           F[4 * d4 + 3] = fmaf(w, f.w, F[4 * d4 + 3]);
         }
         T = Tn;
-        last = bs - rg.x + (uint32_t)j + 1u;
+        last = k * B + (uint32_t)j + 1u;
       }
     }
   }
+  // After an early exit batch k is still in flight: it must land before the
+  // block's shared memory is released.
+  if (k < nbatch && tid == 0 && !*(volatile int*)&s_abort && !mbar_wait(&s_bar[k & 1], (k >> 1) & 1))
+    set_err(a.err, kErrTimeout);
   if (kCount) {
-    // Block sums of the pair counts, one 64-bit atomic per block.
+    // Block sums of the pair counts, one 64-bit atomic per warp.
     unsigned long long v = visits, c = contribs;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -162,10 +218,18 @@ struct BwdCfg {
   static constexpr int GS = NC + 1;                 // per-pixel gradient row stride (odd)
   static constexpr int WS = B + 4;                  // w row stride (16-byte rows)
   static constexpr int SLICE = (32 * WS > B * NC) ? 32 * WS : B * NC;
-  static constexpr size_t smem_floats() {
-    return (size_t)B * kRec + (size_t)B * NC + (size_t)kThreads * GS + (size_t)8 * SLICE + (size_t)8 * B * 8 + B +
-           8 + 4;
+  // Byte offsets in dynamic shared memory: per-pixel gradient rows, warp
+  // slices, geometric warp partials, two staging buffers, the fp32 copy of
+  // bf16 feature rows, list entries of the two staged batches.
+  static constexpr size_t off_G = 0;
+  static constexpr size_t off_slice = off_G + (size_t)kThreads * GS * 4;
+  static constexpr size_t off_geo = off_slice + (size_t)8 * SLICE * 4;
+  static constexpr size_t off_stage = (off_geo + (size_t)8 * B * 8 * 4 + 127) / 128 * 128;
+  __host__ __device__ static constexpr size_t off_wide(int bf16) { return off_stage + 2 * (size_t)stage_bytes(B, D, bf16); }
+  __host__ __device__ static constexpr size_t off_e(int bf16) {
+    return off_wide(bf16) + (bf16 ? (size_t)B * D * 4 : 0);
   }
+  __host__ __device__ static constexpr size_t smem_bytes(int bf16) { return off_e(bf16) + (size_t)(2 * B + 8 + 4) * 4; }
 };
 
 template <int D>
@@ -173,14 +237,18 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
   using K = BwdCfg<D>;
   constexpr int B = K::B, NC = K::NC, GS = K::GS, WS = K::WS, NP = partial_stride(D);
   constexpr int NV = kPartialScalars + D;  // values per row
-  extern __shared__ __align__(16) float smem[];
-  float* s_rec = smem;                       // [B][12]
-  float* s_x = s_rec + B * kRec;             // [B][NC]: rgb, depth, z
-  float* s_G = s_x + B * NC;                 // [256][GS]
-  float* s_slice = s_G + kThreads * GS;      // [8][SLICE]: w[p][j], then P[j][c]
-  float* s_geo = s_slice + 8 * K::SLICE;     // [8][B][8]
-  uint32_t* s_e = reinterpret_cast<uint32_t*>(s_geo + 8 * B * 8);
-  uint32_t* s_jact = s_e + B;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_abort;
+  const bool bf16 = a.feat_bf16 != 0;
+  const uint32_t sbytes = stage_bytes(B, D, a.feat_bf16);
+  float* s_G = reinterpret_cast<float*>(smem + K::off_G);          // [256][GS]
+  float* s_slice = reinterpret_cast<float*>(smem + K::off_slice);  // [8][SLICE]: w[p][j], then P[j][c]
+  float* s_geo = reinterpret_cast<float*>(smem + K::off_geo);      // [8][B][8]
+  unsigned char* s_stage = smem + K::off_stage;                     // [2][sbytes]
+  float* s_wide = reinterpret_cast<float*>(smem + K::off_wide(a.feat_bf16));
+  uint32_t* s_e = reinterpret_cast<uint32_t*>(smem + K::off_e(a.feat_bf16));  // [2][B]
+  uint32_t* s_jact = s_e + 2 * B;
   uint32_t* s_maxn = s_jact + 8;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tile = blockIdx.x;
@@ -222,43 +290,75 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
   float T = Tf;
   float Q = (grow[0] * a.bg[0] + grow[1] * a.bg[1] + grow[2] * a.bg[2]) * Tf;
   const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, nc);
-  if (tid == 0) *s_maxn = 0u;
+  if (tid == 0) {
+    *s_maxn = 0u;
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_init_fence();
+    s_abort = 0;
+  }
   __syncthreads();
   if (lane == 0 && wmax) atomicMax(s_maxn, wmax);
   __syncthreads();
-  const uint32_t end = rg.x + *s_maxn;
-  float* slice = s_slice + warp * K::SLICE;
-  for (uint32_t be = end; be > rg.x;) {
-    const uint32_t bs = be - rg.x > (uint32_t)B ? be - B : rg.x;
-    const int nb = (int)(be - bs);
-    __syncthreads();
-    if (tid < nb) {
-      const uint32_t e = a.sorted_e[bs + tid];
-      float4* d = reinterpret_cast<float4*>(s_rec + tid * kRec);
-      s_e[tid] = e;
-      if ((int64_t)e < a.cap) {
-        const uint32_t g = a.gid_of_emit[e];
-        const float4* r = a.rec + 3 * (size_t)g;
-        const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2);
-        d[0] = r0; d[1] = r1; d[2] = r2;
-        float* x = s_x + tid * NC;
-        x[0] = r1.w; x[1] = r2.x; x[2] = r2.y; x[3] = r1.z;  // rgb, depth
-        load_feat_row<D>(a.feat, a.feat_bf16, g, x + 4);
-      } else {
-        d[2] = make_float4(0.f, 0.f, -1.0f, 0.f);  // radius -1: never included
-      }
+  // Batches walk [rg.x, rg.x + maxn) backwards: batch k covers
+  // [max(rg.x, hi_k - B), hi_k) with hi_k = rg.x + maxn - k B.
+  const uint32_t n = *s_maxn;
+  const uint32_t nbatch = (n + B - 1) / B;
+  auto batch_lo = [&](uint32_t k) -> uint32_t { return n - k * B > (uint32_t)B ? n - (k + 1) * B : 0u; };
+  auto batch_len = [&](uint32_t k) -> int { return (int)(n - k * B - batch_lo(k)); };
+  // List entry and Gaussian of this thread's slot in batch k.
+  auto slot = [&](uint32_t k, uint32_t& e, uint32_t& g) {
+    e = 0u;
+    g = 0u;
+    if (k < nbatch && tid < batch_len(k)) {
+      const uint32_t p = rg.x + batch_lo(k) + (uint32_t)tid;
+      e = __ldg(a.sorted_e + p);
+      g = __ldg(a.sorted_g + p);
     }
+  };
+  uint32_t e_next, g_next;
+  slot(0, e_next, g_next);
+  if (nbatch > 0) {
+    stage_issue<D>(a, s_stage, B, batch_len(0), g_next, &s_bar[0]);
+    if (tid < B) s_e[tid] = e_next;
+  }
+  slot(1, e_next, g_next);
+  float* slice = s_slice + warp * K::SLICE;
+  for (uint32_t k = 0; k < nbatch; ++k) {
+    // Every thread is past batch k-1 (and its combine) here.
     __syncthreads();
-    const uint32_t rel0 = bs - rg.x;
+    if (k + 1 < nbatch) {
+      stage_issue<D>(a, s_stage + ((k + 1) & 1) * (size_t)sbytes, B, batch_len(k + 1), g_next, &s_bar[(k + 1) & 1]);
+      if (tid < B) s_e[((k + 1) & 1) * B + tid] = e_next;
+      slot(k + 2, e_next, g_next);
+    }
+    bool live = true;
+    if (*(volatile int*)&s_abort || !mbar_wait(&s_bar[k & 1], (k >> 1) & 1)) {
+      if (!*(volatile int*)&s_abort) {
+        *(volatile int*)&s_abort = 1;
+        set_err(a.err, kErrTimeout);
+      }
+      live = false;
+    }
+    const unsigned char* buf = s_stage + (k & 1) * (size_t)sbytes;
+    const float* s_rec = reinterpret_cast<const float*>(buf);
+    const float* s_feat = reinterpret_cast<const float*>(buf + (size_t)B * kRec * 4);
+    const int nb = batch_len(k);
+    if (bf16) {
+      widen_bf16<D>(buf + (size_t)B * kRec * 4, s_wide, nb);
+      __syncthreads();
+      s_feat = s_wide;
+    }
+    const uint32_t rel0 = batch_lo(k);
     uint32_t jact = 0;
     if (rel0 < wmax) {
       for (int j = nb - 1; j >= 0; --j) {
         float v[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = 0.0f;
+        for (int q = 0; q < 8; ++q) v[q] = 0.0f;
         float w = 0.0f;
         bool contrib = false;
-        if (rel0 + (uint32_t)j < nc) {
+        if (live && rel0 + (uint32_t)j < nc) {
           const float* rec = s_rec + j * kRec;
           PairEval pe;
           if (eval_pair(rec, pxc, pyc, pe)) {
@@ -267,21 +367,35 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
             const float inv = __fdividef(1.0f, one_m);  // one_m >= 0.01
             T = T * inv;  // transmittance before this Gaussian
             w = pe.alpha * T;
-            const float4* x4 = reinterpret_cast<const float4*>(s_x + j * NC);
-            float s = 0.0f;
+            // s = g . (rgb, depth, feature) of this Gaussian.
+            const float4 r4 = *reinterpret_cast<const float4*>(rec + 4);  // ., ., depth, r
+            const float4 r8 = *reinterpret_cast<const float4*>(rec + 8);  // g, b, ., .
+            const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * D);
+            float s;
+            if (K::GREG) {
+              s = G[0] * r4.w;
+              s = fmaf(G[1], r8.x, s);
+              s = fmaf(G[2], r8.y, s);
+              s = fmaf(G[3], r4.z, s);
+            } else {
+              s = grow[0] * r4.w;
+              s = fmaf(grow[1], r8.x, s);
+              s = fmaf(grow[2], r8.y, s);
+              s = fmaf(grow[3], r4.z, s);
+            }
 #pragma unroll
-            for (int c4 = 0; c4 < NC / 4; ++c4) {
-              const float4 xv = x4[c4];
+            for (int d4 = 0; d4 < D / 4; ++d4) {
+              const float4 xv = f4[d4];
               if (K::GREG) {
-                s = fmaf(G[4 * c4], xv.x, s);
-                s = fmaf(G[4 * c4 + 1], xv.y, s);
-                s = fmaf(G[4 * c4 + 2], xv.z, s);
-                s = fmaf(G[4 * c4 + 3], xv.w, s);
+                s = fmaf(G[4 + 4 * d4], xv.x, s);
+                s = fmaf(G[5 + 4 * d4], xv.y, s);
+                s = fmaf(G[6 + 4 * d4], xv.z, s);
+                s = fmaf(G[7 + 4 * d4], xv.w, s);
               } else {
-                s = fmaf(grow[4 * c4], xv.x, s);
-                s = fmaf(grow[4 * c4 + 1], xv.y, s);
-                s = fmaf(grow[4 * c4 + 2], xv.z, s);
-                s = fmaf(grow[4 * c4 + 3], xv.w, s);
+                s = fmaf(grow[4 + 4 * d4], xv.x, s);
+                s = fmaf(grow[5 + 4 * d4], xv.y, s);
+                s = fmaf(grow[6 + 4 * d4], xv.z, s);
+                s = fmaf(grow[7 + 4 * d4], xv.w, s);
               }
             }
             const float dalpha = T * s - (Q - ga * Tf) * inv;
@@ -362,28 +476,27 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
     if (lane == 0) s_jact[warp] = jact;
     __syncthreads();
     // Fixed-order sum of the warp partials: one row per (tile, entry).
+    const uint32_t* se = s_e + (k & 1) * B;
     for (int item = tid; item < nb * NV; item += kThreads) {
-      // k: 0..5 geometric terms, 6..9 rgb/depth, 10.. features; row index
+      // q: 0..5 geometric terms, 6..9 rgb/depth, 10.. features; row index
       // puts the features first.
-      const int j = item / NV, k = item - j * NV;
+      const int j = item / NV, q = item - j * NV;
       float acc = 0.0f;
 #pragma unroll
       for (int w8 = 0; w8 < 8; ++w8) {
         if ((s_jact[w8] >> j) & 1u)
-          acc += k < 6 ? s_geo[(w8 * B + j) * 8 + k] : s_slice[w8 * K::SLICE + j * NC + (k - 6)];
+          acc += q < 6 ? s_geo[(w8 * B + j) * 8 + q] : s_slice[w8 * K::SLICE + j * NC + (q - 6)];
       }
-      const int col = k < kPartialScalars ? D + k : k - kPartialScalars;
-      if ((int64_t)s_e[j] < a.cap) a.partials[(size_t)s_e[j] * NP + col] = acc;
+      const int col = q < kPartialScalars ? D + q : q - kPartialScalars;
+      if ((int64_t)se[j] < a.cap) a.partials[(size_t)se[j] * NP + col] = acc;
     }
-    if (tid < nb && (int64_t)s_e[tid] < a.cap) atomicOr(a.pflags + (s_e[tid] >> 5), 1u << (s_e[tid] & 31u));
-    be = bs;
+    if (tid < nb && (int64_t)se[tid] < a.cap) atomicOr(a.pflags + (se[tid] >> 5), 1u << (se[tid] & 31u));
   }
 }
 
 template <int D>
 cudaError_t launch_fwd_t(const CompositeArgs& a, cudaStream_t st) {
-  constexpr int B = fwd_batch<D>();
-  const size_t smem = (size_t)B * (kRec + D) * sizeof(float);
+  const size_t smem = fwd_smem_bytes<D>(a.feat_bf16);
   auto k = a.counts ? composite_fwd_kernel<D, true> : composite_fwd_kernel<D, false>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<a.ntiles, kThreads, smem, st>>>(a);
@@ -392,7 +505,7 @@ cudaError_t launch_fwd_t(const CompositeArgs& a, cudaStream_t st) {
 
 template <int D>
 cudaError_t launch_bwd_t(const CompositeArgs& a, cudaStream_t st) {
-  const size_t smem = BwdCfg<D>::smem_floats() * sizeof(float);
+  const size_t smem = BwdCfg<D>::smem_bytes(a.feat_bf16);
   auto k = composite_bwd_kernel<D>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<a.ntiles, kThreads, smem, st>>>(a);

@@ -56,7 +56,7 @@ struct BinArgs {
   uint32_t *dkey[2], *dval[2];  // depth-sort ping-pong (final: index 0)
   uint32_t *offs, *offs_by_gid;
   uint32_t* sorted_e;           // [cap] emission index per list position
-  uint32_t* gid_of_emit;        // [cap] Gaussian of each emission index
+  uint32_t* sorted_g;           // [cap] Gaussian index per list position
   uint32_t* table;              // [ntiles][bblocks] counts, then segment starts
   uint32_t* status;             // decoupled look-back words
   uint32_t* hist;               // depth digit histograms [4][256]
@@ -74,7 +74,7 @@ struct CompositeArgs {
   int W, H, tw, th, tiles_x, D, feat_bf16;
   float bg[3];
   const uint2* ranges;
-  const uint32_t *sorted_e, *gid_of_emit;
+  const uint32_t *sorted_e, *sorted_g;
   const float4* rec;
   const void* feat;
   float *out_rgb, *out_depth, *out_alpha, *out_feat;
@@ -87,6 +87,7 @@ struct CompositeArgs {
   int ntiles;
   int64_t cap;       // list capacity: emission indices at or past it are skipped
   uint64_t* counts;  // non-NULL: counting variant of the forward (no outputs)
+  uint32_t* err;     // header error bits (staging timeouts)
 };
 
 cudaError_t launch_composite_fwd(const CompositeArgs& a, cudaStream_t st);
@@ -96,7 +97,7 @@ struct DumpArgs {
   int64_t cap;
   int P, ntiles, HW;
   const void* hdr;
-  const uint32_t *sorted_e, *gid_of_emit;
+  const uint32_t *sorted_e, *sorted_g;
   const uint2* ranges;
   const uint32_t* ncontrib;
   const float* tfinal;
