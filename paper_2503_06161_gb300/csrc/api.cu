@@ -125,8 +125,7 @@ BinArgs bin_args(const Layout& L, void* ws) {
   }
   b.offs = at<uint32_t>(ws, L.offs);
   b.offs_by_gid = at<uint32_t>(ws, L.offs_by_gid);
-  b.sorted_e = at<uint32_t>(ws, L.sorted_e);
-  b.sorted_g = at<uint32_t>(ws, L.sorted_g);
+  b.sorted = at<uint2>(ws, L.sorted);
   b.table = at<uint32_t>(ws, L.table);
   b.status = at<uint32_t>(ws, L.status);
   b.hist = at<uint32_t>(ws, L.hist);
@@ -150,8 +149,7 @@ CompositeArgs composite_args(const Layout& L, void* ws, int feat_bf16, const voi
   c.feat_bf16 = feat_bf16;
   for (int i = 0; i < 3; ++i) c.bg[i] = bg[i];
   c.ranges = at<uint2>(ws, L.ranges);
-  c.sorted_e = at<uint32_t>(ws, L.sorted_e);
-  c.sorted_g = at<uint32_t>(ws, L.sorted_g);
+  c.sorted = at<uint2>(ws, L.sorted);
   c.rec = at<float4>(ws, L.rec);
   c.feat = feat;
   c.t_final = at<float>(ws, L.tfinal);
@@ -336,8 +334,7 @@ fe_status fe_debug_dump(const void* workspace, size_t workspace_bytes, int P, in
   d.ntiles = L.ntiles;
   d.HW = width * height;
   d.hdr = at<Header>(ws, L.hdr);
-  d.sorted_e = at<uint32_t>(ws, L.sorted_e);
-  d.sorted_g = at<uint32_t>(ws, L.sorted_g);
+  d.sorted = at<uint2>(ws, L.sorted);
   d.ranges = at<uint2>(ws, L.ranges);
   d.ncontrib = at<uint32_t>(ws, L.ncontrib);
   d.tfinal = at<float>(ws, L.tfinal);

@@ -343,7 +343,7 @@ struct ScatterArgs {
   int64_t cap;
   const uint32_t *order, *touched, *offs, *table;
   const ushort4* rect;
-  uint32_t *sorted_e, *sorted_g;
+  uint2* sorted;
   uint2* ranges;
   Header* hdr;
 };
@@ -422,10 +422,7 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(const ScatterArgs
       wc[tile] = (uint16_t)(r + 1u);
       const uint64_t pos = (uint64_t)s_base[tile] + r;
       const uint64_t e = (uint64_t)e0 + k;
-      if (pos < cap) {
-        a.sorted_e[pos] = (uint32_t)e;
-        a.sorted_g[pos] = g;
-      }
+      if (pos < cap) a.sorted[pos] = make_uint2((uint32_t)e, g);
     }
     __syncwarp();
   }
@@ -537,8 +534,7 @@ cudaError_t launch_binning(BinArgs& b, cudaStream_t st) {
   sa.offs = b.offs;
   sa.table = b.table;
   sa.rect = b.rect;
-  sa.sorted_e = b.sorted_e;
-  sa.sorted_g = b.sorted_g;
+  sa.sorted = b.sorted;
   sa.ranges = b.ranges;
   sa.hdr = hdr;
   const size_t scat_smem = (size_t)b.ntiles * 4 + (size_t)8 * b.ntiles * 2;
@@ -556,7 +552,7 @@ __global__ void dump_kernel(const DumpArgs d) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (uint64_t i = i0; i < K; i += stride) {
-    const uint32_t g = d.sorted_g[i];
+    const uint32_t g = d.sorted[i].y;
     if (d.keys) {
       // Tile of list position i: the last tile whose range starts at or
       // before i (empty tiles share the start of the next tile).

@@ -79,7 +79,7 @@ struct Layout {
   int P, D, W, H, tw, th, tiles_x, tiles_y, ntiles, pblocks, bblocks;
   int64_t cap;
   bool with_backward;
-  size_t hdr, rec, rect, touched, dkey[2], dval[2], offs, offs_by_gid, sorted_e, sorted_g, table;
+  size_t hdr, rec, rect, touched, dkey[2], dval[2], offs, offs_by_gid, sorted, table;
   size_t status, hist, ranges, tfinal, ncontrib, partials, pflags, dstate, ddstate, psum;
   size_t status_words, table_blocks;
   size_t total;
@@ -112,8 +112,7 @@ inline Layout make_layout(int P, int D, int W, int H, int tw, int th, int64_t ca
   for (int i = 0; i < 2; ++i) L.dval[i] = take(Pn * 4);
   L.offs = take((Pn + 1) * 4);
   L.offs_by_gid = take(Pn * 4);
-  L.sorted_e = take(Kn * 4);
-  L.sorted_g = take(Kn * 4);
+  L.sorted = take(Kn * 8);
   const size_t table_n = (size_t)L.ntiles * L.bblocks;
   L.table = take(table_n * 4);
   L.table_blocks = (size_t)ceil_div((int64_t)(table_n > 0 ? table_n : 1), kPChunk);

@@ -98,15 +98,15 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
   // Gaussian of this thread's slot in batch k (prefetched a batch ahead).
   auto slot_gid = [&](uint32_t k) -> uint32_t {
     const uint32_t p = k * B + (uint32_t)tid;
-    return (k < nbatch && tid < B && p < n) ? __ldg(a.sorted_g + rg.x + p) : 0u;
+    return (k < nbatch && tid < B && p < n) ? __ldg(&a.sorted[rg.x + p].y) : 0u;
   };
   auto batch_len = [&](uint32_t k) -> int { return (int)min((uint32_t)B, n - k * B); };
   if (nbatch > 0) stage_issue<D>(a, smem, B, batch_len(0), slot_gid(0), &s_bar[0]);
   uint32_t g_next = slot_gid(1);
   float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Z = 0.f;
-  float F[D];
+  float2 F[D / 2];  // feature channels in pairs (packed FP32 FMA)
 #pragma unroll
-  for (int d = 0; d < D; ++d) F[d] = 0.0f;
+  for (int d = 0; d < D / 2; ++d) F[d] = make_float2(0.0f, 0.0f);
   uint32_t last = 0;
   uint32_t visits = 0, contribs = 0;  // only used by the counting variant
   bool done = !inside;
@@ -152,13 +152,12 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
         C2 = fmaf(w, rec[9], C2);
         Z = fmaf(w, rec[6], Z);
         const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * D);
+        const float2 w2 = make_float2(w, w);
 #pragma unroll
         for (int d4 = 0; d4 < D / 4; ++d4) {
           const float4 f = f4[d4];
-          F[4 * d4] = fmaf(w, f.x, F[4 * d4]);
-          F[4 * d4 + 1] = fmaf(w, f.y, F[4 * d4 + 1]);
-          F[4 * d4 + 2] = fmaf(w, f.z, F[4 * d4 + 2]);
-          F[4 * d4 + 3] = fmaf(w, f.w, F[4 * d4 + 3]);
+          F[2 * d4] = __ffma2_rn(w2, make_float2(f.x, f.y), F[2 * d4]);
+          F[2 * d4 + 1] = __ffma2_rn(w2, make_float2(f.z, f.w), F[2 * d4 + 1]);
         }
         T = Tn;
         last = k * B + (uint32_t)j + 1u;
@@ -192,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
     a.out_alpha[p] = 1.0f - T;
     float4* fo = reinterpret_cast<float4*>(a.out_feat + p * D);
 #pragma unroll
-    for (int d4 = 0; d4 < D / 4; ++d4) fo[d4] = make_float4(F[4 * d4], F[4 * d4 + 1], F[4 * d4 + 2], F[4 * d4 + 3]);
+    for (int d4 = 0; d4 < D / 4; ++d4) fo[d4] = make_float4(F[2 * d4].x, F[2 * d4].y, F[2 * d4 + 1].x, F[2 * d4 + 1].y);
     a.t_final[p] = T;
     a.n_contrib[p] = last;
   }
@@ -211,13 +210,14 @@ template <int D>
 struct BwdCfg {
   static constexpr int NC = 4 + D;                  // linear channels
   static constexpr int B = D <= 64 ? 32 : 16;       // entries per batch
-  static constexpr int JG = 8, CG = 4;              // lane grid of the per-warp product
+  static constexpr int JG = 16, CG = 2;             // lane grid of the per-warp product
   static constexpr int JPL = B / JG;                // entries per lane
-  static constexpr int CPL = NC / CG;               // channels per lane
+  static constexpr int CPL = NC / CG;               // channels per lane (even: packed FMA)
   static constexpr bool GREG = D <= 32;             // upstream gradients kept in registers
-  static constexpr int GS = NC + 1;                 // per-pixel gradient row stride (odd)
+  static constexpr int GS = NC + 2;                 // per-pixel gradient row stride (8-byte rows)
   static constexpr int WS = B + 4;                  // w row stride (16-byte rows)
   static constexpr int SLICE = (32 * WS > B * NC) ? 32 * WS : B * NC;
+  static_assert(B % JG == 0 && CPL % 2 == 0 && JPL <= 2, "lane grid of the per-warp product");
   // Byte offsets in dynamic shared memory: per-pixel gradient rows, warp
   // slices, geometric warp partials, two staging buffers, the fp32 copy of
   // bf16 feature rows, list entries of the two staged batches.
@@ -280,10 +280,10 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
       for (int d = 0; d < D; ++d) grow[4 + d] = 0.0f;
     }
   }
-  float G[K::GREG ? NC : 1];
+  float2 G[K::GREG ? NC / 2 : 1];
   if (K::GREG) {
 #pragma unroll
-    for (int c = 0; c < NC; ++c) G[c] = grow[c];
+    for (int c = 0; c < NC / 2; ++c) G[c] = make_float2(grow[2 * c], grow[2 * c + 1]);
   }
   const float Tf = inside ? a.t_final[pix] : 1.0f;
   const uint32_t nc = inside ? a.n_contrib[pix] : 0u;
@@ -312,8 +312,9 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
     g = 0u;
     if (k < nbatch && tid < batch_len(k)) {
       const uint32_t p = rg.x + batch_lo(k) + (uint32_t)tid;
-      e = __ldg(a.sorted_e + p);
-      g = __ldg(a.sorted_g + p);
+      const uint2 eg = __ldg(a.sorted + p);
+      e = eg.x;
+      g = eg.y;
     }
   };
   uint32_t e_next, g_next;
@@ -371,33 +372,17 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
             const float4 r4 = *reinterpret_cast<const float4*>(rec + 4);  // ., ., depth, r
             const float4 r8 = *reinterpret_cast<const float4*>(rec + 8);  // g, b, ., .
             const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * D);
-            float s;
-            if (K::GREG) {
-              s = G[0] * r4.w;
-              s = fmaf(G[1], r8.x, s);
-              s = fmaf(G[2], r8.y, s);
-              s = fmaf(G[3], r4.z, s);
-            } else {
-              s = grow[0] * r4.w;
-              s = fmaf(grow[1], r8.x, s);
-              s = fmaf(grow[2], r8.y, s);
-              s = fmaf(grow[3], r4.z, s);
-            }
+            // Even and odd channels summed in the two halves of a pair.
+            const float2* g2 = reinterpret_cast<const float2*>(grow);
+            float2 s2 = __fmul2_rn(K::GREG ? G[0] : g2[0], make_float2(r4.w, r8.x));
+            s2 = __ffma2_rn(K::GREG ? G[1] : g2[1], make_float2(r8.y, r4.z), s2);
 #pragma unroll
             for (int d4 = 0; d4 < D / 4; ++d4) {
               const float4 xv = f4[d4];
-              if (K::GREG) {
-                s = fmaf(G[4 + 4 * d4], xv.x, s);
-                s = fmaf(G[5 + 4 * d4], xv.y, s);
-                s = fmaf(G[6 + 4 * d4], xv.z, s);
-                s = fmaf(G[7 + 4 * d4], xv.w, s);
-              } else {
-                s = fmaf(grow[4 + 4 * d4], xv.x, s);
-                s = fmaf(grow[5 + 4 * d4], xv.y, s);
-                s = fmaf(grow[6 + 4 * d4], xv.z, s);
-                s = fmaf(grow[7 + 4 * d4], xv.w, s);
-              }
+              s2 = __ffma2_rn(K::GREG ? G[2 + 2 * d4] : g2[2 + 2 * d4], make_float2(xv.x, xv.y), s2);
+              s2 = __ffma2_rn(K::GREG ? G[3 + 2 * d4] : g2[3 + 2 * d4], make_float2(xv.z, xv.w), s2);
             }
+            const float s = s2.x + s2.y;
             const float dalpha = T * s - (Q - ga * Tf) * inv;
             Q = fmaf(w, s, Q);
             if (!pe.clamped) {
@@ -441,36 +426,38 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
       }
       __syncwarp();
       if (jact) {
-        // P[j][c] = sum over the warp's pixels of w[p][j] * G[p][c].
-        const int jg = lane >> 2, cg = lane & 3;
-        float acc[K::JPL][K::CPL];
+        // P[j][c] = sum over the warp's pixels of w[p][j] * G[p][c], channel
+        // pairs in packed FMAs.
+        constexpr int CP2 = K::CPL / 2;
+        const int jg = lane >> 1, cg = lane & 1;
+        float2 acc[K::JPL][CP2];
 #pragma unroll
         for (int jj = 0; jj < K::JPL; ++jj)
 #pragma unroll
-          for (int c = 0; c < K::CPL; ++c) acc[jj][c] = 0.0f;
+          for (int c = 0; c < CP2; ++c) acc[jj][c] = make_float2(0.0f, 0.0f);
 #pragma unroll 4
         for (int p = 0; p < 32; ++p) {
           float wv[K::JPL];
-          if (K::JPL == 4) {
-            const float4 t4 = *reinterpret_cast<const float4*>(slice + p * WS + jg * 4);
-            wv[0] = t4.x; wv[1] = t4.y; wv[2] = t4.z; wv[3] = t4.w;
-          } else {
+          if (K::JPL == 2) {
             const float2 t2 = *reinterpret_cast<const float2*>(slice + p * WS + jg * 2);
             wv[0] = t2.x; wv[1] = t2.y;
+          } else {
+            wv[0] = slice[p * WS + jg];
           }
-          const float* gr = s_G + (warp * 32 + p) * GS + cg * K::CPL;
+          const float2* gr = reinterpret_cast<const float2*>(s_G + (warp * 32 + p) * GS + cg * K::CPL);
 #pragma unroll
-          for (int c = 0; c < K::CPL; ++c) {
-            const float gv = gr[c];
+          for (int c = 0; c < CP2; ++c) {
+            const float2 gv = gr[c];
 #pragma unroll
-            for (int jj = 0; jj < K::JPL; ++jj) acc[jj][c] = fmaf(wv[jj], gv, acc[jj][c]);
+            for (int jj = 0; jj < K::JPL; ++jj) acc[jj][c] = __ffma2_rn(make_float2(wv[jj], wv[jj]), gv, acc[jj][c]);
           }
         }
         __syncwarp();
 #pragma unroll
         for (int jj = 0; jj < K::JPL; ++jj)
 #pragma unroll
-          for (int c = 0; c < K::CPL; ++c) slice[(jg * K::JPL + jj) * NC + cg * K::CPL + c] = acc[jj][c];
+          for (int c = 0; c < CP2; ++c)
+            *reinterpret_cast<float2*>(slice + (jg * K::JPL + jj) * NC + cg * K::CPL + 2 * c) = acc[jj][c];
       }
     }
     if (lane == 0) s_jact[warp] = jact;

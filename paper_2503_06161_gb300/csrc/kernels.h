@@ -55,8 +55,7 @@ struct BinArgs {
   const uint32_t* touched;
   uint32_t *dkey[2], *dval[2];  // depth-sort ping-pong (final: index 0)
   uint32_t *offs, *offs_by_gid;
-  uint32_t* sorted_e;           // [cap] emission index per list position
-  uint32_t* sorted_g;           // [cap] Gaussian index per list position
+  uint2* sorted;                 // [cap] (emission index, Gaussian) per list position
   uint32_t* table;              // [ntiles][bblocks] counts, then segment starts
   uint32_t* status;             // decoupled look-back words
   uint32_t* hist;               // depth digit histograms [4][256]
@@ -74,7 +73,7 @@ struct CompositeArgs {
   int W, H, tw, th, tiles_x, D, feat_bf16;
   float bg[3];
   const uint2* ranges;
-  const uint32_t *sorted_e, *sorted_g;
+  const uint2* sorted;  // (emission index, Gaussian) per list position
   const float4* rec;
   const void* feat;
   float *out_rgb, *out_depth, *out_alpha, *out_feat;
@@ -97,7 +96,7 @@ struct DumpArgs {
   int64_t cap;
   int P, ntiles, HW;
   const void* hdr;
-  const uint32_t *sorted_e, *sorted_g;
+  const uint2* sorted;  // (emission index, Gaussian) per list position
   const uint2* ranges;
   const uint32_t* ncontrib;
   const float* tfinal;
