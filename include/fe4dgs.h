@@ -217,6 +217,52 @@ fe_status fe_l1_loss_grad(const float *pred, const float *target, int64_t n, int
 fe_status fe_l1_loss_grad_noalloc(const float *pred, const float *target, int64_t n, int64_t rows, float *grad,
                                   float *loss, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Semantic decoder (Sec. 3.3, Eq. 9): a pointwise (1x1) convolution of the
+ * rendered feature map from D to 256 channels,
+ *     out[p][c] = sum_d feat[p][d] * weight[c][d] + bias[c],
+ * with BF16 operands and FP32 accumulation on the tensor cores.  The map is
+ * channels-last, as fe_render_forward writes it; the decoder applies no
+ * spatial upsampling.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t HW;               /* pixels (rows of feat), 0 <= HW < 2^31 - 128 */
+  int D;                    /* feature channels: 32 or 64 (else FE_ERR_UNSUPPORTED) */
+  const void *feat;         /* [HW, D] bf16, row-major, 16-byte aligned */
+  const void *weight;       /* [256, D] bf16, row-major, 16-byte aligned */
+  const float *bias;        /* [256] float32 */
+} fe_decoder_args;
+
+/* Bytes of device workspace for the decoder calls: a 256-byte header whose
+ * first word collects device error bits, then per-CTA partial sums of the
+ * loss and of the weight and bias gradients.  0 for an unsupported D. */
+size_t fe_decoder_workspace_size(int64_t HW, int D);
+
+/* out [HW, 256] float32 (16-byte aligned) = the decoder applied to feat.
+ * Asynchronous on `stream`; the caller owns every buffer. */
+fe_status fe_decode_forward(const fe_decoder_args *args, float *out, void *workspace, size_t workspace_bytes,
+                            void *stream);
+
+/* Decoder, L1 feature loss (Eq. 10) and its reverse pass in one launch; the
+ * 256-channel output is never written to memory.  With S[p][c] =
+ * sign(out[p][c] - target[p][c]) (sign(0) = 0):
+ *     *loss        = scale * sum_{p,c} |out - target|
+ *     d_feat[p][d] = scale * sum_c S[p][c] weight[c][d]     [HW, D] float32
+ *     d_weight[c][d] = scale * sum_p S[p][c] feat[p][d]    [256, D] float32
+ *     d_bias[c]    = scale * sum_p S[p][c]                 [256] float32
+ * scale = 1/HW gives Eq. 10 (mean over pixels of the L1 norm over
+ * channels).  target: [HW, 256] row-major, bf16 if target_bf16 else
+ * float32, 16-byte aligned.  loss, d_weight, d_bias are device pointers;
+ * every output is overwritten.  Sums over pixels run in a fixed order, so
+ * results are bitwise reproducible.  Asynchronous on `stream`. */
+fe_status fe_decode_l1(const fe_decoder_args *args, const void *target, int target_bf16, float scale, float *loss,
+                       float *d_feat, float *d_weight, float *d_bias, void *workspace, size_t workspace_bytes,
+                       void *stream);
+
+/* Reads the device error bits of the last decoder call on this workspace
+ * (2 = a pipeline wait timed out).  Synchronises `stream`. */
+fe_status fe_decoder_read_errors(const void *workspace, uint32_t *err, void *stream);
+
 /* Measured single-precision FMA throughput: runs an FMA-chain kernel over
  * the whole GPU for `iters` iterations per thread and writes FLOP/s
  * (2 per FMA) to *flops (host).  Synchronous; used for the FP32 roofline. */

@@ -67,6 +67,10 @@ class fe_stats(ctypes.Structure):
                 ("device_errors", ctypes.c_uint32), ("has_forward", ctypes.c_int32)]
 
 
+class fe_decoder_args(ctypes.Structure):
+    _fields_ = [("HW", c_int64), ("D", c_int), ("feat", c_void_p), ("weight", c_void_p), ("bias", c_void_p)]
+
+
 _P = ctypes.POINTER
 _SIGNATURES = {
     "fe_workspace_size": [c_int, c_int, c_int, c_int, _P(fe_opts), _P(ctypes.c_size_t)],
@@ -84,6 +88,10 @@ _SIGNATURES = {
     "fe_l1_loss_grad_noalloc": [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p, c_void_p],
     "fe_count_pairs": [_P(fe_gaussians), _P(fe_camera), _P(fe_opts), c_void_p, ctypes.c_size_t, c_void_p,
                        c_void_p],
+    "fe_decode_forward": [_P(fe_decoder_args), c_void_p, c_void_p, ctypes.c_size_t, c_void_p],
+    "fe_decode_l1": [_P(fe_decoder_args), c_void_p, c_int, c_float, c_void_p, c_void_p, c_void_p, c_void_p,
+                     c_void_p, ctypes.c_size_t, c_void_p],
+    "fe_decoder_read_errors": [c_void_p, _P(ctypes.c_uint32), c_void_p],
 }
 
 _lib = None
@@ -100,6 +108,8 @@ def load():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = c_int
+        L.fe_decoder_workspace_size.argtypes = [c_int64, c_int]
+        L.fe_decoder_workspace_size.restype = ctypes.c_size_t
         L.fe_status_string.argtypes = [c_int]
         L.fe_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -260,3 +270,40 @@ def fe_probe_fp32_peak(iters: int = 4096, stream=None) -> float:
     f = ctypes.c_double(0.0)
     _check("fe_probe_fp32_peak", load().fe_probe_fp32_peak(int(iters), ctypes.byref(f), _stream(stream)))
     return float(f.value)
+
+
+def make_decoder_args(feat, weight, bias, HW=None) -> fe_decoder_args:
+    """feat [HW, D] and weight [256, D] bf16 tensors, bias [256] float32."""
+    a = fe_decoder_args()
+    a.HW = int(feat.shape[0] if HW is None else HW)
+    a.D = int(weight.shape[1])
+    a.feat = feat.data_ptr() if feat is not None and feat.numel() else None
+    a.weight = weight.data_ptr()
+    a.bias = bias.data_ptr()
+    return a
+
+
+def fe_decoder_workspace_size(HW: int, D: int) -> int:
+    return int(load().fe_decoder_workspace_size(int(HW), int(D)))
+
+
+def fe_decode_forward(args: fe_decoder_args, out, workspace, stream=None):
+    rc = load().fe_decode_forward(ctypes.byref(args), _ptr(out), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _stream(stream))
+    _check("fe_decode_forward", rc)
+
+
+def fe_decode_l1(args: fe_decoder_args, target, scale: float, loss, d_feat, d_weight, d_bias, workspace,
+                 stream=None):
+    import torch
+    rc = load().fe_decode_l1(ctypes.byref(args), _ptr(target), int(target.dtype == torch.bfloat16), float(scale),
+                             _ptr(loss), _ptr(d_feat), _ptr(d_weight), _ptr(d_bias), _ptr(workspace),
+                             workspace.numel() * workspace.element_size(), _stream(stream))
+    _check("fe_decode_l1", rc)
+
+
+def fe_decoder_read_errors(workspace, stream=None) -> int:
+    e = ctypes.c_uint32(0)
+    _check("fe_decoder_read_errors", load().fe_decoder_read_errors(_ptr(workspace), ctypes.byref(e),
+                                                                    _stream(stream)))
+    return int(e.value)

@@ -196,6 +196,15 @@ def make_targets(height: int, width: int, D: int, seed: int = 2, dec_channels: i
     return rgb, feat
 
 
+def make_decoder(D: int, cout: int = 256, seed: int = 3, w_std: float = 0.05, b_std: float = 0.0):
+    """1x1 decoder parameters: weight [cout, D] N(0, w_std) rounded to bf16
+    values (float32 array), bias [cout] N(0, b_std)."""
+    rng = np.random.default_rng(seed)
+    w = bf16_round(rng.normal(0.0, w_std, (cout, D)).astype(np.float32))
+    b = rng.normal(0.0, b_std, cout).astype(np.float32) if b_std > 0 else np.zeros(cout, np.float32)
+    return w, b
+
+
 # Workload presets.  Sizes and distributions are the ones stated for each
 # workload; names describe what they are.
 CONFIGS = {

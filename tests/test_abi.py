@@ -78,3 +78,21 @@ def test_workspace_grows_with_capacity_and_backward(lib):
     b = _lib.fe_workspace_size(5000, 32, 320, 256, _lib.make_opts(max_dups=200000))
     c = _lib.fe_workspace_size(5000, 32, 320, 256, _lib.make_opts(max_dups=200000, forward_only=True))
     assert b > a > c
+
+
+def test_decoder_host_side_status_codes(lib):
+    # Argument checks of the decoder entry points return before any CUDA call.
+    assert lib.fe_decoder_workspace_size(1000, 16) == 0          # D not supported by the decoder
+    assert lib.fe_decoder_workspace_size(-1, 32) == 0
+    a = _lib.fe_decoder_args()
+    a.HW, a.D, a.feat, a.weight, a.bias = 1000, 16, 16, 16, 16
+    args = [None, 0, 1.0, None, None, None, None, None, 0, None]
+    assert lib.fe_decode_l1(ctypes.byref(a), *args) == 4         # FE_ERR_UNSUPPORTED
+    assert lib.fe_decode_forward(ctypes.byref(a), None, None, 0, None) == 4
+    a.D = 32
+    a.weight = 8                                                   # not 16-byte aligned
+    assert lib.fe_decode_l1(ctypes.byref(a), *args) == 1
+    a.weight, a.HW = 16, -5
+    assert lib.fe_decode_forward(ctypes.byref(a), None, None, 0, None) == 1
+    assert lib.fe_decode_l1(None, *args) == 1
+    assert lib.fe_decoder_read_errors(None, None, None) == 1
