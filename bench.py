@@ -34,6 +34,16 @@ WORKLOAD = "endonerf_200k_640x512"
 SMS = 152
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak():
+    """(GB/s, basis) from the measured copy bandwidth next to this file."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
 
 
 def parse():
@@ -130,6 +140,7 @@ def run_ours(args, world, rank, local):
     import torch
 
     from paper_2503_06161_gb300 import _lib, synth
+    from paper_2503_06161_gb300.decoder import Decoder
     from paper_2503_06161_gb300.raster import DeformField, GaussianScene, Rasterizer, camera_struct
 
     torch.cuda.set_device(local)
@@ -147,9 +158,17 @@ def run_ours(args, world, rank, local):
     deform = DeformField.from_numpy(df_np, dev) if df_np is not None else None
     C = df_np.C if df_np is not None else 0
     cam = camera_struct(cam_np)
-    rgb_t_np, feat_t_np = synth.make_targets(H, W, D, seed=2)
+    dec_ch = int(cfg.get("decoder", 0))
+    rgb_t_np, feat_t_np = synth.make_targets(H, W, D, seed=2, dec_channels=dec_ch)
     tgt_rgb = torch.as_tensor(rgb_t_np, device=dev)
     tgt_feat = torch.as_tensor(feat_t_np, device=dev)
+    dec = None
+    if dec_ch:
+        # Decoder workloads: the L1 feature loss is taken on the 256-channel
+        # decoder output against bf16 targets (Eq. 9-10).
+        w_np, b_np = synth.make_decoder(D, seed=3)
+        dec = Decoder(torch.as_tensor(w_np).to(torch.bfloat16).to(dev), torch.as_tensor(b_np).to(dev))
+        tgt_feat = tgt_feat.to(torch.bfloat16)
 
     # Capacity: size the duplicate list from a probe forward (+25%); the
     # timed loop then runs without any host synchronisation.
@@ -163,17 +182,34 @@ def run_ours(args, world, rank, local):
     out = (torch.empty(3, H, W, **kw), torch.empty(H, W, **kw), torch.empty(H, W, **kw), torch.empty(HW, D, **kw))
     g_rgb = torch.empty(3, H, W, **kw)
     g_feat = torch.empty(HW, D, **kw)
+    feat_bf = torch.empty(HW, D, dtype=torch.bfloat16, device=dev) if dec is not None else None
+    dec_out = None
+    if dec is not None:
+        dec.workspace(HW)
+        dec_out = (torch.empty(1, **kw), g_feat, torch.empty(256, D, **kw), torch.empty(256, **kw))
     losses = torch.zeros(2, **kw)
     scratch = torch.empty(2048, **kw)
     grads = dict(means=torch.empty(P, 3, **kw), log_scales=torch.empty(P, 3, **kw), quats=torch.empty(P, 4, **kw),
                  opacity_logits=torch.empty(P, **kw), sh=torch.empty(P, 16, 3, **kw), feat=torch.empty(P, D, **kw))
     flush = torch.empty(L2_FLUSH_BYTES // 4, **kw)
 
-    def step(sc_obj=scene, df_obj=deform):
-        rast.forward(sc_obj, cam, df_obj, t, out=out)
+    def feat_loss(tgt, evs=None):
+        if dec is None:
+            _lib.fe_l1_loss_grad(out[3], tgt, HW, g_feat, losses[1:2], scratch[1024:])
+            return
+        if evs is not None:
+            evs[0].record(stream)
+        dec.l1(feat_bf, tgt, out=dec_out)
+        if evs is not None:
+            evs[1].record(stream)
+
+    def step(sc_obj=scene, df_obj=deform, evs=None):
+        rast.forward(sc_obj, cam, df_obj, t, out=out, feat_bf16=feat_bf)
         _lib.fe_l1_loss_grad(out[0], tgt_rgb, HW, g_rgb, losses[0:1], scratch[:1024])
-        _lib.fe_l1_loss_grad(out[3], tgt_feat, HW, g_feat, losses[1:2], scratch[1024:])
+        feat_loss(tgt_feat, evs)
         rast.backward(sc_obj, cam, df_obj, t, g_rgb, None, None, g_feat, grads=grads)
+
+    stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
         step()
@@ -186,8 +222,7 @@ def run_ours(args, world, rank, local):
 
     # ---- timed fwd+bwd loop: L2 flushed before every step, events per step
     K_steps = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(K_steps)]
-    stream = torch.cuda.current_stream()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(12)] for _ in range(K_steps)]
     for row in ev:
         for e in row:
             e.record(stream)
@@ -202,7 +237,7 @@ def run_ours(args, world, rank, local):
         flush.zero_()
         _lib.set_events(rast.opts, ev[i][1:9])
         ev[i][0].record(stream)
-        step()
+        step(evs=ev[i][10:12])
         ev[i][9].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -216,6 +251,8 @@ def run_ours(args, world, rank, local):
     stages = {n: statistics.mean(ev[i][a].elapsed_time(ev[i][b]) for i in range(K_steps))
               for n, (a, b) in zip(stage_names, bounds)}
     fwd_ms = statistics.mean(ev[i][1].elapsed_time(ev[i][4]) for i in range(K_steps))
+    if dec is not None:
+        stages["decoder_l1"] = statistics.mean(ev[i][10].elapsed_time(ev[i][11]) for i in range(K_steps))
     ms = statistics.mean(step_ms)
     if world > 1:
         tt = torch.tensor([ms], device=dev)
@@ -228,7 +265,7 @@ def run_ours(args, world, rank, local):
     for _ in range(max(3, K_steps)):
         flush.zero_()
         e0.record(stream)
-        rast.forward(scene, cam, deform, t, out=out)
+        rast.forward(scene, cam, deform, t, out=out, feat_bf16=feat_bf)
         e1.record(stream)
         torch.cuda.synchronize()
         fwd_only.append(e0.elapsed_time(e1))
@@ -252,6 +289,15 @@ def run_ours(args, world, rank, local):
         kern[n] = {"ms": round(stages[n], 4), "tflops": round(a, 3), "frac_of_alu_peak": round(a / alu_peak, 4)}
     for n in ("binning", "loss", "feat_grad"):
         kern[n] = {"ms": round(stages[n], 4)}
+    hbm, hbm_basis = hbm_peak()
+    if dec is not None:
+        # Algorithmic bytes of the fused decoder + L1 + reverse: feature map
+        # (bf16) and targets (bf16) read, d_feat (f32) written, weights.
+        dbytes = HW * (2 * D + 2 * dec_ch + 4 * D) + dec_ch * D * 2
+        gbs = dbytes / (stages["decoder_l1"] * 1e-3) / 1e9
+        kern["decoder_l1"] = {"ms": round(stages["decoder_l1"], 4), "gbs": round(gbs, 1),
+                              "frac_of_hbm_peak": round(gbs / hbm, 4), "bytes": int(dbytes),
+                              "peak_basis": hbm_basis}
     dom = max(work, key=lambda n: stages[n])
     ach = work[dom] / (stages[dom] * 1e-3) / 1e12
     roofline = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
@@ -285,9 +331,9 @@ def run_ours(args, world, rank, local):
         def e2e_step():
             for k, v in host.items():
                 dev_in[k].copy_(v, non_blocking=True)
-            rast.forward(sc_e, cam, df_e, t, out=out)
+            rast.forward(sc_e, cam, df_e, t, out=out, feat_bf16=feat_bf)
             _lib.fe_l1_loss_grad(out[0], dev_in["tgt_rgb"], HW, g_rgb, losses[0:1], scratch[:1024])
-            _lib.fe_l1_loss_grad(out[3], dev_in["tgt_feat"], HW, g_feat, losses[1:2], scratch[1024:])
+            feat_loss(dev_in["tgt_feat"])
             rast.backward(sc_e, cam, df_e, t, g_rgb, None, None, g_feat, grads=grads)
             for k, v in grads.items():
                 host_out[k].copy_(v, non_blocking=True)
@@ -309,15 +355,18 @@ def run_ours(args, world, rank, local):
     # forward: deform+project, depth histogram, 4 depth passes, count, table
     # scan, scatter, composite; L1 x2 (2 kernels each); reverse: composite,
     # feature sums, projection chain (+ deformation chain).
+    # (With a decoder, its kernel and fixed-order sum replace the two
+    # feature-L1 kernels.)
     launches_per_step = 10 + 4 + 3 + (1 if deform is not None else 0)
     result = {
         "metric": METRIC, "value": round(world * 1000.0 / ms, 3), "unit": "it/s", "n_gpus": world,
         "steps": K_steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dec is None else "f32 + bf16 mma (decoder)", "data": "synthetic",
         "config": {"workload": args.workload, "gaussians": P, "width": W, "height": H, "D": D,
                    "storage": "bf16 sh/feat" if bf16 else "f32",
                    "deform": f"hexplane 6x{df_np.R}^2x{C} + MLP {C}-64-64-11" if df_np is not None else "static",
-                   "t": t, "step": "deform+project+bin+sort+composite fwd, L1 rgb+feat, full reverse",
+                   "t": t, "step": "deform+project+bin+sort+composite fwd, L1 rgb+feat, full reverse"
+                   + (", feat L1 on the tensor-core decoder D->256 (fused fwd+loss+reverse)" if dec else ""),
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
         "fwd_fps": round(world * 1000.0 / fwd_only_ms, 2), "fwd_ms": round(fwd_only_ms, 4),
         "fwd_ms_in_step": round(fwd_ms, 4),

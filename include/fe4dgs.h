@@ -108,9 +108,12 @@ typedef struct {
 
 /* Render outputs (Eq. 7-8 plus depth): rgb [3,H,W] planar = sum w c + bg T;
  * depth [H,W] = sum w z_cam (not normalised); alpha [H,W] = 1 - T_final;
- * feat [H*W, D] channels-last = sum w z. */
+ * feat [H*W, D] channels-last = sum w z.  feat_bf16 (optional, NULL = not
+ * written; 16-byte aligned): the same map rounded to bf16 (nearest even),
+ * the operand layout of the decoder. */
 typedef struct {
   float *rgb, *depth, *alpha, *feat;
+  void *feat_bf16;
 } fe_outputs;
 
 /* Upstream gradients, same shapes as fe_outputs; any may be NULL (= zero). */

@@ -50,7 +50,8 @@ class fe_opts(ctypes.Structure):
 
 
 class fe_outputs(ctypes.Structure):
-    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("alpha", c_void_p), ("feat", c_void_p)]
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("alpha", c_void_p), ("feat", c_void_p),
+                ("feat_bf16", c_void_p)]
 
 
 class fe_output_grads(ctypes.Structure):
@@ -187,8 +188,8 @@ def fe_workspace_size(P: int, D: int, width: int, height: int, opts: fe_opts) ->
 
 
 def fe_render_forward(g: fe_gaussians, deform, cam: fe_camera, t: float, opts: fe_opts, workspace, rgb, depth,
-                      alpha, feat, stream=None):
-    out = fe_outputs(_ptr(rgb), _ptr(depth), _ptr(alpha), _ptr(feat))
+                      alpha, feat, stream=None, feat_bf16=None):
+    out = fe_outputs(_ptr(rgb), _ptr(depth), _ptr(alpha), _ptr(feat), _ptr(feat_bf16))
     rc = load().fe_render_forward(ctypes.byref(g), ctypes.byref(deform) if deform is not None else None,
                                   ctypes.byref(cam), float(t), ctypes.byref(opts), _ptr(workspace),
                                   workspace.numel() * workspace.element_size(), ctypes.byref(out), _stream(stream))

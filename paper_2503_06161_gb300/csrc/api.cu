@@ -197,6 +197,7 @@ fe_status fe_render_forward(const fe_gaussians* g, const fe_deform* deform, cons
                             void* stream) {
   if (!g || !cam || !out || !workspace) return FE_ERR_INVALID_ARG;
   if (!out->rgb || !out->depth || !out->alpha || !out->feat || !aligned16(out->feat)) return FE_ERR_INVALID_ARG;
+  if (out->feat_bf16 && !aligned16(out->feat_bf16)) return FE_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return FE_ERR_INVALID_ARG;
   Layout L;
   float bg[3];
@@ -218,6 +219,7 @@ fe_status fe_render_forward(const fe_gaussians* g, const fe_deform* deform, cons
   c.out_depth = out->depth;
   c.out_alpha = out->alpha;
   c.out_feat = out->feat;
+  c.out_feat_bf16 = static_cast<uint16_t*>(out->feat_bf16);
   FE_TRY_CUDA(launch_composite_fwd(c, st));
   FE_TRY_CUDA(mark(opts, 3, st));
   return FE_OK;

@@ -192,6 +192,19 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
     float4* fo = reinterpret_cast<float4*>(a.out_feat + p * D);
 #pragma unroll
     for (int d4 = 0; d4 < D / 4; ++d4) fo[d4] = make_float4(F[2 * d4].x, F[2 * d4].y, F[2 * d4 + 1].x, F[2 * d4 + 1].y);
+    if (a.out_feat_bf16) {
+      uint4* fb = reinterpret_cast<uint4*>(a.out_feat_bf16 + p * D);
+#pragma unroll
+      for (int q = 0; q < D / 8; ++q) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(F[4 * q + e].x, F[4 * q + e].y);
+          w4[e] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        fb[q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+      }
+    }
     a.t_final[p] = T;
     a.n_contrib[p] = last;
   }

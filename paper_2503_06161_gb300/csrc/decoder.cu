@@ -5,10 +5,22 @@
 // of Eq. 10 and its reverse pass.
 //
 // One persistent CTA per SM walks 128-pixel tiles.  Warp roles:
-//   warps 0-3  epilogue: tensor memory -> registers (one pixel row per
-//              thread), bias, L1 against the staged target, sign -> S tile
-//   warp 4     producer: TMA tile loads of W (once), F tiles and targets
-//   warp 5     tensor-core issue (one thread) and tensor-memory allocation
+//   warps 0-7  epilogue: tensor memory -> registers (one pixel row per
+//              thread; warps w and w+4 share the rows of lane quarter w and
+//              take channels 0-127 and 128-255), bias, L1 against the staged
+//              target, sign -> S tile written over the target it replaces
+//   warp 8     tensor-core issue (one thread) and tensor-memory allocation
+//   warp 9     TMA loads of W (once) and the F tiles
+//   warps 10-11  TMA loads of the targets of channels 0-127 / 128-255
+//              (separate warps, so that no producer waits behind another's
+//              barrier)
+// The staged target box of 64 bf16 channels x 128 rows has exactly the
+// layout of a 64-channel S panel (128-byte rows, 128B swizzle), so each
+// epilogue thread overwrites its row of targets with its row of signs and
+// the reverse products read S from the target buffer.  Two tile buffers
+// alternate: the epilogue fills tile i+1 while the tensor cores run the
+// reverse products of tile i, and the first product of tile i+1 is issued
+// ahead of the reverse products of tile i.
 // Per tile the MMAs are
 //   acc[p][c]  = sum_d F[p][d] W[c][d]                   (K = D)
 //   dF[p][d]   = sum_c S[p][c] W[c][d]                   (K = 256)
@@ -29,10 +41,12 @@ namespace {
 
 constexpr int kDecN = 256;        // output channels
 constexpr int kDecBM = 128;       // pixels per tile (MMA M)
-constexpr int kDecThreads = 192;  // 4 epilogue warps, producer warp, MMA warp
-constexpr int kTStages = 4;       // target ring depth
-constexpr uint32_t kBoxBytes = 16384;  // one target box: 128 rows x 128 bytes
-constexpr uint32_t kPanel = 16384;     // one S panel: 128 rows x 64 bf16 channels
+constexpr int kEpiWarps = 8;
+constexpr int kWarpMma = kEpiWarps, kWarpF = kEpiWarps + 1, kWarpT0 = kEpiWarps + 2;
+constexpr int kDecThreads = 32 * (kEpiWarps + 4);
+constexpr uint32_t kBoxBytes = 16384;   // one target box: 128 rows x 128 bytes
+constexpr int kTSlots = 8;               // boxes staged: 2 tiles (bf16) or 1 tile (fp32)
+constexpr uint32_t kTBufBytes = 65536;   // one tile buffer of bf16 targets
 constexpr uint32_t kTmemCols = 512;
 // Tensor-memory columns of the accumulators.
 constexpr uint32_t kColAcc = 0, kColDF = 256, kColDW = 320, kColDB = 448;
@@ -51,16 +65,16 @@ struct DecCfg {
   static constexpr uint32_t f_bytes = kDecBM * row_bytes;
   static constexpr uint32_t off_w = 0;
   static constexpr uint32_t off_f = off_w + w_bytes;      // 2 stages
-  static constexpr uint32_t off_s = off_f + 2 * f_bytes;  // 4 panels
-  static constexpr uint32_t off_t = off_s + 4 * kPanel;   // target ring
-  static constexpr uint32_t off_ones = off_t + kTStages * kBoxBytes;
-  static constexpr uint32_t off_bias = off_ones + 4096;
+  static constexpr uint32_t off_t = off_f + 2 * f_bytes;  // target boxes / S panels
+  static constexpr uint32_t off_ones = off_t + kTSlots * kBoxBytes;
+  static constexpr uint32_t off_bias = off_ones + 512;  // one 16 x 16 all-ones operand
   static constexpr uint32_t off_bar = off_bias + kDecN * 4;
   static constexpr uint32_t bytes = off_bar + 256;
   static constexpr size_t launch_bytes = bytes + 1024;  // slack for 1024-byte alignment
   static_assert(D == 32 || D == 64, "decoder feature width");
-  static_assert(off_f % 1024 == 0 && off_s % 1024 == 0 && off_t % 1024 == 0 && off_ones % 1024 == 0,
+  static_assert(off_f % 1024 == 0 && off_t % 1024 == 0,
                 "swizzled operands need 1024-byte aligned buffers");
+  static_assert(launch_bytes <= 232448, "shared memory per block");
 };
 
 struct DecArgs {
@@ -78,8 +92,8 @@ struct DecArgs {
 
 // Barrier slots (8 bytes each) after off_bar.
 enum : int {
-  kBarW = 0, kBarFFull = 1, kBarFEmpty = 3, kBarTFull = 5, kBarTEmpty = 9, kBarAccFull = 13, kBarAccEmpty = 14,
-  kBarSFull = 15, kBarBwd = 16, kBarDrain = 17, kNumBars = 18
+  kBarW = 0, kBarFFull = 1, kBarFEmpty = 3, kBarTFull = 5, kBarTEmpty = kBarTFull + kTSlots,
+  kBarAccFull = kBarTEmpty + 2, kBarAccEmpty, kBarSFull, kBarBwd, kBarDrain, kNumBars
 };
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint64_t layout) {
@@ -141,7 +155,42 @@ __device__ __forceinline__ void tmem_ld1(uint32_t taddr, uint32_t& v) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr) : "memory");
 }
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Completes this thread's outstanding tensor-memory loads.  The registers
+// of the load are in/out operands so that no use of them is scheduled
+// before the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]), "+r"(v[8]),
+        "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]),
+        "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]),
+        "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+      :
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld1(uint32_t& v) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(v) : : "memory");
+}
+
+// 16 consecutive columns (x16 shape).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// Packed bf16 signs of two differences: +-1.0 (0x3F80 | sign bit) per half,
+// 0 where the difference is 0 or the row is masked.
+__device__ __forceinline__ uint32_t sign_pair_bf16(float2 d, bool valid) {
+  const uint32_t hi = __byte_perm(__float_as_uint(d.x), __float_as_uint(d.y), 0x7632);
+  const uint32_t s = (hi & 0x80008000u) | 0x3F803F80u;
+  const uint32_t keep = (d.x != 0.0f ? 0x0000FFFFu : 0u) | (d.y != 0.0f ? 0xFFFF0000u : 0u);
+  return valid ? (s & keep) : 0u;
+}
 
 __device__ __forceinline__ bool dec_wait(uint64_t* bar, uint32_t parity, volatile int* abort, uint32_t* err) {
   if (*abort) return false;
@@ -157,8 +206,11 @@ __global__ void __launch_bounds__(kDecThreads, 1)
                    const __grid_constant__ CUtensorMap tm_t, const DecArgs a) {
   using C = DecCfg<D>;
   constexpr bool kL1 = MODE != kDecForward;
-  constexpr int kBoxCh = MODE == kDecL1F32 ? 32 : 64;  // target channels per box
-  constexpr int kNumBoxes = kDecN / kBoxCh;
+  constexpr bool kTF32 = MODE == kDecL1F32;
+  constexpr int kBoxCh = kTF32 ? 32 : 64;         // target channels per box
+  constexpr int kNumBoxes = kDecN / kBoxCh;       // boxes per tile
+  constexpr int kBufs = kTF32 ? 1 : 2;            // tile buffers
+  constexpr uint32_t kPanel = kTF32 ? 2 * kBoxBytes : kBoxBytes;  // S panel stride
   extern __shared__ unsigned char dsmem_raw[];
   // Swizzled operands are addressed by shared-memory address bits: align the
   // working base to 1024 bytes.
@@ -168,36 +220,37 @@ __global__ void __launch_bounds__(kDecThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::off_bar);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + C::off_bar + kNumBars * 8);
   volatile int* s_abort = reinterpret_cast<volatile int*>(sm + C::off_bar + kNumBars * 8 + 4);
-  float* s_red = reinterpret_cast<float*>(sm + C::off_bar + kNumBars * 8 + 8);  // [4]
+  float* s_red = reinterpret_cast<float*>(sm + C::off_bar + kNumBars * 8 + 8);  // [8]
   float* s_bias = reinterpret_cast<float*>(sm + C::off_bias);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // Tiles of this CTA: blockIdx.x + i * gridDim.x for i < n_mine.
+  const int n_mine = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (tid == 0) {
     mbar_init(&bars[kBarW], 1);
     for (int s = 0; s < 2; ++s) {
       mbar_init(&bars[kBarFFull + s], 1);
       mbar_init(&bars[kBarFEmpty + s], 1);
+      mbar_init(&bars[kBarTEmpty + s], 1);  // tensor-core commit after the reverse products
     }
-    for (int s = 0; s < kTStages; ++s) {
-      mbar_init(&bars[kBarTFull + s], 1);
-      mbar_init(&bars[kBarTEmpty + s], 4);
-    }
+    for (int s = 0; s < kTSlots; ++s) mbar_init(&bars[kBarTFull + s], 1);
     mbar_init(&bars[kBarAccFull], 1);
-    mbar_init(&bars[kBarAccEmpty], 4);
-    mbar_init(&bars[kBarSFull], 4);
+    mbar_init(&bars[kBarAccEmpty], kEpiWarps);
+    mbar_init(&bars[kBarSFull], kEpiWarps);
     mbar_init(&bars[kBarBwd], 1);
     mbar_init(&bars[kBarDrain], 1);
     *s_abort = 0;
     mbar_init_fence();
   }
-  if (warp < 4) {
+  if (warp < kEpiWarps) {
     // All-ones B operand of the bias-gradient product, and the bias.
     uint4* ones = reinterpret_cast<uint4*>(sm + C::off_ones);
-    for (int i = tid; i < 4096 / 16; i += 128) ones[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
-    for (int i = tid; i < kDecN; i += 128) s_bias[i] = a.bias[i];
+    for (int i = tid; i < 512 / 16; i += 32 * kEpiWarps)
+      ones[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    for (int i = tid; i < kDecN; i += 32 * kEpiWarps) s_bias[i] = a.bias[i];
     fence_proxy_async();
   }
-  if (warp == 5) {
+  if (warp == kWarpMma) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
                  "r"(kTmemCols)
                  : "memory");
@@ -208,69 +261,85 @@ __global__ void __launch_bounds__(kDecThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
 
-  if (warp == 4) {
-    // ---------------- producer ----------------
+  if (warp == kWarpF) {
+    // ---------------- W (once) and F tiles ----------------
     if (lane == 0) {
-      uint32_t f_uses = 0, t_uses = 0;
+      uint32_t f_uses = 0;
       mbar_arrive_expect_tx(&bars[kBarW], C::w_bytes);
       tma_2d(sm + C::off_w, &tm_w, 0, 0, &bars[kBarW]);
-      uint32_t i = 0;
-      for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++i) {
+      for (int i = 0; i < n_mine; ++i) {
         const int f = i & 1;
         if (!dec_wait(&bars[kBarFEmpty + f], ((i >> 1) & 1) ^ 1, s_abort, a.err)) break;
         mbar_arrive_expect_tx(&bars[kBarFFull + f], C::f_bytes);
-        tma_2d(sm + C::off_f + f * C::f_bytes, &tm_f, 0, tile * kDecBM, &bars[kBarFFull + f]);
+        tma_2d(sm + C::off_f + f * C::f_bytes, &tm_f, 0, ((int)blockIdx.x + i * (int)gridDim.x) * kDecBM,
+               &bars[kBarFFull + f]);
         ++f_uses;
-        if (kL1) {
-          bool ok = true;
-          for (int b = 0; b < kNumBoxes; ++b, ++t_uses) {
-            const uint32_t r = t_uses % kTStages;
-            if (!dec_wait(&bars[kBarTEmpty + r], ((t_uses / kTStages) & 1) ^ 1, s_abort, a.err)) {
-              ok = false;
-              break;
-            }
-            mbar_arrive_expect_tx(&bars[kBarTFull + r], kBoxBytes);
-            tma_2d(sm + C::off_t + r * kBoxBytes, &tm_t, b * kBoxCh, tile * kDecBM, &bars[kBarTFull + r]);
-          }
-          if (!ok) break;
-        }
       }
       // Every copy issued must have landed before the block leaves.
       for (uint32_t u = f_uses > 2 ? f_uses - 2 : 0; u < f_uses; ++u)
         if (!mbar_wait(&bars[kBarFFull + (u & 1)], (u >> 1) & 1)) set_err(a.err, kErrTimeout);
-      for (uint32_t u = t_uses > kTStages ? t_uses - kTStages : 0; u < t_uses; ++u)
-        if (!mbar_wait(&bars[kBarTFull + u % kTStages], (u / kTStages) & 1)) set_err(a.err, kErrTimeout);
       if (!mbar_wait(&bars[kBarW], 0)) set_err(a.err, kErrTimeout);
     }
-  } else if (warp == 5) {
+  } else if (warp >= kWarpT0) {
+    // ---------------- targets of one channel half ----------------
+    if (kL1 && lane == 0) {
+      const int h = warp - kWarpT0;
+      int issued = 0;
+      for (int i = 0; i < n_mine; ++i) {
+        const int buf = i % kBufs;
+        const int use = i / kBufs;  // uses of this buffer so far
+        if (!dec_wait(&bars[kBarTEmpty + buf], (use & 1) ^ 1, s_abort, a.err)) break;
+        for (int b = h * (kNumBoxes / 2); b < (h + 1) * (kNumBoxes / 2); ++b) {
+          const int slot = buf * kNumBoxes + b;
+          mbar_arrive_expect_tx(&bars[kBarTFull + slot], kBoxBytes);
+          tma_2d(sm + C::off_t + slot * kBoxBytes, &tm_t, b * kBoxCh,
+                 ((int)blockIdx.x + i * (int)gridDim.x) * kDecBM, &bars[kBarTFull + slot]);
+        }
+        issued = i + 1;
+      }
+      // Every copy issued must have landed before the block leaves.
+      for (int i = issued > kBufs ? issued - kBufs : 0; i < issued; ++i)
+        for (int b = h * (kNumBoxes / 2); b < (h + 1) * (kNumBoxes / 2); ++b)
+          if (!mbar_wait(&bars[kBarTFull + (i % kBufs) * kNumBoxes + b], (i / kBufs) & 1))
+            set_err(a.err, kErrTimeout);
+    }
+  } else if (warp == kWarpMma) {
     // ---------------- tensor-core issue ----------------
     if (lane == 0) {
-      const uint32_t s_w = sb + C::off_w, s_s = sb + C::off_s, s_ones = sb + C::off_ones;
+      const uint32_t s_w = sb + C::off_w, s_t = sb + C::off_t, s_ones = sb + C::off_ones;
       constexpr uint32_t id_fwd = mma_idesc(128, kDecN, 0, 0);
       constexpr uint32_t id_df = mma_idesc(128, D, 0, 1);
       constexpr uint32_t id_dw = mma_idesc(128, D, 1, 1);
       constexpr uint32_t id_db = mma_idesc(128, 16, 1, 1);
-      bool ok = dec_wait(&bars[kBarW], 0, s_abort, a.err);
-      uint32_t i = 0;
-      for (int tile = blockIdx.x; ok && tile < a.ntiles; tile += gridDim.x, ++i) {
+      // acc = F W^T: A = F (K-major), B = W (K-major); 16 channels of K are
+      // 32 bytes along each swizzled row.
+      auto forward = [&](int i) -> bool {
         const int f = i & 1;
-        const uint32_t s_f = sb + C::off_f + f * C::f_bytes;
-        if (!dec_wait(&bars[kBarFFull + f], (i >> 1) & 1, s_abort, a.err)) break;
-        if (i > 0 && !dec_wait(&bars[kBarAccEmpty], (i - 1) & 1, s_abort, a.err)) break;
+        if (!dec_wait(&bars[kBarFFull + f], (i >> 1) & 1, s_abort, a.err)) return false;
+        if (i > 0 && !dec_wait(&bars[kBarAccEmpty], (i - 1) & 1, s_abort, a.err)) return false;
         tc_fence_after();
-        // acc = F W^T: A = F (K-major), B = W (K-major); 16 channels of K
-        // are 32 bytes along each swizzled row.
+        const uint32_t s_f = sb + C::off_f + f * C::f_bytes;
 #pragma unroll
         for (int k = 0; k < D / 16; ++k)
           mma_bf16(tmem + kColAcc, smem_desc(s_f + 32 * k, 16, C::sbo, C::layout),
                    smem_desc(s_w + 32 * k, 16, C::sbo, C::layout), id_fwd, k > 0);
         mma_commit(&bars[kBarAccFull]);
+        return true;
+      };
+      bool ok = dec_wait(&bars[kBarW], 0, s_abort, a.err) && (n_mine == 0 || forward(0));
+      for (int i = 0; ok && i < n_mine; ++i) {
+        const int f = i & 1;
         if (!kL1) {
           mma_commit(&bars[kBarFEmpty + f]);
+          if (i + 1 < n_mine && !forward(i + 1)) break;
           continue;
         }
+        // The next tile's forward product goes ahead of this tile's reverse.
+        if (i + 1 < n_mine && !forward(i + 1)) break;
         if (!dec_wait(&bars[kBarSFull], i & 1, s_abort, a.err)) break;
         tc_fence_after();
+        const uint32_t s_s = s_t + (i % kBufs) * kTBufBytes;  // S panels of this tile
+        const uint32_t s_f = sb + C::off_f + f * C::f_bytes;
         // dF = S W: A = S (K-major, 128B swizzle, 64-channel panels),
         // B = W read MN-major (K = channel rows, N = D along each row).
 #pragma unroll
@@ -287,11 +356,12 @@ __global__ void __launch_bounds__(kDecThreads, 1)
             const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
             mma_bf16(tmem + kColDW + 64 * h, ad, smem_desc(s_f + k * 16 * C::row_bytes, 16, C::sbo, C::layout),
                      id_dw, acc);
-            mma_bf16(tmem + kColDB + 16 * h, ad, smem_desc(s_ones + k * 512, 256, 128, kLayoutNone), id_db, acc);
+            mma_bf16(tmem + kColDB + 16 * h, ad, smem_desc(s_ones, 256, 128, kLayoutNone), id_db, acc);
           }
         }
         mma_commit(&bars[kBarBwd]);
         mma_commit(&bars[kBarFEmpty + f]);
+        mma_commit(&bars[kBarTEmpty + (i % kBufs)]);
       }
       // Drain: every issued tensor-core operation completes before the
       // accumulators are read or freed.
@@ -299,156 +369,171 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       if (!mbar_wait(&bars[kBarDrain], 0)) set_err(a.err, kErrTimeout);
     }
   } else {
-    // ---------------- epilogue: warps 0-3, one pixel row per thread ----------------
-    const int r = tid;  // tile row = tensor-memory lane
-    const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+    // ---------------- epilogue: warps 0-7, one pixel row per thread ----------------
+    const int q = warp & 3, h = warp >> 2;  // lane quarter, channel half
+    const int r = q * 32 + lane;            // tile row = tensor-memory lane
+    const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
     float loss = 0.0f;
-    uint32_t t_uses = 0;
-    uint32_t i = 0;
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++i) {
-      if (!dec_wait(&bars[kBarAccFull], i & 1, s_abort, a.err)) break;
+    // This half's D/2 columns of dF for the rows of tile j, scaled, to d_feat.
+    auto store_df = [&](int j) {
+      const int64_t pj = ((int64_t)blockIdx.x + (int64_t)j * gridDim.x) * kDecBM + r;
+      uint32_t v[32];
+      if (D == 32) tmem_ld16(t_row + kColDF + 16 * h, v);
+      else tmem_ld32(t_row + kColDF + 32 * h, v);
+      tmem_wait_ld(v);
+      if (pj < a.HW) {
+        float4* o = reinterpret_cast<float4*>(a.d_feat + pj * D + (D / 2) * h);
+#pragma unroll
+        for (int e = 0; e < D / 8; ++e)
+          o[e] = make_float4(a.scale * __uint_as_float(v[4 * e]), a.scale * __uint_as_float(v[4 * e + 1]),
+                             a.scale * __uint_as_float(v[4 * e + 2]), a.scale * __uint_as_float(v[4 * e + 3]));
+      }
+    };
+    int i = 0;
+    bool ok = true;
+    for (; i < n_mine; ++i) {
+      if (!dec_wait(&bars[kBarAccFull], i & 1, s_abort, a.err)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
-      const int64_t p = (int64_t)tile * kDecBM + r;
+      const int64_t p = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * kDecBM + r;
       const bool valid = p < a.HW;
-      bool ok = true;
-#pragma unroll 1
-      for (int ch = 0; ch < kDecN / 32; ++ch) {
-        uint32_t v[32];
-        tmem_ld32(t_row + kColAcc + 32 * ch, v);
-        tmem_wait_ld();
+      unsigned char* tbuf = sm + C::off_t + (i % kBufs) * kTBufBytes;
+      // Four 32-channel chunks; the load of chunk c+1 is in flight while
+      // chunk c is processed.
+      uint32_t va[32], vb[32];
+      tmem_ld32(t_row + kColAcc + 32 * (4 * h), va);
+      tmem_wait_ld(va);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint32_t(&cur)[32] = (c & 1) ? vb : va;
+        uint32_t(&nxt)[32] = (c & 1) ? va : vb;
+        if (c > 0) tmem_wait_ld(cur);
+        if (c < 3) tmem_ld32(t_row + kColAcc + 32 * (4 * h + c + 1), nxt);
+        const int ch = 4 * h + c;
+        const float2* bias2 = reinterpret_cast<const float2*>(s_bias + 32 * ch);
         if (!kL1) {
           if (valid) {
             float4* o = reinterpret_cast<float4*>(a.out + p * kDecN + 32 * ch);
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-              o[q] = make_float4(__uint_as_float(v[4 * q]) + s_bias[32 * ch + 4 * q],
-                                 __uint_as_float(v[4 * q + 1]) + s_bias[32 * ch + 4 * q + 1],
-                                 __uint_as_float(v[4 * q + 2]) + s_bias[32 * ch + 4 * q + 2],
-                                 __uint_as_float(v[4 * q + 3]) + s_bias[32 * ch + 4 * q + 3]);
+            for (int e = 0; e < 8; ++e) {
+              const float2 lo = __fadd2_rn(make_float2(__uint_as_float(cur[4 * e]), __uint_as_float(cur[4 * e + 1])),
+                                           bias2[2 * e]);
+              const float2 hi = __fadd2_rn(
+                  make_float2(__uint_as_float(cur[4 * e + 2]), __uint_as_float(cur[4 * e + 3])), bias2[2 * e + 1]);
+              o[e] = make_float4(lo.x, lo.y, hi.x, hi.y);
+            }
           }
           continue;
         }
-        const bool first = MODE == kDecL1F32 || (ch & 1) == 0;
-        const bool last = MODE == kDecL1F32 || (ch & 1) == 1;
-        const uint32_t slot = t_uses % kTStages;
-        if (first && !dec_wait(&bars[kBarTFull + slot], (t_uses / kTStages) & 1, s_abort, a.err)) {
+        // Target box of this chunk and its row r (128-byte rows, 16-byte
+        // chunks permuted by row & 7).
+        const int box = kTF32 ? ch : ch >> 1;
+        if ((kTF32 || (c & 1) == 0) &&
+            !dec_wait(&bars[kBarTFull + (i % kBufs) * kNumBoxes + box], (i / kBufs) & 1, s_abort, a.err))
           ok = false;
-          break;
-        }
-        // Target row r of the staged box (128-byte rows, 16-byte chunks
-        // permuted by row & 7).
-        const unsigned char* trow = sm + C::off_t + slot * kBoxBytes + r * 128;
-        float t[32];
-        if (MODE == kDecL1F32) {
+        const unsigned char* trow = tbuf + box * kBoxBytes + r * 128;
+        float2 t2[16];
+        if (kTF32) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const float4 x = *reinterpret_cast<const float4*>(trow + ((q ^ (r & 7)) << 4));
-            t[4 * q] = x.x; t[4 * q + 1] = x.y; t[4 * q + 2] = x.z; t[4 * q + 3] = x.w;
+          for (int e = 0; e < 8; ++e) {
+            const float4 x = *reinterpret_cast<const float4*>(trow + ((e ^ (r & 7)) << 4));
+            t2[2 * e] = make_float2(x.x, x.y);
+            t2[2 * e + 1] = make_float2(x.z, x.w);
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint4 x = *reinterpret_cast<const uint4*>(trow + (((4 * (ch & 1) + q) ^ (r & 7)) << 4));
+          for (int e = 0; e < 4; ++e) {
+            const uint4 x = *reinterpret_cast<const uint4*>(trow + (((4 * (c & 1) + e) ^ (r & 7)) << 4));
             const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              t[8 * q + 2 * e] = __uint_as_float(w4[e] << 16);
-              t[8 * q + 2 * e + 1] = __uint_as_float(w4[e] & 0xFFFF0000u);
-            }
+            for (int k = 0; k < 4; ++k)
+              t2[4 * e + k] = make_float2(__uint_as_float(w4[k] << 16), __uint_as_float(w4[k] & 0xFFFF0000u));
           }
         }
         uint32_t sg[16];
         float part = 0.0f;
 #pragma unroll
-        for (int c2 = 0; c2 < 16; ++c2) {
-          uint32_t h2 = 0;
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int c = 2 * c2 + e;
-            const float d = __uint_as_float(v[c]) + s_bias[32 * ch + c] - t[c];
-            part += fabsf(d);
-            // sign(d) in bf16: +-1.0 (0x3F80 | sign bit), 0 for d == 0.
-            const uint32_t s16 = d != 0.0f ? (((__float_as_uint(d) >> 16) & 0x8000u) | 0x3F80u) : 0u;
-            h2 |= (valid ? s16 : 0u) << (16 * e);
-          }
-          sg[c2] = h2;
+        for (int k = 0; k < 16; ++k) {
+          const float2 o =
+              __fadd2_rn(make_float2(__uint_as_float(cur[2 * k]), __uint_as_float(cur[2 * k + 1])), bias2[k]);
+          const float2 d = __ffma2_rn(t2[k], make_float2(-1.0f, -1.0f), o);  // o - t, one rounding
+          part += fabsf(d.x);
+          part += fabsf(d.y);
+          sg[k] = sign_pair_bf16(d, valid);
         }
         if (valid) loss += part;
-        // S row r, channels 32ch .. 32ch+31: panel ch/2, logical chunks
-        // 4 (ch & 1) .. +3 of the 128-byte row, permuted by row & 7.
-        unsigned char* srow = sm + C::off_s + (ch >> 1) * kPanel + r * 128;
+        // S row r, channels 32ch .. 32ch+31: panel ch/2 of this tile buffer,
+        // logical chunks 4 (ch & 1) .. +3 -- over targets already consumed.
+        unsigned char* srow = tbuf + (ch >> 1) * kPanel + r * 128;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4*>(srow + (((4 * (ch & 1) + q) ^ (r & 7)) << 4)) =
-              make_uint4(sg[4 * q], sg[4 * q + 1], sg[4 * q + 2], sg[4 * q + 3]);
-        if (last) {
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&bars[kBarTEmpty + slot]);
-          ++t_uses;
-        }
+        for (int e = 0; e < 4; ++e)
+          *reinterpret_cast<uint4*>(srow + (((4 * (ch & 1) + e) ^ (r & 7)) << 4)) =
+              make_uint4(sg[4 * e], sg[4 * e + 1], sg[4 * e + 2], sg[4 * e + 3]);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars[kBarAccEmpty]);
       if (!ok) break;
       if (!kL1) continue;
+      // dF of the previous tile (its reverse products ran while this tile
+      // was processed), before this tile's products may overwrite it.
+      if (i > 0) {
+        if (!dec_wait(&bars[kBarBwd], (i - 1) & 1, s_abort, a.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        store_df(i - 1);
+        tc_fence_before();
+      }
       fence_proxy_async();  // S stores -> tensor-core reads
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars[kBarSFull]);
-      if (!dec_wait(&bars[kBarBwd], i & 1, s_abort, a.err)) break;
-      tc_fence_after();
-#pragma unroll
-      for (int h = 0; h < D / 32; ++h) {
-        uint32_t v[32];
-        tmem_ld32(t_row + kColDF + 32 * h, v);
-        tmem_wait_ld();
-        if (valid) {
-          float4* o = reinterpret_cast<float4*>(a.d_feat + p * D + 32 * h);
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            o[q] = make_float4(a.scale * __uint_as_float(v[4 * q]), a.scale * __uint_as_float(v[4 * q + 1]),
-                               a.scale * __uint_as_float(v[4 * q + 2]), a.scale * __uint_as_float(v[4 * q + 3]));
-        }
-      }
     }
     if (kL1) {
-      // Per-CTA partials: dW rows and db of the channels of this lane, the
-      // loss of this CTA (fixed-order sums).
-      asm volatile("bar.sync 1, 128;" ::: "memory");  // epilogue warps only
-      if (!*s_abort) {
-        // The last backward barrier the epilogue waited on covers every
-        // product of this CTA.
+      if (ok && n_mine > 0 && dec_wait(&bars[kBarBwd], (n_mine - 1) & 1, s_abort, a.err)) {
         tc_fence_after();
+        store_df(n_mine - 1);
+      }
+      // Per-CTA partials: the dW rows and db of this half's channels, the
+      // loss of this CTA (fixed-order sums).
+      asm volatile("bar.sync 1, 256;" ::: "memory");  // epilogue warps only
+      if (!*s_abort && n_mine > 0) {
+        // The last backward barrier covers every product of this CTA.
+        tc_fence_after();
+        const int c = h * 128 + r;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int c = h * 128 + r;
+        for (int k = 0; k < D / 32; ++k) {
+          uint32_t v[32];
+          tmem_ld32(t_row + kColDW + 64 * h + 32 * k, v);
+          tmem_wait_ld(v);
+          float4* o = reinterpret_cast<float4*>(a.part_dw + ((size_t)blockIdx.x * kDecN + c) * D + 32 * k);
 #pragma unroll
-          for (int q = 0; q < D / 32; ++q) {
-            uint32_t v[32];
-            tmem_ld32(t_row + kColDW + 64 * h + 32 * q, v);
-            tmem_wait_ld();
-            float4* o = reinterpret_cast<float4*>(a.part_dw + ((size_t)blockIdx.x * kDecN + c) * D + 32 * q);
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-              o[e] = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
-                                 __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
-          }
-          uint32_t vb;
-          tmem_ld1(t_row + kColDB + 16 * h, vb);
-          tmem_wait_ld();
-          a.part_db[(size_t)blockIdx.x * kDecN + c] = __uint_as_float(vb);
+          for (int e = 0; e < 8; ++e)
+            o[e] = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                               __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
         }
+        uint32_t vb1;
+        tmem_ld1(t_row + kColDB + 16 * h, vb1);
+        tmem_wait_ld1(vb1);
+        a.part_db[(size_t)blockIdx.x * kDecN + c] = __uint_as_float(vb1);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
       if (lane == 0) s_red[warp] = loss;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (tid == 0) a.part_loss[blockIdx.x] = (s_red[0] + s_red[1]) + (s_red[2] + s_red[3]);
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (tid == 0) {
+        float sum = 0.0f;
+        for (int w = 0; w < kEpiWarps; ++w) sum += s_red[w];
+        a.part_loss[blockIdx.x] = sum;
+      }
     }
     tc_fence_before();
   }
   __syncthreads();
-  if (warp == 5) {
+  if (warp == kWarpMma) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }

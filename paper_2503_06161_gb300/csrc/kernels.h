@@ -77,6 +77,7 @@ struct CompositeArgs {
   const float4* rec;
   const void* feat;
   float *out_rgb, *out_depth, *out_alpha, *out_feat;
+  uint16_t* out_feat_bf16;  // optional bf16 copy of out_feat
   float* t_final;
   uint32_t* n_contrib;
   // backward

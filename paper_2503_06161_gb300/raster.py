@@ -116,7 +116,9 @@ class Rasterizer:
         return int(self.opts.max_dups) if self.opts.max_dups > 0 else 16 * self.P + 4096
 
     def forward(self, scene: GaussianScene, cam: _lib.fe_camera, deform: DeformField | None = None, t: float = 0.0,
-                out=None):
+                out=None, feat_bf16=None):
+        """(rgb, depth, alpha, feat); feat_bf16: optional [H*W, D] bf16 tensor
+        that also receives the feature map rounded to bf16 (decoder input)."""
         H, W, D = self.height, self.width, self.D
         if out is None:
             kw = dict(dtype=torch.float32, device=self.device)
@@ -125,7 +127,7 @@ class Rasterizer:
         rgb, depth, alpha, feat = out
         for _ in range(4):
             _lib.fe_render_forward(scene.struct(), deform.struct() if deform is not None else None, cam, t,
-                                   self.opts, self.workspace, rgb, depth, alpha, feat)
+                                   self.opts, self.workspace, rgb, depth, alpha, feat, feat_bf16=feat_bf16)
             if not self.auto_grow:
                 break
             st = self.stats(raise_on_error=False)

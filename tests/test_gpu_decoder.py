@@ -124,3 +124,28 @@ def test_decoder_deterministic_and_empty():
     e = dec.l1(ft[:0], tt[:0])
     torch.cuda.synchronize()
     assert e[0].item() == 0.0 and not e[2].any() and not e[3].any()
+
+
+def test_render_writes_bf16_feature_map_for_the_decoder():
+    # The compositing pass's optional bf16 copy of the feature map is the
+    # nearest-even rounding of its fp32 map (numpy rounding, bit for bit),
+    # and feeding it to the fused decoder loss matches the oracle decoder on
+    # those same bf16 values.
+    from gpu_helpers import deformed_case
+    from paper_2503_06161_gb300.raster import DeformField, GaussianScene, Rasterizer, camera_struct
+    sc, cam, df = deformed_case(P=3000, W=150, H=100, D=32)
+    scene = GaussianScene.from_numpy(sc, "cuda", bf16=True)
+    deform = DeformField.from_numpy(df, "cuda")
+    rast = Rasterizer(sc.P, sc.D, cam.width, cam.height, auto_grow=True)
+    fb = torch.empty(cam.width * cam.height, sc.D, dtype=torch.bfloat16, device="cuda")
+    _, _, _, feat = rast.forward(scene, camera_struct(cam), deform, 0.3, feat_bf16=fb)
+    torch.cuda.synchronize()
+    f32 = feat.cpu().numpy()
+    got_bits = fb.cpu().view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(got_bits, synth.bf16_bits(f32))
+    w, b = synth.make_decoder(sc.D, seed=4, b_std=0.1)
+    dec = Decoder(torch.tensor(w).to(torch.bfloat16).cuda(), torch.tensor(b).cuda())
+    tgt = synth.bf16_round(np.random.default_rng(1).normal(size=(f32.shape[0], 256)).astype(np.float32))
+    got = dec.l1(fb, torch.tensor(tgt).to(torch.bfloat16).cuda())
+    torch.cuda.synchronize()
+    _l1_check(synth.bf16_round(f32).astype(np.float64), w, b, tgt, got)
