@@ -266,6 +266,29 @@ fe_status fe_decode_l1(const fe_decoder_args *args, const void *target, int targ
  * (2 = a pipeline wait timed out).  Synchronises `stream`. */
 fe_status fe_decoder_read_errors(const void *workspace, uint32_t *err, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Adam (the optimiser the paper trains with, Sec. 3.3 / Sec. 4.1), with bias
+ * correction, on FP32 master parameters:
+ *     m <- b1 m + (1 - b1) g;   v <- b2 v + (1 - b2) g^2
+ *     p <- p - lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps)
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  float *param;             /* [n] FP32 master, updated in place */
+  const float *grad;        /* [n] */
+  float *m, *v;             /* [n] first and second moments, updated in place (start at 0) */
+  void *param_bf16;         /* optional [n] bf16 copy written from the updated param (nearest
+                               even), e.g. the SH / feature storage the renderer reads; NULL = none */
+  int64_t n;                /* elements, >= 0 */
+  float lr;                 /* learning rate of this group */
+} fe_adam_group;
+
+/* One Adam step over 1..8 parameter groups in a single launch.  step >= 1
+ * is the 1-based step count of the bias correction; 0 <= b1, b2 < 1,
+ * eps >= 0.  param, grad, m, v: device pointers, 16-byte aligned;
+ * param_bf16 8-byte aligned.  Asynchronous on `stream`. */
+fe_status fe_adam_step(const fe_adam_group *groups, int ngroups, int step, float beta1, float beta2, float eps,
+                       void *stream);
+
 /* Measured single-precision FMA throughput: runs an FMA-chain kernel over
  * the whole GPU for `iters` iterations per thread and writes FLOP/s
  * (2 per FMA) to *flops (host).  Synchronous; used for the FP32 roofline. */

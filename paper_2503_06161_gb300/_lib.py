@@ -72,6 +72,11 @@ class fe_decoder_args(ctypes.Structure):
     _fields_ = [("HW", c_int64), ("D", c_int), ("feat", c_void_p), ("weight", c_void_p), ("bias", c_void_p)]
 
 
+class fe_adam_group(ctypes.Structure):
+    _fields_ = [("param", c_void_p), ("grad", c_void_p), ("m", c_void_p), ("v", c_void_p),
+                ("param_bf16", c_void_p), ("n", c_int64), ("lr", c_float)]
+
+
 _P = ctypes.POINTER
 _SIGNATURES = {
     "fe_workspace_size": [c_int, c_int, c_int, c_int, _P(fe_opts), _P(ctypes.c_size_t)],
@@ -93,6 +98,7 @@ _SIGNATURES = {
     "fe_decode_l1": [_P(fe_decoder_args), c_void_p, c_int, c_float, c_void_p, c_void_p, c_void_p, c_void_p,
                      c_void_p, ctypes.c_size_t, c_void_p],
     "fe_decoder_read_errors": [c_void_p, _P(ctypes.c_uint32), c_void_p],
+    "fe_adam_step": [_P(fe_adam_group), c_int, c_int, c_float, c_float, c_float, c_void_p],
 }
 
 _lib = None
@@ -308,3 +314,20 @@ def fe_decoder_read_errors(workspace, stream=None) -> int:
     _check("fe_decoder_read_errors", load().fe_decoder_read_errors(_ptr(workspace), ctypes.byref(e),
                                                                     _stream(stream)))
     return int(e.value)
+
+
+def fe_adam_step(groups, step: int, beta1: float, beta2: float, eps: float, stream=None):
+    """groups: list of dicts with param, grad, m, v (float32 tensors), lr, and
+    optionally param_bf16 (bf16 tensor)."""
+    arr = (fe_adam_group * len(groups))()
+    for k, g in enumerate(groups):
+        arr[k].param = g["param"].data_ptr()
+        arr[k].grad = g["grad"].data_ptr()
+        arr[k].m = g["m"].data_ptr()
+        arr[k].v = g["v"].data_ptr()
+        pb = g.get("param_bf16")
+        arr[k].param_bf16 = pb.data_ptr() if pb is not None else None
+        arr[k].n = int(g["param"].numel())
+        arr[k].lr = float(g["lr"])
+    _check("fe_adam_step", load().fe_adam_step(arr, len(groups), int(step), float(beta1), float(beta2), float(eps),
+                                               _stream(stream)))

@@ -218,7 +218,7 @@ CONFIGS = {
     "batched_300k_16views": dict(P=300_000, D=32, W=640, H=512, f=560.0, lo=(-2, -2, 3),
                                  hi=(2, 2, 8), deform=True, bf16=True, seed=0, views=16),
     "scared_1m_1280x1024": dict(P=1_000_000, D=64, W=1280, H=1024, f=1000.0, lo=(-2, -2, 3),
-                                hi=(2, 2, 8), deform=True, bf16=True, seed=0, decoder=256),
+                                hi=(2, 2, 8), deform=True, bf16=True, seed=0, decoder=256, train=True),
 }
 
 

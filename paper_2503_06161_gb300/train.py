@@ -1,0 +1,104 @@
+"""One training iteration of FE-4DGS on the device (Sec. 3.3 and Sec. 4.1):
+deformation query at time t, render forward (RGB, depth, D-channel
+features), L1 RGB loss, decoder D -> 256 with the L1 feature loss (Eq. 9-10,
+fused forward + reverse), render reverse, and an Adam step on every Gaussian
+parameter and the decoder.
+
+Every step of the iteration runs in the library's kernels; this module only
+owns the device buffers and sequences the C-ABI calls on the current stream,
+with no host synchronisation inside a step.
+
+    tr = Trainer.from_numpy(scene, camera, deform, decoder_w, decoder_b)
+    tr.step(t, target_rgb, target_features)       # losses stay on the device
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+from .decoder import Decoder
+from .optim import Adam
+from .raster import DeformField, GaussianScene, Rasterizer, camera_struct
+
+# Per-group learning rates (constant; the schedules of the paper's training
+# recipe are not part of this pass).
+LR = dict(means=1.6e-4, log_scales=5e-3, quats=1e-3, opacity_logits=5e-2, sh=2.5e-3, feat=2.5e-3,
+          dec_weight=1e-3, dec_bias=1e-3)
+
+
+class Trainer:
+    def __init__(self, masters: dict, sh_degree: int, cam, deform: DeformField | None, decoder: Decoder,
+                 bf16_storage: bool = True, max_dups: int | None = None, lr: dict | None = None, device="cuda"):
+        """masters: float32 device tensors means [P,3], log_scales [P,3],
+        quats [P,4], opacity_logits [P], sh [P,16,3], feat [P,D]."""
+        self.m = masters
+        P, D = masters["means"].shape[0], masters["feat"].shape[1]
+        self.P, self.D = int(P), int(D)
+        self.cam = cam if isinstance(cam, _lib.fe_camera) else camera_struct(cam)
+        self.deform = deform
+        self.dec = decoder
+        self.bf16 = bf16_storage
+        lr = dict(LR, **(lr or {}))
+        # Storage the renderer reads: bf16 copies of SH and features,
+        # refreshed by every Adam step.
+        if bf16_storage:
+            self.sh_store = masters["sh"].to(torch.bfloat16)
+            self.feat_store = masters["feat"].to(torch.bfloat16)
+        else:
+            self.sh_store, self.feat_store = masters["sh"], masters["feat"]
+        self.scene = GaussianScene(masters["means"], masters["log_scales"], masters["quats"],
+                                   masters["opacity_logits"], self.sh_store, self.feat_store, sh_degree)
+        W, H = self.cam.width, self.cam.height
+        self.HW = W * H
+        if max_dups is None:
+            probe = Rasterizer(self.P, self.D, W, H, device=device, max_dups=64 * self.P + 4096, forward_only=True)
+            probe.forward(self.scene, self.cam, deform, 0.5)
+            max_dups = int(probe.stats()["num_dups"] * 1.5) + 4096
+            del probe
+        self.rast = Rasterizer(self.P, self.D, W, H, max_dups=max_dups, device=device, auto_grow=False)
+        kw = dict(dtype=torch.float32, device=device)
+        self.out = (torch.empty(3, H, W, **kw), torch.empty(H, W, **kw), torch.empty(H, W, **kw),
+                    torch.empty(self.HW, self.D, **kw))
+        self.feat_bf = torch.empty(self.HW, self.D, dtype=torch.bfloat16, device=device)
+        self.g_rgb = torch.empty(3, H, W, **kw)
+        self.losses = torch.zeros(2, **kw)
+        self.scratch = torch.empty(1024, **kw)
+        self.dec_out = (self.losses[1:2], torch.empty(self.HW, self.D, **kw), torch.empty(256, self.D, **kw),
+                        torch.empty(256, **kw))
+        self.grads = dict(means=torch.empty(P, 3, **kw), log_scales=torch.empty(P, 3, **kw),
+                          quats=torch.empty(P, 4, **kw), opacity_logits=torch.empty(P, **kw),
+                          sh=torch.empty(P, 16, 3, **kw), feat=torch.empty(P, D, **kw))
+        self.dec_w32 = decoder.weight.float()
+        groups = [dict(param=masters[k], lr=lr[k]) for k in ("means", "log_scales", "quats", "opacity_logits")]
+        groups.append(dict(param=masters["sh"], lr=lr["sh"], param_bf16=self.sh_store if bf16_storage else None))
+        groups.append(dict(param=masters["feat"], lr=lr["feat"],
+                           param_bf16=self.feat_store if bf16_storage else None))
+        groups.append(dict(param=self.dec_w32, lr=lr["dec_weight"], param_bf16=decoder.weight))
+        groups.append(dict(param=decoder.bias, lr=lr["dec_bias"]))
+        self.opt = Adam(groups)
+        self.dec.workspace(self.HW)
+
+    @classmethod
+    def from_numpy(cls, sc, cam, df=None, dec_w=None, dec_b=None, device="cuda", bf16_storage=True, **kw):
+        f = lambda a: torch.as_tensor(a, dtype=torch.float32, device=device).contiguous()
+        masters = dict(means=f(sc.means), log_scales=f(sc.log_scales), quats=f(sc.quats),
+                       opacity_logits=f(sc.opacity_logits), sh=f(sc.sh).reshape(sc.P, 16, 3), feat=f(sc.feat))
+        deform = DeformField.from_numpy(df, device) if df is not None else None
+        dec = Decoder(torch.as_tensor(dec_w).to(torch.bfloat16).to(device), f(dec_b))
+        return cls(masters, int(sc.sh_degree), cam, deform, dec, bf16_storage=bf16_storage, device=device, **kw)
+
+    def forward_backward(self, t: float, tgt_rgb: torch.Tensor, tgt_dec: torch.Tensor):
+        """Losses and gradients of one view at time t (no parameter update)."""
+        self.rast.forward(self.scene, self.cam, self.deform, t, out=self.out, feat_bf16=self.feat_bf)
+        _lib.fe_l1_loss_grad(self.out[0], tgt_rgb, self.HW, self.g_rgb, self.losses[0:1], self.scratch)
+        self.dec.l1(self.feat_bf, tgt_dec, out=self.dec_out)
+        self.rast.backward(self.scene, self.cam, self.deform, t, self.g_rgb, None, None, self.dec_out[1],
+                           grads=self.grads)
+
+    def step(self, t: float, tgt_rgb: torch.Tensor, tgt_dec: torch.Tensor) -> torch.Tensor:
+        """One training iteration; returns the device tensor [L_rgb, L_feat]."""
+        self.forward_backward(t, tgt_rgb, tgt_dec)
+        g = self.grads
+        self.opt.step([g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"], g["feat"],
+                       self.dec_out[2], self.dec_out[3]])
+        return self.losses

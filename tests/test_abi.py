@@ -96,3 +96,19 @@ def test_decoder_host_side_status_codes(lib):
     assert lib.fe_decode_forward(ctypes.byref(a), None, None, 0, None) == 1
     assert lib.fe_decode_l1(None, *args) == 1
     assert lib.fe_decoder_read_errors(None, None, None) == 1
+
+
+def test_adam_host_side_status_codes(lib):
+    g = (_lib.fe_adam_group * 1)()
+    g[0].param = g[0].grad = g[0].m = g[0].v = 16
+    g[0].n = 8
+    g[0].lr = 1.0
+    assert lib.fe_adam_step(None, 1, 1, 0.9, 0.999, 1e-15, None) == 1
+    assert lib.fe_adam_step(g, 0, 1, 0.9, 0.999, 1e-15, None) == 1       # no groups
+    assert lib.fe_adam_step(g, 9, 1, 0.9, 0.999, 1e-15, None) == 1       # more than 8
+    assert lib.fe_adam_step(g, 1, 0, 0.9, 0.999, 1e-15, None) == 1       # step counts from 1
+    assert lib.fe_adam_step(g, 1, 1, 1.0, 0.999, 1e-15, None) == 1       # beta1 must be < 1
+    g[0].m = 20                                                           # misaligned moment
+    assert lib.fe_adam_step(g, 1, 1, 0.9, 0.999, 1e-15, None) == 1
+    g[0].n = 0                                                            # empty group: nothing to do
+    assert lib.fe_adam_step(g, 1, 1, 0.9, 0.999, 1e-15, None) == 0

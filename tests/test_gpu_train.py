@@ -1,0 +1,103 @@
+"""GPU checks of the training iteration: the fused Adam kernel against the
+FP64 oracle's Adam, its bf16 storage copies, and one full iteration
+(render, L1 RGB, decoder L1, reverse, Adam) whose update matches the
+oracle's Adam applied to the iteration's own gradients."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2503_06161_gb300 import _lib, synth  # noqa: E402
+from paper_2503_06161_gb300.optim import Adam  # noqa: E402
+from paper_2503_06161_gb300.train import Trainer  # noqa: E402
+
+from gpu_helpers import deformed_case  # noqa: E402
+
+TOL_ADAM = 2e-6  # relative to the parameter scale: FP32 arithmetic of one update
+# The kernel receives its hyperparameters as float32; the oracle takes those
+# same values.
+B1, B2, EPS = (float(np.float32(x)) for x in (0.9, 0.999, 1e-15))
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def test_adam_matches_oracle_with_tails_and_bf16_copies():
+    rng = np.random.default_rng(0)
+    sizes = [1001, 6, 64 * 3 + 1]  # tails that are not a multiple of 4
+    lrs = [1e-2, 3e-3, 5e-2]
+    ps = [rng.normal(size=n).astype(np.float32) for n in sizes]
+    pt = [torch.tensor(p).cuda() for p in ps]
+    pb = [torch.empty(n, dtype=torch.bfloat16, device="cuda") for n in sizes]
+    opt = Adam([dict(param=p, lr=lr, param_bf16=b) for p, lr, b in zip(pt, lrs, pb)])
+    ref = [(p.astype(np.float64), np.zeros(len(p)), np.zeros(len(p))) for p in ps]
+    for step in range(1, 4):
+        gs = [rng.normal(size=n).astype(np.float32) * (10.0 ** -k) for k, n in enumerate(sizes)]
+        opt.step([torch.tensor(g).cuda() for g in gs])
+        ref = [O.adam_step(p, g, m, v, step, f32(lr), B1, B2, EPS) for (p, m, v), g, lr in zip(ref, gs, lrs)]
+        torch.cuda.synchronize()
+        for k in range(len(sizes)):
+            got = pt[k].cpu().numpy()
+            assert np.max(np.abs(got - ref[k][0])) <= TOL_ADAM * max(1.0, np.max(np.abs(ref[k][0])))
+            for j in (1, 2):  # moments: FP32 rounding relative to their scale
+                got_j = opt.groups[k]["m" if j == 1 else "v"].cpu().numpy()
+                assert np.max(np.abs(got_j - ref[k][j])) <= 1e-6 * np.max(np.abs(ref[k][j]))
+            bits = pb[k].cpu().view(torch.int16).numpy().view(np.uint16)
+            assert np.array_equal(bits, synth.bf16_bits(got))
+
+
+def test_adam_rejects_bad_groups():
+    p = torch.zeros(8, device="cuda")
+    with pytest.raises(_lib.FeError):
+        _lib.fe_adam_step([dict(param=p, grad=p, m=p, v=p, lr=1.0)], 0, 0.9, 0.999, 1e-15)   # step 0
+    q = torch.zeros(9, device="cuda")[1:]  # 4-byte offset: not 16-byte aligned
+    with pytest.raises(_lib.FeError):
+        _lib.fe_adam_step([dict(param=q, grad=q, m=q, v=q, lr=1.0)], 1, 0.9, 0.999, 1e-15)
+
+
+def _trainer(seed=0):
+    sc, cam, df = deformed_case(P=3000, W=150, H=100, D=32, seed=seed)
+    w, b = synth.make_decoder(32, seed=5, b_std=0.1)
+    return Trainer.from_numpy(sc, cam, df, w, b, max_dups=200_000)
+
+
+def test_training_iteration_updates_match_oracle_adam_on_its_gradients():
+    tr = _trainer()
+    H, W = tr.cam.height, tr.cam.width
+    rng = np.random.default_rng(3)
+    tgt_rgb = torch.tensor(rng.random((3, H, W)).astype(np.float32)).cuda()
+    tgt_dec = torch.tensor(rng.normal(size=(H * W, 256)).astype(np.float32)).to(torch.bfloat16).cuda()
+    before = {k: v.detach().cpu().numpy().astype(np.float64) for k, v in tr.m.items()}
+    losses = tr.step(0.4, tgt_rgb, tgt_dec)
+    torch.cuda.synchronize()
+    assert tr.rast.stats()["device_errors"] == 0 and tr.dec.errors() == 0
+    assert np.all(np.isfinite(losses.cpu().numpy()))
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in tr.grads.items()}
+    for k in before:
+        lr = tr.opt.groups[["means", "log_scales", "quats", "opacity_logits", "sh", "feat"].index(k)]["lr"]
+        ref, _, _ = O.adam_step(before[k], g[k], 0.0, 0.0, 1, f32(lr), B1, B2, EPS)
+        got = tr.m[k].cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= TOL_ADAM * max(1.0, np.max(np.abs(ref))), k
+    # The renderer's bf16 storage follows the masters.
+    assert np.array_equal(tr.feat_store.cpu().view(torch.int16).numpy().view(np.uint16),
+                          synth.bf16_bits(tr.m["feat"].cpu().numpy()))
+    # The gradients reached every group (rendered Gaussians move).
+    assert np.abs(g["means"]).sum() > 0 and np.abs(g["feat"]).sum() > 0 and np.abs(g["sh"]).sum() > 0
+
+
+def test_training_is_deterministic():
+    a, b = _trainer(), _trainer()
+    H, W = a.cam.height, a.cam.width
+    rng = np.random.default_rng(4)
+    tgt_rgb = torch.tensor(rng.random((3, H, W)).astype(np.float32)).cuda()
+    tgt_dec = torch.tensor(rng.normal(size=(H * W, 256)).astype(np.float32)).to(torch.bfloat16).cuda()
+    for t in (0.1, 0.7):
+        la = a.step(t, tgt_rgb, tgt_dec).clone()
+        lb = b.step(t, tgt_rgb, tgt_dec).clone()
+        torch.cuda.synchronize()
+        assert torch.equal(la, lb)
+    for k in a.m:
+        assert torch.equal(a.m[k], b.m[k]), k
