@@ -98,6 +98,8 @@ typedef struct {
   float bg[3];              /* background colour added as bg * T_final */
   int64_t max_dups;         /* capacity of the (Gaussian, tile) list; 0 = 16 * P + 4096 */
   int forward_only;         /* 1: workspace without backward storage */
+  int accumulate_grads;     /* backward: 1 = add the gradients to the fe_grads buffers (e.g. a
+                               sum over views rendered one after another); 0 = overwrite */
   void *const *events;      /* profiling: NULL, or host array of 8 cudaEvent_t (NULL entries
                                skipped) recorded on the stream at stage boundaries:
                                forward [0] start [1] after deform+projection [2] after
@@ -121,7 +123,8 @@ typedef struct {
   const float *rgb, *depth, *alpha, *feat;
 } fe_output_grads;
 
-/* Parameter gradients (overwritten, float32 even for bfloat16 storage):
+/* Parameter gradients (overwritten, or added to when fe_opts.accumulate_grads
+ * is set; float32 even for bfloat16 storage):
  * means [P,3], log_scales [P,3], quats [P,4], opacity_logits [P],
  * sh [P,16,3], feat [P,D].  Deformation-network weight gradients are not
  * produced (the canonical mean receives the gradient through the grid). */

@@ -46,7 +46,7 @@ class fe_deform(ctypes.Structure):
 
 class fe_opts(ctypes.Structure):
     _fields_ = [("tile_w", c_int), ("tile_h", c_int), ("bg", c_float * 3), ("max_dups", c_int64),
-                ("forward_only", c_int), ("events", ctypes.POINTER(c_void_p))]
+                ("forward_only", c_int), ("accumulate_grads", c_int), ("events", ctypes.POINTER(c_void_p))]
 
 
 class fe_outputs(ctypes.Structure):
@@ -143,12 +143,13 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def make_opts(tile=(16, 16), bg=(0.0, 0.0, 0.0), max_dups=0, forward_only=False) -> fe_opts:
+def make_opts(tile=(16, 16), bg=(0.0, 0.0, 0.0), max_dups=0, forward_only=False, accumulate=False) -> fe_opts:
     o = fe_opts()
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
     o.bg[:] = [float(x) for x in bg]
     o.max_dups = int(max_dups)
     o.forward_only = 1 if forward_only else 0
+    o.accumulate_grads = 1 if accumulate else 0
     return o
 
 

@@ -267,6 +267,7 @@ fe_status fe_render_backward(const fe_gaussians* g, const fe_deform* deform, con
   gb.d_feat = grads->feat;
   gb.ddstate = at<float>(workspace, L.ddstate);
   gb.psum = at<float>(workspace, L.psum);
+  gb.accumulate = opts && opts->accumulate_grads ? 1 : 0;
   FE_TRY_CUDA(launch_gauss_bwd(ga, gb, st, opts && opts->events ? static_cast<cudaEvent_t>(opts->events[6]) : nullptr));
   FE_TRY_CUDA(mark(opts, 7, st));
   return FE_OK;

@@ -868,7 +868,7 @@ __global__ void __launch_bounds__(kThreads) partial_reduce_kernel(const GaussBwd
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     const int col = lane + 32 * q;
-    if (col < D) b.d_feat[g * D + col] = acc[q];
+    if (col < D) b.d_feat[g * D + col] = b.accumulate ? b.d_feat[g * D + col] + acc[q] : acc[q];
     else if (col < NP) b.psum[g * 12 + (col - D)] = acc[q];
   }
 }
@@ -934,7 +934,12 @@ __global__ void __launch_bounds__(kThreads) gauss_bwd_proj_kernel(const GaussArg
         const int idx = 4 * k4 + j, k = idx / 3, ch = idx % 3;
         v4[j] = k < nb ? gch[ch] * s.Y[k] : 0.0f;
       }
-      reinterpret_cast<float4*>(dsh)[k4] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+      float4 o4 = make_float4(v4[0], v4[1], v4[2], v4[3]);
+      if (b.accumulate) {
+        const float4 old = reinterpret_cast<const float4*>(dsh)[k4];
+        o4 = make_float4(old.x + o4.x, old.y + o4.y, old.z + o4.z, old.w + o4.w);
+      }
+      reinterpret_cast<float4*>(dsh)[k4] = o4;
     }
     float gd[3];
     sh_basis_vjp(s.dir, wk, gd);
@@ -1024,14 +1029,28 @@ __global__ void __launch_bounds__(kThreads) gauss_bwd_proj_kernel(const GaussArg
 #pragma unroll
     for (int i = 0; i < 4; ++i) dqt[i] = (dq[i] - s.q[i] * qd) * s.qinv;
   }
-  b.d_means[3 * g] = dmu[0];
-  b.d_means[3 * g + 1] = dmu[1];
-  b.d_means[3 * g + 2] = dmu[2];
-  b.d_log_scales[3 * g] = dlogs[0];
-  b.d_log_scales[3 * g + 1] = dlogs[1];
-  b.d_log_scales[3 * g + 2] = dlogs[2];
-  reinterpret_cast<float4*>(b.d_quats)[g] = make_float4(dqt[0], dqt[1], dqt[2], dqt[3]);
-  b.d_logits[g] = dlogit;
+  if (b.accumulate) {
+    // With a deformation field the reverse pass through the grid adds this
+    // view's whole mean gradient (dmu + grid term) in one addition.
+    const bool defer_mu = a.has_deform && active;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (!defer_mu) b.d_means[3 * g + i] += dmu[i];
+      b.d_log_scales[3 * g + i] += dlogs[i];
+    }
+    const float4 oq = reinterpret_cast<const float4*>(b.d_quats)[g];
+    reinterpret_cast<float4*>(b.d_quats)[g] = make_float4(oq.x + dqt[0], oq.y + dqt[1], oq.z + dqt[2], oq.w + dqt[3]);
+    b.d_logits[g] += dlogit;
+  } else {
+    b.d_means[3 * g] = dmu[0];
+    b.d_means[3 * g + 1] = dmu[1];
+    b.d_means[3 * g + 2] = dmu[2];
+    b.d_log_scales[3 * g] = dlogs[0];
+    b.d_log_scales[3 * g + 1] = dlogs[1];
+    b.d_log_scales[3 * g + 2] = dlogs[2];
+    reinterpret_cast<float4*>(b.d_quats)[g] = make_float4(dqt[0], dqt[1], dqt[2], dqt[3]);
+    b.d_logits[g] = dlogit;
+  }
   if (a.has_deform) {
     // dd = dL/d delta: d_mu, d_q (pre-normalisation), d_log_s, d_logit; [11] = active flag.
     float4* o = reinterpret_cast<float4*>(b.ddstate + (size_t)g * 12);
@@ -1080,9 +1099,14 @@ __global__ void __launch_bounds__(kThreads, 2) gauss_bwd_deform_kernel(const Gau
   float dg[3];
   hexplane_backward_warp<C>(a, mu0, active, s_df + (size_t)(threadIdx.x & ~31) * C, s_red, dg);
   if (active) {
-    b.d_means[3 * g] += dg[0];
-    b.d_means[3 * g + 1] += dg[1];
-    b.d_means[3 * g + 2] += dg[2];
+    if (b.accumulate) {
+      // This view's mean gradient (projection part + grid part), added once.
+#pragma unroll
+      for (int i = 0; i < 3; ++i) b.d_means[3 * g + i] += dd[i] + dg[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) b.d_means[3 * g + i] += dg[i];
+    }
   }
 }
 

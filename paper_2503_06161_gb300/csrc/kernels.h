@@ -42,6 +42,7 @@ struct GaussBwdArgs {
   float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh, *d_feat;
   float* ddstate;  // [P][12] dL/d delta, [11] = active flag
   float* psum;     // [P][12] sums of the partial rows' scalars
+  int accumulate;  // 1: add to the gradient buffers
 };
 
 cudaError_t launch_gauss_fwd(const GaussArgs& a, cudaStream_t st);

@@ -96,18 +96,34 @@ class Rasterizer:
     the same Rasterizer before the next forward."""
 
     def __init__(self, P: int, D: int, width: int, height: int, tile=(16, 16), bg=(0.0, 0.0, 0.0),
-                 max_dups: int = 0, forward_only: bool = False, device="cuda", auto_grow: bool | None = None):
+                 max_dups: int = 0, forward_only: bool = False, device="cuda", auto_grow: bool | None = None,
+                 accumulate: bool = False, workspace: torch.Tensor | None = None):
+        """accumulate: backward adds to the gradient buffers instead of
+        overwriting them.  workspace: optional uint8 device tensor to use
+        (e.g. one buffer shared by views that are rendered one after the
+        other); it must hold workspace_bytes(...)."""
         self.P, self.D, self.width, self.height = int(P), int(D), int(width), int(height)
         self.tile, self.bg, self.forward_only = tuple(tile), tuple(bg), bool(forward_only)
+        self.accumulate = bool(accumulate)
         self.device = torch.device(device)
         # Without an explicit capacity, check each forward for overflow (one
         # host sync) and grow the duplicate list when needed.
         self.auto_grow = (max_dups == 0) if auto_grow is None else bool(auto_grow)
-        self._alloc(int(max_dups))
+        self._alloc(int(max_dups), workspace)
 
-    def _alloc(self, max_dups: int):
-        self.opts = _lib.make_opts(self.tile, self.bg, max_dups, self.forward_only)
+    @staticmethod
+    def workspace_bytes(P, D, width, height, tile=(16, 16), max_dups=0, forward_only=False) -> int:
+        return _lib.fe_workspace_size(int(P), int(D), int(width), int(height),
+                                      _lib.make_opts(tuple(tile), (0.0, 0.0, 0.0), int(max_dups), forward_only))
+
+    def _alloc(self, max_dups: int, workspace: torch.Tensor | None = None):
+        self.opts = _lib.make_opts(self.tile, self.bg, max_dups, self.forward_only, self.accumulate)
         self.nbytes = _lib.fe_workspace_size(self.P, self.D, self.width, self.height, self.opts)
+        if workspace is not None:
+            if workspace.numel() * workspace.element_size() < self.nbytes or workspace.dtype != torch.uint8:
+                raise ValueError(f"shared workspace too small: {self.nbytes} bytes needed")
+            self.workspace = workspace[:self.nbytes]
+            return
         self.workspace = None
         self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
 
