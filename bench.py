@@ -37,6 +37,25 @@ L2_FLUSH_BYTES = 256 << 20
 HBM_FALLBACK_GBS = 6800.0
 
 
+def kernel_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture
+    (profiles/dram_traffic.json), or None when the capture is of another
+    workload or the kernel's sources changed since it was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if rec["workload"] != workload or h.hexdigest() != rec["sha256"]:
+            return None
+        return int(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def hbm_peak():
     """(GB/s, basis) from the measured copy bandwidth next to this file."""
     try:
@@ -55,6 +74,8 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--t", type=float, default=0.5)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--micro", choices=["decoder", "adam"], default=None,
+                   help="time one HBM-bound kernel alone on the workload's sizes")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -167,7 +188,7 @@ def run_ours(args, world, rank, local):
     dec = None
     if dec_ch:
         # Decoder workloads: the L1 feature loss is taken on the 256-channel
-        # decoder output against bf16 targets (Eq. 9-10).
+        # decoder output against bf16 targets (Sec. 3.3 decoder, Eq. 10 loss).
         w_np, b_np = synth.make_decoder(D, seed=3)
         dec = Decoder(torch.as_tensor(w_np).to(torch.bfloat16).to(dev), torch.as_tensor(b_np).to(dev))
         tgt_feat = tgt_feat.to(torch.bfloat16)
@@ -330,7 +351,7 @@ def run_ours(args, world, rank, local):
     dom = max(work, key=lambda n: stages[n])
     ach = work[dom] / (stages[dom] * 1e-3) / 1e12
     roofline = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
-                "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4), "traffic": kernel_traffic(dom, args.workload),
                 "peak_basis": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz "
                               f"(median SM clock sampled in the timed region; {alu_peak_max:.1f} at 2070 MHz max)",
                 "fma_probe_tflops": round(probe_tflops, 2)}
@@ -415,6 +436,65 @@ def run_ours(args, world, rank, local):
         print(json.dumps(result))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Single-kernel measurements on a workload's sizes (HBM-bound kernels)
+# ---------------------------------------------------------------------------
+def run_micro(args, cfg):
+    """The fused decoder + L1 + reverse over the workload's feature map
+    (D -> 256, bf16 targets), or one Adam step over the workload's Gaussian
+    parameters (FP32 masters, bf16 copies of SH and features); L2 flushed
+    before each timed launch, CUDA events around it."""
+    import torch
+
+    from paper_2503_06161_gb300.decoder import Decoder
+    from paper_2503_06161_gb300.optim import Adam
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    g = torch.Generator().manual_seed(0)
+    HW, D, P = cfg["W"] * cfg["H"], cfg["D"], cfg["P"]
+    if args.micro == "decoder":
+        dec = Decoder.random(D, device=dev)
+        feat = torch.randn(HW, D, generator=g).to(torch.bfloat16).to(dev)
+        tgt = torch.randn(HW, 256, generator=g).to(torch.bfloat16).to(dev)
+        fn = lambda: dec.l1(feat, tgt)
+        nbytes = HW * (2 * D + 2 * 256 + 4 * D) + 256 * D * 2
+        what = f"fused decoder {D}->256 + L1 + reverse over {HW} pixels, bf16 features and targets"
+    else:
+        sizes = [(P * 3, None), (P * 3, None), (P * 4, None), (P, None), (P * 48, "bf16"), (P * D, "bf16")]
+        groups = []
+        for n, copy in sizes:
+            groups.append(dict(param=torch.randn(n, generator=g).to(dev), lr=1e-3,
+                               param_bf16=torch.empty(n, dtype=torch.bfloat16, device=dev) if copy else None))
+        opt = Adam(groups)
+        grads = [torch.randn(n, generator=g).to(dev) for n, _ in sizes]
+        fn = lambda: opt.step(grads)
+        nbytes = sum(n * (28 + (2 if c else 0)) for n, c in sizes)
+        what = f"Adam over {P} Gaussians' parameters ({sum(n for n, _ in sizes)} floats, bf16 SH/feature copies)"
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(0)
+    clocks.start()
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    peak, basis = hbm_peak()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    print(json.dumps({"micro": args.micro, "workload": args.workload, "what": what, "ms": round(ms, 4),
+                      "bytes": int(nbytes), "roofline": {"bound": "hbm", "achieved": round(gbs, 1),
+                                                        "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                                                        "peak_basis": basis},
+                      "steps": args.steps, "warmup": args.warmup, "clocks": clk}))
 
 
 # ---------------------------------------------------------------------------
@@ -623,6 +703,10 @@ def main():
         return
     from paper_2503_06161_gb300 import synth
     cfg = synth.CONFIGS[args.workload]
+    if args.micro:
+        if rank == 0:
+            run_micro(args, cfg)
+        return
     if cfg.get("views"):
         run_batch(args, world, rank, local, cfg)
         return

@@ -224,7 +224,7 @@ fe_status fe_l1_loss_grad_noalloc(const float *pred, const float *target, int64_
                                   float *loss, void *stream);
 
 /* ------------------------------------------------------------------------
- * Semantic decoder (Sec. 3.3, Eq. 9): a pointwise (1x1) convolution of the
+ * Semantic decoder (Sec. 3.3): a pointwise (1x1) convolution of the
  * rendered feature map from D to 256 channels,
  *     out[p][c] = sum_d feat[p][d] * weight[c][d] + bias[c],
  * with BF16 operands and FP32 accumulation on the tensor cores.  The map is
@@ -270,7 +270,7 @@ fe_status fe_decode_l1(const fe_decoder_args *args, const void *target, int targ
 fe_status fe_decoder_read_errors(const void *workspace, uint32_t *err, void *stream);
 
 /* ------------------------------------------------------------------------
- * Adam (the optimiser the paper trains with, Sec. 3.3 / Sec. 4.1), with bias
+ * Adam (the optimiser the paper trains with, Sec. 4.1), with bias
  * correction, on FP32 master parameters:
  *     m <- b1 m + (1 - b1) g;   v <- b2 v + (1 - b2) g^2
  *     p <- p - lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps)

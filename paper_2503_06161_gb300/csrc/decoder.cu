@@ -1,4 +1,4 @@
-// Semantic decoder of the rendered feature map (Sec. 3.3, Eq. 9-10): a 1x1
+// Semantic decoder of the rendered feature map (Sec. 3.3): a 1x1
 // convolution from D to 256 channels, out[p][c] = sum_d F[p][d] W[c][d] + b[c],
 // on the 5th-generation tensor cores (tcgen05, BF16 operands, FP32
 // accumulators in tensor memory), optionally fused with the L1 feature loss

@@ -1,4 +1,4 @@
-// Adam update of the Gaussian parameters (Sec. 3.3 trains with Adam; the
+// Adam update of the Gaussian parameters (Sec. 4.1 trains with Adam; the
 // update is the standard one with bias correction):
 //   m <- b1 m + (1 - b1) g,   v <- b2 v + (1 - b2) g^2,
 //   p <- p - lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),

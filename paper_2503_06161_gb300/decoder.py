@@ -1,4 +1,4 @@
-"""Torch-facing API of the semantic decoder (Sec. 3.3, Eq. 9-10).
+"""Torch-facing API of the semantic decoder (Sec. 3.3; feature loss Eq. 10).
 
 The decoder is a 1x1 convolution from the D rendered feature channels to
 256, run by the library's tensor-core kernel on BF16 operands with FP32

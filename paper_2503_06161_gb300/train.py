@@ -1,6 +1,6 @@
-"""One training iteration of FE-4DGS on the device (Sec. 3.3 and Sec. 4.1):
+"""One training iteration of FE-4DGS on the device (Sec. 3.3, Sec. 3.4, Sec. 4.1):
 deformation query at time t, render forward (RGB, depth, D-channel
-features), L1 RGB loss, decoder D -> 256 with the L1 feature loss (Eq. 9-10,
+features), L1 RGB loss, decoder D -> 256 with the L1 feature loss (Eq. 10,
 fused forward + reverse), render reverse, and an Adam step on every Gaussian
 parameter and the decoder.
 

@@ -1,4 +1,4 @@
-"""GPU parity of the tensor-core decoder (Sec. 3.3, Eq. 9-10) against the
+"""GPU parity of the tensor-core decoder (Sec. 3.3, loss of Eq. 10) against the
 FP64 oracle, through the C ABI.
 
 Inputs are rounded to bf16 first and the oracle consumes the rounded values,
