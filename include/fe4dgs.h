@@ -292,6 +292,13 @@ typedef struct {
 fe_status fe_adam_step(const fe_adam_group *groups, int ngroups, int step, float beta1, float beta2, float eps,
                        void *stream);
 
+/* dst[i] = ((srcs[0][i] + srcs[1][i]) + srcs[2][i]) + ... in this fixed
+ * order (e.g. gradients of views rendered on separate streams, combined
+ * reproducibly).  srcs: host array of 1..8 device pointers; dst and every
+ * source float32 [n], 16-byte aligned; dst may alias srcs[0].  Asynchronous
+ * on `stream`.  The paper has no counterpart: a batching utility. */
+fe_status fe_sum_f32(float *dst, const float *const *srcs, int nsrc, int64_t n, void *stream);
+
 /* Measured single-precision FMA throughput: runs an FMA-chain kernel over
  * the whole GPU for `iters` iterations per thread and writes FLOP/s
  * (2 per FMA) to *flops (host).  Synchronous; used for the FP32 roofline. */

@@ -99,6 +99,7 @@ _SIGNATURES = {
                      c_void_p, ctypes.c_size_t, c_void_p],
     "fe_decoder_read_errors": [c_void_p, _P(ctypes.c_uint32), c_void_p],
     "fe_adam_step": [_P(fe_adam_group), c_int, c_int, c_float, c_float, c_float, c_void_p],
+    "fe_sum_f32": [c_void_p, _P(c_void_p), c_int, c_int64, c_void_p],
 }
 
 _lib = None
@@ -332,3 +333,10 @@ def fe_adam_step(groups, step: int, beta1: float, beta2: float, eps: float, stre
         arr[k].lr = float(g["lr"])
     _check("fe_adam_step", load().fe_adam_step(arr, len(groups), int(step), float(beta1), float(beta2), float(eps),
                                                _stream(stream)))
+
+
+def fe_sum_f32(dst, srcs, stream=None):
+    """dst = srcs[0] + srcs[1] + ... (float32 tensors of equal size), summed
+    left to right."""
+    arr = (c_void_p * len(srcs))(*[c_void_p(x.data_ptr()) for x in srcs])
+    _check("fe_sum_f32", load().fe_sum_f32(_ptr(dst), arr, len(srcs), int(dst.numel()), _stream(stream)))

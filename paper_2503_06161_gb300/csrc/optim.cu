@@ -83,11 +83,51 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamBatch b) {
 
 bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+constexpr int kSumMaxSrc = 8;
+struct SumArgs {
+  const float* src[kSumMaxSrc];
+  int nsrc;
+};
+
+// dst = ((src0 + src1) + src2) + ..., element by element, four at a time.
+__global__ void __launch_bounds__(256) sum_kernel(float* __restrict__ dst, const SumArgs s, int64_t n) {
+  const int64_t n4 = n / 4;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 acc = __ldg(reinterpret_cast<const float4*>(s.src[0]) + i);
+    for (int k = 1; k < s.nsrc; ++k) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(s.src[k]) + i);
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    reinterpret_cast<float4*>(dst)[i] = acc;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < (unsigned)(n - 4 * n4)) {
+    const int64_t i = 4 * n4 + threadIdx.x;
+    float acc = s.src[0][i];
+    for (int k = 1; k < s.nsrc; ++k) acc += s.src[k][i];
+    dst[i] = acc;
+  }
+}
+
 }  // namespace
 
 }  // namespace fe
 
 using namespace fe;
+
+extern "C" fe_status fe_sum_f32(float* dst, const float* const* srcs, int nsrc, int64_t n, void* stream) {
+  if (!dst || !srcs || nsrc < 1 || nsrc > kSumMaxSrc || n < 0 || !al16(dst)) return FE_ERR_INVALID_ARG;
+  SumArgs s{};
+  s.nsrc = nsrc;
+  for (int k = 0; k < nsrc; ++k) {
+    if (!srcs[k] || !al16(srcs[k])) return FE_ERR_INVALID_ARG;
+    s.src[k] = srcs[k];
+  }
+  if (n == 0) return FE_OK;
+  const int64_t blocks = (n / 4 + 255) / 256 + 1;
+  const int grid = (int)(blocks < 152 * 8 ? blocks : 152 * 8);
+  sum_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(dst, s, n);
+  return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+}
 
 extern "C" fe_status fe_adam_step(const fe_adam_group* groups, int ngroups, int step, float beta1, float beta2,
                                   float eps, void* stream) {

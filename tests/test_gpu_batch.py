@@ -45,7 +45,8 @@ def test_batched_graph_matches_per_view_sum_and_oracle():
     scene = GaussianScene.from_numpy(sc, "cuda")
     deform = DeformField.from_numpy(df, "cuda")
     views = _views(sc, cams, ts)
-    br = BatchRenderer(scene, deform, views, Autotuner())
+    br = BatchRenderer(scene, deform, views, Autotuner(), streams=2)
+    assert br.S == 2
     br.capture()
     br.replay()
     torch.cuda.synchronize()
@@ -56,13 +57,19 @@ def test_batched_graph_matches_per_view_sum_and_oracle():
     torch.cuda.synchronize()
     for k in got:
         assert torch.equal(got[k], br.grads[k]), k
-    # Per-view renders with the same tile shapes, summed in view order.
-    ref = None
-    for v, b, shape in zip(views, br.bufs, br.tile_shapes):
+    # Per-view renders with the same tile shapes, summed in the batch's
+    # order: within each stream in view order, then the streams in order.
+    per_stream = [None] * br.S
+    for k, (v, b, shape) in enumerate(zip(views, br.bufs, br.tile_shapes)):
         r = Rasterizer(sc.P, sc.D, v.cam.width, v.cam.height, tile=shape, auto_grow=True)
         r.forward(scene, v.cam, deform, v.t)
         g = r.backward(scene, v.cam, deform, v.t, b["g_rgb"], None, None, b["g_feat"])
-        ref = {k: x.clone() for k, x in g.items()} if ref is None else {k: ref[k] + g[k] for k in ref}
+        s = br.stream_of[k]
+        per_stream[s] = ({n: x.clone() for n, x in g.items()} if per_stream[s] is None
+                         else {n: per_stream[s][n] + g[n] for n in g})
+    ref = per_stream[0]
+    for s in range(1, br.S):
+        ref = {n: ref[n] + per_stream[s][n] for n in ref}
     torch.cuda.synchronize()
     for k in ref:
         assert torch.equal(ref[k], got[k]), k
@@ -109,3 +116,20 @@ def test_autotuner_choice_is_result_neutral():
     for k in a:
         assert rel_err(a[k].cpu().numpy(), plain.grads[k].cpu().numpy()) <= 1e-4, k
     assert torch.equal(la, plain.losses)
+
+
+def test_streams_do_not_change_images_and_sum_within_rounding():
+    sc, df, cams, ts = _case(seed=2)
+    scene = GaussianScene.from_numpy(sc, "cuda")
+    deform = DeformField.from_numpy(df, "cuda")
+    views = _views(sc, cams, ts)
+    one = BatchRenderer(scene, deform, views, None, streams=1)
+    four = BatchRenderer(scene, deform, views, None, streams=4)
+    one.capture()
+    four.capture()
+    one.replay()
+    four.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(one.losses, four.losses)
+    for k in one.grads:
+        assert rel_err(four.grads[k].cpu().numpy(), one.grads[k].cpu().numpy()) <= 1e-5, k
