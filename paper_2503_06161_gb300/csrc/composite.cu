@@ -134,33 +134,55 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
       __syncthreads();
       s_feat = s_wide;
     }
-    if (!done) {
-      for (int j = 0; j < nb; ++j) {
-        const float* rec = s_rec + j * kRec;
-        PairEval pe;
-        if (kCount) ++visits;
-        if (!eval_pair(rec, pxc, pyc, pe)) continue;
-        const float Tn = __fmul_rn(T, __fsub_rn(1.0f, pe.alpha));
-        if (Tn < kTMin) {
-          done = true;
-          break;
-        }
-        if (kCount) ++contribs;
-        const float w = pe.alpha * T;
-        C0 = fmaf(w, rec[7], C0);
-        C1 = fmaf(w, rec[8], C1);
-        C2 = fmaf(w, rec[9], C2);
-        Z = fmaf(w, rec[6], Z);
-        const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * D);
-        const float2 w2 = make_float2(w, w);
+    // Blend entry j (pe: its evaluation); true once the pixel is done.
+    auto blend = [&](int j, const PairEval& pe) -> bool {
+      const float* rec = s_rec + j * kRec;
+      const float Tn = __fmul_rn(T, __fsub_rn(1.0f, pe.alpha));
+      if (Tn < kTMin) {
+        done = true;
+        return true;
+      }
+      if (kCount) ++contribs;
+      const float w = pe.alpha * T;
+      C0 = fmaf(w, rec[7], C0);
+      C1 = fmaf(w, rec[8], C1);
+      C2 = fmaf(w, rec[9], C2);
+      Z = fmaf(w, rec[6], Z);
+      const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * D);
+      const float2 w2 = make_float2(w, w);
 #pragma unroll
-        for (int d4 = 0; d4 < D / 4; ++d4) {
-          const float4 f = f4[d4];
-          F[2 * d4] = __ffma2_rn(w2, make_float2(f.x, f.y), F[2 * d4]);
-          F[2 * d4 + 1] = __ffma2_rn(w2, make_float2(f.z, f.w), F[2 * d4 + 1]);
+      for (int d4 = 0; d4 < D / 4; ++d4) {
+        const float4 f = f4[d4];
+        F[2 * d4] = __ffma2_rn(w2, make_float2(f.x, f.y), F[2 * d4]);
+        F[2 * d4 + 1] = __ffma2_rn(w2, make_float2(f.z, f.w), F[2 * d4 + 1]);
+      }
+      T = Tn;
+      last = k * B + (uint32_t)j + 1u;
+      return false;
+    };
+    if (!done) {
+      if (kCount) {
+        // Counting form: every listed pair up to termination.
+        for (int j = 0; j < nb; ++j) {
+          PairEval pe;
+          ++visits;
+          if (eval_pair(s_rec + j * kRec, pxc, pyc, pe) && blend(j, pe)) break;
         }
-        T = Tn;
-        last = k * B + (uint32_t)j + 1u;
+      } else {
+        // Two entries evaluated ahead of their (ordered) blending: the two
+        // evaluations are independent, only the blend carries T.
+        int j = 0;
+        for (; j + 1 < nb; j += 2) {
+          PairEval p0, p1;
+          const bool h0 = eval_pair(s_rec + j * kRec, pxc, pyc, p0);
+          const bool h1 = eval_pair(s_rec + (j + 1) * kRec, pxc, pyc, p1);
+          if (h0 && blend(j, p0)) break;
+          if (h1 && blend(j + 1, p1)) break;
+        }
+        if (!done && j == nb - 1) {
+          PairEval pe;
+          if (eval_pair(s_rec + j * kRec, pxc, pyc, pe)) blend(j, pe);
+        }
       }
     }
   }
