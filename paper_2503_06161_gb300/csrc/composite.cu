@@ -268,7 +268,7 @@ struct BwdCfg {
 };
 
 template <int D>
-__global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const CompositeArgs a) {
+__global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kernel(const CompositeArgs a) {
   using K = BwdCfg<D>;
   constexpr int B = K::B, NC = K::NC, GS = K::GS, WS = K::WS, NP = partial_stride(D);
   constexpr int NV = kPartialScalars + D;  // values per row
@@ -388,51 +388,48 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
     const uint32_t rel0 = batch_lo(k);
     uint32_t jact = 0;
     if (rel0 < wmax) {
-      for (int j = nb - 1; j >= 0; --j) {
+      // Entry j given its evaluation (hit: the pixel includes it): the T
+      // replay, the gradient terms, and their warp sums.
+      auto entry = [&](int j, bool hit, const PairEval& pe) {
         float v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[q] = 0.0f;
         float w = 0.0f;
-        bool contrib = false;
-        if (live && rel0 + (uint32_t)j < nc) {
+        if (hit) {
           const float* rec = s_rec + j * kRec;
-          PairEval pe;
-          if (eval_pair(rec, pxc, pyc, pe)) {
-            contrib = true;
-            const float one_m = 1.0f - pe.alpha;
-            const float inv = __fdividef(1.0f, one_m);  // one_m >= 0.01
-            T = T * inv;  // transmittance before this Gaussian
-            w = pe.alpha * T;
-            // s = g . (rgb, depth, feature) of this Gaussian.
-            const float4 r4 = *reinterpret_cast<const float4*>(rec + 4);  // ., ., depth, r
-            const float4 r8 = *reinterpret_cast<const float4*>(rec + 8);  // g, b, ., .
-            const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * D);
-            // Even and odd channels summed in the two halves of a pair.
-            const float2* g2 = reinterpret_cast<const float2*>(grow);
-            float2 s2 = __fmul2_rn(K::GREG ? G[0] : g2[0], make_float2(r4.w, r8.x));
-            s2 = __ffma2_rn(K::GREG ? G[1] : g2[1], make_float2(r8.y, r4.z), s2);
+          const float one_m = 1.0f - pe.alpha;
+          const float inv = __fdividef(1.0f, one_m);  // one_m >= 0.01
+          T = T * inv;  // transmittance before this Gaussian
+          w = pe.alpha * T;
+          // s = g . (rgb, depth, feature) of this Gaussian.
+          const float4 r4 = *reinterpret_cast<const float4*>(rec + 4);  // ., ., depth, r
+          const float4 r8 = *reinterpret_cast<const float4*>(rec + 8);  // g, b, ., .
+          const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * D);
+          // Even and odd channels summed in the two halves of a pair.
+          const float2* g2 = reinterpret_cast<const float2*>(grow);
+          float2 s2 = __fmul2_rn(K::GREG ? G[0] : g2[0], make_float2(r4.w, r8.x));
+          s2 = __ffma2_rn(K::GREG ? G[1] : g2[1], make_float2(r8.y, r4.z), s2);
 #pragma unroll
-            for (int d4 = 0; d4 < D / 4; ++d4) {
-              const float4 xv = f4[d4];
-              s2 = __ffma2_rn(K::GREG ? G[2 + 2 * d4] : g2[2 + 2 * d4], make_float2(xv.x, xv.y), s2);
-              s2 = __ffma2_rn(K::GREG ? G[3 + 2 * d4] : g2[3 + 2 * d4], make_float2(xv.z, xv.w), s2);
-            }
-            const float s = s2.x + s2.y;
-            const float dalpha = T * s - (Q - ga * Tf) * inv;
-            Q = fmaf(w, s, Q);
-            if (!pe.clamped) {
-              const float dp2 = dalpha * pe.alpha * kLn2;
-              v[0] = -dp2 * (2.0f * rec[2] * pe.dx + rec[3] * pe.dy);
-              v[1] = -dp2 * (2.0f * rec[4] * pe.dy + rec[3] * pe.dx);
-              v[2] = dp2 * pe.dx * pe.dx;
-              v[3] = dp2 * pe.dx * pe.dy;
-              v[4] = dp2 * pe.dy * pe.dy;
-              v[5] = dalpha * pe.G;
-            }
+          for (int d4 = 0; d4 < D / 4; ++d4) {
+            const float4 xv = f4[d4];
+            s2 = __ffma2_rn(K::GREG ? G[2 + 2 * d4] : g2[2 + 2 * d4], make_float2(xv.x, xv.y), s2);
+            s2 = __ffma2_rn(K::GREG ? G[3 + 2 * d4] : g2[3 + 2 * d4], make_float2(xv.z, xv.w), s2);
+          }
+          const float s = s2.x + s2.y;
+          const float dalpha = T * s - (Q - ga * Tf) * inv;
+          Q = fmaf(w, s, Q);
+          if (!pe.clamped) {
+            const float dp2 = dalpha * pe.alpha * kLn2;
+            v[0] = -dp2 * (2.0f * rec[2] * pe.dx + rec[3] * pe.dy);
+            v[1] = -dp2 * (2.0f * rec[4] * pe.dy + rec[3] * pe.dx);
+            v[2] = dp2 * pe.dx * pe.dx;
+            v[3] = dp2 * pe.dx * pe.dy;
+            v[4] = dp2 * pe.dy * pe.dy;
+            v[5] = dalpha * pe.G;
           }
         }
         slice[lane * WS + j] = w;
-        if (__ballot_sync(0xFFFFFFFFu, contrib)) {
+        if (__ballot_sync(0xFFFFFFFFu, hit)) {
           jact |= 1u << j;
           // Reduce-scatter of v[0..7] over the warp: lane 4m ends with index m.
           const int b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1;
@@ -458,6 +455,23 @@ __global__ void __launch_bounds__(kThreads) composite_bwd_kernel(const Composite
           const int m = lane >> 2;
           if ((lane & 3) == 0 && m < 6) s_geo[(warp * B + j) * 8 + m] = v[0];
         }
+      };
+      auto evaluate = [&](int j, PairEval& pe) -> bool {
+        return live && rel0 + (uint32_t)j < nc && eval_pair(s_rec + j * kRec, pxc, pyc, pe);
+      };
+      // Two entries evaluated ahead of their (ordered, back to front) replay.
+      int j = nb - 1;
+      for (; j >= 1; j -= 2) {
+        PairEval pa, pb;
+        const bool ha = evaluate(j, pa);
+        const bool hb = evaluate(j - 1, pb);
+        entry(j, ha, pa);
+        entry(j - 1, hb, pb);
+      }
+      if (j == 0) {
+        PairEval pe;
+        const bool h = evaluate(0, pe);
+        entry(0, h, pe);
       }
       __syncwarp();
       if (jact) {
