@@ -160,6 +160,7 @@ CompositeArgs composite_args(const Layout& L, void* ws, int feat_bf16, const voi
   if (L.with_backward) {
     c.partials = at<float>(ws, L.partials);
     c.pflags = at<uint32_t>(ws, L.pflags);
+    c.cmask = at<uint32_t>(ws, L.cmask);
   }
   return c;
 }

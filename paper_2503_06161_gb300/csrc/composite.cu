@@ -110,6 +110,14 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
   uint32_t last = 0;
   uint32_t visits = 0, contribs = 0;  // only used by the counting variant
   bool done = !inside;
+  // Entries of the current batch this pixel blended, per 32-entry group
+  // (up to four groups: B <= 128).
+  constexpr int NG = B / 32;
+  static_assert(NG >= 1 && NG <= 4, "blend masks cover at most four groups");
+  uint32_t cm0 = 0u, cm1 = 0u, cm2 = 0u, cm3 = 0u;
+  const bool track = !kCount && a.cmask != nullptr;
+  const size_t cslot0 = (size_t)(rg.x >> 5) + (size_t)tile;
+  const int lane = tid & 31, warp = tid >> 5;
   uint32_t k = 0;
   for (; k < nbatch; ++k) {
     // Every thread is past batch k-1 here, so its buffer may be refilled.
@@ -158,6 +166,14 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
       }
       T = Tn;
       last = k * B + (uint32_t)j + 1u;
+      if (track) {
+        const uint32_t bit = 1u << (j & 31);
+        const int g = j >> 5;
+        cm0 |= g == 0 ? bit : 0u;
+        if (NG > 1) cm1 |= g == 1 ? bit : 0u;
+        if (NG > 2) cm2 |= g == 2 ? bit : 0u;
+        if (NG > 3) cm3 |= g == 3 ? bit : 0u;
+      }
       return false;
     };
     if (!done) {
@@ -184,6 +200,15 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
           if (eval_pair(s_rec + j * kRec, pxc, pyc, pe)) blend(j, pe);
         }
       }
+    }
+    if (track) {
+      // The warp's blended entries of each group of this batch.
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const uint32_t m = __reduce_or_sync(0xFFFFFFFFu, g == 0 ? cm0 : g == 1 ? cm1 : g == 2 ? cm2 : cm3);
+        if (lane == 0 && k * B + 32u * g < n) a.cmask[(cslot0 + (k * B) / 32 + g) * 8 + warp] = m;
+      }
+      cm0 = cm1 = cm2 = cm3 = 0u;
     }
   }
   // After an early exit batch k is still in flight: it must land before the
@@ -339,8 +364,14 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
   // [max(rg.x, hi_k - B), hi_k) with hi_k = rg.x + maxn - k B.
   const uint32_t n = *s_maxn;
   const uint32_t nbatch = (n + B - 1) / B;
-  auto batch_lo = [&](uint32_t k) -> uint32_t { return n - k * B > (uint32_t)B ? n - (k + 1) * B : 0u; };
-  auto batch_len = [&](uint32_t k) -> int { return (int)(n - k * B - batch_lo(k)); };
+  // Batches aligned to multiples of B from the tile start (the first one
+  // processed, the last in list order, may be short).
+  auto batch_lo = [&](uint32_t k) -> uint32_t { return (nbatch - 1 - k) * (uint32_t)B; };
+  auto batch_len = [&](uint32_t k) -> int { return (int)min((uint32_t)B, n - batch_lo(k)); };
+  // With 32-entry batches the forward's masks say which entries blended in
+  // some pixel of this warp; the others are skipped.
+  const bool masked = B == 32 && a.cmask != nullptr;
+  const size_t cslot0 = (size_t)(rg.x >> 5) + (size_t)tile;
   // List entry and Gaussian of this thread's slot in batch k.
   auto slot = [&](uint32_t k, uint32_t& e, uint32_t& g) {
     e = 0u;
@@ -388,6 +419,14 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
     const uint32_t rel0 = batch_lo(k);
     uint32_t jact = 0;
     if (rel0 < wmax) {
+      const uint32_t lenmask = nb >= 32 ? 0xFFFFFFFFu : ((1u << nb) - 1u);
+      uint32_t todo = masked ? __ldg(a.cmask + (cslot0 + rel0 / 32) * 8 + warp) & lenmask : lenmask;
+      // Entries not visited keep w = 0.
+      {
+        float4* wrow = reinterpret_cast<float4*>(slice + lane * WS);
+#pragma unroll
+        for (int q = 0; q < B / 4; ++q) wrow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       // Entry j given its evaluation (hit: the pixel includes it): the T
       // replay, the gradient terms, and their warp sums.
       auto entry = [&](int j, bool hit, const PairEval& pe) {
@@ -428,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
             v[5] = dalpha * pe.G;
           }
         }
-        slice[lane * WS + j] = w;
+        if (hit) slice[lane * WS + j] = w;
         if (__ballot_sync(0xFFFFFFFFu, hit)) {
           jact |= 1u << j;
           // Reduce-scatter of v[0..7] over the warp: lane 4m ends with index m.
@@ -459,19 +498,22 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
       auto evaluate = [&](int j, PairEval& pe) -> bool {
         return live && rel0 + (uint32_t)j < nc && eval_pair(s_rec + j * kRec, pxc, pyc, pe);
       };
-      // Two entries evaluated ahead of their (ordered, back to front) replay.
-      int j = nb - 1;
-      for (; j >= 1; j -= 2) {
+      // The entries to visit, back to front, two evaluated ahead of their
+      // (ordered) replay.
+      while (todo) {
+        const int ja = 31 - __clz(todo);
+        todo &= ~(1u << ja);
         PairEval pa, pb;
-        const bool ha = evaluate(j, pa);
-        const bool hb = evaluate(j - 1, pb);
-        entry(j, ha, pa);
-        entry(j - 1, hb, pb);
-      }
-      if (j == 0) {
-        PairEval pe;
-        const bool h = evaluate(0, pe);
-        entry(0, h, pe);
+        const bool ha = evaluate(ja, pa);
+        if (todo) {
+          const int jb = 31 - __clz(todo);
+          todo &= ~(1u << jb);
+          const bool hb = evaluate(jb, pb);
+          entry(ja, ha, pa);
+          entry(jb, hb, pb);
+        } else {
+          entry(ja, ha, pa);
+        }
       }
       __syncwarp();
       if (jact) {

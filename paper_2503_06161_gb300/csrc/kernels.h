@@ -89,6 +89,7 @@ struct CompositeArgs {
   int64_t cap;       // list capacity: emission indices at or past it are skipped
   uint64_t* counts;  // non-NULL: counting variant of the forward (no outputs)
   uint32_t* err;     // header error bits (staging timeouts)
+  uint32_t* cmask;   // NULL, or per (tile, 32-entry group, warp) masks of blended entries
 };
 
 cudaError_t launch_composite_fwd(const CompositeArgs& a, cudaStream_t st);
