@@ -553,12 +553,19 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
     }
     if (lane == 0) s_jact[warp] = jact;
     __syncthreads();
-    // Fixed-order sum of the warp partials: one row per (tile, entry).
+    // Fixed-order sum of the warp partials: one row per (tile, entry) that
+    // some pixel of the tile blended (the other rows stay unwritten and
+    // unflagged, i.e. zero).
     const uint32_t* se = s_e + (k & 1) * B;
-    for (int item = tid; item < nb * NV; item += kThreads) {
+    uint32_t bm = 0;
+#pragma unroll
+    for (int w8 = 0; w8 < 8; ++w8) bm |= s_jact[w8];
+    const int nact = __popc(bm);
+    for (int item = tid; item < nact * NV; item += kThreads) {
       // q: 0..5 geometric terms, 6..9 rgb/depth, 10.. features; row index
       // puts the features first.
-      const int j = item / NV, q = item - j * NV;
+      const int ja = item / NV, q = item - ja * NV;
+      const int j = (int)__fns(bm, 0, ja + 1);  // the ja-th active entry
       float acc = 0.0f;
 #pragma unroll
       for (int w8 = 0; w8 < 8; ++w8) {
@@ -568,7 +575,8 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
       const int col = q < kPartialScalars ? D + q : q - kPartialScalars;
       if ((int64_t)se[j] < a.cap) a.partials[(size_t)se[j] * NP + col] = acc;
     }
-    if (tid < nb && (int64_t)se[tid] < a.cap) atomicOr(a.pflags + (se[tid] >> 5), 1u << (se[tid] & 31u));
+    if (tid < nb && ((bm >> tid) & 1u) && (int64_t)se[tid] < a.cap)
+      atomicOr(a.pflags + (se[tid] >> 5), 1u << (se[tid] & 31u));
   }
 }
 
