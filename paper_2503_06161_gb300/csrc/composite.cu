@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
       __syncthreads();
       s_feat = s_wide;
     }
+    uint32_t cur = 0u;  // blended entries of the current 32-entry group
     // Blend entry j (pe: its evaluation); true once the pixel is done.
     auto blend = [&](int j, const PairEval& pe) -> bool {
       const float* rec = s_rec + j * kRec;
@@ -166,14 +167,7 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
       }
       T = Tn;
       last = k * B + (uint32_t)j + 1u;
-      if (track) {
-        const uint32_t bit = 1u << (j & 31);
-        const int g = j >> 5;
-        cm0 |= g == 0 ? bit : 0u;
-        if (NG > 1) cm1 |= g == 1 ? bit : 0u;
-        if (NG > 2) cm2 |= g == 2 ? bit : 0u;
-        if (NG > 3) cm3 |= g == 3 ? bit : 0u;
-      }
+      cur |= 1u << (j & 31);
       return false;
     };
     if (!done) {
@@ -185,19 +179,28 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
           if (eval_pair(s_rec + j * kRec, pxc, pyc, pe) && blend(j, pe)) break;
         }
       } else {
-        // Two entries evaluated ahead of their (ordered) blending: the two
-        // evaluations are independent, only the blend carries T.
-        int j = 0;
-        for (; j + 1 < nb; j += 2) {
-          PairEval p0, p1;
-          const bool h0 = eval_pair(s_rec + j * kRec, pxc, pyc, p0);
-          const bool h1 = eval_pair(s_rec + (j + 1) * kRec, pxc, pyc, p1);
-          if (h0 && blend(j, p0)) break;
-          if (h1 && blend(j + 1, p1)) break;
-        }
-        if (!done && j == nb - 1) {
-          PairEval pe;
-          if (eval_pair(s_rec + j * kRec, pxc, pyc, pe)) blend(j, pe);
+        // Groups of 32 entries; within a group two entries are evaluated
+        // ahead of their (ordered) blending: the two evaluations are
+        // independent, only the blend carries T.
+        for (int g = 0; g < NG && !done; ++g) {
+          const int je = min(nb, 32 * g + 32);
+          int j = 32 * g;
+          cur = 0u;
+          for (; j + 1 < je; j += 2) {
+            PairEval p0, p1;
+            const bool h0 = eval_pair(s_rec + j * kRec, pxc, pyc, p0);
+            const bool h1 = eval_pair(s_rec + (j + 1) * kRec, pxc, pyc, p1);
+            if (h0 && blend(j, p0)) break;
+            if (h1 && blend(j + 1, p1)) break;
+          }
+          if (!done && j == je - 1) {
+            PairEval pe;
+            if (eval_pair(s_rec + j * kRec, pxc, pyc, pe)) blend(j, pe);
+          }
+          cm0 |= g == 0 ? cur : 0u;
+          if (NG > 1) cm1 |= g == 1 ? cur : 0u;
+          if (NG > 2) cm2 |= g == 2 ? cur : 0u;
+          if (NG > 3) cm3 |= g == 3 ? cur : 0u;
         }
       }
     }
