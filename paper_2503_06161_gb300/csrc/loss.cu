@@ -36,14 +36,27 @@ __global__ void __launch_bounds__(256) l1_grad_kernel(const float* __restrict__ 
   int64_t done = 0;
   if (vec) {
     const int64_t n4 = n / 4;
-    for (int64_t i = i0; i < n4; i += stride) {
-      const float4 p = reinterpret_cast<const float4*>(pred)[i];
-      const float4 t = reinterpret_cast<const float4*>(target)[i];
+    auto sg = [&](float d) { return d > 0.0f ? inv_rows : (d < 0.0f ? -inv_rows : 0.0f); };
+    auto one = [&](const float4 p, const float4 t, int64_t i) {
       const float d0 = p.x - t.x, d1 = p.y - t.y, d2 = p.z - t.z, d3 = p.w - t.w;
       acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
-      auto sg = [&](float d) { return d > 0.0f ? inv_rows : (d < 0.0f ? -inv_rows : 0.0f); };
       reinterpret_cast<float4*>(grad)[i] = make_float4(sg(d0), sg(d1), sg(d2), sg(d3));
+    };
+    // Four groups in flight per thread; the additions keep the same order
+    // as one group at a time.
+    int64_t i = i0;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+      float4 p[4], t[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        p[u] = __ldcs(reinterpret_cast<const float4*>(pred) + i + u * stride);
+        t[u] = __ldcs(reinterpret_cast<const float4*>(target) + i + u * stride);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) one(p[u], t[u], i + u * stride);
     }
+    for (; i < n4; i += stride)
+      one(reinterpret_cast<const float4*>(pred)[i], reinterpret_cast<const float4*>(target)[i], i);
     done = n4 * 4;
   }
   for (int64_t i = done + i0; i < n; i += stride) {
