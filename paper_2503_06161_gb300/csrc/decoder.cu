@@ -58,14 +58,23 @@ constexpr uint64_t kLayoutNone = 0, kLayout128B = 2, kLayout64B = 4;
 
 template <int D>
 struct DecCfg {
+  // F tiles in flight (D = 64: two, its larger tiles fill shared memory).
+  static constexpr int kFStages = D == 32 ? 3 : 2;
+  static_assert(kFStages <= 3, "barrier slots for three F stages");
   static constexpr uint32_t row_bytes = D * 2;  // one F / W row in bf16
   static constexpr uint64_t layout = D == 64 ? kLayout128B : kLayout64B;
   static constexpr uint32_t sbo = 8 * row_bytes;  // stride of 8-row groups
   static constexpr uint32_t w_bytes = kDecN * row_bytes;
   static constexpr uint32_t f_bytes = kDecBM * row_bytes;
+  // D = 32: each F stage is followed by an all-ones panel of the same
+  // shape, so one product (N = D + 16) yields dW and, in its extra columns,
+  // db; and dF is double-buffered in tensor memory.  D = 64 has no room for
+  // either (shared memory, tensor-memory columns).
+  static constexpr bool merged = D == 32;
+  static constexpr uint32_t f_stride = merged ? 2 * f_bytes : f_bytes;
   static constexpr uint32_t off_w = 0;
-  static constexpr uint32_t off_f = off_w + w_bytes;      // 2 stages
-  static constexpr uint32_t off_t = off_f + 2 * f_bytes;  // target boxes / S panels
+  static constexpr uint32_t off_f = off_w + w_bytes;                  // kFStages stages
+  static constexpr uint32_t off_t = off_f + kFStages * f_stride;      // target boxes / S panels
   static constexpr uint32_t off_ones = off_t + kTSlots * kBoxBytes;
   static constexpr uint32_t off_bias = off_ones + 512;  // one 16 x 16 all-ones operand
   static constexpr uint32_t off_bar = off_bias + kDecN * 4;
@@ -92,8 +101,12 @@ struct DecArgs {
 
 // Barrier slots (8 bytes each) after off_bar.
 enum : int {
-  kBarW = 0, kBarFFull = 1, kBarFEmpty = 3, kBarTFull = 5, kBarTEmpty = kBarTFull + kTSlots,
-  kBarAccFull = kBarTEmpty + 2, kBarAccEmpty, kBarSFull, kBarBwd, kBarDrain, kNumBars
+  kBarW = 0, kBarFFull = 1, kBarFEmpty = kBarFFull + 3, kBarTFull = kBarFEmpty + 3,  // up to 3 F stages
+  kBarTEmpty = kBarTFull + kTSlots,
+  kBarAccFull = kBarTEmpty + 2, kBarAccEmpty,
+  kBarSFull,                // [2] and
+  kBarBwd = kBarSFull + 2,  // [2]: tiles alternate, so no wait can see its barrier two phases on
+  kBarDrain = kBarBwd + 2, kNumBars
 };
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint64_t layout) {
@@ -200,6 +213,30 @@ __device__ __forceinline__ bool dec_wait(uint64_t* bar, uint32_t parity, volatil
   return false;
 }
 
+// Non-suspending poll (the tensor-core thread spins: its waits are on the
+// critical path of every tile).
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+template <bool kSpin>
+__device__ __forceinline__ bool dec_spin(uint64_t* bar, uint32_t parity, volatile int* abort, uint32_t* err) {
+  if (!kSpin) return dec_wait(bar, parity, abort, err);
+  if (*abort) return false;
+  for (int i = 0; i < (1 << 26); ++i)
+    if (mbar_test(bar, parity)) return true;
+  *abort = 1;
+  set_err(err, kErrTimeout);
+  return false;
+}
+
+
 template <int D, int MODE>
 __global__ void __launch_bounds__(kDecThreads, 1)
     decoder_kernel(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_w,
@@ -228,16 +265,18 @@ __global__ void __launch_bounds__(kDecThreads, 1)
 
   if (tid == 0) {
     mbar_init(&bars[kBarW], 1);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < C::kFStages; ++s) {
       mbar_init(&bars[kBarFFull + s], 1);
       mbar_init(&bars[kBarFEmpty + s], 1);
-      mbar_init(&bars[kBarTEmpty + s], 1);  // tensor-core commit after the reverse products
     }
+    for (int s = 0; s < 2; ++s) mbar_init(&bars[kBarTEmpty + s], 1);  // commit after the reverse products
     for (int s = 0; s < kTSlots; ++s) mbar_init(&bars[kBarTFull + s], 1);
     mbar_init(&bars[kBarAccFull], 1);
     mbar_init(&bars[kBarAccEmpty], kEpiWarps);
     mbar_init(&bars[kBarSFull], kEpiWarps);
+    mbar_init(&bars[kBarSFull + 1], kEpiWarps);
     mbar_init(&bars[kBarBwd], 1);
+    mbar_init(&bars[kBarBwd + 1], 1);
     mbar_init(&bars[kBarDrain], 1);
     *s_abort = 0;
     mbar_init_fence();
@@ -247,6 +286,12 @@ __global__ void __launch_bounds__(kDecThreads, 1)
     uint4* ones = reinterpret_cast<uint4*>(sm + C::off_ones);
     for (int i = tid; i < 512 / 16; i += 32 * kEpiWarps)
       ones[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    if (C::merged)
+      for (int s = 0; s < C::kFStages; ++s) {
+        uint4* op = reinterpret_cast<uint4*>(sm + C::off_f + s * C::f_stride + C::f_bytes);
+        for (int i = tid; i < (int)(C::f_bytes / 16); i += 32 * kEpiWarps)
+          op[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+      }
     for (int i = tid; i < kDecN; i += 32 * kEpiWarps) s_bias[i] = a.bias[i];
     fence_proxy_async();
   }
@@ -268,16 +313,16 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       mbar_arrive_expect_tx(&bars[kBarW], C::w_bytes);
       tma_2d(sm + C::off_w, &tm_w, 0, 0, &bars[kBarW]);
       for (int i = 0; i < n_mine; ++i) {
-        const int f = i & 1;
-        if (!dec_wait(&bars[kBarFEmpty + f], ((i >> 1) & 1) ^ 1, s_abort, a.err)) break;
+        const int f = i % C::kFStages;
+        if (!dec_wait(&bars[kBarFEmpty + f], ((i / C::kFStages) & 1) ^ 1, s_abort, a.err)) break;
         mbar_arrive_expect_tx(&bars[kBarFFull + f], C::f_bytes);
-        tma_2d(sm + C::off_f + f * C::f_bytes, &tm_f, 0, ((int)blockIdx.x + i * (int)gridDim.x) * kDecBM,
+        tma_2d(sm + C::off_f + f * C::f_stride, &tm_f, 0, ((int)blockIdx.x + i * (int)gridDim.x) * kDecBM,
                &bars[kBarFFull + f]);
         ++f_uses;
       }
       // Every copy issued must have landed before the block leaves.
-      for (uint32_t u = f_uses > 2 ? f_uses - 2 : 0; u < f_uses; ++u)
-        if (!mbar_wait(&bars[kBarFFull + (u & 1)], (u >> 1) & 1)) set_err(a.err, kErrTimeout);
+      for (uint32_t u = f_uses > C::kFStages ? f_uses - C::kFStages : 0; u < f_uses; ++u)
+        if (!mbar_wait(&bars[kBarFFull + u % C::kFStages], (u / C::kFStages) & 1)) set_err(a.err, kErrTimeout);
       if (!mbar_wait(&bars[kBarW], 0)) set_err(a.err, kErrTimeout);
     }
   } else if (warp >= kWarpT0) {
@@ -309,16 +354,16 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       const uint32_t s_w = sb + C::off_w, s_t = sb + C::off_t, s_ones = sb + C::off_ones;
       constexpr uint32_t id_fwd = mma_idesc(128, kDecN, 0, 0);
       constexpr uint32_t id_df = mma_idesc(128, D, 0, 1);
-      constexpr uint32_t id_dw = mma_idesc(128, D, 1, 1);
+      constexpr uint32_t id_dw = mma_idesc(128, C::merged ? D + 16 : D, 1, 1);
       constexpr uint32_t id_db = mma_idesc(128, 16, 1, 1);
       // acc = F W^T: A = F (K-major), B = W (K-major); 16 channels of K are
       // 32 bytes along each swizzled row.
       auto forward = [&](int i) -> bool {
-        const int f = i & 1;
-        if (!dec_wait(&bars[kBarFFull + f], (i >> 1) & 1, s_abort, a.err)) return false;
-        if (i > 0 && !dec_wait(&bars[kBarAccEmpty], (i - 1) & 1, s_abort, a.err)) return false;
+        const int f = i % C::kFStages;
+        if (!dec_spin<C::merged>(&bars[kBarFFull + f], (i / C::kFStages) & 1, s_abort, a.err)) return false;
+        if (i > 0 && !dec_spin<C::merged>(&bars[kBarAccEmpty], (i - 1) & 1, s_abort, a.err)) return false;
         tc_fence_after();
-        const uint32_t s_f = sb + C::off_f + f * C::f_bytes;
+        const uint32_t s_f = sb + C::off_f + f * C::f_stride;
 #pragma unroll
         for (int k = 0; k < D / 16; ++k)
           mma_bf16(tmem + kColAcc, smem_desc(s_f + 32 * k, 16, C::sbo, C::layout),
@@ -328,7 +373,7 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       };
       bool ok = dec_wait(&bars[kBarW], 0, s_abort, a.err) && (n_mine == 0 || forward(0));
       for (int i = 0; ok && i < n_mine; ++i) {
-        const int f = i & 1;
+        const int f = i % C::kFStages;
         if (!kL1) {
           mma_commit(&bars[kBarFEmpty + f]);
           if (i + 1 < n_mine && !forward(i + 1)) break;
@@ -336,15 +381,16 @@ __global__ void __launch_bounds__(kDecThreads, 1)
         }
         // The next tile's forward product goes ahead of this tile's reverse.
         if (i + 1 < n_mine && !forward(i + 1)) break;
-        if (!dec_wait(&bars[kBarSFull], i & 1, s_abort, a.err)) break;
+        if (!dec_spin<C::merged>(&bars[kBarSFull + (i & 1)], (i >> 1) & 1, s_abort, a.err)) break;
         tc_fence_after();
         const uint32_t s_s = s_t + (i % kBufs) * kTBufBytes;  // S panels of this tile
-        const uint32_t s_f = sb + C::off_f + f * C::f_bytes;
+        const uint32_t s_f = sb + C::off_f + f * C::f_stride;
+        const uint32_t col_df = kColDF + (C::merged ? (i & 1) * D : 0);  // dF buffer of this tile
         // dF = S W: A = S (K-major, 128B swizzle, 64-channel panels),
         // B = W read MN-major (K = channel rows, N = D along each row).
 #pragma unroll
         for (int k = 0; k < kDecN / 16; ++k)
-          mma_bf16(tmem + kColDF, smem_desc(s_s + (k >> 2) * kPanel + (k & 3) * 32, 16, 1024, kLayout128B),
+          mma_bf16(tmem + col_df, smem_desc(s_s + (k >> 2) * kPanel + (k & 3) * 32, 16, 1024, kLayout128B),
                    smem_desc(s_w + k * 16 * C::row_bytes, 16, C::sbo, C::layout), id_df, k > 0);
         // dW += S^T F and db += S^T 1: A = S read MN-major (M = channels,
         // two 64-channel panels per half), B = F read MN-major / all ones.
@@ -354,12 +400,15 @@ __global__ void __launch_bounds__(kDecThreads, 1)
           for (int k = 0; k < kDecBM / 16; ++k) {
             const uint64_t ad = smem_desc(s_s + h * 2 * kPanel + k * 2048, kPanel, 1024, kLayout128B);
             const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
-            mma_bf16(tmem + kColDW + 64 * h, ad, smem_desc(s_f + k * 16 * C::row_bytes, 16, C::sbo, C::layout),
-                     id_dw, acc);
-            mma_bf16(tmem + kColDB + 16 * h, ad, smem_desc(s_ones, 256, 128, kLayoutNone), id_db, acc);
+            // Merged: B = [F | ones] along N (the ones panel one stride on).
+            mma_bf16(tmem + kColDW + 64 * h, ad,
+                     smem_desc(s_f + k * 16 * C::row_bytes, C::merged ? C::f_bytes : 16, C::sbo, C::layout), id_dw,
+                     acc);
+            if (!C::merged)
+              mma_bf16(tmem + kColDB + 16 * h, ad, smem_desc(s_ones, 256, 128, kLayoutNone), id_db, acc);
           }
         }
-        mma_commit(&bars[kBarBwd]);
+        mma_commit(&bars[kBarBwd + (i & 1)]);
         mma_commit(&bars[kBarFEmpty + f]);
         mma_commit(&bars[kBarTEmpty + (i % kBufs)]);
       }
@@ -378,8 +427,9 @@ __global__ void __launch_bounds__(kDecThreads, 1)
     auto store_df = [&](int j) {
       const int64_t pj = ((int64_t)blockIdx.x + (int64_t)j * gridDim.x) * kDecBM + r;
       uint32_t v[32];
-      if (D == 32) tmem_ld16(t_row + kColDF + 16 * h, v);
-      else tmem_ld32(t_row + kColDF + 32 * h, v);
+      const uint32_t col = kColDF + (C::merged ? (j & 1) * D : 0);  // dF buffer of tile j
+      if (D == 32) tmem_ld16(t_row + col + 16 * h, v);
+      else tmem_ld32(t_row + col + 32 * h, v);
       tmem_wait_ld(v);
       if (pj < a.HW) {
         float4* o = reinterpret_cast<float4*>(a.d_feat + pj * D + (D / 2) * h);
@@ -477,10 +527,27 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       if (lane == 0) mbar_arrive(&bars[kBarAccEmpty]);
       if (!ok) break;
       if (!kL1) continue;
+      if (C::merged) {
+        // dF is double-buffered: release this tile's S at once, then store
+        // the previous tile's dF (its reverse products ran meanwhile).
+        fence_proxy_async();  // S stores -> tensor-core reads
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars[kBarSFull + (i & 1)]);
+        if (i > 0) {
+          if (!dec_wait(&bars[kBarBwd + ((i - 1) & 1)], ((i - 1) >> 1) & 1, s_abort, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          store_df(i - 1);
+          tc_fence_before();
+        }
+        continue;
+      }
       // dF of the previous tile (its reverse products ran while this tile
       // was processed), before this tile's products may overwrite it.
       if (i > 0) {
-        if (!dec_wait(&bars[kBarBwd], (i - 1) & 1, s_abort, a.err)) {
+        if (!dec_wait(&bars[kBarBwd + ((i - 1) & 1)], ((i - 1) >> 1) & 1, s_abort, a.err)) {
           ok = false;
           break;
         }
@@ -490,10 +557,11 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       }
       fence_proxy_async();  // S stores -> tensor-core reads
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bars[kBarSFull]);
+      if (lane == 0) mbar_arrive(&bars[kBarSFull + (i & 1)]);
     }
     if (kL1) {
-      if (ok && n_mine > 0 && dec_wait(&bars[kBarBwd], (n_mine - 1) & 1, s_abort, a.err)) {
+      if (ok && n_mine > 0 &&
+          dec_wait(&bars[kBarBwd + ((n_mine - 1) & 1)], ((n_mine - 1) >> 1) & 1, s_abort, a.err)) {
         tc_fence_after();
         store_df(n_mine - 1);
       }
@@ -516,7 +584,8 @@ __global__ void __launch_bounds__(kDecThreads, 1)
                                __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
         }
         uint32_t vb1;
-        tmem_ld1(t_row + kColDB + 16 * h, vb1);
+        // db: a column of its own, or (merged) column D of the dW product.
+        tmem_ld1(t_row + (C::merged ? kColDW + 64 * h + D : kColDB + 16 * h), vb1);
         tmem_wait_ld1(vb1);
         a.part_db[(size_t)blockIdx.x * kDecN + c] = __uint_as_float(vb1);
       }
