@@ -74,6 +74,7 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--t", type=float, default=0.5)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--D", type=int, default=None, help="feature width override (16, 32, 64, 128): D sweep")
     p.add_argument("--micro", choices=["decoder", "adam"], default=None,
                    help="time one HBM-bound kernel alone on the workload's sizes")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -172,7 +173,7 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     cfg = synth.CONFIGS[args.workload]
-    sc, cam_np, df_np = synth.config_inputs(args.workload)
+    sc, cam_np, df_np = synth.config_inputs(args.workload, D=args.D)
     t = (args.t + rank / max(world, 1)) % 1.0 if world > 1 else args.t
     P, D, W, H = sc.P, sc.D, cam_np.width, cam_np.height
     HW = W * H

@@ -222,12 +222,13 @@ CONFIGS = {
 }
 
 
-def config_inputs(name: str, P: int | None = None):
+def config_inputs(name: str, P: int | None = None, D: int | None = None):
     """(scene, camera, deform-or-None) for a named workload; ``P`` overrides
-    the Gaussian count (same distributions) for scaled-down test cases."""
+    the Gaussian count (same distributions) for scaled-down test cases, ``D``
+    the feature width (feature-width sweeps)."""
     c = CONFIGS[name]
     n = c["P"] if P is None else P
-    scene = make_scene(n, c["D"], c["lo"], c["hi"], seed=c["seed"], bf16_storage=c["bf16"])
+    scene = make_scene(n, c["D"] if D is None else D, c["lo"], c["hi"], seed=c["seed"], bf16_storage=c["bf16"])
     cam = make_camera(c["W"], c["H"], c["f"])
     deform = make_deform(n, bbox_min=(-2, -2, 3), bbox_max=(2, 2, 8)) if c["deform"] else None
     return scene, cam, deform
