@@ -112,3 +112,13 @@ def test_adam_host_side_status_codes(lib):
     assert lib.fe_adam_step(g, 1, 1, 0.9, 0.999, 1e-15, None) == 1
     g[0].n = 0                                                            # empty group: nothing to do
     assert lib.fe_adam_step(g, 1, 1, 0.9, 0.999, 1e-15, None) == 0
+
+
+def test_sum_host_side_status_codes(lib):
+    srcs = (ctypes.c_void_p * 2)(16, 32)
+    assert lib.fe_sum_f32(None, srcs, 2, 8, None) == 1
+    assert lib.fe_sum_f32(16, None, 2, 8, None) == 1
+    assert lib.fe_sum_f32(16, srcs, 0, 8, None) == 1          # no sources
+    assert lib.fe_sum_f32(16, srcs, 9, 8, None) == 1          # more than 8
+    assert lib.fe_sum_f32(8, srcs, 2, 8, None) == 1           # misaligned destination
+    assert lib.fe_sum_f32(16, srcs, 2, 0, None) == 0          # nothing to add
