@@ -164,7 +164,7 @@ def run_ours(args, world, rank, local):
     from paper_2503_06161_gb300 import _lib, synth
     from paper_2503_06161_gb300.decoder import Decoder
     from paper_2503_06161_gb300.optim import Adam
-    from paper_2503_06161_gb300.train import LR
+    from paper_2503_06161_gb300.train import LAMBDA_DEPTH, LR
     from paper_2503_06161_gb300.raster import DeformField, GaussianScene, Rasterizer, camera_struct
 
     torch.cuda.set_device(local)
@@ -211,12 +211,18 @@ def run_ours(args, world, rank, local):
     if dec is not None:
         dec.workspace(HW)
         dec_out = (torch.empty(1, **kw), g_feat, torch.empty(256, D, **kw), torch.empty(256, **kw))
-    losses = torch.zeros(2, **kw)
-    scratch = torch.empty(2048, **kw)
+    losses = torch.zeros(3, **kw)
+    scratch = torch.empty(3072, **kw)
     grads = dict(means=torch.empty(P, 3, **kw), log_scales=torch.empty(P, 3, **kw), quats=torch.empty(P, 4, **kw),
                  opacity_logits=torch.empty(P, **kw), sh=torch.empty(P, 16, 3, **kw), feat=torch.empty(P, D, **kw))
     opt = None
+    tgt_depth = g_depth = None
     if cfg.get("train"):
+        # The training loss adds lambda_depth * L1 depth against a depth map
+        # (Eq. 11).
+        tgt_depth = torch.as_tensor(synth.make_depth_target(H, W, cfg["lo"][2], cfg["hi"][2]), device=dev)
+        g_depth = torch.empty(H, W, **kw)
+        depth_rows = round(HW / LAMBDA_DEPTH)
         # Training workloads: Adam on FP32 masters of every Gaussian
         # parameter and the decoder; bf16 SH / feature / decoder storage is
         # refreshed from the masters by the same launch.
@@ -233,7 +239,7 @@ def run_ours(args, world, rank, local):
 
     def feat_loss(tgt, evs=None):
         if dec is None:
-            _lib.fe_l1_loss_grad(out[3], tgt, HW, g_feat, losses[1:2], scratch[1024:])
+            _lib.fe_l1_loss_grad(out[3], tgt, HW, g_feat, losses[1:2], scratch[1024:2048])
             return
         if evs is not None:
             evs[0].record(stream)
@@ -241,11 +247,16 @@ def run_ours(args, world, rank, local):
         if evs is not None:
             evs[1].record(stream)
 
+    def depth_loss(tgt):
+        if tgt is not None:
+            _lib.fe_l1_loss_grad(out[1], tgt, depth_rows, g_depth, losses[2:3], scratch[2048:])
+
     def step(sc_obj=scene, df_obj=deform, evs=None):
         rast.forward(sc_obj, cam, df_obj, t, out=out, feat_bf16=feat_bf)
         _lib.fe_l1_loss_grad(out[0], tgt_rgb, HW, g_rgb, losses[0:1], scratch[:1024])
         feat_loss(tgt_feat, evs)
-        rast.backward(sc_obj, cam, df_obj, t, g_rgb, None, None, g_feat, grads=grads)
+        depth_loss(tgt_depth)
+        rast.backward(sc_obj, cam, df_obj, t, g_rgb, g_depth, None, g_feat, grads=grads)
         if opt is not None:
             if evs is not None:
                 evs[2].record(stream)
@@ -368,12 +379,14 @@ def run_ours(args, world, rank, local):
         host = {k: v.detach().cpu().pin_memory() for k, v in dict(
             means=scene.means, log_scales=scene.log_scales, quats=scene.quats, opacity_logits=scene.opacity_logits,
             sh=scene.sh, feat=scene.feat, tgt_rgb=tgt_rgb, tgt_feat=tgt_feat).items()}
+        if tgt_depth is not None:
+            host["tgt_depth"] = tgt_depth.cpu().pin_memory()
         if deform is not None:
             for k in ("planes", "w1", "b1", "w2", "b2", "wh", "bh", "noise"):
                 host["df_" + k] = getattr(deform, k).detach().cpu().pin_memory()
         dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
         host_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in grads.items()}
-        host_loss = torch.empty(2).pin_memory()
+        host_loss = torch.empty(3).pin_memory()
         sc_e = GaussianScene(dev_in["means"], dev_in["log_scales"], dev_in["quats"], dev_in["opacity_logits"],
                              dev_in["sh"], dev_in["feat"], scene.sh_degree)
         df_e = None
@@ -382,7 +395,7 @@ def run_ours(args, world, rank, local):
                                dev_in["df_b2"], dev_in["df_wh"], dev_in["df_bh"], deform.bbox_min, deform.bbox_max,
                                dev_in["df_noise"], deform.noise_scale)
         h2d = sum(v.numel() * v.element_size() for v in host.values())
-        d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + 8
+        d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + host_loss.numel() * 4
 
         def e2e_step():
             for k, v in host.items():
@@ -390,7 +403,8 @@ def run_ours(args, world, rank, local):
             rast.forward(sc_e, cam, df_e, t, out=out, feat_bf16=feat_bf)
             _lib.fe_l1_loss_grad(out[0], dev_in["tgt_rgb"], HW, g_rgb, losses[0:1], scratch[:1024])
             feat_loss(dev_in["tgt_feat"])
-            rast.backward(sc_e, cam, df_e, t, g_rgb, None, None, g_feat, grads=grads)
+            depth_loss(dev_in.get("tgt_depth"))
+            rast.backward(sc_e, cam, df_e, t, g_rgb, g_depth, None, g_feat, grads=grads)
             if opt is not None:
                 opt.step([grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"], grads["sh"],
                           grads["feat"], dec_out[2], dec_out[3]])
@@ -416,7 +430,9 @@ def run_ours(args, world, rank, local):
     # feature sums, projection chain (+ deformation chain).
     # (With a decoder, its kernel and fixed-order sum replace the two
     # feature-L1 kernels.)
-    launches_per_step = 10 + 4 + 3 + (1 if deform is not None else 0) + (1 if opt is not None else 0)
+    # Training adds the depth L1 (2 kernels) and the Adam launch.
+    launches_per_step = (10 + 4 + 3 + (1 if deform is not None else 0) + (1 if opt is not None else 0)
+                         + (2 if tgt_depth is not None else 0))
     result = {
         "metric": METRIC, "value": round(world * 1000.0 / ms, 3), "unit": "it/s", "n_gpus": world,
         "steps": K_steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,

@@ -196,6 +196,18 @@ def make_targets(height: int, width: int, D: int, seed: int = 2, dec_channels: i
     return rgb, feat
 
 
+def make_depth_target(height: int, width: int, near: float, far: float, seed: int = 4):
+    """Depth-map target (the stereo depth a training view supervises with):
+    a smooth surface between near and far plus N(0, 1%) noise, [H,W]."""
+    rng = np.random.default_rng(seed)
+    y, x = np.meshgrid(np.linspace(0.0, 1.0, height), np.linspace(0.0, 1.0, width), indexing="ij")
+    a = rng.uniform(0.0, 2.0 * np.pi, 3)
+    s = 0.5 + 0.25 * np.sin(2.0 * np.pi * x + a[0]) * np.cos(np.pi * y + a[1]) + 0.2 * np.sin(3.0 * y + a[2])
+    d = near + (far - near) * np.clip(s, 0.0, 1.0)
+    d = d * (1.0 + 0.01 * rng.normal(size=d.shape))
+    return d.astype(np.float32)
+
+
 def make_decoder(D: int, cout: int = 256, seed: int = 3, w_std: float = 0.05, b_std: float = 0.0):
     """1x1 decoder parameters: weight [cout, D] N(0, w_std) rounded to bf16
     values (float32 array), bias [cout] N(0, b_std)."""

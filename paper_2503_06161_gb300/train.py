@@ -20,6 +20,10 @@ from .decoder import Decoder
 from .optim import Adam
 from .raster import DeformField, GaussianScene, Rasterizer, camera_struct
 
+# Loss weights of Eq. 11 (RGB, depth, feature); the TV term acts on the
+# deformation planes, whose gradients this pass does not produce.
+LAMBDA_RGB, LAMBDA_DEPTH, LAMBDA_FEAT = 1.0, 0.01, 1.0
+
 # Per-group learning rates (constant; the schedules of the paper's training
 # recipe are not part of this pass).
 LR = dict(means=1.6e-4, log_scales=5e-3, quats=1e-3, opacity_logits=5e-2, sh=2.5e-3, feat=2.5e-3,
@@ -61,8 +65,9 @@ class Trainer:
                     torch.empty(self.HW, self.D, **kw))
         self.feat_bf = torch.empty(self.HW, self.D, dtype=torch.bfloat16, device=device)
         self.g_rgb = torch.empty(3, H, W, **kw)
-        self.losses = torch.zeros(2, **kw)
-        self.scratch = torch.empty(1024, **kw)
+        self.g_depth = torch.empty(H, W, **kw)
+        self.losses = torch.zeros(3, **kw)  # L_rgb, L_feat, lambda_depth * L_depth
+        self.scratch = torch.empty(2, 1024, **kw)
         self.dec_out = (self.losses[1:2], torch.empty(self.HW, self.D, **kw), torch.empty(256, self.D, **kw),
                         torch.empty(256, **kw))
         self.grads = dict(means=torch.empty(P, 3, **kw), log_scales=torch.empty(P, 3, **kw),
@@ -87,17 +92,30 @@ class Trainer:
         dec = Decoder(torch.as_tensor(dec_w).to(torch.bfloat16).to(device), f(dec_b))
         return cls(masters, int(sc.sh_degree), cam, deform, dec, bf16_storage=bf16_storage, device=device, **kw)
 
-    def forward_backward(self, t: float, tgt_rgb: torch.Tensor, tgt_dec: torch.Tensor):
-        """Losses and gradients of one view at time t (no parameter update)."""
+    def forward_backward(self, t: float, tgt_rgb: torch.Tensor, tgt_dec: torch.Tensor,
+                         tgt_depth: torch.Tensor | None = None):
+        """Losses and gradients of one view at time t (no parameter update):
+        L1 RGB, the decoder's L1 feature loss, and (with a depth target) the
+        weighted L1 depth loss of Eq. 11."""
         self.rast.forward(self.scene, self.cam, self.deform, t, out=self.out, feat_bf16=self.feat_bf)
-        _lib.fe_l1_loss_grad(self.out[0], tgt_rgb, self.HW, self.g_rgb, self.losses[0:1], self.scratch)
+        _lib.fe_l1_loss_grad(self.out[0], tgt_rgb, self.HW, self.g_rgb, self.losses[0:1], self.scratch[0])
         self.dec.l1(self.feat_bf, tgt_dec, out=self.dec_out)
-        self.rast.backward(self.scene, self.cam, self.deform, t, self.g_rgb, None, None, self.dec_out[1],
+        g_depth = None
+        if tgt_depth is not None:
+            # lambda_depth * mean |depth - target|: the L1 kernel's row count
+            # HW / lambda_depth gives the weighted loss and gradient.
+            _lib.fe_l1_loss_grad(self.out[1], tgt_depth, round(self.HW / LAMBDA_DEPTH), self.g_depth,
+                                 self.losses[2:3], self.scratch[1])
+            g_depth = self.g_depth
+        self.rast.backward(self.scene, self.cam, self.deform, t, self.g_rgb, g_depth, None, self.dec_out[1],
                            grads=self.grads)
 
-    def step(self, t: float, tgt_rgb: torch.Tensor, tgt_dec: torch.Tensor) -> torch.Tensor:
-        """One training iteration; returns the device tensor [L_rgb, L_feat]."""
-        self.forward_backward(t, tgt_rgb, tgt_dec)
+    def step(self, t: float, tgt_rgb: torch.Tensor, tgt_dec: torch.Tensor,
+             tgt_depth: torch.Tensor | None = None) -> torch.Tensor:
+        """One training iteration; returns the device tensor
+        [L_rgb, L_feat, lambda_depth * L_depth] (the last 0 without a depth
+        target)."""
+        self.forward_backward(t, tgt_rgb, tgt_dec, tgt_depth)
         g = self.grads
         self.opt.step([g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"], g["feat"],
                        self.dec_out[2], self.dec_out[3]])

@@ -101,3 +101,41 @@ def test_training_is_deterministic():
         assert torch.equal(la, lb)
     for k in a.m:
         assert torch.equal(a.m[k], b.m[k]), k
+
+
+def test_depth_term_of_the_loss():
+    """lambda_depth * L1 depth (Eq. 11): its value against an FP64 mean of the
+    rendered depth, its per-pixel gradient, and its share of the parameter
+    gradients (the reverse pass is linear in the image gradients, so the
+    iteration with the depth term equals the one without plus a depth-only
+    reverse)."""
+    from paper_2503_06161_gb300.train import LAMBDA_DEPTH
+    tr = _trainer(seed=1)
+    H, W = tr.cam.height, tr.cam.width
+    rng = np.random.default_rng(5)
+    tgt_rgb = torch.tensor(rng.random((3, H, W)).astype(np.float32)).cuda()
+    tgt_dec = torch.tensor(rng.normal(size=(H * W, 256)).astype(np.float32)).to(torch.bfloat16).cuda()
+    tgt_depth = torch.tensor(rng.uniform(0.0, 4.0, size=(H, W)).astype(np.float32)).cuda()
+    t = 0.6
+    tr.forward_backward(t, tgt_rgb, tgt_dec)
+    torch.cuda.synchronize()
+    base = {k: v.clone() for k, v in tr.grads.items()}
+    assert tr.losses[2].item() == 0.0
+    tr.forward_backward(t, tgt_rgb, tgt_dec, tgt_depth)
+    torch.cuda.synchronize()
+    depth = tr.out[1].cpu().numpy().astype(np.float64)
+    diff = depth - tgt_depth.cpu().numpy().astype(np.float64)
+    ref_loss = LAMBDA_DEPTH * np.mean(np.abs(diff))
+    assert abs(tr.losses[2].item() - ref_loss) <= 1e-5 * ref_loss
+    inv = np.float32(1.0) / np.float32(round(H * W / LAMBDA_DEPTH))
+    assert np.array_equal(tr.g_depth.cpu().numpy(), (np.sign(diff) * inv).astype(np.float32))
+    full = {k: v.clone() for k, v in tr.grads.items()}
+    zr, zf = torch.zeros_like(tr.g_rgb), torch.zeros_like(tr.dec_out[1])
+    tr.rast.backward(tr.scene, tr.cam, tr.deform, t, zr, tr.g_depth, None, zf, grads=tr.grads)
+    torch.cuda.synchronize()
+    for k in ("means", "log_scales", "quats", "opacity_logits"):
+        d = tr.grads[k].cpu().numpy().astype(np.float64)
+        assert np.abs(d).sum() > 0, k
+        got = full[k].cpu().numpy().astype(np.float64) - base[k].cpu().numpy().astype(np.float64)
+        scale = np.sqrt(np.mean(full[k].cpu().numpy().astype(np.float64) ** 2))
+        assert np.max(np.abs(got - d)) <= 1e-4 * scale, k
