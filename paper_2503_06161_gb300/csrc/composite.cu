@@ -276,7 +276,7 @@ struct BwdCfg {
   static constexpr int JG = 16, CG = 2;             // lane grid of the per-warp product
   static constexpr int JPL = B / JG;                // entries per lane
   static constexpr int CPL = NC / CG;               // channels per lane (even: packed FMA)
-  static constexpr bool GREG = D <= 32;             // upstream gradients kept in registers
+  static constexpr bool GREG = D <= 64;             // upstream gradients kept in registers
   static constexpr int GS = NC + 2;                 // per-pixel gradient row stride (8-byte rows)
   static constexpr int WS = B + 4;                  // w row stride (16-byte rows)
   static constexpr int SLICE = (32 * WS > B * NC) ? 32 * WS : B * NC;
