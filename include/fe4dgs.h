@@ -299,6 +299,101 @@ fe_status fe_adam_step(const fe_adam_group *groups, int ngroups, int step, float
  * on `stream`.  The paper has no counterpart: a batching utility. */
 fe_status fe_sum_f32(float *dst, const float *const *srcs, int nsrc, int64_t n, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Full FST deformation module (Sec. 3.2, Eq. 4-6; Appendix A).
+ *
+ * Each Gaussian's canonical centre mu and the time t are encoded by a
+ * multi-resolution HexPlane: coordinates are normalised to [-1, 1] by the
+ * scene box (t in [0, 1] -> [-1, 1]); level l (0 <= l < levels) holds six
+ * planes xy, xz, yz, xt, yt, zt with FE_FST_CHANNELS channels, spatial axes
+ * of rs << l nodes and a time axis of rt nodes (grid corners at +-1,
+ * positions clamped to the border, bilinear sampling); a level's feature is
+ * the channel-wise product of its six samples and f is the concatenation
+ * of the levels' features (levels * 32 values).  The decoder MLP F_out
+ * (width 64, depth 8: Linear(f) then seven ReLU -> Linear(64, 64)) gives h;
+ * each branch g in (mu, R, S, o) applies ReLU -> Linear(64, 32),
+ * ReLU -> Linear(32, 32) giving h_g and ReLU -> Linear(32, d_g) giving the
+ * offset (d_g = 3, 4, 3, 1: Eq. 4); the semantic updater F_feat applies
+ * ReLU -> Linear(128, 64), ReLU -> Linear(64, D) to [h_mu, h_R, h_S, h_o],
+ * giving dz (Eq. 5).  The deformed Gaussian (Eq. 6) in the renderer's
+ * parameterisation: mu + d_mu, q + d_R (normalised by the renderer),
+ * log s + d_S, opacity logit + d_o, z + dz.
+ *
+ * Parameter layout.  planes: level-major, then plane-major in the order
+ * above, each [R_a][R_b][32] float32 (channels innermost; R_a, R_b the node
+ * counts of the plane's two axes).  mlp: one float32 array holding, for
+ * each linear layer in the order F_out 0..7, branch mu (E1, E2, head),
+ * branch R, branch S, branch o, F_feat (Z1, Z2), its weight [out][in]
+ * row-major followed by its bias [out].
+ * ------------------------------------------------------------------------ */
+#define FE_FST_WIDTH 64
+#define FE_FST_DEPTH 8
+#define FE_FST_CHANNELS 32
+#define FE_FST_MAX_LEVELS 4
+
+typedef struct {
+  int levels;            /* 1..4 */
+  int rs, rt;            /* base spatial node count (level l: rs << l) and time node count, >= 2 */
+  int D;                 /* semantic channels of dz: 16, 32, 64 or 128 */
+  const float *planes;   /* device, fe_fst_plane_floats(levels, rs, rt) floats, 16-byte aligned */
+  const float *mlp;      /* device, fe_fst_mlp_floats(levels, D) floats, 16-byte aligned */
+  float bbox_min[3], bbox_max[3];   /* scene box of the coordinate normalisation */
+} fe_fst;
+
+/* Float counts of the plane and MLP arrays (0 for invalid arguments). */
+int64_t fe_fst_plane_floats(int levels, int rs, int rt);
+int64_t fe_fst_mlp_floats(int levels, int D);
+
+/* Device workspace of fe_fst_forward / fe_fst_backward for P Gaussians.
+ * with_backward = 0: forward only (inference); 1: the forward also keeps
+ * the per-Gaussian activations the reverse pass reads (about 3.9 KB per
+ * Gaussian at 4 levels). */
+fe_status fe_fst_workspace_size(int P, int levels, int D, int with_backward, size_t *bytes);
+
+/* Deformation of P Gaussians at time t.  Inputs (device, canonical, the
+ * fe_gaussians layouts): means [P,3], quats [P,4], log_scales [P,3],
+ * opacity_logits [P], feat [P,D] (bf16 if feat_bf16, else float32).
+ * Outputs (device, caller-owned, overwritten): the deformed arrays in the
+ * same layouts, feat_t in the same type as feat (bf16 outputs rounded to
+ * nearest even).  Outputs must not alias inputs.  With with_backward the
+ * workspace (fe_fst_workspace_size with with_backward = 1) keeps the state
+ * fe_fst_backward needs; it must not be touched in between.  Asynchronous
+ * on `stream`. */
+fe_status fe_fst_forward(const fe_fst *fst, int P, const float *means, const float *quats, const float *log_scales,
+                         const float *opacity_logits, const void *feat, int feat_bf16, float t, float *means_t,
+                         float *quats_t, float *log_scales_t, float *opacity_logits_t, void *feat_t,
+                         void *workspace, size_t workspace_bytes, int with_backward, void *stream);
+
+/* Reverse pass of the last fe_fst_forward (with_backward = 1, same fst, P,
+ * means and t).  Inputs: the gradients of the loss with respect to the
+ * deformed arrays (device float32, layouts as above; d_feat_t [P,D]) --
+ * e.g. the fe_grads of a render of the deformed Gaussians.  Because the
+ * offsets are added, these are also the gradients of the offsets and of
+ * the canonical quats, log_scales, opacity logits and features.  Outputs
+ * (device float32, overwritten):
+ *   d_means   [P,3]  d_means_t plus the path through the HexPlane
+ *                    coordinates (may alias d_means_t);
+ *   d_planes         like planes: summed with float atomics, so the order
+ *                    of the additions (and the last bits) can vary between
+ *                    runs;
+ *   d_mlp            like mlp: per-block partial sums reduced in a fixed
+ *                    order (reproducible bit for bit).
+ * Asynchronous on `stream`. */
+fe_status fe_fst_backward(const fe_fst *fst, int P, const float *means, float t, const float *d_means_t,
+                          const float *d_quats_t, const float *d_log_scales_t, const float *d_opacity_logits_t,
+                          const float *d_feat_t, float *d_means, float *d_planes, float *d_mlp, void *workspace,
+                          size_t workspace_bytes, void *stream);
+
+/* Total-variation smoothness of the planes (the L_TV term of Eq. 11): for
+ * every plane of the first `levels` levels, the mean over its nodes and
+ * channels of the squared difference of neighbouring nodes along each of
+ * its two axes, summed over planes and axes, times `weight`.  Writes the
+ * weighted loss to *loss (one device float) and ADDS weight * dL_TV/dplanes
+ * to d_planes (so it composes with fe_fst_backward's plane gradients).
+ * scratch: device array of at least 1024 floats.  Deterministic.
+ * Asynchronous on `stream`. */
+fe_status fe_fst_tv(const fe_fst *fst, float weight, float *loss, float *d_planes, float *scratch, void *stream);
+
 /* Measured single-precision FMA throughput: runs an FMA-chain kernel over
  * the whole GPU for `iters` iterations per thread and writes FLOP/s
  * (2 per FMA) to *flops (host).  Synchronous; used for the FP32 roofline. */

@@ -77,6 +77,11 @@ class fe_adam_group(ctypes.Structure):
                 ("param_bf16", c_void_p), ("n", c_int64), ("lr", c_float)]
 
 
+class fe_fst(ctypes.Structure):
+    _fields_ = [("levels", c_int), ("rs", c_int), ("rt", c_int), ("D", c_int), ("planes", c_void_p),
+                ("mlp", c_void_p), ("bbox_min", c_float * 3), ("bbox_max", c_float * 3)]
+
+
 _P = ctypes.POINTER
 _SIGNATURES = {
     "fe_workspace_size": [c_int, c_int, c_int, c_int, _P(fe_opts), _P(ctypes.c_size_t)],
@@ -100,6 +105,11 @@ _SIGNATURES = {
     "fe_decoder_read_errors": [c_void_p, _P(ctypes.c_uint32), c_void_p],
     "fe_adam_step": [_P(fe_adam_group), c_int, c_int, c_float, c_float, c_float, c_void_p],
     "fe_sum_f32": [c_void_p, _P(c_void_p), c_int, c_int64, c_void_p],
+    "fe_fst_workspace_size": [c_int, c_int, c_int, c_int, _P(ctypes.c_size_t)],
+    "fe_fst_forward": [_P(fe_fst), c_int] + [c_void_p] * 5 + [c_int, c_float] + [c_void_p] * 6
+                      + [ctypes.c_size_t, c_int, c_void_p],
+    "fe_fst_backward": [_P(fe_fst), c_int, c_void_p, c_float] + [c_void_p] * 9 + [ctypes.c_size_t, c_void_p],
+    "fe_fst_tv": [_P(fe_fst), c_float, c_void_p, c_void_p, c_void_p, c_void_p],
 }
 
 _lib = None
@@ -116,6 +126,10 @@ def load():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = c_int
+        for name in ("fe_fst_plane_floats", "fe_fst_mlp_floats"):
+            getattr(L, name).restype = c_int64
+        L.fe_fst_plane_floats.argtypes = [c_int, c_int, c_int]
+        L.fe_fst_mlp_floats.argtypes = [c_int, c_int]
         L.fe_decoder_workspace_size.argtypes = [c_int64, c_int]
         L.fe_decoder_workspace_size.restype = ctypes.c_size_t
         L.fe_status_string.argtypes = [c_int]
@@ -340,3 +354,54 @@ def fe_sum_f32(dst, srcs, stream=None):
     left to right."""
     arr = (c_void_p * len(srcs))(*[c_void_p(x.data_ptr()) for x in srcs])
     _check("fe_sum_f32", load().fe_sum_f32(_ptr(dst), arr, len(srcs), int(dst.numel()), _stream(stream)))
+
+
+# --- full FST deformation module ---------------------------------------------
+def make_fst(levels: int, rs: int, rt: int, D: int, planes, mlp, bbox_min, bbox_max) -> fe_fst:
+    f = fe_fst()
+    f.levels, f.rs, f.rt, f.D = int(levels), int(rs), int(rt), int(D)
+    f.planes = _ptr(planes)
+    f.mlp = _ptr(mlp)
+    for a in range(3):
+        f.bbox_min[a] = float(bbox_min[a])
+        f.bbox_max[a] = float(bbox_max[a])
+    return f
+
+
+def fe_fst_plane_floats(levels: int, rs: int, rt: int) -> int:
+    return int(load().fe_fst_plane_floats(levels, rs, rt))
+
+
+def fe_fst_mlp_floats(levels: int, D: int) -> int:
+    return int(load().fe_fst_mlp_floats(levels, D))
+
+
+def fe_fst_workspace_size(P: int, levels: int, D: int, with_backward: bool) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_fst_workspace_size", load().fe_fst_workspace_size(P, levels, D, int(with_backward), ctypes.byref(n)))
+    return int(n.value)
+
+
+def fe_fst_forward(fst: fe_fst, P: int, means, quats, log_scales, logits, feat, t: float, means_t, quats_t,
+                   log_scales_t, logits_t, feat_t, workspace, with_backward: bool, stream=None):
+    import torch
+    rc = load().fe_fst_forward(ctypes.byref(fst), int(P), _ptr(means), _ptr(quats), _ptr(log_scales), _ptr(logits),
+                               _ptr(feat), int(feat.dtype == torch.bfloat16), float(t), _ptr(means_t),
+                               _ptr(quats_t), _ptr(log_scales_t), _ptr(logits_t), _ptr(feat_t), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), int(with_backward), _stream(stream))
+    _check("fe_fst_forward", rc)
+
+
+def fe_fst_backward(fst: fe_fst, P: int, means, t: float, d_means_t, d_quats_t, d_log_scales_t, d_logits_t,
+                    d_feat_t, d_means, d_planes, d_mlp, workspace, stream=None):
+    rc = load().fe_fst_backward(ctypes.byref(fst), int(P), _ptr(means), float(t), _ptr(d_means_t), _ptr(d_quats_t),
+                                _ptr(d_log_scales_t), _ptr(d_logits_t), _ptr(d_feat_t), _ptr(d_means),
+                                _ptr(d_planes), _ptr(d_mlp), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream(stream))
+    _check("fe_fst_backward", rc)
+
+
+def fe_fst_tv(fst: fe_fst, weight: float, loss, d_planes, scratch, stream=None):
+    rc = load().fe_fst_tv(ctypes.byref(fst), float(weight), _ptr(loss), _ptr(d_planes), _ptr(scratch),
+                          _stream(stream))
+    _check("fe_fst_tv", rc)

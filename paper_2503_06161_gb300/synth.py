@@ -186,6 +186,49 @@ def make_deform(P: int, C: int = 32, R: int = 64, seed: int = 1,
                   xi, float(noise_scale))
 
 
+# Layer shapes of the full FST module in the flat parameter order of the
+# library interface: F_out (L*32 -> 64, then 7 x 64 -> 64), per branch mu, R,
+# S, o (64 -> 32, 32 -> 32, 32 -> d_g), F_feat (128 -> 64, 64 -> D).
+def fst_layer_shapes(levels: int, D: int):
+    out = [(64, levels * 32)] + [(64, 64)] * 7
+    for d in (3, 4, 3, 1):
+        out += [(32, 64), (32, 32), (d, 32)]
+    return out + [(64, 128), (D, 64)]
+
+
+def fst_plane_shapes(levels: int, rs: int, rt: int):
+    out = []
+    for lv in range(levels):
+        res = (rs << lv, rs << lv, rs << lv, rt)
+        for a, b in ((0, 1), (0, 2), (1, 2), (0, 3), (1, 3), (2, 3)):
+            out.append((res[a], res[b], 32))
+    return out
+
+
+def make_fst(levels: int = 4, rs: int = 64, rt: int = 100, D: int = 32, seed: int = 5, plane_std: float = 0.1,
+             head_std: float = 0.01, dz_std: float = 0.1, bias_std: float = 0.0):
+    """Seeded parameters of the full FST deformation module as the two flat
+    float32 arrays of the library interface: planes ~ N(1, plane_std);
+    hidden layers N(0, sqrt(2 / fan_in)); branch heads N(0, head_std /
+    sqrt(fan_in)) (small offsets); the dz layer N(0, dz_std / sqrt(fan_in));
+    biases N(0, bias_std)."""
+    rng = np.random.default_rng(seed)
+    planes = np.concatenate([rng.normal(1.0, plane_std, s).astype(np.float32).ravel()
+                             for s in fst_plane_shapes(levels, rs, rt)])
+    parts = []
+    shapes = fst_layer_shapes(levels, D)
+    heads = {10, 13, 16, 19}
+    for k, (o, i) in enumerate(shapes):
+        std = np.sqrt(2.0 / i)
+        if k in heads:
+            std = head_std / np.sqrt(i)
+        if k == len(shapes) - 1:
+            std = dz_std / np.sqrt(i)
+        parts.append(rng.normal(0.0, std, (o, i)).astype(np.float32).ravel())
+        parts.append((rng.normal(0.0, bias_std, o) if bias_std > 0 else np.zeros(o)).astype(np.float32))
+    return planes, np.concatenate(parts)
+
+
 def make_targets(height: int, width: int, D: int, seed: int = 2, dec_channels: int = 0):
     """Random L1 targets: rgb U(0,1) [3,H,W]; features N(0,1) [H*W, D] (or
     [H*W, dec_channels] when a decoder output is the target)."""

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_layouts_match_header(tmp_path):
     structs = ["fe_camera", "fe_gaussians", "fe_deform", "fe_opts", "fe_outputs", "fe_output_grads", "fe_grads",
-               "fe_stats"]
+               "fe_stats", "fe_fst"]
     c = "#include <stdio.h>\n#include <stddef.h>\n#include \"fe4dgs.h\"\nint main(void){\n"
     for s in structs:
         c += f'printf("{s} %zu\\n", sizeof({s}));\n'
@@ -122,3 +122,36 @@ def test_sum_host_side_status_codes(lib):
     assert lib.fe_sum_f32(16, srcs, 9, 8, None) == 1          # more than 8
     assert lib.fe_sum_f32(8, srcs, 2, 8, None) == 1           # misaligned destination
     assert lib.fe_sum_f32(16, srcs, 2, 0, None) == 0          # nothing to add
+
+
+def test_fst_sizes_and_host_side_status_codes(lib):
+    import numpy as np
+    from paper_2503_06161_gb300 import synth
+    for levels, rs, rt, D in [(1, 4, 4, 16), (4, 64, 100, 32), (3, 6, 7, 128)]:
+        want_p = sum(a * b * c for a, b, c in synth.fst_plane_shapes(levels, rs, rt))
+        want_m = sum(o * i + o for o, i in synth.fst_layer_shapes(levels, D))
+        assert lib.fe_fst_plane_floats(levels, rs, rt) == want_p
+        assert lib.fe_fst_mlp_floats(levels, D) == want_m
+    assert lib.fe_fst_plane_floats(0, 4, 4) == 0 and lib.fe_fst_plane_floats(5, 4, 4) == 0
+    assert lib.fe_fst_plane_floats(2, 1, 4) == 0 and lib.fe_fst_mlp_floats(2, 24) == 0
+    n = ctypes.c_size_t(0)
+    assert lib.fe_fst_workspace_size(1000, 4, 32, 0, ctypes.byref(n)) == 0
+    fwd_only = n.value
+    assert lib.fe_fst_workspace_size(1000, 4, 32, 1, ctypes.byref(n)) == 0
+    assert n.value > fwd_only + 1000 * 4 * 900      # the activations kept for the reverse pass
+    assert lib.fe_fst_workspace_size(1000, 4, 24, 1, ctypes.byref(n)) == 4   # D not compiled in
+    assert lib.fe_fst_workspace_size(-1, 4, 32, 1, ctypes.byref(n)) == 1
+    f = _lib.fe_fst()
+    f.levels, f.rs, f.rt, f.D = 2, 8, 6, 32
+    for a in range(3):
+        f.bbox_max[a] = 1.0
+    ws = ctypes.c_void_p(256)
+    args = [None] * 5
+    assert lib.fe_fst_forward(None, 1, *args, 0, 0.5, *args, ws, 1 << 30, 1, None) == 1
+    assert lib.fe_fst_forward(ctypes.byref(f), 1, *args, 0, 0.5, *args, ws, 16, 1, None) == 3   # workspace
+    assert lib.fe_fst_forward(ctypes.byref(f), 1, *args, 0, 0.5, *args, ws, 1 << 30, 1, None) == 1  # NULLs
+    f.D = 24
+    assert lib.fe_fst_forward(ctypes.byref(f), 1, *args, 0, 0.5, *args, ws, 1 << 30, 1, None) == 4
+    f.D = 32
+    f.bbox_max[1] = -1.0                                                 # empty box
+    assert lib.fe_fst_forward(ctypes.byref(f), 1, *args, 0, 0.5, *args, ws, 1 << 30, 1, None) == 1
