@@ -534,6 +534,156 @@ def batch_views(cfg):
     return out
 
 
+def fst_macs(levels: int, D: int) -> int:
+    """Multiply-adds of the full FST MLP per Gaussian (F_out, branches,
+    semantic updater)."""
+    return (levels * 32 * 64 + 7 * 64 * 64 + 4 * (64 * 32 + 32 * 32) + 32 * (3 + 4 + 3 + 1) + 128 * 64 + 64 * D)
+
+
+def run_train_fst(args, world, rank, local, cfg):
+    """Training iteration with the full FST module around the renderer
+    (deform -> render -> L1 rgb + decoder L1 + depth -> reverse -> FST reverse
+    + TV -> Adam on Gaussians, decoder, planes and MLP)."""
+    import torch
+
+    from paper_2503_06161_gb300 import synth
+    from paper_2503_06161_gb300.fst import FSTDeform
+    from paper_2503_06161_gb300.train import Trainer
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sc, cam_np, _ = synth.config_inputs(args.workload, D=args.D)
+    P, D, W, H = sc.P, sc.D, cam_np.width, cam_np.height
+    fc = cfg["fst"]
+    levels, rs, rt = fc["levels"], fc["rs"], fc["rt"]
+    planes, mlp = synth.make_fst(levels, rs, rt, D, seed=1)
+    fst = FSTDeform.from_numpy(planes, mlp, levels, rs, rt, D, cfg["lo"], cfg["hi"], P, device=dev)
+    w_np, b_np = synth.make_decoder(D, seed=3)
+    tr = Trainer.from_numpy(sc, cam_np, None, w_np, b_np, device=dev, fst=fst)
+    t = (args.t + rank / max(world, 1)) % 1.0 if world > 1 else args.t
+    rgb_np, dec_np = synth.make_targets(H, W, D, seed=2, dec_channels=256)
+    tgt = dict(rgb=torch.as_tensor(rgb_np, device=dev), dec=torch.as_tensor(dec_np).to(torch.bfloat16).to(dev),
+               depth=torch.as_tensor(synth.make_depth_target(H, W, cfg["lo"][2], cfg["hi"][2]), device=dev))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        tr.step(t, tgt["rgb"], tgt["dec"], tgt["depth"])
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    for row in ev:
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(K):
+        flush.zero_()
+        ev[i][0].record(stream)
+        tr.step(t, tgt["rgb"], tgt["dec"], tgt["depth"], events=ev[i][1:5])
+        ev[i][5].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = statistics.mean(ev[i][0].elapsed_time(ev[i][5]) for i in range(K))
+    names = ["fst_forward", "render_forward_losses", "render_reverse", "fst_reverse_tv", "adam"]
+    stages = {n: round(statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(K)), 4)
+              for j, n in enumerate(names)}
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    # The FST kernels alone (same state), for their rooflines.
+    scene_t = fst.forward(tr.scene, t)
+    g = {k: v.clone() for k, v in tr.grads.items()}
+
+    def timed(fn, n=max(3, K)):
+        out = []
+        for _ in range(n):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    f_ms = timed(lambda: fst.forward(tr.scene, t))
+    b_ms = timed(lambda: fst.backward(tr.scene, t, dict(g, means=g["means"].clone())))
+    tvl = torch.zeros(1, device=dev)
+    tv_ms = timed(lambda: fst.tv(0.03, tvl, tr.scratch[2]))
+    del scene_t
+    clock_mhz = clk.get("sm_mhz") or 2070.0
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+    flop_f = 2.0 * fst_macs(levels, D) * P
+    kern = {"fst_forward": {"ms": round(f_ms, 4), "tflops": round(flop_f / f_ms / 1e9, 3),
+                            "frac_of_alu_peak": round(flop_f / f_ms / 1e9 / alu_peak, 4)},
+            "fst_reverse": {"ms": round(b_ms, 4), "tflops": round(2 * flop_f / b_ms / 1e9, 3),
+                            "frac_of_alu_peak": round(2 * flop_f / b_ms / 1e9 / alu_peak, 4)}}
+    hbm, basis = hbm_peak()
+    tv_bytes = fst.planes.numel() * 12   # read planes, read + write plane gradients
+    kern["fst_tv"] = {"ms": round(tv_ms, 4), "gbs": round(tv_bytes / tv_ms / 1e6, 1),
+                      "frac_of_hbm_peak": round(tv_bytes / tv_ms / 1e6 / hbm, 4), "peak_basis": basis}
+    dom = "fst_reverse" if b_ms >= f_ms else "fst_forward"
+    ach = kern[dom]["tflops"]
+    # End to end: the step's targets copied in from pinned host memory, the
+    # losses read back.
+    host = {k: v.cpu().pin_memory() for k, v in tgt.items()}
+    dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    host_loss = torch.empty(4).pin_memory()
+
+    def e2e_step():
+        for k, v in host.items():
+            dev_in[k].copy_(v, non_blocking=True)
+        losses = tr.step(t, dev_in["rgb"], dev_in["dec"], dev_in["depth"])
+        host_loss.copy_(losses, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    for _ in range(K):
+        e2e_step()
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = x0.elapsed_time(x1) / K
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    result = {
+        "metric": METRIC, "value": round(world * 1000.0 / ms, 3), "unit": "it/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "gaussians": P, "width": W, "height": H, "D": D,
+                   "fst": f"{levels} levels x {rs}^3 x {rt} x 32ch, F_out 8x64, branches 2x32, updater 128-64-{D}",
+                   "step": "FST fwd + render fwd + L1 rgb / decoder L1 / depth + render reverse + FST reverse "
+                           "+ TV + Adam (Gaussians, decoder, planes, MLP)",
+                   "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
+        "stage_ms": stages, "kernels": kern,
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": ach, "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+                     "frac": round(ach / alu_peak, 4), "traffic": None,
+                     "peak_basis": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz"},
+        "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": "it/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": 16, "ms_per_step": round(e2e_ms, 4)},
+        "device_errors": int(tr.rast.stats()["device_errors"]), "clocks": clk,
+        # per step: FST forward 2 (pack, forward); render forward 10; L1 rgb 2,
+        # decoder 2, depth L1 2; render reverse 3; FST reverse 2 (reverse,
+        # reduce); TV 2; Adam 2 (Gaussians + decoder, planes + MLP)
+        "gpu_launches": 27 * K,
+    }
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_batch(args, world, rank, local, cfg):
     import torch
 
@@ -731,6 +881,9 @@ def main():
         return
     if cfg.get("views"):
         run_batch(args, world, rank, local, cfg)
+        return
+    if cfg.get("fst"):
+        run_train_fst(args, world, rank, local, cfg)
         return
     run_ours(args, world, rank, local)
 

@@ -94,6 +94,8 @@ bool make_geom(const fe_fst* f, int P, FstGeom& g) {
       off += (int64_t)res[pair_a(k)] * res[pair_b(k)] * kFC;
     }
   }
+  for (int k = 0; k < f->levels * 6; ++k)
+    if ((int64_t)g.pra[k] * g.prb[k] * kFC > (int64_t)0x7FFFFFFF) return false;  // 32-bit plane indexing
   g.sf = 0;
   g.sz = f->levels * kFC;
   g.se1 = g.sz + kFDepth * kFW;
@@ -825,48 +827,54 @@ struct TvArgs {
   const float* planes;
   float* d_planes;
   float weight;
-  float* partial;  // [gridDim.x]
+  float* partial;  // [planes][kTvBlocks]
 };
 
+constexpr int kTvBlocks = 40;  // blocks per plane (grid.y = plane)
+
+// One plane per grid row; each thread takes four channels of a node (the
+// planes are channels-last, so a float4 per neighbour).  The loss partials
+// are summed in a fixed order afterwards.
 __global__ void __launch_bounds__(256) fst_tv_kernel(const TvArgs a) {
   __shared__ float s_w[8];
   const FstGeom& g = a.g;
-  const int64_t total = plane_floats(g);
+  const int k = blockIdx.y;
+  const int ra = g.pra[k], rb = g.prb[k];
+  const float4* pl = reinterpret_cast<const float4*>(a.planes + g.poff[k]);
+  float4* dp = reinterpret_cast<float4*>(a.d_planes + g.poff[k]);
+  const int q4 = kFC / 4;
+  const int total = ra * rb * q4;
+  const float ia = 1.0f / (float)((int64_t)(ra - 1) * rb * kFC), ib = 1.0f / (float)((int64_t)ra * (rb - 1) * kFC);
   float acc = 0.0f;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int k = 0;
-    while (k + 1 < g.levels * 6 && e >= g.poff[k + 1]) ++k;
-    const int64_t r = e - g.poff[k];
-    const int ra = g.pra[k], rb = g.prb[k];
-    const int c = (int)(r % kFC);
-    const int64_t node = r / kFC;
-    const int i = (int)(node / rb), j = (int)(node % rb);
-    const float* pl = a.planes + g.poff[k];
-    const float v = pl[r];
-    const float na = (float)((int64_t)(ra - 1) * rb * kFC), nb = (float)((int64_t)ra * (rb - 1) * kFC);
-    float gr = 0.0f;
-    if (i + 1 < ra) {
-      const float d = pl[((int64_t)(i + 1) * rb + j) * kFC + c] - v;
-      acc += d * d / na;
-      gr -= 2.0f * d / na;
-    }
-    if (i > 0) gr += 2.0f * (v - pl[((int64_t)(i - 1) * rb + j) * kFC + c]) / na;
-    if (j + 1 < rb) {
-      const float d = pl[((int64_t)i * rb + j + 1) * kFC + c] - v;
-      acc += d * d / nb;
-      gr -= 2.0f * d / nb;
-    }
-    if (j > 0) gr += 2.0f * (v - pl[((int64_t)i * rb + j - 1) * kFC + c]) / nb;
-    a.d_planes[e] += a.weight * gr;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int node = e / q4;
+    const int i = node / rb, j = node - i * rb;
+    const float4 v = pl[e];
+    float4 gr = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto term = [&](const float4 n, float w, bool forward) {
+      // forward: n is the next node (difference n - v, counted in the loss)
+      const float4 d = forward ? make_float4(n.x - v.x, n.y - v.y, n.z - v.z, n.w - v.w)
+                               : make_float4(v.x - n.x, v.y - n.y, v.z - n.z, v.w - n.w);
+      if (forward) acc += (d.x * d.x + d.y * d.y + d.z * d.z + d.w * d.w) * w;
+      const float s = forward ? -2.0f * w : 2.0f * w;
+      gr.x += s * d.x; gr.y += s * d.y; gr.z += s * d.z; gr.w += s * d.w;
+    };
+    if (i + 1 < ra) term(pl[e + rb * q4], ia, true);
+    if (i > 0) term(pl[e - rb * q4], ia, false);
+    if (j + 1 < rb) term(pl[e + q4], ib, true);
+    if (j > 0) term(pl[e - q4], ib, false);
+    float4 o = dp[e];
+    o.x += a.weight * gr.x; o.y += a.weight * gr.y; o.z += a.weight * gr.z; o.w += a.weight * gr.w;
+    dp[e] = o;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
   if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    float s = 0.0f;
-    for (int w = 0; w < 8; ++w) s += s_w[w];
-    a.partial[blockIdx.x] = s;
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t += s_w[w];
+    a.partial[k * kTvBlocks + blockIdx.x] = t;
   }
 }
 
@@ -1056,8 +1064,8 @@ extern "C" fe_status fe_fst_tv(const fe_fst* fst, float weight, float* loss, flo
   a.d_planes = d_planes;
   a.weight = weight;
   a.partial = scratch;
-  const int grid = 1024;
-  fst_tv_kernel<<<grid, 256, 0, st>>>(a);
-  fst_tv_finish<<<1, 32, 0, st>>>(scratch, grid, weight, loss);
+  const int np = g.levels * 6;  // at most 24 planes x kTvBlocks partials <= 1024 scratch floats
+  fst_tv_kernel<<<dim3(kTvBlocks, np), 256, 0, st>>>(a);
+  fst_tv_finish<<<1, 32, 0, st>>>(scratch, np * kTvBlocks, weight, loss);
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }

@@ -31,9 +31,25 @@ class Adam:
         self.beta1, self.beta2, self.eps = beta1, beta2, eps
         self.t = 0
 
-    def step(self, grads):
+    def step(self, grads, lrs=None):
+        """One update; lrs (optional, one float per group) overrides the
+        groups' learning rates for this and later steps (schedules)."""
         if len(grads) != len(self.groups):
             raise ValueError("one gradient per group")
+        if lrs is not None:
+            if len(lrs) != len(self.groups):
+                raise ValueError("one learning rate per group")
+            for g, lr in zip(self.groups, lrs):
+                g["lr"] = float(lr)
         self.t += 1
         _lib.fe_adam_step([dict(g, grad=gr.contiguous()) for g, gr in zip(self.groups, grads)], self.t,
                           self.beta1, self.beta2, self.eps)
+
+
+def exp_lr(step: int, lr_init: float, lr_final: float, max_steps: int) -> float:
+    """Log-linear decay from lr_init to lr_final over max_steps (held at
+    lr_final afterwards), the schedule form of the paper's hyperparameter
+    table (initial / final rates, Appendix)."""
+    import math
+    r = min(max(step / max(max_steps, 1), 0.0), 1.0)
+    return math.exp(math.log(lr_init) * (1.0 - r) + math.log(lr_final) * r)

@@ -274,6 +274,11 @@ CONFIGS = {
                                  hi=(2, 2, 8), deform=True, bf16=True, seed=0, views=16),
     "scared_1m_1280x1024": dict(P=1_000_000, D=64, W=1280, H=1024, f=1000.0, lo=(-2, -2, 3),
                                 hi=(2, 2, 8), deform=True, bf16=True, seed=0, decoder=256, train=True),
+    # Training with the full FST module (4-level HexPlane 64^3 x 100, depth-8
+    # MLP, branches, semantic updater; Sec. 3.2, Appendix A) and the TV term.
+    "fst_200k_640x512_train": dict(P=200_000, D=32, W=640, H=512, f=560.0, lo=(-2, -2, 3), hi=(2, 2, 8),
+                                   deform=False, bf16=True, seed=0, decoder=256, train=True,
+                                   fst=dict(levels=4, rs=64, rt=100)),
 }
 
 

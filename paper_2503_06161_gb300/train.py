@@ -1,8 +1,10 @@
 """One training iteration of FE-4DGS on the device (Sec. 3.3, Sec. 3.4, Sec. 4.1):
 deformation query at time t, render forward (RGB, depth, D-channel
 features), L1 RGB loss, decoder D -> 256 with the L1 feature loss (Eq. 10,
-fused forward + reverse), render reverse, and an Adam step on every Gaussian
-parameter and the decoder.
+fused forward + reverse), the weighted depth and TV terms of Eq. 11, render
+reverse, and an Adam step on every Gaussian parameter, the decoder and (with
+the full FST module) the planes and every MLP weight, under the paper's
+exponential learning-rate schedules.
 
 Every step of the iteration runs in the library's kernels; this module only
 owns the device buffers and sequences the C-ABI calls on the current stream,
@@ -17,25 +19,37 @@ import torch
 
 from . import _lib
 from .decoder import Decoder
-from .optim import Adam
+from .fst import FSTDeform
+from .optim import Adam, exp_lr
 from .raster import DeformField, GaussianScene, Rasterizer, camera_struct
 
-# Loss weights of Eq. 11 (RGB, depth, feature); the TV term acts on the
-# deformation planes, whose gradients this pass does not produce.
-LAMBDA_RGB, LAMBDA_DEPTH, LAMBDA_FEAT = 1.0, 0.01, 1.0
+# Loss weights of Eq. 11 (RGB, depth, feature, TV).
+LAMBDA_RGB, LAMBDA_DEPTH, LAMBDA_FEAT, LAMBDA_TV = 1.0, 0.01, 1.0, 0.03
 
-# Per-group learning rates (constant; the schedules of the paper's training
-# recipe are not part of this pass).
+# Initial per-group learning rates.  Position, grid and deformation follow
+# the paper's hyperparameter table (SCARED column) and decay log-linearly to
+# the final rates of SCHEDULE over SCHEDULE_STEPS (the table's position LR
+# max steps); the other groups keep a constant rate.
 LR = dict(means=1.6e-4, log_scales=5e-3, quats=1e-3, opacity_logits=5e-2, sh=2.5e-3, feat=2.5e-3,
-          dec_weight=1e-3, dec_bias=1e-3)
+          dec_weight=1e-3, dec_bias=1e-3, grid=1.6e-3, deformation=8e-5)
+SCHEDULE = dict(means=1.6e-6, grid=1.6e-5, deformation=8e-7)
+SCHEDULE_STEPS = 3000
 
 
 class Trainer:
     def __init__(self, masters: dict, sh_degree: int, cam, deform: DeformField | None, decoder: Decoder,
-                 bf16_storage: bool = True, max_dups: int | None = None, lr: dict | None = None, device="cuda"):
+                 bf16_storage: bool = True, max_dups: int | None = None, lr: dict | None = None, device="cuda",
+                 fst: FSTDeform | None = None, schedule: bool = True):
         """masters: float32 device tensors means [P,3], log_scales [P,3],
-        quats [P,4], opacity_logits [P], sh [P,16,3], feat [P,D]."""
+        quats [P,4], opacity_logits [P], sh [P,16,3], feat [P,D].  deform:
+        the single-level field evaluated inside the renderer, or fst: the
+        full FST module (Sec. 3.2) run around it (not both)."""
+        if deform is not None and fst is not None:
+            raise ValueError("one deformation model: deform or fst")
         self.m = masters
+        self.fst = fst
+        self.schedule = bool(schedule)
+        self.lr = dict(LR, **(lr or {}))
         P, D = masters["means"].shape[0], masters["feat"].shape[1]
         self.P, self.D = int(P), int(D)
         self.cam = cam if isinstance(cam, _lib.fe_camera) else camera_struct(cam)
@@ -56,7 +70,7 @@ class Trainer:
         self.HW = W * H
         if max_dups is None:
             probe = Rasterizer(self.P, self.D, W, H, device=device, max_dups=64 * self.P + 4096, forward_only=True)
-            probe.forward(self.scene, self.cam, deform, 0.5)
+            probe.forward(fst.forward(self.scene, 0.5) if fst is not None else self.scene, self.cam, deform, 0.5)
             max_dups = int(probe.stats()["num_dups"] * 1.5) + 4096
             del probe
         self.rast = Rasterizer(self.P, self.D, W, H, max_dups=max_dups, device=device, auto_grow=False)
@@ -66,8 +80,9 @@ class Trainer:
         self.feat_bf = torch.empty(self.HW, self.D, dtype=torch.bfloat16, device=device)
         self.g_rgb = torch.empty(3, H, W, **kw)
         self.g_depth = torch.empty(H, W, **kw)
-        self.losses = torch.zeros(3, **kw)  # L_rgb, L_feat, lambda_depth * L_depth
-        self.scratch = torch.empty(2, 1024, **kw)
+        # L_rgb, L_feat, lambda_depth * L_depth, lambda_TV * L_TV
+        self.losses = torch.zeros(4, **kw)
+        self.scratch = torch.empty(3, 1024, **kw)
         self.dec_out = (self.losses[1:2], torch.empty(self.HW, self.D, **kw), torch.empty(256, self.D, **kw),
                         torch.empty(256, **kw))
         self.grads = dict(means=torch.empty(P, 3, **kw), log_scales=torch.empty(P, 3, **kw),
@@ -81,6 +96,10 @@ class Trainer:
         groups.append(dict(param=self.dec_w32, lr=lr["dec_weight"], param_bf16=decoder.weight))
         groups.append(dict(param=decoder.bias, lr=lr["dec_bias"]))
         self.opt = Adam(groups)
+        self.opt_fst = None
+        if fst is not None:
+            self.opt_fst = Adam([dict(param=fst.planes, lr=lr["grid"]), dict(param=fst.mlp, lr=lr["deformation"])])
+        self.steps = 0
         self.dec.workspace(self.HW)
 
     @classmethod
@@ -93,11 +112,16 @@ class Trainer:
         return cls(masters, int(sc.sh_degree), cam, deform, dec, bf16_storage=bf16_storage, device=device, **kw)
 
     def forward_backward(self, t: float, tgt_rgb: torch.Tensor, tgt_dec: torch.Tensor,
-                         tgt_depth: torch.Tensor | None = None):
+                         tgt_depth: torch.Tensor | None = None, events=None):
         """Losses and gradients of one view at time t (no parameter update):
         L1 RGB, the decoder's L1 feature loss, and (with a depth target) the
-        weighted L1 depth loss of Eq. 11."""
-        self.rast.forward(self.scene, self.cam, self.deform, t, out=self.out, feat_bf16=self.feat_bf)
+        weighted L1 depth loss of Eq. 11.  events: optional CUDA events
+        recorded after the deformation, the losses, the render reverse and
+        the FST reverse (profiling)."""
+        rec = (lambda i: events[i].record()) if events is not None else (lambda i: None)
+        scene = self.fst.forward(self.scene, t) if self.fst is not None else self.scene
+        rec(0)
+        self.rast.forward(scene, self.cam, self.deform, t, out=self.out, feat_bf16=self.feat_bf)
         _lib.fe_l1_loss_grad(self.out[0], tgt_rgb, self.HW, self.g_rgb, self.losses[0:1], self.scratch[0])
         self.dec.l1(self.feat_bf, tgt_dec, out=self.dec_out)
         g_depth = None
@@ -107,16 +131,35 @@ class Trainer:
             _lib.fe_l1_loss_grad(self.out[1], tgt_depth, round(self.HW / LAMBDA_DEPTH), self.g_depth,
                                  self.losses[2:3], self.scratch[1])
             g_depth = self.g_depth
-        self.rast.backward(self.scene, self.cam, self.deform, t, self.g_rgb, g_depth, None, self.dec_out[1],
+        rec(1)
+        self.rast.backward(scene, self.cam, self.deform, t, self.g_rgb, g_depth, None, self.dec_out[1],
                            grads=self.grads)
+        rec(2)
+        if self.fst is not None:
+            # Deformed-Gaussian gradients -> canonical, planes and weights;
+            # then lambda_TV * L_TV on the planes.
+            self.fst.backward(self.scene, t, self.grads)
+            self.fst.tv(LAMBDA_TV, self.losses[3:4], self.scratch[2])
+        rec(3)
 
     def step(self, t: float, tgt_rgb: torch.Tensor, tgt_dec: torch.Tensor,
-             tgt_depth: torch.Tensor | None = None) -> torch.Tensor:
+             tgt_depth: torch.Tensor | None = None, events=None) -> torch.Tensor:
         """One training iteration; returns the device tensor
-        [L_rgb, L_feat, lambda_depth * L_depth] (the last 0 without a depth
-        target)."""
-        self.forward_backward(t, tgt_rgb, tgt_dec, tgt_depth)
+        [L_rgb, L_feat, lambda_depth * L_depth, lambda_TV * L_TV] (depth 0
+        without a depth target, TV 0 without the FST module)."""
+        self.forward_backward(t, tgt_rgb, tgt_dec, tgt_depth, events)
         g = self.grads
+        lrs = None
+        if self.schedule:
+            lr = dict(self.lr, means=exp_lr(self.steps, self.lr["means"], SCHEDULE["means"], SCHEDULE_STEPS))
+            lrs = [lr[k] for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "feat", "dec_weight",
+                                   "dec_bias")]
         self.opt.step([g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"], g["feat"],
-                       self.dec_out[2], self.dec_out[3]])
+                       self.dec_out[2], self.dec_out[3]], lrs)
+        if self.fst is not None:
+            fl = None
+            if self.schedule:
+                fl = [exp_lr(self.steps, self.lr[k], SCHEDULE[k], SCHEDULE_STEPS) for k in ("grid", "deformation")]
+            self.opt_fst.step([self.fst.d_planes, self.fst.d_mlp], fl)
+        self.steps += 1
         return self.losses

@@ -139,3 +139,40 @@ def test_depth_term_of_the_loss():
         got = full[k].cpu().numpy().astype(np.float64) - base[k].cpu().numpy().astype(np.float64)
         scale = np.sqrt(np.mean(full[k].cpu().numpy().astype(np.float64) ** 2))
         assert np.max(np.abs(got - d)) <= 1e-4 * scale, k
+
+
+def test_training_with_the_full_fst_module():
+    """One iteration with the full FST module (Sec. 3.2) around the renderer:
+    lambda_TV * L_TV against the oracle on the pre-step planes, and the
+    planes / MLP / canonical-mean updates equal to the oracle's Adam on the
+    iteration's own gradients (scheduled learning rates at step 0 are the
+    initial ones)."""
+    from oracle import fst as OF
+    from paper_2503_06161_gb300.fst import FSTDeform
+    from paper_2503_06161_gb300.train import LAMBDA_TV, LR
+    levels, rs, rt = 2, 16, 10
+    sc, cam, _ = deformed_case(P=3000, W=150, H=100, D=32, seed=4)
+    planes, mlp = synth.make_fst(levels, rs, rt, 32, seed=6, plane_std=0.1, head_std=0.05)
+    fst = FSTDeform.from_numpy(planes, mlp, levels, rs, rt, 32, (-1, -1, 2), (1, 1, 4), sc.P)
+    w, b = synth.make_decoder(32, seed=5, b_std=0.1)
+    tr = Trainer.from_numpy(sc, cam, None, w, b, max_dups=200_000, fst=fst)
+    H, W = tr.cam.height, tr.cam.width
+    rng = np.random.default_rng(8)
+    tgt_rgb = torch.tensor(rng.random((3, H, W)).astype(np.float32)).cuda()
+    tgt_dec = torch.tensor(rng.normal(size=(H * W, 256)).astype(np.float32)).to(torch.bfloat16).cuda()
+    tgt_depth = torch.tensor(synth.make_depth_target(H, W, 2.0, 4.0)).cuda()
+    p0, m0 = fst.planes.cpu().numpy().astype(np.float64), fst.mlp.cpu().numpy().astype(np.float64)
+    mu0 = tr.m["means"].cpu().numpy().astype(np.float64)
+    losses = tr.step(0.35, tgt_rgb, tgt_dec, tgt_depth)
+    torch.cuda.synchronize()
+    assert tr.rast.stats()["device_errors"] == 0 and tr.dec.errors() == 0
+    L = losses.cpu().numpy()
+    assert np.all(np.isfinite(L)) and L[2] > 0
+    ref_tv, _ = OF.tv_loss(OF.unpack_planes(p0, levels, rs, rt), levels)
+    assert abs(L[3] - LAMBDA_TV * ref_tv) <= 1e-5 * LAMBDA_TV * ref_tv
+    for got, before, grad, lr in ((fst.planes, p0, fst.d_planes, LR["grid"]), (fst.mlp, m0, fst.d_mlp, LR["deformation"]),
+                                  (tr.m["means"], mu0, tr.grads["means"], LR["means"])):
+        g = grad.cpu().numpy().astype(np.float64)
+        assert np.abs(g).sum() > 0
+        ref, _, _ = O.adam_step(before, g, 0.0, 0.0, 1, f32(lr), B1, B2, EPS)
+        assert np.max(np.abs(got.cpu().numpy() - ref)) <= TOL_ADAM * max(1.0, np.max(np.abs(ref)))
