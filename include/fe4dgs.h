@@ -367,7 +367,8 @@ fe_status fe_fst_forward(const fe_fst *fst, int P, const float *means, const flo
 /* Reverse pass of the last fe_fst_forward (with_backward = 1, same fst, P,
  * means and t).  Inputs: the gradients of the loss with respect to the
  * deformed arrays (device float32, layouts as above; d_feat_t [P,D]) --
- * e.g. the fe_grads of a render of the deformed Gaussians.  Because the
+ * e.g. the fe_grads of a render of the deformed Gaussians; d_feat_t 16-byte
+ * aligned.  Because the
  * offsets are added, these are also the gradients of the offsets and of
  * the canonical quats, log_scales, opacity logits and features.  Outputs
  * (device float32, overwritten):

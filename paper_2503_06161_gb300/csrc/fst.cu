@@ -4,19 +4,22 @@
 // extractors and heads, and the semantic updater F_feat giving dz; forward
 // and reverse, including the gradients of the planes and of every weight.
 //
-// Forward: one thread per Gaussian for the MLP chain (activations in
-// registers, weights from a 16-byte-aligned transposed copy, packed FP32
-// FMA over output pairs); the HexPlane is sampled lane-cooperatively (the
-// warp takes its 32 Gaussians one at a time, lane = channel, so each corner
-// fetch is one coalesced 128-byte line of the channels-last planes).
+// A block holds 128 Gaussians and every layer is a block product: the
+// activations sit in shared memory (row per Gaussian), each thread owns an
+// 8-Gaussian x TN-output register tile of packed FP32 FMAs and streams
+// weights from 16-byte-aligned copies in the workspace (transposed for the
+// forward, row-major for the reverse).  The HexPlane is sampled
+// lane-cooperatively (the warp takes its 32 Gaussians one at a time, lane =
+// channel, so each corner fetch is one coalesced 128-byte line of the
+// channels-last planes).
 //
-// Reverse (persistent blocks of 128 Gaussians): each thread back-propagates
-// its Gaussian through the layers (weights from an aligned row-major copy),
-// and every layer's weight gradient sum_g delta_g x_g^T over the block's
-// Gaussians is a block-level product from shared memory, added into the
-// block's own partial (reduced over blocks in a fixed order afterwards:
-// reproducible).  Plane gradients are scattered with coalesced float
-// atomics (the only order-dependent sum of this file).
+// Reverse (persistent blocks): per layer, the input gradient delta W is the
+// same tile product, the ReLU masks come from the stored activations, and
+// the weight gradient sum_g delta_g x_g^T over the block's Gaussians is a
+// second block product added into the block's own partial (reduced over
+// blocks in a fixed order afterwards: reproducible).  Plane gradients are
+// scattered with coalesced float atomics (the only order-dependent sum of
+// this file).
 #include <cstdint>
 
 #include "common.cuh"
@@ -125,9 +128,6 @@ int bwd_blocks(int P) {
   return chunks < 2 * 152 ? chunks : 2 * 152;
 }
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
-// Row stride of the forward's per-thread shared-memory row: the level
-// features, later relu(h).
-__host__ __device__ constexpr int fwd_row(int levels) { return (levels * kFC > 2 * kFW ? levels * kFC : 2 * kFW) + 4; }
 struct WsLayout {
   size_t wt, wn, act, dv, part, total;
 };
@@ -191,94 +191,142 @@ __device__ __forceinline__ void grid_axes(const FstGeom& g, const float* mu, flo
 }
 
 // ---------------------------------------------------------------------------
-// Dense layer pieces: accumulators in registers, the layer input in the
-// thread's own shared-memory row.  y (pairs) += W x, with W^T rows of `ld`
-// floats (16-byte aligned) starting at wt.
+// Block products.  A block holds 128 Gaussians; activations live in shared
+// memory row-major per Gaussian ([128][kFRow] floats).  Thread (mt, nt) =
+// (tid % 16, tid / 16) owns rows mt + 16 r (r < 8) and TN consecutive output
+// columns from n0 = nt * TN: per step of four inputs it reads eight 16-byte
+// row slices from shared memory and TN weights per input from L1, then
+// issues 16 TN packed FMAs.
 // ---------------------------------------------------------------------------
-template <int NIN, int NOUT>
-__device__ __forceinline__ void dense_t(const float* __restrict__ wt, int ld, const float* x, float2* y,
-                                        int nin = NIN) {
-#pragma unroll 2
-  for (int i = 0; i < nin; ++i) {
-    const float2 xi = make_float2(x[i], x[i]);
-    const float4* w4 = reinterpret_cast<const float4*>(wt + (size_t)i * ld);
+template <int TN>
+__device__ __forceinline__ void tile_zero(float2 (&acc)[8][TN / 2]) {
 #pragma unroll
-    for (int q = 0; q < NOUT / 4; ++q) {
-      const float4 w = __ldg(w4 + q);
-      y[2 * q] = __ffma2_rn(make_float2(w.x, w.y), xi, y[2 * q]);
-      y[2 * q + 1] = __ffma2_rn(make_float2(w.z, w.w), xi, y[2 * q + 1]);
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < TN / 2; ++c) acc[r][c] = make_float2(0.0f, 0.0f);
+}
+
+// acc[r][c] += sum_k X[(mt + 16 r) * kFRow + k] * B[k * ldb + n0 + (2c, 2c+1)],
+// k < K (multiple of 8); B rows 8-byte aligned at n0.
+template <int TN, bool kSharedB = false>
+__device__ __forceinline__ void tile_mma(const float* X, int K, const float* __restrict__ B, int ldb, int mt, int n0,
+                                         float2 (&acc)[8][TN / 2]) {
+#pragma unroll 2
+  for (int k = 0; k < K; k += 4) {
+    float4 xv[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) xv[r] = *reinterpret_cast<const float4*>(X + (mt + 16 * r) * kFRow + k);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      float2 b[TN / 2];
+      const float2* brow = reinterpret_cast<const float2*>(B + (size_t)(k + kk) * ldb + n0);
+#pragma unroll
+      for (int c = 0; c < TN / 2; ++c) b[c] = kSharedB ? brow[c] : __ldg(brow + c);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float xk = kk == 0 ? xv[r].x : (kk == 1 ? xv[r].y : (kk == 2 ? xv[r].z : xv[r].w));
+        const float2 x2 = make_float2(xk, xk);
+#pragma unroll
+        for (int c = 0; c < TN / 2; ++c) acc[r][c] = __ffma2_rn(x2, b[c], acc[r][c]);
+      }
     }
   }
 }
 
-template <int N>
-__device__ __forceinline__ void load_bias(const float* __restrict__ b, float2* y) {
+// Layer epilogue: z = acc + bias; relu(z) -> Y (shared, column offset yc)
+// and optionally -> act slots (valid rows only).  The reverse pass needs
+// only relu(z): it is the next layer's input, and z > 0 iff relu(z) > 0.
+template <int TN>
+__device__ __forceinline__ void tile_out(const float2 (&acc)[8][TN / 2], const float* __restrict__ bias, int mt,
+                                         int n0, float* act, int P, int slot, int p0, float* Y, int yc) {
+  float2 bb[TN / 2];
 #pragma unroll
-  for (int q = 0; q < N / 4; ++q) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(b) + q);
-    y[2 * q] = make_float2(v.x, v.y);
-    y[2 * q + 1] = make_float2(v.z, v.w);
-  }
-}
-
-template <int N>
-__device__ __forceinline__ void put_relu(float* row, const float2* y) {
+  for (int c = 0; c < TN / 2; ++c) bb[c] = __ldg(reinterpret_cast<const float2*>(bias + n0) + c);
 #pragma unroll
-  for (int q = 0; q < N / 4; ++q)
-    reinterpret_cast<float4*>(row)[q] = make_float4(fmaxf(y[2 * q].x, 0.0f), fmaxf(y[2 * q].y, 0.0f),
-                                                    fmaxf(y[2 * q + 1].x, 0.0f), fmaxf(y[2 * q + 1].y, 0.0f));
-}
-
-template <int N>
-__device__ __forceinline__ void relu_of(const float2* y, float* x) {
+  for (int r = 0; r < 8; ++r) {
+    const int m = mt + 16 * r;
 #pragma unroll
-  for (int q = 0; q < N / 2; ++q) {
-    x[2 * q] = fmaxf(y[q].x, 0.0f);
-    x[2 * q + 1] = fmaxf(y[q].y, 0.0f);
-  }
-}
-
-// d x (pairs) += W^T delta with W row-major rows of `ld` floats at wn
-// (rows 16-byte aligned), columns [0, NIN).
-template <int NOUT, int NIN>
-__device__ __forceinline__ void dense_back(const float* __restrict__ wn, int ld, const float* delta, float2* dx) {
-#pragma unroll 2
-  for (int o = 0; o < NOUT; ++o) {
-    const float2 d = make_float2(delta[o], delta[o]);
-    const float4* w4 = reinterpret_cast<const float4*>(wn + (size_t)o * ld);
-#pragma unroll
-    for (int q = 0; q < NIN / 4; ++q) {
-      const float4 w = __ldg(w4 + q);
-      dx[2 * q] = __ffma2_rn(make_float2(w.x, w.y), d, dx[2 * q]);
-      dx[2 * q + 1] = __ffma2_rn(make_float2(w.z, w.w), d, dx[2 * q + 1]);
+    for (int c = 0; c < TN / 2; ++c) {
+      const float z0 = fmaxf(acc[r][c].x + bb[c].x, 0.0f), z1 = fmaxf(acc[r][c].y + bb[c].y, 0.0f);
+      if (act && p0 + m < P) {
+        act[(size_t)(slot + n0 + 2 * c) * P + p0 + m] = z0;
+        act[(size_t)(slot + n0 + 2 * c + 1) * P + p0 + m] = z1;
+      }
+      *reinterpret_cast<float2*>(Y + m * kFRow + yc + n0 + 2 * c) = make_float2(z0, z1);
     }
   }
 }
 
+// Row m of Y (columns [yc, yc + N)) <- rows [slot, slot + N) of the
+// [slot][P] array src at Gaussian p0 + m (zeros past the end), as 4-byte
+// asynchronous copies; complete after cp_async_wait_all() and a barrier.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(dst)), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 template <int N>
-__device__ __forceinline__ void zero2(float2* y) {
-#pragma unroll
-  for (int q = 0; q < N / 2; ++q) y[q] = make_float2(0.0f, 0.0f);
+__device__ __forceinline__ void rows_async(float* Y, int yc, const float* src, int P, int slot, int p0, int m,
+                                           int ys = kFRow) {
+  const bool valid = p0 + m < P;
+  const float* s0 = src + (size_t)slot * P + (valid ? p0 + m : 0);
+#pragma unroll 16
+  for (int q = 0; q < N; ++q) cp_async4(Y + m * ys + yc + q, s0 + (size_t)q * P, valid);
 }
 
-// Activation slot store / load ([slot][P], coalesced over the block).
-template <int N>
-__device__ __forceinline__ void store_slots(float* act, int P, int slot, int p, const float2* y) {
-#pragma unroll
-  for (int q = 0; q < N / 2; ++q) {
-    act[(size_t)(slot + 2 * q) * P + p] = y[q].x;
-    act[(size_t)(slot + 2 * q + 1) * P + p] = y[q].y;
-  }
+
+// Weight tiles staged into shared memory with cp.async, two buffers: the
+// tile of the next product is in flight while the current one runs.  (The
+// waits are the hardware's group waits: no spinning.)
+struct WTile {
+  int64_t off;           // float offset of the tile's first element
+  int rows, cols, ld;    // copied as [rows][cols] from rows of `ld` floats
+};
+constexpr int kMaxWTiles = 40;
+constexpr int kWBuf = 4096;   // floats per staging buffer (forward)
+constexpr int kWBufR = 2048;  // floats per staging buffer (reverse)
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
-template <int N>
-__device__ __forceinline__ void load_slots(const float* act, int P, int slot, int p, bool valid, float* x) {
-#pragma unroll
-  for (int q = 0; q < N; ++q) x[q] = valid ? __ldg(act + (size_t)(slot + q) * P + p) : 0.0f;
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Issue the copy of tile t (if any) into buffer t & 1; always commits a
+// group so that "all but the newest group" names tile t - 1.  The caller
+// guarantees no thread still reads buffer t & 1.
+template <int kBuf = kWBuf>
+__device__ __forceinline__ void stage_tile(const WTile* tiles, int ntiles, int t, const float* __restrict__ base,
+                                           float* wbuf) {
+  if (t < ntiles) {
+    const WTile w = tiles[t];
+    float* dst = wbuf + (t & 1) * kBuf;
+    const int c4 = w.cols / 4, n = w.rows * c4;
+    for (int i = threadIdx.x; i < n; i += kFThreads) {
+      const int r = i / c4, c = i - r * c4;
+      cp_async16(dst + r * w.cols + 4 * c, base + w.off + (size_t)r * w.ld + 4 * c);
+    }
+  }
+  cp_async_commit();
+}
+
+// Tile t: start tile t + 1, wait for tile t, make it visible to the block.
+template <int kBuf = kWBuf>
+__device__ __forceinline__ const float* next_tile(const WTile* tiles, int ntiles, int& t, const float* base,
+                                                  float* wbuf) {
+  stage_tile<kBuf>(tiles, ntiles, t + 1, base, wbuf);
+  cp_async_wait1();
+  __syncthreads();
+  const float* w = wbuf + (t & 1) * kBuf;
+  ++t;
+  return w;
 }
 
 struct FwdArgs {
   FstGeom g;
   const float *planes, *wt;
+  WTile tiles[kMaxWTiles];
+  int ntiles;
   const float *means, *quats, *log_scales, *logits;
   const void* feat;
   int feat_bf16;
@@ -324,106 +372,142 @@ __device__ __forceinline__ float level_feature(const FstGeom& g, const float* __
   return f;
 }
 
+constexpr size_t kFwdSmem = ((size_t)2 * kFThreads * kFRow + 2 * kWBuf) * 4;
+
 template <int D>
 __global__ void __launch_bounds__(kFThreads, 2) fst_fwd_kernel(const FwdArgs a) {
-  __shared__ int s_ci[kFThreads][kFMaxL * 4];
-  __shared__ float s_cf[kFThreads][kFMaxL * 4];
-  extern __shared__ __align__(16) float s_f[];  // [128][FS]: HexPlane features, then relu(h)
+  extern __shared__ __align__(16) float s_buf[];
+  float* A = s_buf;                        // [128][kFRow]
+  float* B = s_buf + kFThreads * kFRow;    // [128][kFRow]
+  float* wbuf = s_buf + 2 * kFThreads * kFRow;  // [2][kWBuf] staged weight tiles
+  int wt_i = 0;
+  stage_tile(a.tiles, a.ntiles, 0, a.wt, wbuf);
   const FstGeom& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int p = blockIdx.x * kFThreads + tid;
+  const int mt = tid & 15, nt = tid >> 4;
+  const int p0 = blockIdx.x * kFThreads;
+  const int p = p0 + tid;
   const bool valid = p < g.P;
-  const int FS = fwd_row(g.levels);
+  const int P = g.P;
+  float* act = a.act;
+  // Grid axes of every Gaussian, parked in B (ints in columns [0, 16),
+  // fractions in [16, 32)) while the planes are sampled into A.
+  int* ci_row = reinterpret_cast<int*>(B + tid * kFRow);
+  float* cf_row = B + tid * kFRow + kFMaxL * 4;
   float mu[3] = {0.0f, 0.0f, 0.0f};
   if (valid) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) mu[k] = a.means[(size_t)p * 3 + k];
   }
-  grid_axes(g, mu, a.t, s_ci[tid], s_cf[tid]);
+  grid_axes(g, mu, a.t, ci_row, cf_row);
   __syncwarp();
-  // HexPlane features of the warp's Gaussians, lane = channel.
-  const int gbase = blockIdx.x * kFThreads + warp * 32;
-  for (int j = 0; j < 32 && gbase + j < g.P; ++j) {
-    const int r = warp * 32 + j;
-    for (int lv = 0; lv < g.levels; ++lv)
-      s_f[r * FS + lv * kFC + lane] = level_feature(g, a.planes, lv, s_ci[r], s_cf[r], lane);
+  // F_out layer 0 over f, two levels (64 columns of f) at a time.
+  float2 acc[8][4];
+  tile_zero<8>(acc);
+  for (int l0 = 0; l0 < g.levels; l0 += 2) {
+    const int nl = g.levels - l0 < 2 ? g.levels - l0 : 2;
+    const int nw = P - (p0 + warp * 32) < 32 ? P - (p0 + warp * 32) : 32;  // Gaussians of this warp (may be <= 0)
+    for (int j = 0; j < nw; j += 2) {
+      const int r = warp * 32 + j;
+      const bool two = j + 1 < nw;
+      const int* ci0 = reinterpret_cast<const int*>(B + r * kFRow);
+      const float* cf0 = B + r * kFRow + kFMaxL * 4;
+      const int* ci1 = two ? reinterpret_cast<const int*>(B + (r + 1) * kFRow) : ci0;
+      const float* cf1 = two ? B + (r + 1) * kFRow + kFMaxL * 4 : cf0;
+      for (int lv = l0; lv < l0 + nl; ++lv) {
+        const float f0 = level_feature(g, a.planes, lv, ci0, cf0, lane);
+        const float f1 = level_feature(g, a.planes, lv, ci1, cf1, lane);
+        A[r * kFRow + (lv - l0) * kFC + lane] = f0;
+        if (two) A[(r + 1) * kFRow + (lv - l0) * kFC + lane] = f1;
+      }
+    }
+    __syncthreads();
+    if (act && valid) {
+      for (int c = 0; c < nl * kFC; ++c) act[(size_t)(g.sf + l0 * kFC + c) * P + p] = A[tid * kFRow + c];
+    }
+    {
+      const float* w = next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf);
+      tile_mma<8, true>(A, nl * kFC, w, kFW, mt, nt * 8, acc);
+    }
+    __syncthreads();
   }
-  __syncwarp();
-  if (!valid) return;  // no block-wide barrier follows
-  float* frow = s_f + tid * FS;
-  float* act = a.act;
-  const int P = g.P;
-  // F_out: z0 = W0 f + b0, then z_j = W_j relu(z_{j-1}) + b_j.
-  float2 h[kFW / 2];
-  load_bias<kFW>(a.wt + g.ab[0], h);
-  if (act) {
-    for (int c = 0; c < g.levels * kFC; ++c) act[(size_t)(g.sf + c) * P + p] = frow[c];
-  }
-  dense_t<kFMaxL * kFC, kFW>(a.wt + g.aw[0], kFW, frow, h, g.levels * kFC);
-  if (act) store_slots<kFW>(act, P, g.sz, p, h);
+  tile_out<8>(acc, a.wt + g.ab[0], mt, nt * 8, act, P, g.sz, p0, B, 0);
+  __syncthreads();
+  // z_j = W_j relu(z_{j-1}) + b_j; layer j reads (j odd ? B : A).
   for (int j = 1; j < kFDepth; ++j) {
-    put_relu<kFW>(frow, h);
-    load_bias<kFW>(a.wt + g.ab[j], h);
-    dense_t<kFW, kFW>(a.wt + g.aw[j], kFW, frow, h);
-    if (act) store_slots<kFW>(act, P, g.sz + j * kFW, p, h);
+    float* src = (j & 1) ? B : A;
+    float* dst = (j & 1) ? A : B;
+    tile_zero<8>(acc);
+    tile_mma<8, true>(src, kFW, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFW, mt, nt * 8, acc);
+    tile_out<8>(acc, a.wt + g.ab[j], mt, nt * 8, act, P, g.sz + j * kFW, p0, dst, 0);
+    __syncthreads();
   }
-  // relu(h) stays in row[0, 64) while the branches run; row[64, 96) holds
-  // relu(e1), row[96, 128) relu(h_g).
-  put_relu<kFW>(frow, h);
-  // Branches and the semantic updater's first layer (accumulated per branch).
-  float2 v[kFW / 2];
-  load_bias<kFW>(a.wt + g.ab[kLZ1], v);
+  // relu(h) is in A.  Branches: e1 -> B[0, 32), h_g -> B[32, 64); the
+  // semantic updater's first layer accumulates over the branches.
+  float2 v[8][4];
+  tile_zero<8>(v);
   float out[11];
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     const int l1 = branch_e1(b);
     {
-      float2 e1[kFHalf / 2];
-      load_bias<kFHalf>(a.wt + g.ab[l1], e1);
-      dense_t<kFW, kFHalf>(a.wt + g.aw[l1], kFHalf, frow, e1);
-      if (act) store_slots<kFHalf>(act, P, g.se1 + b * kFHalf, p, e1);
-      put_relu<kFHalf>(frow + kFW, e1);
+      float2 e[8][2];
+      tile_zero<4>(e);
+      tile_mma<4, true>(A, kFW, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFHalf, mt, nt * 4, e);
+      tile_out<4>(e, a.wt + g.ab[l1], mt, nt * 4, act, P, g.se1 + b * kFHalf, p0, B, 0);
     }
+    __syncthreads();
     {
-      float2 hg[kFHalf / 2];
-      load_bias<kFHalf>(a.wt + g.ab[l1 + 1], hg);
-      dense_t<kFHalf, kFHalf>(a.wt + g.aw[l1 + 1], kFHalf, frow + kFW, hg);
-      if (act) store_slots<kFHalf>(act, P, g.shg + b * kFHalf, p, hg);
-      put_relu<kFHalf>(frow + kFW + kFHalf, hg);
+      float2 e[8][2];
+      tile_zero<4>(e);
+      tile_mma<4, true>(B, kFHalf, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFHalf, mt, nt * 4, e);
+      tile_out<4>(e, a.wt + g.ab[l1 + 1], mt, nt * 4, act, P, g.shg + b * kFHalf, p0, B, kFHalf);
     }
-    const float* hgr = frow + kFW + kFHalf;
+    __syncthreads();
+    // Head (this thread's own Gaussian): offset = H relu(h_g) + b.
     constexpr int dgs[4] = {3, 4, 3, 1}, oos[4] = {0, 3, 7, 10};
-    const int dg = dgs[b], oo = oos[b];
+    const float* hgr = B + tid * kFRow + kFHalf;
     const float* wt_h = a.wt + g.aw[l1 + 2];  // [32][dg]
     const float* bh = a.wt + g.ab[l1 + 2];
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
-      if (o < dg) {
+      if (o < dgs[b]) {
         float s = __ldg(bh + o);
-#pragma unroll
-        for (int i = 0; i < kFHalf; ++i) s = fmaf(__ldg(wt_h + i * dg + o), hgr[i], s);
-        out[oo + o] = s;
+#pragma unroll 8
+        for (int i = 0; i < kFHalf; ++i) s = fmaf(__ldg(wt_h + i * dgs[b] + o), hgr[i], s);
+        out[oos[b] + o] = s;
       }
     }
-    dense_t<kFHalf, kFW>(a.wt + g.aw[kLZ1] + (size_t)b * kFHalf * kFW, kFW, hgr, v);
+    tile_mma<8, true>(B + kFHalf, kFHalf, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFW, mt, nt * 8, v);
+    __syncthreads();
   }
-  if (act) store_slots<kFW>(act, P, g.sv, p, v);
-  put_relu<kFW>(frow, v);
-  const float* vr = frow;
-  // dz = Z2 relu(v) + b, in column chunks of at most 32.
-  constexpr int ZC = D < 32 ? D : 32;
+  tile_out<8>(v, a.wt + g.ab[kLZ1], mt, nt * 8, act, P, g.sv, p0, A, 0);
+  __syncthreads();
+  // dz = Z2 relu(v) + b, 64 columns at a time.
+  constexpr int ZN = D < 64 ? D : 64, ZT = ZN / 8;
 #pragma unroll
-  for (int c0 = 0; c0 < D; c0 += ZC) {
-    float2 z[ZC / 2];
-    load_bias<ZC>(a.wt + g.ab[kLZ2] + c0, z);
-    dense_t<kFW, ZC>(a.wt + g.aw[kLZ2] + c0, D, vr, z);
+  for (int c0 = 0; c0 < D; c0 += ZN) {
+    float2 z[8][ZT / 2];
+    tile_zero<ZT>(z);
+    tile_mma<ZT, true>(A, kFW, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), ZN, mt, nt * ZT, z);
+    float2 bb[ZT / 2];
 #pragma unroll
-    for (int q = 0; q < ZC / 2; ++q) {
-      const size_t i0 = (size_t)p * D + c0 + 2 * q;
-      store_feat(a.feat_t, a.feat_bf16, i0, load_feat(a.feat, a.feat_bf16, i0) + z[q].x);
-      store_feat(a.feat_t, a.feat_bf16, i0 + 1, load_feat(a.feat, a.feat_bf16, i0 + 1) + z[q].y);
+    for (int c = 0; c < ZT / 2; ++c) bb[c] = __ldg(reinterpret_cast<const float2*>(a.wt + g.ab[kLZ2] + c0 + nt * ZT) + c);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int pm = p0 + mt + 16 * r;
+      if (pm < P) {
+#pragma unroll
+        for (int c = 0; c < ZT / 2; ++c) {
+          const size_t i0 = (size_t)pm * D + c0 + nt * ZT + 2 * c;
+          store_feat(a.feat_t, a.feat_bf16, i0, load_feat(a.feat, a.feat_bf16, i0) + z[r][c].x + bb[c].x);
+          store_feat(a.feat_t, a.feat_bf16, i0 + 1, load_feat(a.feat, a.feat_bf16, i0 + 1) + z[r][c].y + bb[c].y);
+        }
+      }
     }
+    __syncthreads();
   }
+  if (!valid) return;
   // Deformed Gaussian (Eq. 6): offsets added to the canonical parameters.
 #pragma unroll
   for (int k = 0; k < 3; ++k) a.means_t[(size_t)p * 3 + k] = mu[k] + out[k];
@@ -446,30 +530,43 @@ struct BwdArgs {
   float *d_means, *d_planes;
   float* dv;    // [64][P]: delta of F_feat's first layer
   float* part;  // [gridDim.x][mlp_aligned]
+  WTile tiles[kMaxWTiles];  // row-major weight tiles in order of use (per chunk)
+  int ntiles;
 };
 
 // pw[o * ldw + i] (+)= sum over the block's 128 Gaussians of
 // s_d[g][o] * s_x[g][i], o < NO (<= 64), i < NI (multiple of 8, <= 64);
-// pb[o] (+)= sum_g s_d[g][o] when pb is set.  Ends with a barrier.
-__device__ void block_outer(const float* s_d, const float* s_x, int NO, int NI, float* pw, int ldw, float* pb,
-                            bool first) {
-  __syncthreads();
-  const int nog = (NO + 3) / 4, ntile = nog * (NI / 8);
+// pb[o] (+)= sum_g s_d[g][o] when pb is set.  Tiles of TO outputs x 8
+// inputs per thread (TO chosen so that the 128 threads have work); the bias
+// sum runs as two fixed-order halves of independent partial sums.  Starts
+// and ends with a barrier.
+template <int TO>
+__device__ __forceinline__ void outer_tiles(const float* s_d, int ds, const float* s_x, int xs, int NO, int NI,
+                                            float* pw, int ldw, bool first) {
+  const int nog = (NO + TO - 1) / TO, ntile = nog * (NI / 8);
   for (int tile = threadIdx.x; tile < ntile; tile += kFThreads) {
-    const int o0 = (tile % nog) * 4, i0 = (tile / nog) * 8;
-    float2 acc[4][4];
+    const int o0 = (tile % nog) * TO, i0 = (tile / nog) * 8;
+    float2 acc[TO][4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < TO; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.0f, 0.0f);
 #pragma unroll 4
     for (int gg = 0; gg < kFThreads; ++gg) {
-      const float4 d = *reinterpret_cast<const float4*>(s_d + gg * kFRow + o0);
-      const float4 x0 = *reinterpret_cast<const float4*>(s_x + gg * kFRow + i0);
-      const float4 x1 = *reinterpret_cast<const float4*>(s_x + gg * kFRow + i0 + 4);
-      const float dv[4] = {d.x, d.y, d.z, d.w};
+      float dv[TO];
+      if (TO == 4) {
+        const float4 d = *reinterpret_cast<const float4*>(s_d + gg * ds + o0);
+        dv[0] = d.x; dv[TO > 1 ? 1 : 0] = d.y; dv[TO > 2 ? 2 : 0] = d.z; dv[TO > 3 ? 3 : 0] = d.w;
+      } else if (TO == 2) {
+        const float2 d = *reinterpret_cast<const float2*>(s_d + gg * ds + o0);
+        dv[0] = d.x; dv[TO > 1 ? 1 : 0] = d.y;
+      } else {
+        dv[0] = s_d[gg * ds + o0];
+      }
+      const float4 x0 = *reinterpret_cast<const float4*>(s_x + gg * xs + i0);
+      const float4 x1 = *reinterpret_cast<const float4*>(s_x + gg * xs + i0 + 4);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < TO; ++r) {
         const float2 dd = make_float2(dv[r], dv[r]);
         acc[r][0] = __ffma2_rn(dd, make_float2(x0.x, x0.y), acc[r][0]);
         acc[r][1] = __ffma2_rn(dd, make_float2(x0.z, x0.w), acc[r][1]);
@@ -478,7 +575,7 @@ __device__ void block_outer(const float* s_d, const float* s_x, int NO, int NI, 
       }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < TO; ++r) {
       if (o0 + r < NO) {
         float* row = pw + (size_t)(o0 + r) * ldw + i0;
 #pragma unroll
@@ -494,282 +591,269 @@ __device__ void block_outer(const float* s_d, const float* s_x, int NO, int NI, 
       }
     }
   }
+}
+
+__device__ void block_outer(const float* s_d, int ds, const float* s_x, int xs, int NO, int NI, float* pw, int ldw,
+                            float* pb, bool first) {
+  __shared__ float s_red[kFThreads];
+  __syncthreads();
+  if (NO >= 4 && (NO / 4) * (NI / 8) >= kFThreads)
+    outer_tiles<4>(s_d, ds, s_x, xs, NO, NI, pw, ldw, first);
+  else if (NO >= 2 && (NO / 2) * (NI / 8) >= kFThreads / 2)
+    outer_tiles<2>(s_d, ds, s_x, xs, NO, NI, pw, ldw, first);
+  else
+    outer_tiles<1>(s_d, ds, s_x, xs, NO, NI, pw, ldw, first);
   if (pb) {
-    for (int o = threadIdx.x; o < NO; o += kFThreads) {
-      float s = 0.0f;
-      for (int gg = 0; gg < kFThreads; ++gg) s += s_d[gg * kFRow + o];
-      pb[o] = first ? s : pb[o] + s;
+    const int o = threadIdx.x & 63, half = threadIdx.x >> 6;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    if (o < NO) {
+#pragma unroll 4
+      for (int gg = half * 64; gg < half * 64 + 64; gg += 4) {
+        s0 += s_d[gg * ds + o];
+        s1 += s_d[(gg + 1) * ds + o];
+        s2 += s_d[(gg + 2) * ds + o];
+        s3 += s_d[(gg + 3) * ds + o];
+      }
+    }
+    s_red[threadIdx.x] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (threadIdx.x < NO) {
+      const float v = s_red[threadIdx.x] + s_red[threadIdx.x + 64];
+      pb[threadIdx.x] = first ? v : pb[threadIdx.x] + v;
     }
   }
   __syncthreads();
 }
 
-template <int N>
-__device__ __forceinline__ void put_row(float* s, const float* x) {
+// Lane-cooperative reverse of one level's HexPlane sample for NG Gaussians
+// at once (lane = channel, dfc[q] = d f of this channel for Gaussian q): all
+// corner fetches are issued before any arithmetic, plane gradients by
+// atomics, coordinate gradients summed over the warp into dc[q][0..2]
+// (lane 0 adds).
+template <int NG>
+__device__ __forceinline__ void plane_backward(const FstGeom& g, const float* __restrict__ planes, float* d_planes,
+                                               int lv, const int* const* ci, const float* const* cf, const float* dfc,
+                                               int lane, float* const* dc) {
+  float q00[NG][6], q01[NG][6], q10[NG][6], q11[NG][6];
 #pragma unroll
-  for (int q = 0; q < N / 4; ++q) reinterpret_cast<float4*>(s)[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-}
-template <int N>
-__device__ __forceinline__ void put_row_relu(float* s, const float* z) {
+  for (int n = 0; n < NG; ++n) {
 #pragma unroll
-  for (int q = 0; q < N / 4; ++q)
-    reinterpret_cast<float4*>(s)[q] = make_float4(fmaxf(z[4 * q], 0.f), fmaxf(z[4 * q + 1], 0.f),
-                                                  fmaxf(z[4 * q + 2], 0.f), fmaxf(z[4 * q + 3], 0.f));
-}
-template <int N>
-__device__ __forceinline__ void mask_pairs(const float2* dx, const float* z, float* delta) {
-#pragma unroll
-  for (int q = 0; q < N / 2; ++q) {
-    delta[2 * q] = z[2 * q] > 0.0f ? dx[q].x : 0.0f;
-    delta[2 * q + 1] = z[2 * q + 1] > 0.0f ? dx[q].y : 0.0f;
+    for (int k = 0; k < 6; ++k) {
+      const int ia = ci[n][lv * 4 + pair_a(k)] & 0x3FFFFFFF, ib = ci[n][lv * 4 + pair_b(k)] & 0x3FFFFFFF;
+      const int rb = g.prb[lv * 6 + k];
+      const float* base = planes + g.poff[lv * 6 + k] + ((size_t)ia * rb + ib) * kFC + lane;
+      q00[n][k] = __ldg(base);
+      q01[n][k] = __ldg(base + kFC);
+      q10[n][k] = __ldg(base + (size_t)rb * kFC);
+      q11[n][k] = __ldg(base + (size_t)rb * kFC + kFC);
+    }
   }
-}
-
-// delta[i] = dx[i] where the stored pre-activation z[i] > 0, else 0.
-template <int N>
-__device__ __forceinline__ void mask_slots(const float2* dx, const float* act, int P, int slot, int p, bool valid,
-                                           float* delta) {
 #pragma unroll
-  for (int q = 0; q < N / 2; ++q) {
-    const float z0 = valid ? __ldg(act + (size_t)(slot + 2 * q) * P + p) : 0.0f;
-    const float z1 = valid ? __ldg(act + (size_t)(slot + 2 * q + 1) * P + p) : 0.0f;
-    delta[2 * q] = z0 > 0.0f ? dx[q].x : 0.0f;
-    delta[2 * q + 1] = z1 > 0.0f ? dx[q].y : 0.0f;
-  }
-}
-template <int N>
-__device__ __forceinline__ void store_rows(float* dst, int P, int p, bool valid, const float* x) {
-  if (!valid) return;
+  for (int n = 0; n < NG; ++n) {
+    float smp[6];
 #pragma unroll
-  for (int q = 0; q < N; ++q) dst[(size_t)q * P + p] = x[q];
-}
-// dx (pairs) += W^T delta with delta read from rows [NOUT][P] of src.
-template <int NOUT, int NIN>
-__device__ __forceinline__ void dense_back_rows(const float* __restrict__ wn, int ld, const float* src, int P, int p,
-                                                bool valid, float2* dx) {
-#pragma unroll 2
-  for (int o = 0; o < NOUT; ++o) {
-    const float dv = valid ? src[(size_t)o * P + p] : 0.0f;
-    const float2 d = make_float2(dv, dv);
-    const float4* w4 = reinterpret_cast<const float4*>(wn + (size_t)o * ld);
+    for (int k = 0; k < 6; ++k) {
+      const float fa = cf[n][lv * 4 + pair_a(k)], fb = cf[n][lv * 4 + pair_b(k)];
+      smp[k] = (1.0f - fa) * ((1.0f - fb) * q00[n][k] + fb * q01[n][k]) + fa * ((1.0f - fb) * q10[n][k] + fb * q11[n][k]);
+    }
+    float dcl[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int q = 0; q < NIN / 4; ++q) {
-      const float4 w = __ldg(w4 + q);
-      dx[2 * q] = __ffma2_rn(make_float2(w.x, w.y), d, dx[2 * q]);
-      dx[2 * q + 1] = __ffma2_rn(make_float2(w.z, w.w), d, dx[2 * q + 1]);
+    for (int k = 0; k < 6; ++k) {
+      float others = 1.0f;
+#pragma unroll
+      for (int m = 0; m < 6; ++m)
+        if (m != k) others *= smp[m];
+      const float ds = dfc[n] * others;
+      const int A = pair_a(k), B = pair_b(k);
+      const int ca = ci[n][lv * 4 + A], cb = ci[n][lv * 4 + B];
+      const int ia = ca & 0x3FFFFFFF, ib = cb & 0x3FFFFFFF;
+      const float fa = cf[n][lv * 4 + A], fb = cf[n][lv * 4 + B];
+      const int rb = g.prb[lv * 6 + k];
+      float* dbase = d_planes + g.poff[lv * 6 + k] + ((size_t)ia * rb + ib) * kFC + lane;
+      atomicAdd(dbase, (1.0f - fa) * (1.0f - fb) * ds);
+      atomicAdd(dbase + kFC, (1.0f - fa) * fb * ds);
+      atomicAdd(dbase + (size_t)rb * kFC, fa * (1.0f - fb) * ds);
+      atomicAdd(dbase + (size_t)rb * kFC + kFC, fa * fb * ds);
+      if (!(ca >> 30))  // A is always a spatial axis
+        dcl[A] += ds * ((1.0f - fb) * (q10[n][k] - q00[n][k]) + fb * (q11[n][k] - q01[n][k])) * 0.5f *
+                  (float)(g.pra[lv * 6 + k] - 1);
+      if (B < 3 && !(cb >> 30))
+        dcl[B < 3 ? B : 0] += ds * ((1.0f - fa) * (q01[n][k] - q00[n][k]) + fa * (q11[n][k] - q10[n][k])) * 0.5f *
+                              (float)(rb - 1);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float v = dcl[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+      dcl[k] = v;
+    }
+    if (lane == 0) {
+      dc[n][0] += dcl[0];
+      dc[n][1] += dcl[1];
+      dc[n][2] += dcl[2];
     }
   }
 }
 
-// Lane-cooperative reverse of one level's HexPlane sample for one Gaussian
-// (lane = channel, dfc = d f of this channel): plane gradients by atomics,
-// coordinate gradients summed over the warp into dc[0..2] (lane 0 adds).
-__device__ __forceinline__ void plane_backward(const FstGeom& g, const float* __restrict__ planes, float* d_planes,
-                                               int lv, const int* ci, const float* cf, float dfc, int lane,
-                                               float* dc) {
-  float smp[6], q00[6], q01[6], q10[6], q11[6];
+// Y[m][yc + n] <- (X[m][xc + n] > 0 ? acc : 0) for the thread's tile (the
+// ReLU mask read from the stored relu(z) inputs); dv rows optionally copied
+// to global [n][P].
+template <int TN>
+__device__ __forceinline__ void tile_mask(const float2 (&acc)[8][TN / 2], const float* X, int xc, float* Y, int yc,
+                                          int mt, int n0, float* rows, int P, int p0, int xs = kFRow) {
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const int ia = ci[lv * 4 + pair_a(k)] & 0x3FFFFFFF, ib = ci[lv * 4 + pair_b(k)] & 0x3FFFFFFF;
-    const float fa = cf[lv * 4 + pair_a(k)], fb = cf[lv * 4 + pair_b(k)];
-    const int rb = g.prb[lv * 6 + k];
-    const float* base = planes + g.poff[lv * 6 + k] + ((size_t)ia * rb + ib) * kFC + lane;
-    q00[k] = __ldg(base);
-    q01[k] = __ldg(base + kFC);
-    q10[k] = __ldg(base + (size_t)rb * kFC);
-    q11[k] = __ldg(base + (size_t)rb * kFC + kFC);
-    smp[k] = (1.0f - fa) * ((1.0f - fb) * q00[k] + fb * q01[k]) + fa * ((1.0f - fb) * q10[k] + fb * q11[k]);
-  }
-  float dcl[3] = {0.f, 0.f, 0.f};
+  for (int r = 0; r < 8; ++r) {
+    const int m = mt + 16 * r;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    float others = 1.0f;
-#pragma unroll
-    for (int m = 0; m < 6; ++m)
-      if (m != k) others *= smp[m];
-    const float ds = dfc * others;
-    const int A = pair_a(k), B = pair_b(k);
-    const int ca = ci[lv * 4 + A], cb = ci[lv * 4 + B];
-    const int ia = ca & 0x3FFFFFFF, ib = cb & 0x3FFFFFFF;
-    const float fa = cf[lv * 4 + A], fb = cf[lv * 4 + B];
-    const int rb = g.prb[lv * 6 + k];
-    float* dbase = d_planes + g.poff[lv * 6 + k] + ((size_t)ia * rb + ib) * kFC + lane;
-    atomicAdd(dbase, (1.0f - fa) * (1.0f - fb) * ds);
-    atomicAdd(dbase + kFC, (1.0f - fa) * fb * ds);
-    atomicAdd(dbase + (size_t)rb * kFC, fa * (1.0f - fb) * ds);
-    atomicAdd(dbase + (size_t)rb * kFC + kFC, fa * fb * ds);
-    if (!(ca >> 30))  // A is always a spatial axis
-      dcl[A] += ds * ((1.0f - fb) * (q10[k] - q00[k]) + fb * (q11[k] - q01[k])) * 0.5f * (float)(g.pra[lv * 6 + k] - 1);
-    if (B < 3 && !(cb >> 30))
-      dcl[B < 3 ? B : 0] += ds * ((1.0f - fa) * (q01[k] - q00[k]) + fa * (q11[k] - q10[k])) * 0.5f * (float)(rb - 1);
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    float s = dcl[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    dcl[k] = s;
-  }
-  if (lane == 0) {
-    dc[0] += dcl[0];
-    dc[1] += dcl[1];
-    dc[2] += dcl[2];
+    for (int c = 0; c < TN / 2; ++c) {
+      const float2 x = *reinterpret_cast<const float2*>(X + m * xs + xc + n0 + 2 * c);
+      const float2 d = make_float2(x.x > 0.0f ? acc[r][c].x : 0.0f, x.y > 0.0f ? acc[r][c].y : 0.0f);
+      *reinterpret_cast<float2*>(Y + m * kFRow + yc + n0 + 2 * c) = d;
+      if (rows && p0 + m < P) {
+        rows[(size_t)(n0 + 2 * c) * P + p0 + m] = d.x;
+        rows[(size_t)(n0 + 2 * c + 1) * P + p0 + m] = d.y;
+      }
+    }
   }
 }
+
+constexpr int kTRow = 36;  // row stride of the small third buffer
+constexpr size_t kBwdSmem = ((size_t)(2 * kFRow + kTRow) * kFThreads + 2 * kWBufR) * 4;
+static_assert(kTRow * kFThreads >= 2 * kFThreads * kFMaxL * 4, "grid axes alias the third buffer");
 
 template <int D>
 __global__ void __launch_bounds__(kFThreads, 2) fst_bwd_kernel(const BwdArgs a) {
   extern __shared__ __align__(16) float s_dyn[];
-  float* s_d = s_dyn;                       // [128][kFRow]: deltas of a layer
-  float* s_x = s_dyn + kFThreads * kFRow;   // [128][kFRow]: inputs of a layer
-  __shared__ int s_ci[kFThreads][kFMaxL * 4];
-  __shared__ float s_cf[kFThreads][kFMaxL * 4];
+  float* SD = s_dyn;                            // [128][kFRow]: deltas
+  float* SX = s_dyn + kFThreads * kFRow;        // [128][kFRow]: layer inputs
+  float* ST = s_dyn + 2 * kFThreads * kFRow;    // [128][kTRow]: relu(h_g) | head deltas; grid axes
+  float* wbuf = ST + kFThreads * kTRow;         // [2][kWBufR] staged weight tiles
+  int (*s_ci)[kFMaxL * 4] = reinterpret_cast<int (*)[kFMaxL * 4]>(ST);
+  float (*s_cf)[kFMaxL * 4] = reinterpret_cast<float (*)[kFMaxL * 4]>(ST + kFThreads * kFMaxL * 4);
   __shared__ float s_dc[kFThreads][4];
   const FstGeom& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int mt = tid & 15, nt = tid >> 4;
   const int P = g.P;
   const int nchunk = (P + kFThreads - 1) / kFThreads;
   float* part = a.part + (size_t)blockIdx.x * g.mlp_aligned;
-  float* sd = s_d + tid * kFRow;
-  float* sx = s_x + tid * kFRow;
   const float* act = a.act;
   for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
     const bool first = chunk == (int)blockIdx.x;
-    const int p = chunk * kFThreads + tid;
+    const int p0 = chunk * kFThreads;
+    const int p = p0 + tid;
     const bool valid = p < P;
-    const int pc = valid ? p : 0;
-    // ---- F_feat, second layer: delta = d dz, input relu(v).
-    {
-      float v[kFW];
-      load_slots<kFW>(act, P, g.sv, pc, valid, v);
-      put_row_relu<kFW>(sx, v);
-    }
-    float2 dx[kFW / 2];
-    zero2<kFW>(dx);
-#pragma unroll
-    for (int c0 = 0; c0 < D; c0 += 64) {
-      constexpr int NC = D < 64 ? D : 64;
-      {
-        float dz[NC];
-#pragma unroll
-        for (int q = 0; q < NC; ++q) dz[q] = valid ? __ldg(a.d_feat_t + (size_t)p * D + c0 + q) : 0.0f;
-        put_row<NC>(sd, dz);
-        dense_back<NC, kFW>(a.wn + g.aw[kLZ2] + (size_t)c0 * kFW, kFW, sd, dx);
+    int wt_i = 0;
+    stage_tile<kWBufR>(a.tiles, a.ntiles, 0, a.wn, wbuf);
+    // ---- F_feat second layer: delta = d dz; input relu(v).
+    rows_async<kFW>(SX, 0, act, P, g.sv, p0, tid);
+    float2 acc[8][4];
+    tile_zero<8>(acc);
+    constexpr int NC = D < 64 ? D : 64;
+    for (int c0 = 0; c0 < D; c0 += NC) {
+      for (int q = 0; q < NC; q += 4)
+        *reinterpret_cast<float4*>(SD + tid * kFRow + q) =
+            valid ? __ldg(reinterpret_cast<const float4*>(a.d_feat_t + (size_t)p * D + c0 + q)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      cp_async_wait_all();
+      block_outer(SD, kFRow, SX, kFRow, NC, kFW, part + g.aw[kLZ2] + (size_t)c0 * kFW, kFW, part + g.ab[kLZ2] + c0, first);
+      for (int r0 = 0; r0 < NC; r0 += 32) {
+        if (r0) __syncthreads();
+        const float* w = next_tile<kWBufR>(a.tiles, a.ntiles, wt_i, a.wn, wbuf);
+        tile_mma<8, true>(SD + r0, NC - r0 < 32 ? NC - r0 : 32, w, kFW, mt, nt * 8, acc);
       }
-      block_outer(s_d, s_x, NC, kFW, part + g.aw[kLZ2] + (size_t)c0 * kFW, kFW, part + g.ab[kLZ2] + c0, first);
+      __syncthreads();
     }
-    // delta of F_feat's first layer; kept in the workspace for the branches.
-    {
-      float dv[kFW];
-      mask_slots<kFW>(dx, act, P, g.sv, pc, valid, dv);
-      put_row<kFW>(sd, dv);
-      store_rows<kFW>(a.dv, P, pc, valid, dv);
-    }
-#pragma unroll
+    // delta_v (kept in SD and in the workspace for the branches).
+    tile_mask<8>(acc, SX, 0, SD, 0, mt, nt * 8, a.dv, P, p0);
+    // ---- F_feat first layer: input relu(u), u = [h_mu, h_R, h_S, h_o].
     for (int half = 0; half < 2; ++half) {
-      {
-        float u[kFW];
-        load_slots<kFW>(act, P, g.shg + half * kFW, pc, valid, u);
-        put_row_relu<kFW>(sx, u);
-      }
-      block_outer(s_d, s_x, kFW, kFW, part + g.aw[kLZ1] + half * kFW, 4 * kFHalf, half ? nullptr : part + g.ab[kLZ1],
+      __syncthreads();
+      rows_async<kFW>(SX, 0, act, P, g.shg + half * kFW, p0, tid);
+      cp_async_wait_all();
+      block_outer(SD, kFRow, SX, kFRow, kFW, kFW, part + g.aw[kLZ1] + half * kFW, 4 * kFHalf, half ? nullptr : part + g.ab[kLZ1],
                   first);
     }
-    // ---- Branches.
-    float2 drh[kFW / 2];
-    zero2<kFW>(drh);
+    // ---- Branches; d relu(h) accumulates over them.
+    float2 drh[8][4];
+    tile_zero<8>(drh);
     const float* dsrc[4] = {a.d_means_t, a.d_quats_t, a.d_log_scales_t, a.d_logits_t};
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       constexpr int dgs[4] = {3, 4, 3, 1};
       const int dg = dgs[b], l1 = branch_e1(b);
-      float dhg[kFHalf];
-      {
-        float hg[kFHalf];
-        load_slots<kFHalf>(act, P, g.shg + b * kFHalf, pc, valid, hg);
-        float dh[4] = {0.f, 0.f, 0.f, 0.f};
+      // delta_v rows -> SX; relu(h_g) and the head deltas -> ST.
+      __syncthreads();
+      rows_async<kFW>(SX, 0, a.dv, P, 0, p0, tid);
+      rows_async<kFHalf>(ST, 0, act, P, g.shg + b * kFHalf, p0, tid, kTRow);
 #pragma unroll
-        for (int o = 0; o < 4; ++o)
-          if (o < dg && valid) dh[o] = __ldg(dsrc[b] + (size_t)p * dg + o);
-        // head: delta = d offset, input relu(h_g).
-        put_row<4>(sd, dh);
-        put_row_relu<kFHalf>(sx, hg);
-        // d relu(h_g): from the head and from F_feat's first layer.
-        float2 d2[kFHalf / 2];
-        zero2<kFHalf>(d2);
+      for (int o = 0; o < 4; ++o) ST[tid * kTRow + kFHalf + o] = (o < dg && valid) ? __ldg(dsrc[b] + (size_t)p * dg + o) : 0.0f;
+      cp_async_wait_all();
+      __syncthreads();
+      // d relu(h_g) = Z1[:, branch b]^T delta_v + H^T d offset, masked.
+      float2 e[8][2];
+      tile_zero<4>(e);
+      tile_mma<4, true>(SX, kFW, next_tile<kWBufR>(a.tiles, a.ntiles, wt_i, a.wn, wbuf), kFHalf, mt, nt * 4, e);
+      {
         const float* wh = a.wn + g.aw[l1 + 2];  // [dg][32]
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          if (o < dg) {
-            const float2 d = make_float2(dh[o], dh[o]);
+        for (int r = 0; r < 8; ++r) {
+          const float* dh = ST + (mt + 16 * r) * kTRow + kFHalf;
 #pragma unroll
-            for (int q = 0; q < kFHalf / 4; ++q) {
-              const float4 w = __ldg(reinterpret_cast<const float4*>(wh + o * kFHalf) + q);
-              d2[2 * q] = __ffma2_rn(make_float2(w.x, w.y), d, d2[2 * q]);
-              d2[2 * q + 1] = __ffma2_rn(make_float2(w.z, w.w), d, d2[2 * q + 1]);
+          for (int o = 0; o < 4; ++o) {
+            if (o < dg) {
+              const float2 d2 = make_float2(dh[o], dh[o]);
+#pragma unroll
+              for (int c = 0; c < 2; ++c)
+                e[r][c] = __ffma2_rn(d2, __ldg(reinterpret_cast<const float2*>(wh + o * kFHalf + nt * 4) + c), e[r][c]);
             }
           }
         }
-        dense_back_rows<kFW, kFHalf>(a.wn + g.aw[kLZ1] + b * kFHalf, 4 * kFHalf, a.dv, P, pc, valid, d2);
-        mask_pairs<kFHalf>(d2, hg, dhg);
       }
-      block_outer(s_d, s_x, dg, kFHalf, part + g.aw[l1 + 2], kFHalf, part + g.ab[l1 + 2], first);
-      // E2: input relu(e1).
-      float de1[kFHalf];
-      {
-        float e1[kFHalf];
-        load_slots<kFHalf>(act, P, g.se1 + b * kFHalf, pc, valid, e1);
-        put_row<kFHalf>(sd, dhg);
-        put_row_relu<kFHalf>(sx, e1);
-        float2 de[kFHalf / 2];
-        zero2<kFHalf>(de);
-        dense_back<kFHalf, kFHalf>(a.wn + g.aw[l1 + 1], kFHalf, sd, de);
-        mask_pairs<kFHalf>(de, e1, de1);
-      }
-      block_outer(s_d, s_x, kFHalf, kFHalf, part + g.aw[l1 + 1], kFHalf, part + g.ab[l1 + 1], first);
-      // E1: input relu(h).
-      {
-        float h7[kFW];
-        load_slots<kFW>(act, P, g.sz + (kFDepth - 1) * kFW, pc, valid, h7);
-        put_row_relu<kFW>(sx, h7);
-      }
-      put_row<kFHalf>(sd, de1);
-      dense_back<kFHalf, kFW>(a.wn + g.aw[l1], kFW, sd, drh);
-      block_outer(s_d, s_x, kFHalf, kFW, part + g.aw[l1], kFW, part + g.ab[l1], first);
+      tile_mask<4>(e, ST, 0, SD, 0, mt, nt * 4, nullptr, P, p0, kTRow);   // delta_hg -> SD[0, 32)
+      // head: delta = d offset (ST[32, 36)), input relu(h_g) (ST[0, 32)).
+      block_outer(ST + kFHalf, kTRow, ST, kTRow, dg, kFHalf, part + g.aw[l1 + 2], kFHalf, part + g.ab[l1 + 2], first);
+      // E2: delta_hg (SD[0, 32)), input relu(e1).
+      rows_async<kFHalf>(SX, 0, act, P, g.se1 + b * kFHalf, p0, tid);
+      cp_async_wait_all();
+      block_outer(SD, kFRow, SX, kFRow, kFHalf, kFHalf, part + g.aw[l1 + 1], kFHalf, part + g.ab[l1 + 1], first);
+      tile_zero<4>(e);
+      tile_mma<4, true>(SD, kFHalf, next_tile<kWBufR>(a.tiles, a.ntiles, wt_i, a.wn, wbuf), kFHalf, mt, nt * 4, e);
+      __syncthreads();
+      tile_mask<4>(e, SX, 0, SD, 0, mt, nt * 4, nullptr, P, p0);   // delta_e1 -> SD[0, 32)
+      __syncthreads();
+      // E1: delta_e1, input relu(h).
+      rows_async<kFW>(SX, 0, act, P, g.sz + (kFDepth - 1) * kFW, p0, tid);
+      cp_async_wait_all();
+      block_outer(SD, kFRow, SX, kFRow, kFHalf, kFW, part + g.aw[l1], kFW, part + g.ab[l1], first);
+      tile_mma<8, true>(SD, kFHalf, next_tile<kWBufR>(a.tiles, a.ntiles, wt_i, a.wn, wbuf), kFW, mt, nt * 8, drh);
     }
-    // ---- F_out, last layer first.
-    float delta[kFW];
-    mask_slots<kFW>(drh, act, P, g.sz + (kFDepth - 1) * kFW, pc, valid, delta);
+    // ---- F_out, last layer first.  SX holds relu(h).
+    __syncthreads();
+    tile_mask<8>(drh, SX, 0, SD, 0, mt, nt * 8, nullptr, P, p0);
     for (int j = kFDepth - 1; j >= 1; --j) {
-      {
-        float zp[kFW];
-        load_slots<kFW>(act, P, g.sz + (j - 1) * kFW, pc, valid, zp);
-        put_row_relu<kFW>(sx, zp);
-      }
-      put_row<kFW>(sd, delta);
-      float2 d3[kFW / 2];
-      zero2<kFW>(d3);
-      dense_back<kFW, kFW>(a.wn + g.aw[j], kFW, sd, d3);
-      block_outer(s_d, s_x, kFW, kFW, part + g.aw[j], kFW, part + g.ab[j], first);
-      mask_slots<kFW>(d3, act, P, g.sz + (j - 1) * kFW, pc, valid, delta);
+      __syncthreads();
+      rows_async<kFW>(SX, 0, act, P, g.sz + (j - 1) * kFW, p0, tid);
+      cp_async_wait_all();
+      block_outer(SD, kFRow, SX, kFRow, kFW, kFW, part + g.aw[j], kFW, part + g.ab[j], first);
+      tile_zero<8>(acc);
+      tile_mma<8, true>(SD, 32, next_tile<kWBufR>(a.tiles, a.ntiles, wt_i, a.wn, wbuf), kFW, mt, nt * 8, acc);
+      __syncthreads();
+      tile_mma<8, true>(SD + 32, 32, next_tile<kWBufR>(a.tiles, a.ntiles, wt_i, a.wn, wbuf), kFW, mt, nt * 8, acc);
+      __syncthreads();
+      tile_mask<8>(acc, SX, 0, SD, 0, mt, nt * 8, nullptr, P, p0);
     }
     // First layer: input f.
     const int nf = g.levels * kFC;
-    put_row<kFW>(sd, delta);
     for (int c0 = 0; c0 < nf; c0 += kFW) {
       const int nc = nf - c0 < kFW ? nf - c0 : kFW;
-      {
-        float f[kFW];
-        load_slots<kFW>(act, P, g.sf + c0, pc, valid, f);
-        if (nc < kFW) {
-#pragma unroll
-          for (int q = kFC; q < kFW; ++q) f[q] = 0.0f;
-        }
-        put_row<kFW>(sx, f);
-      }
-      block_outer(s_d, s_x, kFW, nc, part + g.aw[0] + c0, nf, c0 ? nullptr : part + g.ab[0], first);
+      __syncthreads();
+      if (nc == kFW) rows_async<kFW>(SX, 0, act, P, g.sf + c0, p0, tid);
+      else rows_async<kFC>(SX, 0, act, P, g.sf + c0, p0, tid);
+      cp_async_wait_all();
+      block_outer(SD, kFRow, SX, kFRow, kFW, nc, part + g.aw[0] + c0, nf, c0 ? nullptr : part + g.ab[0], first);
     }
-    // ---- HexPlane: d f per level, lane-cooperative over the warp's Gaussians.
+    // ---- HexPlane: d f per level into SX[0, 32), then lane-cooperative.
     float mu[3] = {0.f, 0.f, 0.f};
     if (valid) {
 #pragma unroll
@@ -777,21 +861,34 @@ __global__ void __launch_bounds__(kFThreads, 2) fst_bwd_kernel(const BwdArgs a) 
     }
     grid_axes(g, mu, a.t, s_ci[tid], s_cf[tid]);
     s_dc[tid][0] = s_dc[tid][1] = s_dc[tid][2] = 0.0f;
-    const int gbase = chunk * kFThreads + warp * 32;
     for (int lv = 0; lv < g.levels; ++lv) {
-      float2 dfl[kFC / 2];
-      zero2<kFC>(dfl);
-      dense_back<kFW, kFC>(a.wn + g.aw[0] + lv * kFC, nf, sd, dfl);
-      __syncwarp();
+      float2 e[8][2];
+      tile_zero<4>(e);
+      tile_mma<4, true>(SD, kFW, next_tile<kWBufR>(a.tiles, a.ntiles, wt_i, a.wn, wbuf), kFC, mt, nt * 4, e);
+      __syncthreads();
 #pragma unroll
-      for (int q = 0; q < kFC / 2; ++q) {
-        sx[2 * q] = dfl[q].x;
-        sx[2 * q + 1] = dfl[q].y;
-      }
-      __syncwarp();
-      for (int j = 0; j < 32 && gbase + j < P; ++j) {
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          *reinterpret_cast<float2*>(SX + (mt + 16 * r) * kFRow + nt * 4 + 2 * c) = e[r][c];
+      __syncthreads();
+      const int nw = P - (p0 + warp * 32) < 32 ? P - (p0 + warp * 32) : 32;  // Gaussians of this warp
+      int j = 0;
+      for (; j + 1 < nw; j += 2) {
         const int r = warp * 32 + j;
-        plane_backward(g, a.planes, a.d_planes, lv, s_ci[r], s_cf[r], s_x[r * kFRow + lane], lane, s_dc[r]);
+        const int* ci[2] = {s_ci[r], s_ci[r + 1]};
+        const float* cf[2] = {s_cf[r], s_cf[r + 1]};
+        const float dfc[2] = {SX[r * kFRow + lane], SX[(r + 1) * kFRow + lane]};
+        float* dc[2] = {s_dc[r], s_dc[r + 1]};
+        plane_backward<2>(g, a.planes, a.d_planes, lv, ci, cf, dfc, lane, dc);
+      }
+      if (j < nw) {
+        const int r = warp * 32 + j;
+        const int* ci[1] = {s_ci[r]};
+        const float* cf[1] = {s_cf[r]};
+        const float dfc[1] = {SX[r * kFRow + lane]};
+        float* dc[1] = {s_dc[r]};
+        plane_backward<1>(g, a.planes, a.d_planes, lv, ci, cf, dfc, lane, dc);
       }
     }
     __syncwarp();
@@ -800,10 +897,9 @@ __global__ void __launch_bounds__(kFThreads, 2) fst_bwd_kernel(const BwdArgs a) 
       for (int k = 0; k < 3; ++k)
         a.d_means[(size_t)p * 3 + k] = a.d_means_t[(size_t)p * 3 + k] + s_dc[tid][k] * g.scale[k];
     }
-    __syncthreads();  // s_x rows are rewritten by the next chunk's products
+    __syncthreads();  // the buffers are rewritten by the next chunk
   }
 }
-
 
 // d_mlp (caller's packed layout) = sum over blocks, in block order, of the
 // partials (aligned layout).
@@ -935,7 +1031,7 @@ namespace {
 template <int D>
 cudaError_t launch_fst_fwd(const FwdArgs& a, cudaStream_t st) {
   const int blocks = (a.g.P + kFThreads - 1) / kFThreads;
-  const size_t smem = (size_t)kFThreads * fwd_row(a.g.levels) * 4;
+  const size_t smem = kFwdSmem;
   auto k = fst_fwd_kernel<D>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<blocks, kFThreads, smem, st>>>(a);
@@ -944,7 +1040,7 @@ cudaError_t launch_fst_fwd(const FwdArgs& a, cudaStream_t st) {
 
 template <int D>
 cudaError_t launch_fst_bwd(const BwdArgs& a, int nblk, cudaStream_t st) {
-  const size_t smem = (size_t)2 * kFThreads * kFRow * 4;
+  const size_t smem = kBwdSmem;
   auto k = fst_bwd_kernel<D>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<nblk, kFThreads, smem, st>>>(a);
@@ -993,6 +1089,24 @@ extern "C" fe_status fe_fst_forward(const fe_fst* fst, int P, const float* means
   a.logits_t = opacity_logits_t;
   a.feat_t = feat_t;
   a.act = with_backward ? reinterpret_cast<float*>(ws + w.act) : nullptr;
+  // Weight tiles of the transposed copy in the order the kernel uses them.
+  {
+    int n = 0;
+    auto add = [&](int64_t off, int rows, int cols, int ld) { a.tiles[n++] = WTile{off, rows, cols, ld}; };
+    for (int l0 = 0; l0 < g.levels; l0 += 2) {
+      const int nl = g.levels - l0 < 2 ? g.levels - l0 : 2;
+      add(g.aw[0] + (int64_t)l0 * kFC * kFW, nl * kFC, kFW, kFW);
+    }
+    for (int j = 1; j < kFDepth; ++j) add(g.aw[j], kFW, kFW, kFW);
+    for (int b = 0; b < 4; ++b) {
+      add(g.aw[branch_e1(b)], kFW, kFHalf, kFHalf);
+      add(g.aw[branch_e1(b) + 1], kFHalf, kFHalf, kFHalf);
+      add(g.aw[kLZ1] + (int64_t)b * kFHalf * kFW, kFHalf, kFW, kFW);
+    }
+    const int zn = g.D < 64 ? g.D : 64;
+    for (int c0 = 0; c0 < g.D; c0 += zn) add(g.aw[kLZ2] + c0, kFW, zn, g.D);
+    a.ntiles = n;
+  }
   cudaError_t e = cudaErrorInvalidValue;
   switch (g.D) {
     case 16: e = launch_fst_fwd<16>(a, st); break;
@@ -1020,7 +1134,7 @@ extern "C" fe_status fe_fst_backward(const fe_fst* fst, int P, const float* mean
   if (cudaMemsetAsync(d_planes, 0, (size_t)plane_floats(g) * 4, st) != cudaSuccess) return FE_ERR_CUDA;
   if (P == 0) return cudaMemsetAsync(d_mlp, 0, (size_t)g.mlp_packed * 4, st) == cudaSuccess ? FE_OK : FE_ERR_CUDA;
   if (!fst->planes || !means || !d_means_t || !d_quats_t || !d_log_scales_t || !d_opacity_logits_t || !d_feat_t ||
-      !d_means)
+      !d_means || !al16p(d_feat_t))
     return FE_ERR_INVALID_ARG;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   BwdArgs a{};
@@ -1039,6 +1153,27 @@ extern "C" fe_status fe_fst_backward(const fe_fst* fst, int P, const float* mean
   a.d_planes = d_planes;
   a.dv = reinterpret_cast<float*>(ws + w.dv);
   a.part = reinterpret_cast<float*>(ws + w.part);
+  // Row-major weight tiles (at most 2048 floats) in the order the kernel
+  // uses them for every chunk.
+  {
+    int n = 0;
+    auto add = [&](int64_t off, int rows, int cols, int ld) { a.tiles[n++] = WTile{off, rows, cols, ld}; };
+    const int nc = g.D < 64 ? g.D : 64;
+    for (int c0 = 0; c0 < g.D; c0 += nc)
+      for (int r0 = 0; r0 < nc; r0 += 32) add(g.aw[kLZ2] + (int64_t)(c0 + r0) * kFW, nc - r0 < 32 ? nc - r0 : 32, kFW, kFW);
+    for (int b = 0; b < 4; ++b) {
+      add(g.aw[kLZ1] + b * kFHalf, kFW, kFHalf, 4 * kFHalf);
+      add(g.aw[branch_e1(b) + 1], kFHalf, kFHalf, kFHalf);
+      add(g.aw[branch_e1(b)], kFHalf, kFW, kFW);
+    }
+    for (int j = kFDepth - 1; j >= 1; --j) {
+      add(g.aw[j], 32, kFW, kFW);
+      add(g.aw[j] + 32 * kFW, 32, kFW, kFW);
+    }
+    const int nf = g.levels * kFC;
+    for (int lv = 0; lv < g.levels; ++lv) add(g.aw[0] + lv * kFC, kFW, kFC, nf);
+    a.ntiles = n;
+  }
   const int nblk = bwd_blocks(P);
   cudaError_t e = cudaErrorInvalidValue;
   switch (g.D) {
