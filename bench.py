@@ -75,7 +75,8 @@ def parse():
     p.add_argument("--t", type=float, default=0.5)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--D", type=int, default=None, help="feature width override (16, 32, 64, 128): D sweep")
-    p.add_argument("--micro", choices=["decoder", "adam"], default=None,
+    p.add_argument("--P", type=int, default=None, help="Gaussian count override (--micro fst: profiling sizes)")
+    p.add_argument("--micro", choices=["decoder", "adam", "fst"], default=None,
                    help="time one HBM-bound kernel alone on the workload's sizes")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -476,8 +477,27 @@ def run_micro(args, cfg):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     g = torch.Generator().manual_seed(0)
-    HW, D, P = cfg["W"] * cfg["H"], cfg["D"], cfg["P"]
-    if args.micro == "decoder":
+    HW, D, P = cfg["W"] * cfg["H"], cfg["D"], cfg["P"] if args.P is None else args.P
+    if args.micro == "fst":
+        # The full FST module alone: forward (keeping the reverse state) and
+        # reverse from random deformed-Gaussian gradients.
+        from paper_2503_06161_gb300 import synth
+        from paper_2503_06161_gb300.fst import FSTDeform
+        from paper_2503_06161_gb300.raster import GaussianScene
+        fc = cfg.get("fst", dict(levels=4, rs=64, rt=100))
+        sc = synth.make_scene(P, D, cfg["lo"], cfg["hi"], seed=0)
+        planes, mlp = synth.make_fst(fc["levels"], fc["rs"], fc["rt"], D, seed=1)
+        scene = GaussianScene.from_numpy(sc, dev)
+        fst = FSTDeform.from_numpy(planes, mlp, fc["levels"], fc["rs"], fc["rt"], D, cfg["lo"], cfg["hi"], P, device=dev)
+        up = {k: torch.randn(*s, generator=g).to(dev) for k, s in
+              dict(means=(P, 3), quats=(P, 4), log_scales=(P, 3), opacity_logits=(P,), feat=(P, D)).items()}
+
+        def fn():
+            fst.forward(scene, 0.5)
+            fst.backward(scene, 0.5, dict(up, means=up["means"].clone()))
+        nbytes = fst.planes.numel() * 4
+        what = f"full FST module forward + reverse over {P} Gaussians ({fc['levels']} levels)"
+    elif args.micro == "decoder":
         dec = Decoder.random(D, device=dev)
         feat = torch.randn(HW, D, generator=g).to(torch.bfloat16).to(dev)
         tgt = torch.randn(HW, 256, generator=g).to(torch.bfloat16).to(dev)
@@ -510,6 +530,16 @@ def run_micro(args, cfg):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    if args.micro == "fst":
+        fl = 6.0 * fst_macs(fc["levels"], D) * P   # forward 2 M, reverse 4 M flop per Gaussian
+        mhz = clk.get("sm_mhz") or 2070.0
+        peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        tf = fl / (ms * 1e-3) / 1e12
+        print(json.dumps({"micro": "fst", "workload": args.workload, "what": what, "ms": round(ms, 4),
+                          "roofline": {"bound": "alu", "achieved": round(tf, 3), "peak": round(peak, 2),
+                                       "unit": "TFLOP/s", "frac": round(tf / peak, 4)},
+                          "steps": args.steps, "warmup": args.warmup, "clocks": clk}))
+        return
     peak, basis = hbm_peak()
     gbs = nbytes / (ms * 1e-3) / 1e9
     print(json.dumps({"micro": args.micro, "workload": args.workload, "what": what, "ms": round(ms, 4),
