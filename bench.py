@@ -157,6 +157,32 @@ def flops_composite_bwd(visits, contribs, D):
 
 
 # ---------------------------------------------------------------------------
+# Replicas over ranks (one process per GPU): each rank renders its own
+# timestamp of the same scene, no collective on the data path; the step time
+# is the maximum over ranks and the value counts every rank's work.
+# ---------------------------------------------------------------------------
+def replica_time(t: float, rank: int, world: int) -> float:
+    """Timestamp of this rank's replica: ranks spread evenly over [0, 1)."""
+    return (t + rank / max(world, 1)) % 1.0 if world > 1 else t
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's step time (all-reduce MAX; identity at N=1)."""
+    if world <= 1:
+        return ms
+    import torch
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(ms: float, world: int, units_per_rank: float = 1.0) -> float:
+    """Units per second of the whole job: every rank processed its units in
+    at most ms."""
+    return world * units_per_rank * 1000.0 / ms
+
+
+# ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
 def run_ours(args, world, rank, local):
@@ -175,7 +201,7 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     cfg = synth.CONFIGS[args.workload]
     sc, cam_np, df_np = synth.config_inputs(args.workload, D=args.D)
-    t = (args.t + rank / max(world, 1)) % 1.0 if world > 1 else args.t
+    t = replica_time(args.t, rank, world)
     P, D, W, H = sc.P, sc.D, cam_np.width, cam_np.height
     HW = W * H
     bf16 = bool(cfg.get("bf16", False))
@@ -313,10 +339,7 @@ def run_ours(args, world, rank, local):
     if opt is not None:
         stages["adam"] = statistics.mean(ev[i][12].elapsed_time(ev[i][13]) for i in range(K_steps))
     ms = statistics.mean(step_ms)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, world, dev)
 
     # ---- forward-only FPS (rendering, the paper's speed metric): a
     # forward-only workspace (no reverse-pass state), as inference uses.
@@ -593,7 +616,7 @@ def run_train_fst(args, world, rank, local, cfg):
     fst = FSTDeform.from_numpy(planes, mlp, levels, rs, rt, D, cfg["lo"], cfg["hi"], P, device=dev)
     w_np, b_np = synth.make_decoder(D, seed=3)
     tr = Trainer.from_numpy(sc, cam_np, None, w_np, b_np, device=dev, fst=fst)
-    t = (args.t + rank / max(world, 1)) % 1.0 if world > 1 else args.t
+    t = replica_time(args.t, rank, world)
     rgb_np, dec_np = synth.make_targets(H, W, D, seed=2, dec_channels=256)
     tgt = dict(rgb=torch.as_tensor(rgb_np, device=dev), dec=torch.as_tensor(dec_np).to(torch.bfloat16).to(dev),
                depth=torch.as_tensor(synth.make_depth_target(H, W, cfg["lo"][2], cfg["hi"][2]), device=dev))
@@ -626,10 +649,7 @@ def run_train_fst(args, world, rank, local, cfg):
     names = ["fst_forward", "render_forward_losses", "render_reverse", "fst_reverse_tv", "adam"]
     stages = {n: round(statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(K)), 4)
               for j, n in enumerate(names)}
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, world, dev)
     # The FST kernels alone (same state), for their rooflines.
     scene_t = fst.forward(tr.scene, t)
     g = {k: v.clone() for k, v in tr.grads.items()}
@@ -764,10 +784,7 @@ def run_batch(args, world, rank, local, cfg):
         torch.distributed.barrier()
     clk = clocks.stop()
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, world, dev)
     # Per-stage times and pair counts from one eager pass with stage events.
     stages = {n: 0.0 for n in ("deform_project", "binning", "composite_fwd", "loss", "composite_bwd", "feat_grad",
                                "gauss_bwd")}
