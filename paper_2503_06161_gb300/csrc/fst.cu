@@ -574,20 +574,21 @@ __device__ __forceinline__ void outer_tiles(const float* s_d, int ds, const floa
         acc[r][3] = __ffma2_rn(dd, make_float2(x1.z, x1.w), acc[r][3]);
       }
     }
+    // Read-modify-write of the block's partial one tile row at a time: the
+    // row's two 16-byte loads are issued together, then added and stored.
 #pragma unroll
     for (int r = 0; r < TO; ++r) {
       if (o0 + r < NO) {
-        float* row = pw + (size_t)(o0 + r) * ldw + i0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          float2 v = acc[r][c];
-          if (!first) {
-            v.x += row[2 * c];
-            v.y += row[2 * c + 1];
-          }
-          row[2 * c] = v.x;
-          row[2 * c + 1] = v.y;
+        float4* row = reinterpret_cast<float4*>(pw + (size_t)(o0 + r) * ldw + i0);
+        float4 v0 = make_float4(acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y);
+        float4 v1 = make_float4(acc[r][2].x, acc[r][2].y, acc[r][3].x, acc[r][3].y);
+        if (!first) {
+          const float4 a0 = row[0], a1 = row[1];
+          v0.x += a0.x; v0.y += a0.y; v0.z += a0.z; v0.w += a0.w;
+          v1.x += a1.x; v1.y += a1.y; v1.z += a1.z; v1.w += a1.w;
         }
+        row[0] = v0;
+        row[1] = v1;
       }
     }
   }
