@@ -407,18 +407,25 @@ __global__ void __launch_bounds__(kFThreads, 2) fst_fwd_kernel(const FwdArgs a) 
   for (int l0 = 0; l0 < g.levels; l0 += 2) {
     const int nl = g.levels - l0 < 2 ? g.levels - l0 : 2;
     const int nw = P - (p0 + warp * 32) < 32 ? P - (p0 + warp * 32) : 32;  // Gaussians of this warp (may be <= 0)
-    for (int j = 0; j < nw; j += 2) {
+    for (int j = 0; j < nw; j += 4) {
+      // Four Gaussians at a time (the last group repeats a valid row in
+      // place of missing ones and does not store them).
       const int r = warp * 32 + j;
-      const bool two = j + 1 < nw;
-      const int* ci0 = reinterpret_cast<const int*>(B + r * kFRow);
-      const float* cf0 = B + r * kFRow + kFMaxL * 4;
-      const int* ci1 = two ? reinterpret_cast<const int*>(B + (r + 1) * kFRow) : ci0;
-      const float* cf1 = two ? B + (r + 1) * kFRow + kFMaxL * 4 : cf0;
+      const int* ci[4];
+      const float* cf[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int rq = j + q < nw ? r + q : r;
+        ci[q] = reinterpret_cast<const int*>(B + rq * kFRow);
+        cf[q] = B + rq * kFRow + kFMaxL * 4;
+      }
       for (int lv = l0; lv < l0 + nl; ++lv) {
-        const float f0 = level_feature(g, a.planes, lv, ci0, cf0, lane);
-        const float f1 = level_feature(g, a.planes, lv, ci1, cf1, lane);
-        A[r * kFRow + (lv - l0) * kFC + lane] = f0;
-        if (two) A[(r + 1) * kFRow + (lv - l0) * kFC + lane] = f1;
+        float f[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f[q] = level_feature(g, a.planes, lv, ci[q], cf[q], lane);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (j + q < nw) A[(r + q) * kFRow + (lv - l0) * kFC + lane] = f[q];
       }
     }
     __syncthreads();
