@@ -926,23 +926,27 @@ __global__ void fst_reduce_kernel(const FstGeom g, const float* __restrict__ par
 // ---------------------------------------------------------------------------
 // Total variation of the planes (L_TV of Eq. 11).
 // ---------------------------------------------------------------------------
+constexpr int kTvMaxBlocks = 1024;  // loss partials (the caller's scratch)
+
 struct TvArgs {
   FstGeom g;
   const float* planes;
   float* d_planes;
   float weight;
-  float* partial;  // [planes][kTvBlocks]
+  float* partial;                   // [gridDim.x]
+  int bstart[kFMaxL * 6 + 1];       // first block of each plane (blocks in proportion to plane size)
 };
 
-constexpr int kTvBlocks = 40;  // blocks per plane (grid.y = plane)
-
-// One plane per grid row; each thread takes four channels of a node (the
-// planes are channels-last, so a float4 per neighbour).  The loss partials
-// are summed in a fixed order afterwards.
+// Each plane gets a share of the blocks in proportion to its size; each
+// thread takes four channels of a node (the planes are channels-last, so a
+// float4 per neighbour).  One loss partial per block, summed in a fixed
+// order afterwards.
 __global__ void __launch_bounds__(256) fst_tv_kernel(const TvArgs a) {
   __shared__ float s_w[8];
   const FstGeom& g = a.g;
-  const int k = blockIdx.y;
+  int k = 0;
+  while (k + 1 < g.levels * 6 && (int)blockIdx.x >= a.bstart[k + 1]) ++k;
+  const int b0 = a.bstart[k], nb = a.bstart[k + 1] - b0;
   const int ra = g.pra[k], rb = g.prb[k];
   const float4* pl = reinterpret_cast<const float4*>(a.planes + g.poff[k]);
   float4* dp = reinterpret_cast<float4*>(a.d_planes + g.poff[k]);
@@ -950,7 +954,7 @@ __global__ void __launch_bounds__(256) fst_tv_kernel(const TvArgs a) {
   const int total = ra * rb * q4;
   const float ia = 1.0f / (float)((int64_t)(ra - 1) * rb * kFC), ib = 1.0f / (float)((int64_t)ra * (rb - 1) * kFC);
   float acc = 0.0f;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+  for (int e = ((int)blockIdx.x - b0) * blockDim.x + threadIdx.x; e < total; e += nb * blockDim.x) {
     const int node = e / q4;
     const int i = node / rb, j = node - i * rb;
     const float4 v = pl[e];
@@ -978,7 +982,7 @@ __global__ void __launch_bounds__(256) fst_tv_kernel(const TvArgs a) {
   if (threadIdx.x == 0) {
     float t = 0.0f;
     for (int w = 0; w < 8; ++w) t += s_w[w];
-    a.partial[k * kTvBlocks + blockIdx.x] = t;
+    a.partial[blockIdx.x] = t;
   }
 }
 
@@ -1207,8 +1211,18 @@ extern "C" fe_status fe_fst_tv(const fe_fst* fst, float weight, float* loss, flo
   a.d_planes = d_planes;
   a.weight = weight;
   a.partial = scratch;
-  const int np = g.levels * 6;  // at most 24 planes x kTvBlocks partials <= 1024 scratch floats
-  fst_tv_kernel<<<dim3(kTvBlocks, np), 256, 0, st>>>(a);
-  fst_tv_finish<<<1, 32, 0, st>>>(scratch, np * kTvBlocks, weight, loss);
+  // Blocks per plane in proportion to its size (at least one), at most
+  // kTvMaxBlocks in all.
+  const int np = g.levels * 6;
+  const double total = (double)plane_floats(g);
+  const int budget = kTvMaxBlocks - np;
+  a.bstart[0] = 0;
+  for (int k = 0; k < np; ++k) {
+    const double n = (double)g.pra[k] * g.prb[k] * kFC;
+    a.bstart[k + 1] = a.bstart[k] + 1 + (int)(budget * n / total);
+  }
+  const int nblk = a.bstart[np];
+  fst_tv_kernel<<<nblk, 256, 0, st>>>(a);
+  fst_tv_finish<<<1, 32, 0, st>>>(scratch, nblk, weight, loss);
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
