@@ -257,35 +257,42 @@ __device__ __forceinline__ void load_mlp(const GaussArgs& a, float* sw) {
 // h2pre = W2 relu(W1 f + b1) + b2, streamed over the first-layer units so
 // only f and the 64 second-layer accumulators live in registers; m1 gets
 // bit i set where first-layer unit i is active.
+// Packed FP32 FMAs throughout: the first-layer dot keeps even and odd
+// channels in the two halves of a pair (two independent chains), the
+// second-layer accumulators are output pairs.
 template <int C>
 __device__ __forceinline__ void mlp_hidden2(const float* sw, const float f[C], float h2[kHidden], uint64_t& m1) {
   using L = Mlp<C>;
+  float2 h2p[kHidden / 2];
 #pragma unroll
-  for (int o = 0; o < kHidden; ++o) h2[o] = sw[L::kB2 + o];
+  for (int o = 0; o < kHidden / 2; ++o) h2p[o] = make_float2(sw[L::kB2 + 2 * o], sw[L::kB2 + 2 * o + 1]);
   m1 = 0;
 #pragma unroll 1
   for (int o1 = 0; o1 < kHidden; ++o1) {
     const float4* w1r = reinterpret_cast<const float4*>(sw + L::kW1 + o1 * C);
-    float acc = sw[L::kB1 + o1];
+    float2 acc2 = make_float2(sw[L::kB1 + o1], 0.0f);
 #pragma unroll
     for (int c4 = 0; c4 < C / 4; ++c4) {
       const float4 w = w1r[c4];
-      acc = fmaf(w.x, f[4 * c4], acc);
-      acc = fmaf(w.y, f[4 * c4 + 1], acc);
-      acc = fmaf(w.z, f[4 * c4 + 2], acc);
-      acc = fmaf(w.w, f[4 * c4 + 3], acc);
+      acc2 = __ffma2_rn(make_float2(w.x, w.y), make_float2(f[4 * c4], f[4 * c4 + 1]), acc2);
+      acc2 = __ffma2_rn(make_float2(w.z, w.w), make_float2(f[4 * c4 + 2], f[4 * c4 + 3]), acc2);
     }
+    const float acc = acc2.x + acc2.y;
     m1 |= (uint64_t)(acc > 0.0f) << o1;
     const float h = fmaxf(acc, 0.0f);
+    const float2 hh = make_float2(h, h);
     const float4* w2r = reinterpret_cast<const float4*>(sw + L::kW2t + o1 * kHidden);
 #pragma unroll
     for (int o4 = 0; o4 < kHidden / 4; ++o4) {
       const float4 w = w2r[o4];
-      h2[4 * o4] = fmaf(w.x, h, h2[4 * o4]);
-      h2[4 * o4 + 1] = fmaf(w.y, h, h2[4 * o4 + 1]);
-      h2[4 * o4 + 2] = fmaf(w.z, h, h2[4 * o4 + 2]);
-      h2[4 * o4 + 3] = fmaf(w.w, h, h2[4 * o4 + 3]);
+      h2p[2 * o4] = __ffma2_rn(make_float2(w.x, w.y), hh, h2p[2 * o4]);
+      h2p[2 * o4 + 1] = __ffma2_rn(make_float2(w.z, w.w), hh, h2p[2 * o4 + 1]);
     }
+  }
+#pragma unroll
+  for (int o = 0; o < kHidden / 2; ++o) {
+    h2[2 * o] = h2p[o].x;
+    h2[2 * o + 1] = h2p[o].y;
   }
 }
 
@@ -305,16 +312,14 @@ __device__ __forceinline__ void mlp_forward(const float* sw, const float f[C], f
 #pragma unroll
   for (int k = 0; k < kHeads; ++k) {
     const float4* wr = reinterpret_cast<const float4*>(sw + L::kWh + k * kHidden);
-    float acc = sw[L::kBh + k];
+    float2 acc2 = make_float2(sw[L::kBh + k], 0.0f);
 #pragma unroll
     for (int o4 = 0; o4 < kHidden / 4; ++o4) {
       const float4 w = wr[o4];
-      acc = fmaf(w.x, h2[4 * o4], acc);
-      acc = fmaf(w.y, h2[4 * o4 + 1], acc);
-      acc = fmaf(w.z, h2[4 * o4 + 2], acc);
-      acc = fmaf(w.w, h2[4 * o4 + 3], acc);
+      acc2 = __ffma2_rn(make_float2(w.x, w.y), make_float2(h2[4 * o4], h2[4 * o4 + 1]), acc2);
+      acc2 = __ffma2_rn(make_float2(w.z, w.w), make_float2(h2[4 * o4 + 2], h2[4 * o4 + 3]), acc2);
     }
-    delta[k] = acc;
+    delta[k] = acc2.x + acc2.y;
   }
 }
 
@@ -336,30 +341,34 @@ __device__ __forceinline__ void mlp_backward(const float* sw, uint64_t m1, uint6
     acc = fmaf(a2.z, dd[10], acc);
     g2[o] = ((m2 >> o) & 1ull) ? acc : 0.0f;
   }
+  float2 dfp[C / 2];
 #pragma unroll
-  for (int c = 0; c < C; ++c) df[c] = 0.0f;
+  for (int c = 0; c < C / 2; ++c) dfp[c] = make_float2(0.0f, 0.0f);
 #pragma unroll 1
   for (int o1 = 0; o1 < kHidden; ++o1) {
     if (!((m1 >> o1) & 1ull)) continue;
     const float4* w2r = reinterpret_cast<const float4*>(sw + L::kW2t + o1 * kHidden);
-    float d1 = 0.0f;
+    float2 d2 = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int o4 = 0; o4 < kHidden / 4; ++o4) {
       const float4 w = w2r[o4];
-      d1 = fmaf(w.x, g2[4 * o4], d1);
-      d1 = fmaf(w.y, g2[4 * o4 + 1], d1);
-      d1 = fmaf(w.z, g2[4 * o4 + 2], d1);
-      d1 = fmaf(w.w, g2[4 * o4 + 3], d1);
+      d2 = __ffma2_rn(make_float2(w.x, w.y), make_float2(g2[4 * o4], g2[4 * o4 + 1]), d2);
+      d2 = __ffma2_rn(make_float2(w.z, w.w), make_float2(g2[4 * o4 + 2], g2[4 * o4 + 3]), d2);
     }
+    const float d1 = d2.x + d2.y;
+    const float2 dd1 = make_float2(d1, d1);
     const float4* w1r = reinterpret_cast<const float4*>(sw + L::kW1 + o1 * C);
 #pragma unroll
     for (int c4 = 0; c4 < C / 4; ++c4) {
       const float4 w = w1r[c4];
-      df[4 * c4] = fmaf(w.x, d1, df[4 * c4]);
-      df[4 * c4 + 1] = fmaf(w.y, d1, df[4 * c4 + 1]);
-      df[4 * c4 + 2] = fmaf(w.z, d1, df[4 * c4 + 2]);
-      df[4 * c4 + 3] = fmaf(w.w, d1, df[4 * c4 + 3]);
+      dfp[2 * c4] = __ffma2_rn(make_float2(w.x, w.y), dd1, dfp[2 * c4]);
+      dfp[2 * c4 + 1] = __ffma2_rn(make_float2(w.z, w.w), dd1, dfp[2 * c4 + 1]);
     }
+  }
+#pragma unroll
+  for (int c = 0; c < C / 2; ++c) {
+    df[2 * c] = dfp[c].x;
+    df[2 * c + 1] = dfp[c].y;
   }
 }
 
