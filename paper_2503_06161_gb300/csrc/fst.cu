@@ -129,7 +129,7 @@ int bwd_blocks(int P) {
 }
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 struct WsLayout {
-  size_t wt, wn, act, dv, part, total;
+  size_t wt, wn, act, dv, df, part, total;
 };
 WsLayout ws_layout(const FstGeom& g, int with_backward) {
   WsLayout w{};
@@ -137,7 +137,8 @@ WsLayout ws_layout(const FstGeom& g, int with_backward) {
   w.wn = w.wt + al256((size_t)g.mlp_aligned * 4);
   w.act = w.wn + al256((size_t)g.mlp_aligned * 4);
   w.dv = w.act + (with_backward ? al256((size_t)g.nslots * g.P * 4) : 0);
-  w.part = w.dv + (with_backward ? al256((size_t)kFW * g.P * 4) : 0);
+  w.df = w.dv + (with_backward ? al256((size_t)kFW * g.P * 4) : 0);
+  w.part = w.df + (with_backward ? al256((size_t)g.levels * kFC * g.P * 4) : 0);
   w.total = w.part + (with_backward ? al256((size_t)bwd_blocks(g.P) * g.mlp_aligned * 4) : 0);
   return w;
 }
@@ -536,6 +537,7 @@ struct BwdArgs {
   const float *d_means_t, *d_quats_t, *d_log_scales_t, *d_logits_t, *d_feat_t;
   float *d_means, *d_planes;
   float* dv;    // [64][P]: delta of F_feat's first layer
+  float* df;    // [P][levels * 32]: d f, read by the HexPlane reverse kernel
   float* part;  // [gridDim.x][mlp_aligned]
   WTile tiles[kMaxWTiles];  // row-major weight tiles in order of use (per chunk)
   int ntiles;
@@ -728,7 +730,7 @@ __device__ __forceinline__ void tile_mask(const float2 (&acc)[8][TN / 2], const 
 
 constexpr int kTRow = 36;  // row stride of the small third buffer
 constexpr size_t kBwdSmem = ((size_t)(2 * kFRow + kTRow) * kFThreads + 2 * kWBufR) * 4;
-static_assert(kTRow * kFThreads >= 2 * kFThreads * kFMaxL * 4, "grid axes alias the third buffer");
+
 
 template <int D>
 __global__ void __launch_bounds__(kFThreads, 2) fst_bwd_kernel(const BwdArgs a) {
@@ -737,9 +739,6 @@ __global__ void __launch_bounds__(kFThreads, 2) fst_bwd_kernel(const BwdArgs a) 
   float* SX = s_dyn + kFThreads * kFRow;        // [128][kFRow]: layer inputs
   float* ST = s_dyn + 2 * kFThreads * kFRow;    // [128][kTRow]: relu(h_g) | head deltas; grid axes
   float* wbuf = ST + kFThreads * kTRow;         // [2][kWBufR] staged weight tiles
-  int (*s_ci)[kFMaxL * 4] = reinterpret_cast<int (*)[kFMaxL * 4]>(ST);
-  float (*s_cf)[kFMaxL * 4] = reinterpret_cast<float (*)[kFMaxL * 4]>(ST + kFThreads * kFMaxL * 4);
-  __shared__ float s_dc[kFThreads][4];
   const FstGeom& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int mt = tid & 15, nt = tid >> 4;
@@ -861,14 +860,8 @@ __global__ void __launch_bounds__(kFThreads, 2) fst_bwd_kernel(const BwdArgs a) 
       cp_async_wait_all();
       block_outer(SD, kFRow, SX, kFRow, kFW, nc, part + g.aw[0] + c0, nf, c0 ? nullptr : part + g.ab[0], first);
     }
-    // ---- HexPlane: d f per level into SX[0, 32), then lane-cooperative.
-    float mu[3] = {0.f, 0.f, 0.f};
-    if (valid) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) mu[k] = a.means[(size_t)p * 3 + k];
-    }
-    grid_axes(g, mu, a.t, s_ci[tid], s_cf[tid]);
-    s_dc[tid][0] = s_dc[tid][1] = s_dc[tid][2] = 0.0f;
+    // ---- d f = W0^T delta_0, 32 columns per level, staged in SX and
+    // written Gaussian-major for the HexPlane reverse kernel.
     for (int lv = 0; lv < g.levels; ++lv) {
       float2 e[8][2];
       tile_zero<4>(e);
@@ -880,32 +873,73 @@ __global__ void __launch_bounds__(kFThreads, 2) fst_bwd_kernel(const BwdArgs a) 
         for (int c = 0; c < 2; ++c)
           *reinterpret_cast<float2*>(SX + (mt + 16 * r) * kFRow + nt * 4 + 2 * c) = e[r][c];
       __syncthreads();
-      const int nw = P - (p0 + warp * 32) < 32 ? P - (p0 + warp * 32) : 32;  // Gaussians of this warp
-      int j = 0;
-      for (; j + 1 < nw; j += 2) {
-        const int r = warp * 32 + j;
-        const int* ci[2] = {s_ci[r], s_ci[r + 1]};
-        const float* cf[2] = {s_cf[r], s_cf[r + 1]};
-        const float dfc[2] = {SX[r * kFRow + lane], SX[(r + 1) * kFRow + lane]};
-        float* dc[2] = {s_dc[r], s_dc[r + 1]};
-        plane_backward<2>(g, a.planes, a.d_planes, lv, ci, cf, dfc, lane, dc);
-      }
-      if (j < nw) {
-        const int r = warp * 32 + j;
-        const int* ci[1] = {s_ci[r]};
-        const float* cf[1] = {s_cf[r]};
-        const float dfc[1] = {SX[r * kFRow + lane]};
-        float* dc[1] = {s_dc[r]};
-        plane_backward<1>(g, a.planes, a.d_planes, lv, ci, cf, dfc, lane, dc);
-      }
-    }
-    __syncwarp();
-    if (valid) {
+      if (valid) {
+        float4* dst = reinterpret_cast<float4*>(a.df + (size_t)p * nf + lv * kFC);
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
-        a.d_means[(size_t)p * 3 + k] = a.d_means_t[(size_t)p * 3 + k] + s_dc[tid][k] * g.scale[k];
+        for (int q = 0; q < kFC / 4; ++q) dst[q] = *reinterpret_cast<const float4*>(SX + tid * kFRow + 4 * q);
+      }
     }
     __syncthreads();  // the buffers are rewritten by the next chunk
+  }
+}
+
+// HexPlane reverse: per Gaussian and level, d f (Gaussian-major rows) through
+// the channel-wise product and the bilinear weights -- plane gradients by
+// coalesced atomics, the canonical mean's gradient summed over the warp
+// (one warp owns each Gaussian: reproducible).  A light kernel with many
+// warps per SM, so many corner fetches are in flight.
+constexpr int kHexThreads = 256;
+struct HexArgs {
+  FstGeom g;
+  const float *planes, *means, *df, *d_means_t;
+  float t;
+  float *d_means, *d_planes;
+};
+
+__global__ void __launch_bounds__(kHexThreads, 3) fst_hex_bwd_kernel(const HexArgs a) {
+  __shared__ int s_ci[kHexThreads][kFMaxL * 4];
+  __shared__ float s_cf[kHexThreads][kFMaxL * 4];
+  __shared__ float s_dc[kHexThreads][4];
+  const FstGeom& g = a.g;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int P = g.P, nf = g.levels * kFC;
+  const int p0 = blockIdx.x * kHexThreads;
+  const int p = p0 + tid;
+  const bool valid = p < P;
+  float mu[3] = {0.f, 0.f, 0.f};
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) mu[k] = a.means[(size_t)p * 3 + k];
+  }
+  grid_axes(g, mu, a.t, s_ci[tid], s_cf[tid]);
+  s_dc[tid][0] = s_dc[tid][1] = s_dc[tid][2] = 0.0f;
+  __syncwarp();
+  const int nw = P - (p0 + warp * 32) < 32 ? P - (p0 + warp * 32) : 32;  // Gaussians of this warp
+  for (int lv = 0; lv < g.levels; ++lv) {
+    int j = 0;
+    for (; j + 1 < nw; j += 2) {
+      const int r = warp * 32 + j;
+      const int* ci[2] = {s_ci[r], s_ci[r + 1]};
+      const float* cf[2] = {s_cf[r], s_cf[r + 1]};
+      const float dfc[2] = {__ldg(a.df + (size_t)(p0 + r) * nf + lv * kFC + lane),
+                            __ldg(a.df + (size_t)(p0 + r + 1) * nf + lv * kFC + lane)};
+      float* dc[2] = {s_dc[r], s_dc[r + 1]};
+      plane_backward<2>(g, a.planes, a.d_planes, lv, ci, cf, dfc, lane, dc);
+    }
+    if (j < nw) {
+      const int r = warp * 32 + j;
+      const int* ci[1] = {s_ci[r]};
+      const float* cf[1] = {s_cf[r]};
+      const float dfc[1] = {__ldg(a.df + (size_t)(p0 + r) * nf + lv * kFC + lane)};
+      float* dc[1] = {s_dc[r]};
+      plane_backward<1>(g, a.planes, a.d_planes, lv, ci, cf, dfc, lane, dc);
+    }
+  }
+  __syncwarp();
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      a.d_means[(size_t)p * 3 + k] = a.d_means_t[(size_t)p * 3 + k] + s_dc[tid][k] * g.scale[k];
   }
 }
 
@@ -1164,6 +1198,7 @@ extern "C" fe_status fe_fst_backward(const fe_fst* fst, int P, const float* mean
   a.d_means = d_means;
   a.d_planes = d_planes;
   a.dv = reinterpret_cast<float*>(ws + w.dv);
+  a.df = reinterpret_cast<float*>(ws + w.df);
   a.part = reinterpret_cast<float*>(ws + w.part);
   // Row-major weight tiles (at most 2048 floats) in the order the kernel
   // uses them for every chunk.
@@ -1195,6 +1230,18 @@ extern "C" fe_status fe_fst_backward(const fe_fst* fst, int P, const float* mean
     case 128: e = launch_fst_bwd<128>(a, nblk, st); break;
   }
   if (e != cudaSuccess) return FE_ERR_CUDA;
+  {
+    HexArgs h{};
+    h.g = g;
+    h.planes = fst->planes;
+    h.means = means;
+    h.df = a.df;
+    h.d_means_t = d_means_t;
+    h.t = t;
+    h.d_means = d_means;
+    h.d_planes = d_planes;
+    fst_hex_bwd_kernel<<<(P + kHexThreads - 1) / kHexThreads, kHexThreads, 0, st>>>(h);
+  }
   fst_reduce_kernel<<<(int)((g.mlp_packed + 255) / 256), 256, 0, st>>>(g, a.part, nblk, d_mlp);
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
