@@ -896,7 +896,7 @@ struct HexArgs {
   float *d_means, *d_planes;
 };
 
-__global__ void __launch_bounds__(kHexThreads, 3) fst_hex_bwd_kernel(const HexArgs a) {
+__global__ void __launch_bounds__(kHexThreads, 2) fst_hex_bwd_kernel(const HexArgs a) {
   __shared__ int s_ci[kHexThreads][kFMaxL * 4];
   __shared__ float s_cf[kHexThreads][kFMaxL * 4];
   __shared__ float s_dc[kHexThreads][4];
