@@ -129,13 +129,14 @@ int bwd_blocks(int P) {
 }
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 struct WsLayout {
-  size_t wt, wn, act, dv, df, part, total;
+  size_t wt, wn, f, act, dv, df, part, total;
 };
 WsLayout ws_layout(const FstGeom& g, int with_backward) {
   WsLayout w{};
   w.wt = kWsHeader;
   w.wn = w.wt + al256((size_t)g.mlp_aligned * 4);
-  w.act = w.wn + al256((size_t)g.mlp_aligned * 4);
+  w.f = w.wn + al256((size_t)g.mlp_aligned * 4);
+  w.act = w.f + al256((size_t)g.levels * kFC * g.P * 4);
   w.dv = w.act + (with_backward ? al256((size_t)g.nslots * g.P * 4) : 0);
   w.df = w.dv + (with_backward ? al256((size_t)kFW * g.P * 4) : 0);
   w.part = w.df + (with_backward ? al256((size_t)g.levels * kFC * g.P * 4) : 0);
@@ -290,6 +291,10 @@ constexpr int kWBufR = 2048;  // floats per staging buffer (reverse)
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
@@ -335,6 +340,7 @@ struct FwdArgs {
   float *means_t, *quats_t, *log_scales_t, *logits_t;
   void* feat_t;
   float* act;  // NULL: forward only
+  const float* f;  // [P][levels * 32] HexPlane features from fst_sample_kernel
 };
 
 __device__ __forceinline__ float load_feat(const void* f, int bf16, size_t i) {
@@ -373,6 +379,57 @@ __device__ __forceinline__ float level_feature(const FstGeom& g, const float* __
   return f;
 }
 
+// HexPlane features f of every Gaussian (lane-cooperative, four Gaussians
+// per iteration), written Gaussian-major [P][levels * 32] for the MLP
+// kernel.  A light kernel with many warps per SM, so many corner fetches
+// are in flight.
+constexpr int kSampThreads = 256;
+struct SampArgs {
+  FstGeom g;
+  const float *planes, *means;
+  float t;
+  float* f;
+};
+
+__global__ void __launch_bounds__(kSampThreads, 2) fst_sample_kernel(const SampArgs a) {
+  __shared__ int s_ci[kSampThreads][kFMaxL * 4];
+  __shared__ float s_cf[kSampThreads][kFMaxL * 4];
+  const FstGeom& g = a.g;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int P = g.P, nf = g.levels * kFC;
+  const int p0 = blockIdx.x * kSampThreads;
+  const int p = p0 + tid;
+  float mu[3] = {0.0f, 0.0f, 0.0f};
+  if (p < P) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) mu[k] = a.means[(size_t)p * 3 + k];
+  }
+  grid_axes(g, mu, a.t, s_ci[tid], s_cf[tid]);
+  __syncwarp();
+  const int nw = P - (p0 + warp * 32) < 32 ? P - (p0 + warp * 32) : 32;  // Gaussians of this warp (may be <= 0)
+  for (int j = 0; j < nw; j += 4) {
+    // Four Gaussians at a time (a missing one repeats a valid row and is
+    // not stored).
+    const int r = warp * 32 + j;
+    const int* ci[4];
+    const float* cf[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int rq = j + q < nw ? r + q : r;
+      ci[q] = s_ci[rq];
+      cf[q] = s_cf[rq];
+    }
+    for (int lv = 0; lv < g.levels; ++lv) {
+      float f[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) f[q] = level_feature(g, a.planes, lv, ci[q], cf[q], lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (j + q < nw) a.f[(size_t)(p0 + r + q) * nf + lv * kFC + lane] = f[q];
+    }
+  }
+}
+
 constexpr size_t kFwdSmem = ((size_t)2 * kFThreads * kFRow + 2 * kWBuf) * 4;
 
 template <int D>
@@ -384,50 +441,29 @@ __global__ void __launch_bounds__(kFThreads, 2) fst_fwd_kernel(const FwdArgs a) 
   int wt_i = 0;
   stage_tile(a.tiles, a.ntiles, 0, a.wt, wbuf);
   const FstGeom& g = a.g;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int mt = tid & 15, nt = tid >> 4;
   const int p0 = blockIdx.x * kFThreads;
   const int p = p0 + tid;
   const bool valid = p < g.P;
   const int P = g.P;
   float* act = a.act;
-  // Grid axes of every Gaussian, parked in B (ints in columns [0, 16),
-  // fractions in [16, 32)) while the planes are sampled into A.
-  int* ci_row = reinterpret_cast<int*>(B + tid * kFRow);
-  float* cf_row = B + tid * kFRow + kFMaxL * 4;
   float mu[3] = {0.0f, 0.0f, 0.0f};
   if (valid) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) mu[k] = a.means[(size_t)p * 3 + k];
   }
-  grid_axes(g, mu, a.t, ci_row, cf_row);
-  __syncwarp();
-  // F_out layer 0 over f, two levels (64 columns of f) at a time.
+  // F_out layer 0 over f (written Gaussian-major by the sampling kernel),
+  // two levels (64 columns) at a time, copied into A asynchronously.
+  const int nf = g.levels * kFC;
   float2 acc[8][4];
   tile_zero<8>(acc);
   for (int l0 = 0; l0 < g.levels; l0 += 2) {
     const int nl = g.levels - l0 < 2 ? g.levels - l0 : 2;
-    const int nw = P - (p0 + warp * 32) < 32 ? P - (p0 + warp * 32) : 32;  // Gaussians of this warp (may be <= 0)
-    for (int j = 0; j < nw; j += 4) {
-      // Four Gaussians at a time (the last group repeats a valid row in
-      // place of missing ones and does not store them).
-      const int r = warp * 32 + j;
-      const int* ci[4];
-      const float* cf[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int rq = j + q < nw ? r + q : r;
-        ci[q] = reinterpret_cast<const int*>(B + rq * kFRow);
-        cf[q] = B + rq * kFRow + kFMaxL * 4;
-      }
-      for (int lv = l0; lv < l0 + nl; ++lv) {
-        float f[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) f[q] = level_feature(g, a.planes, lv, ci[q], cf[q], lane);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (j + q < nw) A[(r + q) * kFRow + (lv - l0) * kFC + lane] = f[q];
-      }
+    {
+      const float* src = a.f + (size_t)(valid ? p : 0) * nf + l0 * kFC;
+      for (int q = 0; q < nl * kFC; q += 4) cp_async16_zfill(A + tid * kFRow + q, src + q, valid);
+      cp_async_wait_all();
     }
     __syncthreads();
     if (act && valid) {
@@ -740,7 +776,7 @@ __global__ void __launch_bounds__(kFThreads, 2) fst_bwd_kernel(const BwdArgs a) 
   float* ST = s_dyn + 2 * kFThreads * kFRow;    // [128][kTRow]: relu(h_g) | head deltas; grid axes
   float* wbuf = ST + kFThreads * kTRow;         // [2][kWBufR] staged weight tiles
   const FstGeom& g = a.g;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int mt = tid & 15, nt = tid >> 4;
   const int P = g.P;
   const int nchunk = (P + kFThreads - 1) / kFThreads;
@@ -1116,7 +1152,7 @@ extern "C" fe_status fe_fst_forward(const fe_fst* fst, int P, const float* means
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   float* wt = reinterpret_cast<float*>(ws + w.wt);
   float* wn = reinterpret_cast<float*>(ws + w.wn);
-  if (cudaMemsetAsync(wt, 0, w.act - w.wt, st) != cudaSuccess) return FE_ERR_CUDA;
+  if (cudaMemsetAsync(wt, 0, w.f - w.wt, st) != cudaSuccess) return FE_ERR_CUDA;
   fst_pack_kernel<<<(int)((g.mlp_packed + 255) / 256), 256, 0, st>>>(g, fst->mlp, wt, wn);
   FwdArgs a{};
   a.g = g;
@@ -1135,6 +1171,16 @@ extern "C" fe_status fe_fst_forward(const fe_fst* fst, int P, const float* means
   a.logits_t = opacity_logits_t;
   a.feat_t = feat_t;
   a.act = with_backward ? reinterpret_cast<float*>(ws + w.act) : nullptr;
+  a.f = reinterpret_cast<const float*>(ws + w.f);
+  {
+    SampArgs sa{};
+    sa.g = g;
+    sa.planes = fst->planes;
+    sa.means = means;
+    sa.t = t;
+    sa.f = reinterpret_cast<float*>(ws + w.f);
+    fst_sample_kernel<<<(P + kSampThreads - 1) / kSampThreads, kSampThreads, 0, st>>>(sa);
+  }
   // Weight tiles of the transposed copy in the order the kernel uses them.
   {
     int n = 0;
