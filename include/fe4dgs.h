@@ -345,9 +345,11 @@ int64_t fe_fst_plane_floats(int levels, int rs, int rt);
 int64_t fe_fst_mlp_floats(int levels, int D);
 
 /* Device workspace of fe_fst_forward / fe_fst_backward for P Gaussians.
- * with_backward = 0: forward only (inference); 1: the forward also keeps
- * the per-Gaussian activations the reverse pass reads (about 3.9 KB per
- * Gaussian at 4 levels). */
+ * with_backward = 0: forward only (inference; the HexPlane features, 0.5 KB
+ * per Gaussian at 4 levels); 1: the forward also keeps the per-Gaussian
+ * activations the reverse pass reads, and the reverse's own per-Gaussian
+ * buffers (about 5.1 KB per Gaussian at 4 levels in all), plus per-block
+ * partial sums of the weight gradients. */
 fe_status fe_fst_workspace_size(int P, int levels, int D, int with_backward, size_t *bytes);
 
 /* Deformation of P Gaussians at time t.  Inputs (device, canonical, the

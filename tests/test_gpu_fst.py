@@ -94,6 +94,7 @@ def test_backward_matches_oracle(P, levels, rs, rt, D):
     out, _ = _oracle_forward(sc, pl, ly, t, levels, rs, rt, False)
     rel, cell = OF.margins(out["state"])
     drop = (rel < RELU_MARGIN) | (cell < CELL_MARGIN)
+    assert drop.sum() < 0.1 * P   # the comparison is not emptied by the protocol
     up = _upstream(P, D, seed=P)
     for k in up:
         up[k][drop] = 0.0
