@@ -30,7 +30,9 @@ namespace {
 
 constexpr int kFW = 64, kFHalf = 32, kFDepth = 8, kFC = 32, kFMaxL = 4;
 constexpr int kFLayers = kFDepth + 12 + 2;
-constexpr int kFThreads = 128;
+constexpr int kFThreads = 128;     // threads of the reverse product kernel
+constexpr int kFM = 128;           // Gaussians per block of the product kernels
+constexpr int kFwdThreads = 256;   // threads of the forward product kernel
 constexpr int kFRow = 68;  // shared-memory row stride (floats) of the block products
 constexpr int kLZ1 = kFDepth + 12, kLZ2 = kFDepth + 13;
 
@@ -200,24 +202,25 @@ __device__ __forceinline__ void grid_axes(const FstGeom& g, const float* mu, flo
 // row slices from shared memory and TN weights per input from L1, then
 // issues 16 TN packed FMAs.
 // ---------------------------------------------------------------------------
-template <int TN>
-__device__ __forceinline__ void tile_zero(float2 (&acc)[8][TN / 2]) {
+template <int TN, int TM = 8>
+__device__ __forceinline__ void tile_zero(float2 (&acc)[TM][TN / 2]) {
 #pragma unroll
-  for (int r = 0; r < 8; ++r)
+  for (int r = 0; r < TM; ++r)
 #pragma unroll
     for (int c = 0; c < TN / 2; ++c) acc[r][c] = make_float2(0.0f, 0.0f);
 }
 
 // acc[r][c] += sum_k X[(mt + 16 r) * kFRow + k] * B[k * ldb + n0 + (2c, 2c+1)],
 // k < K (multiple of 8); B rows 8-byte aligned at n0.
-template <int TN, bool kSharedB = false>
+template <int TN, bool kSharedB = false, int TM = 8>
 __device__ __forceinline__ void tile_mma(const float* X, int K, const float* __restrict__ B, int ldb, int mt, int n0,
-                                         float2 (&acc)[8][TN / 2]) {
+                                         float2 (&acc)[TM][TN / 2]) {
+  constexpr int RG = kFM / TM;  // row groups: thread rows are mt + RG r
 #pragma unroll 2
   for (int k = 0; k < K; k += 4) {
-    float4 xv[8];
+    float4 xv[TM];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) xv[r] = *reinterpret_cast<const float4*>(X + (mt + 16 * r) * kFRow + k);
+    for (int r = 0; r < TM; ++r) xv[r] = *reinterpret_cast<const float4*>(X + (mt + RG * r) * kFRow + k);
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
       float2 b[TN / 2];
@@ -225,7 +228,7 @@ __device__ __forceinline__ void tile_mma(const float* X, int K, const float* __r
 #pragma unroll
       for (int c = 0; c < TN / 2; ++c) b[c] = kSharedB ? brow[c] : __ldg(brow + c);
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
+      for (int r = 0; r < TM; ++r) {
         const float xk = kk == 0 ? xv[r].x : (kk == 1 ? xv[r].y : (kk == 2 ? xv[r].z : xv[r].w));
         const float2 x2 = make_float2(xk, xk);
 #pragma unroll
@@ -238,15 +241,16 @@ __device__ __forceinline__ void tile_mma(const float* X, int K, const float* __r
 // Layer epilogue: z = acc + bias; relu(z) -> Y (shared, column offset yc)
 // and optionally -> act slots (valid rows only).  The reverse pass needs
 // only relu(z): it is the next layer's input, and z > 0 iff relu(z) > 0.
-template <int TN>
-__device__ __forceinline__ void tile_out(const float2 (&acc)[8][TN / 2], const float* __restrict__ bias, int mt,
+template <int TN, int TM = 8>
+__device__ __forceinline__ void tile_out(const float2 (&acc)[TM][TN / 2], const float* __restrict__ bias, int mt,
                                          int n0, float* act, int P, int slot, int p0, float* Y, int yc) {
+  constexpr int RG = kFM / TM;
   float2 bb[TN / 2];
 #pragma unroll
   for (int c = 0; c < TN / 2; ++c) bb[c] = __ldg(reinterpret_cast<const float2*>(bias + n0) + c);
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int m = mt + 16 * r;
+  for (int r = 0; r < TM; ++r) {
+    const int m = mt + RG * r;
 #pragma unroll
     for (int c = 0; c < TN / 2; ++c) {
       const float z0 = fmaxf(acc[r][c].x + bb[c].x, 0.0f), z1 = fmaxf(acc[r][c].y + bb[c].y, 0.0f);
@@ -308,7 +312,7 @@ __device__ __forceinline__ void stage_tile(const WTile* tiles, int ntiles, int t
     const WTile w = tiles[t];
     float* dst = wbuf + (t & 1) * kBuf;
     const int c4 = w.cols / 4, n = w.rows * c4;
-    for (int i = threadIdx.x; i < n; i += kFThreads) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int r = i / c4, c = i - r * c4;
       cp_async16(dst + r * w.cols + 4 * c, base + w.off + (size_t)r * w.ld + 4 * c);
     }
@@ -430,22 +434,27 @@ __global__ void __launch_bounds__(kSampThreads, 2) fst_sample_kernel(const SampA
   }
 }
 
-constexpr size_t kFwdSmem = ((size_t)2 * kFThreads * kFRow + 2 * kWBuf) * 4;
+constexpr size_t kFwdSmem = ((size_t)2 * kFM * kFRow + 2 * kWBuf) * 4;
 
 template <int D>
-__global__ void __launch_bounds__(kFThreads, 2) fst_fwd_kernel(const FwdArgs a) {
+__global__ void __launch_bounds__(kFwdThreads, 2) fst_fwd_kernel(const FwdArgs a) {
+  // 256 threads over 128 Gaussians: thread (mt, nt) = (tid % 32, tid / 32)
+  // owns rows mt + 32 r (r < 4) of every product; threads below 128 also own
+  // Gaussian p0 + tid for the per-Gaussian parts (f rows, heads, outputs).
+  constexpr int TM = 4;
   extern __shared__ __align__(16) float s_buf[];
   float* A = s_buf;                        // [128][kFRow]
-  float* B = s_buf + kFThreads * kFRow;    // [128][kFRow]
-  float* wbuf = s_buf + 2 * kFThreads * kFRow;  // [2][kWBuf] staged weight tiles
+  float* B = s_buf + kFM * kFRow;          // [128][kFRow]
+  float* wbuf = s_buf + 2 * kFM * kFRow;   // [2][kWBuf] staged weight tiles
   int wt_i = 0;
   stage_tile(a.tiles, a.ntiles, 0, a.wt, wbuf);
   const FstGeom& g = a.g;
   const int tid = threadIdx.x;
-  const int mt = tid & 15, nt = tid >> 4;
-  const int p0 = blockIdx.x * kFThreads;
+  const int mt = tid & 31, nt = tid >> 5;
+  const bool owner = tid < kFM;
+  const int p0 = blockIdx.x * kFM;
   const int p = p0 + tid;
-  const bool valid = p < g.P;
+  const bool valid = owner && p < g.P;
   const int P = g.P;
   float* act = a.act;
   float mu[3] = {0.0f, 0.0f, 0.0f};
@@ -456,11 +465,11 @@ __global__ void __launch_bounds__(kFThreads, 2) fst_fwd_kernel(const FwdArgs a) 
   // F_out layer 0 over f (written Gaussian-major by the sampling kernel),
   // two levels (64 columns) at a time, copied into A asynchronously.
   const int nf = g.levels * kFC;
-  float2 acc[8][4];
-  tile_zero<8>(acc);
+  float2 acc[TM][4];
+  tile_zero<8, TM>(acc);
   for (int l0 = 0; l0 < g.levels; l0 += 2) {
     const int nl = g.levels - l0 < 2 ? g.levels - l0 : 2;
-    {
+    if (owner) {
       const float* src = a.f + (size_t)(valid ? p : 0) * nf + l0 * kFC;
       for (int q = 0; q < nl * kFC; q += 4) cp_async16_zfill(A + tid * kFRow + q, src + q, valid);
       cp_async_wait_all();
@@ -471,75 +480,77 @@ __global__ void __launch_bounds__(kFThreads, 2) fst_fwd_kernel(const FwdArgs a) 
     }
     {
       const float* w = next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf);
-      tile_mma<8, true>(A, nl * kFC, w, kFW, mt, nt * 8, acc);
+      tile_mma<8, true, TM>(A, nl * kFC, w, kFW, mt, nt * 8, acc);
     }
     __syncthreads();
   }
-  tile_out<8>(acc, a.wt + g.ab[0], mt, nt * 8, act, P, g.sz, p0, B, 0);
+  tile_out<8, TM>(acc, a.wt + g.ab[0], mt, nt * 8, act, P, g.sz, p0, B, 0);
   __syncthreads();
   // z_j = W_j relu(z_{j-1}) + b_j; layer j reads (j odd ? B : A).
   for (int j = 1; j < kFDepth; ++j) {
     float* src = (j & 1) ? B : A;
     float* dst = (j & 1) ? A : B;
-    tile_zero<8>(acc);
-    tile_mma<8, true>(src, kFW, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFW, mt, nt * 8, acc);
-    tile_out<8>(acc, a.wt + g.ab[j], mt, nt * 8, act, P, g.sz + j * kFW, p0, dst, 0);
+    tile_zero<8, TM>(acc);
+    tile_mma<8, true, TM>(src, kFW, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFW, mt, nt * 8, acc);
+    tile_out<8, TM>(acc, a.wt + g.ab[j], mt, nt * 8, act, P, g.sz + j * kFW, p0, dst, 0);
     __syncthreads();
   }
   // relu(h) is in A.  Branches: e1 -> B[0, 32), h_g -> B[32, 64); the
   // semantic updater's first layer accumulates over the branches.
-  float2 v[8][4];
-  tile_zero<8>(v);
+  float2 v[TM][4];
+  tile_zero<8, TM>(v);
   float out[11];
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     const int l1 = branch_e1(b);
     {
-      float2 e[8][2];
-      tile_zero<4>(e);
-      tile_mma<4, true>(A, kFW, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFHalf, mt, nt * 4, e);
-      tile_out<4>(e, a.wt + g.ab[l1], mt, nt * 4, act, P, g.se1 + b * kFHalf, p0, B, 0);
+      float2 e[TM][2];
+      tile_zero<4, TM>(e);
+      tile_mma<4, true, TM>(A, kFW, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFHalf, mt, nt * 4, e);
+      tile_out<4, TM>(e, a.wt + g.ab[l1], mt, nt * 4, act, P, g.se1 + b * kFHalf, p0, B, 0);
     }
     __syncthreads();
     {
-      float2 e[8][2];
-      tile_zero<4>(e);
-      tile_mma<4, true>(B, kFHalf, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFHalf, mt, nt * 4, e);
-      tile_out<4>(e, a.wt + g.ab[l1 + 1], mt, nt * 4, act, P, g.shg + b * kFHalf, p0, B, kFHalf);
+      float2 e[TM][2];
+      tile_zero<4, TM>(e);
+      tile_mma<4, true, TM>(B, kFHalf, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFHalf, mt, nt * 4, e);
+      tile_out<4, TM>(e, a.wt + g.ab[l1 + 1], mt, nt * 4, act, P, g.shg + b * kFHalf, p0, B, kFHalf);
     }
     __syncthreads();
-    // Head (this thread's own Gaussian): offset = H relu(h_g) + b.
+    // Head (the owner thread's own Gaussian): offset = H relu(h_g) + b.
     constexpr int dgs[4] = {3, 4, 3, 1}, oos[4] = {0, 3, 7, 10};
-    const float* hgr = B + tid * kFRow + kFHalf;
-    const float* wt_h = a.wt + g.aw[l1 + 2];  // [32][dg]
-    const float* bh = a.wt + g.ab[l1 + 2];
+    if (owner) {
+      const float* hgr = B + tid * kFRow + kFHalf;
+      const float* wt_h = a.wt + g.aw[l1 + 2];  // [32][dg]
+      const float* bh = a.wt + g.ab[l1 + 2];
 #pragma unroll
-    for (int o = 0; o < 4; ++o) {
-      if (o < dgs[b]) {
-        float s = __ldg(bh + o);
+      for (int o = 0; o < 4; ++o) {
+        if (o < dgs[b]) {
+          float s = __ldg(bh + o);
 #pragma unroll 8
-        for (int i = 0; i < kFHalf; ++i) s = fmaf(__ldg(wt_h + i * dgs[b] + o), hgr[i], s);
-        out[oos[b] + o] = s;
+          for (int i = 0; i < kFHalf; ++i) s = fmaf(__ldg(wt_h + i * dgs[b] + o), hgr[i], s);
+          out[oos[b] + o] = s;
+        }
       }
     }
-    tile_mma<8, true>(B + kFHalf, kFHalf, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFW, mt, nt * 8, v);
+    tile_mma<8, true, TM>(B + kFHalf, kFHalf, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), kFW, mt, nt * 8, v);
     __syncthreads();
   }
-  tile_out<8>(v, a.wt + g.ab[kLZ1], mt, nt * 8, act, P, g.sv, p0, A, 0);
+  tile_out<8, TM>(v, a.wt + g.ab[kLZ1], mt, nt * 8, act, P, g.sv, p0, A, 0);
   __syncthreads();
   // dz = Z2 relu(v) + b, 64 columns at a time.
   constexpr int ZN = D < 64 ? D : 64, ZT = ZN / 8;
 #pragma unroll
   for (int c0 = 0; c0 < D; c0 += ZN) {
-    float2 z[8][ZT / 2];
-    tile_zero<ZT>(z);
-    tile_mma<ZT, true>(A, kFW, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), ZN, mt, nt * ZT, z);
+    float2 z[TM][ZT / 2];
+    tile_zero<ZT, TM>(z);
+    tile_mma<ZT, true, TM>(A, kFW, next_tile(a.tiles, a.ntiles, wt_i, a.wt, wbuf), ZN, mt, nt * ZT, z);
     float2 bb[ZT / 2];
 #pragma unroll
     for (int c = 0; c < ZT / 2; ++c) bb[c] = __ldg(reinterpret_cast<const float2*>(a.wt + g.ab[kLZ2] + c0 + nt * ZT) + c);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int pm = p0 + mt + 16 * r;
+    for (int r = 0; r < TM; ++r) {
+      const int pm = p0 + mt + (kFM / TM) * r;
       if (pm < P) {
 #pragma unroll
         for (int c = 0; c < ZT / 2; ++c) {
@@ -1112,11 +1123,11 @@ namespace {
 
 template <int D>
 cudaError_t launch_fst_fwd(const FwdArgs& a, cudaStream_t st) {
-  const int blocks = (a.g.P + kFThreads - 1) / kFThreads;
+  const int blocks = (a.g.P + kFM - 1) / kFM;
   const size_t smem = kFwdSmem;
   auto k = fst_fwd_kernel<D>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k<<<blocks, kFThreads, smem, st>>>(a);
+  k<<<blocks, kFwdThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
