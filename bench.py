@@ -781,23 +781,44 @@ def run_train_fst(args, world, rank, local, cfg):
     ach = kern[dom]["tflops"]
     # End to end: the step's targets copied in from pinned host memory, the
     # losses read back.
+    # Two target sets: step i+1's targets upload on a copy stream while step
+    # i computes; each step's losses are read back.
     host = {k: v.cpu().pin_memory() for k, v in tgt.items()}
-    dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
-    host_loss = torch.empty(4).pin_memory()
+    sets = [dict(d_in={k: torch.empty_like(v, device=dev) for k, v in host.items()},
+                 loss=torch.empty(4, dtype=torch.float32, device=dev), h_loss=torch.empty(4).pin_memory())
+            for _ in range(2)]
+    cs = torch.cuda.Stream(device=dev)
+    ev_h2d = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_comp = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def e2e_step():
-        for k, v in host.items():
-            dev_in[k].copy_(v, non_blocking=True)
-        losses = tr.step(t, dev_in["rgb"], dev_in["dec"], dev_in["depth"])
-        host_loss.copy_(losses, non_blocking=True)
+    def upload(si):
+        with torch.cuda.stream(cs):
+            cs.wait_event(ev_comp[si])
+            for k, v in host.items():
+                sets[si]["d_in"][k].copy_(v, non_blocking=True)
+            ev_h2d[si].record(cs)
 
-    for _ in range(2):
-        e2e_step()
+    def run(n):
+        start = torch.cuda.Event()
+        start.record(stream)
+        cs.wait_event(start)
+        upload(0)
+        for i in range(n):
+            si = i % 2
+            if i + 1 < n:
+                upload((i + 1) % 2)
+            stream.wait_event(ev_h2d[si])
+            d_in = sets[si]["d_in"]
+            losses = tr.step(t, d_in["rgb"], d_in["dec"], d_in["depth"])
+            sets[si]["loss"].copy_(losses)
+            ev_comp[si].record(stream)
+            sets[si]["h_loss"].copy_(sets[si]["loss"], non_blocking=True)
+
+    run(2)
     torch.cuda.synchronize()
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     x0.record(stream)
-    for _ in range(K):
-        e2e_step()
+    run(K)
     x1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = x0.elapsed_time(x1) / K
