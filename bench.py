@@ -493,10 +493,8 @@ def run_ours(args, world, rank, local):
                     S["d_in"][k].copy_(v, non_blocking=True)
                 ev_h2d[si].record(h2d_stream)
 
-        def compute(si):
+        def compute_body(si):
             S = sets[si]
-            stream.wait_event(ev_h2d[si])
-            stream.wait_event(ev_d2h[si])                # its gradients of two steps ago are read back
             rast.forward(S["sc"], cam, S["df"], t, out=out, feat_bf16=feat_bf)
             _lib.fe_l1_loss_grad(out[0], S["d_in"]["tgt_rgb"], HW, g_rgb, losses[0:1], scratch[:1024])
             feat_loss(S["d_in"]["tgt_feat"])
@@ -506,6 +504,31 @@ def run_ours(args, world, rank, local):
                 opt.step([S["grads"]["means"], S["grads"]["log_scales"], S["grads"]["quats"],
                           S["grads"]["opacity_logits"], S["grads"]["sh"], S["grads"]["feat"], dec_out[2], dec_out[3]])
             S["loss"].copy_(losses)
+
+        # Without an optimizer each set's compute is one CUDA graph, as in
+        # the device-time loop (Adam's step count is a host value).
+        set_graphs = [None, None]
+        if opt is None and not args.eager:
+            for si in range(2):
+                side = torch.cuda.Stream(device=dev)
+                side.wait_stream(stream)
+                gph = torch.cuda.CUDAGraph()
+                with torch.cuda.stream(side):
+                    compute_body(si)
+                    side.synchronize()
+                    with torch.cuda.graph(gph, stream=side):
+                        compute_body(si)
+                stream.wait_stream(side)
+                set_graphs[si] = gph
+            torch.cuda.synchronize()
+
+        def compute(si):
+            stream.wait_event(ev_h2d[si])
+            stream.wait_event(ev_d2h[si])                # its gradients of two steps ago are read back
+            if set_graphs[si] is not None:
+                set_graphs[si].replay()
+            else:
+                compute_body(si)
             ev_comp[si].record(stream)
 
         def download(si):
