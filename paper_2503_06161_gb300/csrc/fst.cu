@@ -4,22 +4,30 @@
 // extractors and heads, and the semantic updater F_feat giving dz; forward
 // and reverse, including the gradients of the planes and of every weight.
 //
-// A block holds 128 Gaussians and every layer is a block product: the
-// activations sit in shared memory (row per Gaussian), each thread owns an
-// 8-Gaussian x TN-output register tile of packed FP32 FMAs and streams
-// weights from 16-byte-aligned copies in the workspace (transposed for the
-// forward, row-major for the reverse).  The HexPlane is sampled
-// lane-cooperatively (the warp takes its 32 Gaussians one at a time, lane =
-// channel, so each corner fetch is one coalesced 128-byte line of the
-// channels-last planes).
-//
-// Reverse (persistent blocks): per layer, the input gradient delta W is the
-// same tile product, the ReLU masks come from the stored activations, and
-// the weight gradient sum_g delta_g x_g^T over the block's Gaussians is a
-// second block product added into the block's own partial (reduced over
-// blocks in a fixed order afterwards: reproducible).  Plane gradients are
-// scattered with coalesced float atomics (the only order-dependent sum of
-// this file).
+// Kernels, in launch order:
+//   fst_pack_kernel     16-byte-aligned transposed and row-major copies of
+//                       the weights in the workspace;
+//   fst_sample_kernel   HexPlane features f, lane-cooperative (the warp takes
+//                       its Gaussians four at a time, lane = channel, so each
+//                       corner fetch is one coalesced 128-byte line of the
+//                       channels-last planes), written Gaussian-major;
+//   fst_fwd_kernel      the MLP: a block holds 128 Gaussians and every layer
+//                       is a block product -- activations in shared memory
+//                       (a row per Gaussian), each thread a register tile of
+//                       packed FP32 FMAs, weight tiles staged by cp.async --
+//                       writing the deformed Gaussians and relu(z) of every
+//                       hidden layer for the reverse;
+//   fst_bwd_kernel      (persistent blocks) per layer the input gradient
+//                       delta W as the same tile product, the ReLU masks from
+//                       the stored relu(z), and the weight gradient
+//                       sum_g delta_g x_g^T as a second block product added
+//                       into the block's own partial; writes d f;
+//   fst_hex_bwd_kernel  the HexPlane reverse: plane gradients by coalesced
+//                       float atomics (the only order-dependent sum of this
+//                       file), the canonical mean's gradient;
+//   fst_reduce_kernel   the weight gradients: the blocks' partials summed in
+//                       block order (reproducible bit for bit);
+//   fst_tv_kernel       the TV term and its plane gradient.
 #include <cstdint>
 
 #include "common.cuh"
@@ -122,8 +130,9 @@ __host__ __device__ int64_t plane_floats(const FstGeom& g) {
 }
 
 // Workspace: header | transposed weights (aligned) | row-major weights
-// (aligned) | activations [nslots][P] | per-block partials of the weight
-// gradients [nblk][mlp_aligned].
+// (aligned) | f [P][levels*32] | with the reverse: relu activations
+// [nslots][P], F_feat delta [64][P], d f [P][levels*32], per-block partials
+// of the weight gradients [nblk][mlp_aligned].
 constexpr size_t kWsHeader = 256;
 int bwd_blocks(int P) {
   const int chunks = (P + kFThreads - 1) / kFThreads;
@@ -196,11 +205,12 @@ __device__ __forceinline__ void grid_axes(const FstGeom& g, const float* mu, flo
 
 // ---------------------------------------------------------------------------
 // Block products.  A block holds 128 Gaussians; activations live in shared
-// memory row-major per Gaussian ([128][kFRow] floats).  Thread (mt, nt) =
-// (tid % 16, tid / 16) owns rows mt + 16 r (r < 8) and TN consecutive output
-// columns from n0 = nt * TN: per step of four inputs it reads eight 16-byte
-// row slices from shared memory and TN weights per input from L1, then
-// issues 16 TN packed FMAs.
+// memory row-major per Gaussian ([128][kFRow] floats).  Thread (mt, nt)
+// owns rows mt + (128 / TM) r (r < TM) and TN consecutive output columns
+// from n0 = nt * TN (TM = 8 with 128 threads: mt = tid % 16, nt = tid / 16;
+// TM = 4 with 256 threads: mt = tid % 32, nt = tid / 32): per step of four
+// inputs it reads TM 16-byte row slices from shared memory and TN weights
+// per input, then issues 2 TM TN packed FMAs.
 // ---------------------------------------------------------------------------
 template <int TN, int TM = 8>
 __device__ __forceinline__ void tile_zero(float2 (&acc)[TM][TN / 2]) {
@@ -210,8 +220,8 @@ __device__ __forceinline__ void tile_zero(float2 (&acc)[TM][TN / 2]) {
     for (int c = 0; c < TN / 2; ++c) acc[r][c] = make_float2(0.0f, 0.0f);
 }
 
-// acc[r][c] += sum_k X[(mt + 16 r) * kFRow + k] * B[k * ldb + n0 + (2c, 2c+1)],
-// k < K (multiple of 8); B rows 8-byte aligned at n0.
+// acc[r][c] += sum_k X[(mt + RG r) * kFRow + k] * B[k * ldb + n0 + (2c, 2c+1)],
+// RG = 128 / TM, k < K (multiple of 8); B rows 8-byte aligned at n0.
 template <int TN, bool kSharedB = false, int TM = 8>
 __device__ __forceinline__ void tile_mma(const float* X, int K, const float* __restrict__ B, int ldb, int mt, int n0,
                                          float2 (&acc)[TM][TN / 2]) {
