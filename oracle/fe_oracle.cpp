@@ -768,10 +768,12 @@ int or_render(const or_scene* sc, const or_deform* df, const or_camera* cam, dou
 // with respect to every canonical parameter (overwritten, all P rows).
 // Upstream arrays are per listed pixel: g_rgb [npix,3], g_depth/g_alpha
 // [npix], g_feat [npix,D].
+// d_uv (optional, [P][2]): the gradient of the loss with respect to each
+// Gaussian's projected centre (u, v) in pixels.
 int or_backward(const or_scene* sc, const or_deform* df, const or_camera* cam, double t, const double* bg,
                 int npix, const int* pix, const double* g_rgb, const double* g_depth, const double* g_alpha,
                 const double* g_feat, double* d_means, double* d_log_scales, double* d_quats, double* d_logits,
-                double* d_sh, double* d_feat) {
+                double* d_sh, double* d_feat, double* d_uv) {
   if (!sc || !cam || sc->D > kMaxD || (df && df->enabled && df->C > kMaxC)) return 1;
   const int P = sc->P, D = sc->D;
   const int NS = 10;  // du dv dA dB dC dop drgb[3] ddepth
@@ -838,6 +840,11 @@ int or_backward(const or_scene* sc, const or_deform* df, const or_camera* cam, d
 #pragma omp parallel for schedule(dynamic, 256)
   for (int g = 0; g < P; ++g)
     gaussian_backward(*sc, df, *cam, gs[g], &sg[(size_t)g * NS], g, d_means, d_log_scales, d_quats, d_logits, d_sh);
+  if (d_uv)
+    for (int g = 0; g < P; ++g) {
+      d_uv[2 * g] = sg[(size_t)g * NS];
+      d_uv[2 * g + 1] = sg[(size_t)g * NS + 1];
+    }
   return 0;
 }
 

@@ -105,7 +105,7 @@ def _setup(L):
                             ctypes.POINTER(ctypes.c_uint64)]
     L.or_backward.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Deform), ctypes.POINTER(_Camera),
                               ctypes.c_double, _dp, ctypes.c_int, _ip, _dp, _dp, _dp, _dp,
-                              _dp, _dp, _dp, _dp, _dp, _dp]
+                              _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.or_tile_bin.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_float), _ip, ctypes.POINTER(ctypes.c_float),
                               ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
@@ -229,9 +229,11 @@ def render(scene, camera, deform=None, t: float = 0.0, bg=(0.0, 0.0, 0.0), pixel
 
 
 def backward(scene, camera, deform=None, t: float = 0.0, bg=(0.0, 0.0, 0.0), pixels=None,
-             g_rgb=None, g_depth=None, g_alpha=None, g_feat=None) -> dict:
+             g_rgb=None, g_depth=None, g_alpha=None, g_feat=None, want_uv: bool = False) -> dict:
     """FP64 gradients of sum(g . outputs) over the listed pixels w.r.t.
-    means, log_scales, quats, opacity_logits, sh [P,16,3], feat [P,D]."""
+    means, log_scales, quats, opacity_logits, sh [P,16,3], feat [P,D]; with
+    want_uv also "uv" [P,2], the gradient w.r.t. each projected centre
+    (pixels)."""
     L = lib()
     keep = _Keep()
     sc, cam, df = _marshal(scene, camera, deform, keep)
@@ -245,10 +247,12 @@ def backward(scene, camera, deform=None, t: float = 0.0, bg=(0.0, 0.0, 0.0), pix
     out = dict(means=np.zeros((P, 3)), log_scales=np.zeros((P, 3)), quats=np.zeros((P, 4)),
                opacity_logits=np.zeros(P), sh=np.zeros((P, 16, 3)), feat=np.zeros((P, D)))
     bgv = keep.d(np.asarray(bg))
+    if want_uv:
+        out["uv"] = np.zeros((P, 2))
     rc = L.or_backward(ctypes.byref(sc), ctypes.byref(df), ctypes.byref(cam), float(t), _ptr(bgv), n,
                        _ptr(pix, _ip), _ptr(gr), _ptr(gz), _ptr(ga), _ptr(gf), _ptr(out["means"]),
                        _ptr(out["log_scales"]), _ptr(out["quats"]), _ptr(out["opacity_logits"]),
-                       _ptr(out["sh"]), _ptr(out["feat"]))
+                       _ptr(out["sh"]), _ptr(out["feat"]), _ptr(out["uv"]) if want_uv else None)
     if rc:
         raise RuntimeError(f"or_backward failed: {rc}")
     return out
