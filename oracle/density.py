@@ -68,8 +68,29 @@ def quat_to_rot(q):
     return R
 
 
-def decide(means, log_scales, quats, logits, accum, count, grad_thresh, dense_scale, min_opacity):
-    """Per-Gaussian decision: 0 keep, 1 clone, 2 split, -1 prune."""
+def decide(means, log_scales, quats, logits, accum, count, grad_thresh, dense_scale, min_opacity,
+           precision: str = "f64"):
+    """Per-Gaussian decision: 0 keep, 1 clone, 2 split, -1 prune.
+
+    precision "f64" is the definition as stated.  "f32" takes the same
+    decision in single precision, for comparison with a single-precision
+    implementation: since sigmoid and exp are strictly increasing,
+    sigmoid(x) < m is x < log(m / (1 - m)) and max exp(ls) > s is
+    max ls > log(s); the two thresholds are formed in double and rounded to
+    float32 once, and the mean statistic is one float32 division, so the
+    decision involves no transcendental function of a per-Gaussian value."""
+    if precision == "f32":
+        f = np.float32
+        cnt = np.asarray(count, np.int64)
+        acc = np.asarray(accum, f)
+        avg = np.where(cnt > 0, acc / np.maximum(cnt, 1).astype(f), f(0.0))
+        m, ds = float(min_opacity), float(dense_scale)
+        lmin = f(-np.inf) if m <= 0 else f(np.inf) if m >= 1 else f(np.log(m / (1.0 - m)))
+        ldense = f(-np.inf) if ds <= 0 else f(np.log(ds))
+        high = avg >= f(grad_thresh)
+        big = np.max(np.asarray(log_scales, f), axis=1) > ldense
+        d = np.where(high, np.where(big, 2, 1), 0)
+        return np.where(np.asarray(logits, f) < lmin, -1, d)
     count = np.asarray(count)
     avg = np.where(count > 0, np.asarray(accum, np.float64) / np.maximum(count, 1), 0.0)
     big = np.max(np.exp(np.asarray(log_scales, np.float64)), axis=1) > dense_scale

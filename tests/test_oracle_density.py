@@ -70,6 +70,36 @@ def test_threshold_is_on_the_mean_over_views():
     assert d[1] == 0 and d[2] == 2        # 0.004 / 2 = 0.002 still qualifies
 
 
+def test_single_precision_decision_agrees_with_the_definition():
+    """The f32 decision (thresholds mapped through logit and log) equals the
+    FP64 definition wherever no input lies within float32 rounding of a
+    threshold, and it flips exactly at the mapped thresholds."""
+    rng = np.random.default_rng(5)
+    P = 20000
+    ls = rng.normal(np.log(0.03), 0.8, size=(P, 3)).astype(np.float32)
+    logits = rng.normal(0.0, 4.0, size=P).astype(np.float32)
+    cnt = rng.integers(0, 6, size=P)
+    acc = (rng.exponential(2e-4, size=P) * cnt).astype(np.float32)
+    args = (None, ls, None, logits, acc, cnt, 2e-4, 0.05, 0.005)
+    d64 = DN.decide(*args)
+    d32 = DN.decide(*args, precision="f32")
+    avg = np.where(cnt > 0, acc.astype(float) / np.maximum(cnt, 1), 0.0)
+    near = (np.abs(avg - 2e-4) < 1e-10) | (np.abs(ls.max(axis=1) - np.log(0.05)) < 1e-6) \
+        | (np.abs(logits - np.log(0.005 / 0.995)) < 1e-5)
+    assert near.sum() < P // 1000 and len(set(d64.tolist())) == 4
+    assert np.array_equal(d32[~near], d64[~near])
+    # exactly at the float32 thresholds
+    lmin, ldense = np.float32(np.log(0.005 / 0.995)), np.float32(np.log(0.05))
+    edge_logits = np.array([lmin, np.nextafter(lmin, np.float32(-np.inf))], np.float32)
+    e = DN.decide(None, np.full((2, 3), -5.0, np.float32), None, edge_logits, np.zeros(2, np.float32), np.ones(2),
+                  1.0, 0.05, 0.005, precision="f32")
+    assert e.tolist() == [0, -1]
+    edge_ls = np.array([[ldense] * 3, [np.nextafter(ldense, np.float32(np.inf))] * 3], np.float32)
+    e = DN.decide(None, edge_ls, None, np.zeros(2, np.float32), np.ones(2, np.float32), np.ones(2), 1e-3, 0.05,
+                  0.005, precision="f32")
+    assert e.tolist() == [1, 2]
+
+
 def test_screen_stats_and_opacity_reset_closed_forms():
     d_uv = np.array([[3.0, 4.0], [1.0, 0.0], [0.0, 0.0]])
     acc, cnt = DN.screen_grad_stats(d_uv, [True, False, True], width=2, height=2)   # W/2 = H/2 = 1
