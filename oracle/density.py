@@ -100,16 +100,18 @@ def decide(means, log_scales, quats, logits, accum, count, grad_thresh, dense_sc
     return np.where(op < min_opacity, -1, d)
 
 
-def densify(params: dict, state: dict, accum, count, normals, grad_thresh, dense_scale, min_opacity):
+def densify(params: dict, state: dict, accum, count, normals, grad_thresh, dense_scale, min_opacity,
+            precision: str = "f64"):
     """params: means [P,3], log_scales [P,3], quats [P,4], opacity_logits [P]
     and any other per-Gaussian arrays (copied); state: per-Gaussian optimiser
-    arrays (kept for survivors, zero for new ones); normals [P,2,3].
-    Returns (new params, new state, decision)."""
+    arrays (kept for survivors, zero for new ones); normals [P,2,3];
+    precision: that of the decision (see decide).  Returns (new params, new
+    state, decision)."""
     means = np.asarray(params["means"], np.float64)
     log_scales = np.asarray(params["log_scales"], np.float64)
     quats = np.asarray(params["quats"], np.float64)
     d = decide(means, log_scales, quats, params["opacity_logits"], accum, count, grad_thresh, dense_scale,
-               min_opacity)
+               min_opacity, precision)
     keep = np.flatnonzero((d == 0) | (d == 1))
     clone = np.flatnonzero(d == 1)
     split = np.flatnonzero(d == 2)
