@@ -76,7 +76,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--D", type=int, default=None, help="feature width override (16, 32, 64, 128): D sweep")
     p.add_argument("--P", type=int, default=None, help="Gaussian count override (--micro fst: profiling sizes)")
-    p.add_argument("--micro", choices=["decoder", "adam", "fst"], default=None,
+    p.add_argument("--micro", choices=["decoder", "adam", "fst", "densify"], default=None,
                    help="time one HBM-bound kernel alone on the workload's sizes")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--eager", action="store_true", help="time the step eagerly instead of as one CUDA graph")
@@ -638,6 +638,34 @@ def run_micro(args, cfg):
             fst.backward(scene, 0.5, dict(up, means=up["means"].clone()))
         nbytes = fst.planes.numel() * 4
         what = f"full FST module forward + reverse over {P} Gaussians ({fc['levels']} levels)"
+    elif args.micro == "densify":
+        # Adaptive density control over the training state of the workload's
+        # Gaussians: FP32 parameters, bf16 render copies of SH and features,
+        # two Adam moments per parameter; statistics as after some iterations.
+        from paper_2503_06161_gb300 import _lib, synth
+        sc = synth.make_scene(P, D, cfg["lo"], cfg["hi"], seed=0)
+        acc, cnt, nrm = synth.make_density_stats(P)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
+        params = dict(means=t(sc.means), log_scales=t(sc.log_scales), quats=t(sc.quats),
+                      opacity_logits=t(sc.opacity_logits), sh=t(sc.sh).reshape(P, 16, 3), feat=t(sc.feat))
+        keys = list(params)
+        params["sh_store"], params["feat_store"] = params["sh"].to(torch.bfloat16), params["feat"].to(torch.bfloat16)
+        state = {k + s: torch.randn(params[k].shape, generator=g).to(dev) for k in keys for s in (".m", ".v")}
+        role = dict(means=_lib.FE_ATTR_MEANS, log_scales=_lib.FE_ATTR_LOG_SCALES)
+        attrs = [(v, torch.empty((2 * P,) + tuple(v.shape[1:]), dtype=v.dtype, device=dev),
+                  role.get(k, _lib.FE_ATTR_COPY)) for k, v in params.items()]
+        attrs += [(v, torch.empty((2 * P,) + tuple(v.shape[1:]), dtype=v.dtype, device=dev), _lib.FE_ATTR_STATE)
+                  for v in state.values()]
+        row_bytes = sum(v.element_size() * v[0].numel() for v, _, _ in attrs)
+        accum, count, normals = t(acc), t(cnt), t(nrm)
+        new_P = torch.zeros(1, dtype=torch.int64, device=dev)
+        ws = torch.empty(_lib.fe_densify_workspace_size(P), dtype=torch.uint8, device=dev)
+        extent = 0.5 * float(np.linalg.norm(np.subtract(cfg["hi"], cfg["lo"])))
+        fn = lambda: _lib.fe_densify(P, params["means"], params["log_scales"], params["quats"],
+                                     params["opacity_logits"], accum, count, normals, 2e-4, 0.01 * extent, 0.005,
+                                     attrs, 2 * P, new_P, ws)
+        what = (f"densify / prune of {P} Gaussians' training state ({row_bytes} B per Gaussian: FP32 parameters, "
+                f"bf16 SH/feature copies, two Adam moments)")
     elif args.micro == "decoder":
         dec = Decoder.random(D, device=dev)
         feat = torch.randn(HW, D, generator=g).to(torch.bfloat16).to(dev)
@@ -671,6 +699,13 @@ def run_micro(args, cfg):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    extra = {}
+    if args.micro == "densify":
+        # Each input row read once, each output row written once, plus the
+        # statistics (accum, count) of every Gaussian.
+        n = int(new_P.item())
+        nbytes = row_bytes * (P + n) + 8 * P
+        extra = {"P": P, "new_P": n, "row_bytes": row_bytes}
     if args.micro == "fst":
         fl = 6.0 * fst_macs(fc["levels"], D) * P   # forward 2 M, reverse 4 M flop per Gaussian
         mhz = clk.get("sm_mhz") or 2070.0
@@ -683,7 +718,7 @@ def run_micro(args, cfg):
         return
     peak, basis = hbm_peak()
     gbs = nbytes / (ms * 1e-3) / 1e9
-    print(json.dumps({"micro": args.micro, "workload": args.workload, "what": what, "ms": round(ms, 4),
+    print(json.dumps({"micro": args.micro, "workload": args.workload, "what": what, "ms": round(ms, 4), **extra,
                       "bytes": int(nbytes), "roofline": {"bound": "hbm", "achieved": round(gbs, 1),
                                                         "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
                                                         "peak_basis": basis},

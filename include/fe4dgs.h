@@ -397,6 +397,76 @@ fe_status fe_fst_backward(const fe_fst *fst, int P, const float *means, float t,
  * Asynchronous on `stream`. */
 fe_status fe_fst_tv(const fe_fst *fst, float weight, float *loss, float *d_planes, float *scratch, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Adaptive density control.  The paper trains with densification, pruning
+ * and opacity resets (its appendix hyperparameter table gives the
+ * percent-dense fraction and the reset / prune intervals) without stating
+ * the procedure; these entry points implement the adaptive density control
+ * of the 3D Gaussian splatting lineage it builds on:
+ *   statistics  per Gaussian, the sum over the views in which it touched a
+ *               tile of |(dL/du W/2, dL/dv H/2)| -- the gradient of the loss
+ *               with respect to its projected centre in normalised device
+ *               coordinates -- and the number of such views;
+ *   densify     a Gaussian whose mean statistic is >= grad_thresh is cloned
+ *               (an identical copy appended) when its largest scale
+ *               exp(log_scale) is <= dense_scale, and otherwise split: it is
+ *               replaced by two Gaussians with centres mu + R(q) (s * n_i),
+ *               n_i the caller's N(0, I3) draws, and scales s / 1.6, the
+ *               other parameters copied;
+ *   prune       Gaussians with sigmoid(opacity logit) < min_opacity, and
+ *               their copies, are dropped;
+ *   order       surviving originals in index order, then clones in index
+ *               order, then split children (two per parent, parent order);
+ *   reset       opacity logits capped at logit(max_opacity).
+ * ------------------------------------------------------------------------ */
+
+/* After fe_render_backward on `workspace` (same P, D, width, height, opts):
+ * accum[g] += |(dL/du W/2, dL/dv H/2)| and count[g] += 1 for every Gaussian
+ * that touched a tile in that view.  accum float32 [P], count int32 [P],
+ * device, caller-owned (zero them to start).  Asynchronous on `stream`. */
+fe_status fe_screen_grad_stats(const void *workspace, size_t workspace_bytes, int P, int D, int width, int height,
+                               const fe_opts *opts, float *accum, int32_t *count, void *stream);
+
+#define FE_ATTR_COPY 0        /* copied to survivors, clones and split children */
+#define FE_ATTR_MEANS 1       /* [P][3] float32: children get mu + R(q)(s * n_i) */
+#define FE_ATTR_LOG_SCALES 2  /* [P][3] float32: children get log_scale + log(1 / 1.6) */
+#define FE_ATTR_STATE 3       /* optimiser state: survivors keep it, new Gaussians get 0 */
+
+typedef struct {
+  const void *src;   /* device, [P][width] elements */
+  void *dst;         /* device, [capacity][width] elements, must not alias src */
+  int width;         /* elements per Gaussian, >= 1 */
+  int elem_bytes;    /* 4 (float32) or 2 (bf16; FE_ATTR_COPY and FE_ATTR_STATE only) */
+  int role;          /* FE_ATTR_* */
+} fe_attr;
+
+typedef struct {
+  int P;
+  const float *means, *log_scales, *quats, *opacity_logits;  /* device: the decision inputs */
+  const float *accum;                /* device [P]: statistics from fe_screen_grad_stats */
+  const int32_t *count;              /* device [P] */
+  const float *normals;              /* device [P][2][3]: N(0,1) draws for split children */
+  float grad_thresh, dense_scale, min_opacity;
+  const fe_attr *attrs;              /* host array of nattrs descriptors (1..32) */
+  int nattrs;
+  int64_t capacity;                  /* rows of every dst; must be >= 2 P */
+} fe_densify_args;
+
+/* Device workspace of fe_densify for P Gaussians. */
+size_t fe_densify_workspace_size(int P);
+
+/* Writes every attribute's densified rows to its dst and the new Gaussian
+ * count to *new_P (one device int64).  The result is deterministic (fixed
+ * scan order).  FE_ERR_INVALID_ARG for NULL pointers, unaligned float
+ * arrays or capacity < 2 P; FE_ERR_WORKSPACE for a small workspace.
+ * Asynchronous on `stream`. */
+fe_status fe_densify(const fe_densify_args *args, int64_t *new_P, void *workspace, size_t workspace_bytes,
+                     void *stream);
+
+/* logits[g] = min(logits[g], log(max_opacity / (1 - max_opacity))), g < P,
+ * 0 < max_opacity < 1.  Asynchronous on `stream`. */
+fe_status fe_reset_opacity(float *logits, int64_t P, float max_opacity, void *stream);
+
 /* Measured single-precision FMA throughput: runs an FMA-chain kernel over
  * the whole GPU for `iters` iterations per thread and writes FLOP/s
  * (2 per FMA) to *flops (host).  Synchronous; used for the FP32 roofline. */

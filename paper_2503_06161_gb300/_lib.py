@@ -8,6 +8,7 @@ There is no fallback: if the library is missing the import fails.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -82,6 +83,19 @@ class fe_fst(ctypes.Structure):
                 ("mlp", c_void_p), ("bbox_min", c_float * 3), ("bbox_max", c_float * 3)]
 
 
+class fe_attr(ctypes.Structure):
+    _fields_ = [("src", c_void_p), ("dst", c_void_p), ("width", c_int), ("elem_bytes", c_int), ("role", c_int)]
+
+
+class fe_densify_args(ctypes.Structure):
+    _fields_ = [("P", c_int), ("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p),
+                ("opacity_logits", c_void_p), ("accum", c_void_p), ("count", c_void_p), ("normals", c_void_p),
+                ("grad_thresh", c_float), ("dense_scale", c_float), ("min_opacity", c_float),
+                ("attrs", c_void_p), ("nattrs", c_int), ("capacity", c_int64)]
+
+
+FE_ATTR_COPY, FE_ATTR_MEANS, FE_ATTR_LOG_SCALES, FE_ATTR_STATE = 0, 1, 2, 3
+
 _P = ctypes.POINTER
 _SIGNATURES = {
     "fe_workspace_size": [c_int, c_int, c_int, c_int, _P(fe_opts), _P(ctypes.c_size_t)],
@@ -110,6 +124,10 @@ _SIGNATURES = {
                       + [ctypes.c_size_t, c_int, c_void_p],
     "fe_fst_backward": [_P(fe_fst), c_int, c_void_p, c_float] + [c_void_p] * 9 + [ctypes.c_size_t, c_void_p],
     "fe_fst_tv": [_P(fe_fst), c_float, c_void_p, c_void_p, c_void_p, c_void_p],
+    "fe_screen_grad_stats": [c_void_p, ctypes.c_size_t, c_int, c_int, c_int, c_int, _P(fe_opts), c_void_p,
+                             c_void_p, c_void_p],
+    "fe_densify": [_P(fe_densify_args), c_void_p, c_void_p, ctypes.c_size_t, c_void_p],
+    "fe_reset_opacity": [c_void_p, c_int64, c_float, c_void_p],
 }
 
 _lib = None
@@ -130,6 +148,8 @@ def load():
             getattr(L, name).restype = c_int64
         L.fe_fst_plane_floats.argtypes = [c_int, c_int, c_int]
         L.fe_fst_mlp_floats.argtypes = [c_int, c_int]
+        L.fe_densify_workspace_size.argtypes = [c_int]
+        L.fe_densify_workspace_size.restype = ctypes.c_size_t
         L.fe_decoder_workspace_size.argtypes = [c_int64, c_int]
         L.fe_decoder_workspace_size.restype = ctypes.c_size_t
         L.fe_status_string.argtypes = [c_int]
@@ -405,3 +425,46 @@ def fe_fst_tv(fst: fe_fst, weight: float, loss, d_planes, scratch, stream=None):
     rc = load().fe_fst_tv(ctypes.byref(fst), float(weight), _ptr(loss), _ptr(d_planes), _ptr(scratch),
                           _stream(stream))
     _check("fe_fst_tv", rc)
+
+
+# --- adaptive density control --------------------------------------------------
+def fe_screen_grad_stats(workspace, P: int, D: int, width: int, height: int, opts: fe_opts, accum, count,
+                         stream=None):
+    rc = load().fe_screen_grad_stats(_ptr(workspace), workspace.numel() * workspace.element_size(), int(P), int(D),
+                                     int(width), int(height), ctypes.byref(opts), _ptr(accum), _ptr(count),
+                                     _stream(stream))
+    _check("fe_screen_grad_stats", rc)
+
+
+def fe_densify_workspace_size(P: int) -> int:
+    return int(load().fe_densify_workspace_size(int(P)))
+
+
+def fe_densify(P: int, means, log_scales, quats, opacity_logits, accum, count, normals, grad_thresh: float,
+               dense_scale: float, min_opacity: float, attrs, capacity: int, new_P, workspace, stream=None):
+    """attrs: list of (src, dst, role) with src [P, ...] and dst [capacity, ...]
+    tensors of float32 (any role) or bf16 (FE_ATTR_COPY / FE_ATTR_STATE)."""
+    import torch
+    arr = (fe_attr * len(attrs))()
+    for k, (src, dst, role) in enumerate(attrs):
+        arr[k].src = src.data_ptr()
+        arr[k].dst = dst.data_ptr()
+        arr[k].width = math.prod(src.shape[1:])
+        arr[k].elem_bytes = 2 if src.dtype == torch.bfloat16 else 4
+        arr[k].role = int(role)
+    a = fe_densify_args()
+    a.P = int(P)
+    a.means, a.log_scales, a.quats = _ptr(means), _ptr(log_scales), _ptr(quats)
+    a.opacity_logits, a.accum, a.count, a.normals = _ptr(opacity_logits), _ptr(accum), _ptr(count), _ptr(normals)
+    a.grad_thresh, a.dense_scale, a.min_opacity = float(grad_thresh), float(dense_scale), float(min_opacity)
+    a.attrs = ctypes.cast(arr, c_void_p)
+    a.nattrs = len(attrs)
+    a.capacity = int(capacity)
+    rc = load().fe_densify(ctypes.byref(a), _ptr(new_P), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                           _stream(stream))
+    _check("fe_densify", rc)
+
+
+def fe_reset_opacity(logits, max_opacity: float, stream=None):
+    _check("fe_reset_opacity", load().fe_reset_opacity(_ptr(logits), int(logits.numel()), float(max_opacity),
+                                                       _stream(stream)))

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfe4dgs.so")
-SOURCES = ["api.cu", "gauss.cu", "binning.cu", "composite.cu", "loss.cu", "decoder.cu", "optim.cu", "fst.cu"]
+SOURCES = ["api.cu", "gauss.cu", "binning.cu", "composite.cu", "loss.cu", "decoder.cu", "optim.cu", "fst.cu", "density.cu"]
 HEADERS = ["common.cuh", "kernels.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -321,6 +321,21 @@ fe_status fe_read_stats(const void* workspace, size_t workspace_bytes, int P, in
   return FE_OK;
 }
 
+fe_status fe_screen_grad_stats(const void* workspace, size_t workspace_bytes, int P, int D, int width, int height,
+                               const fe_opts* opts, float* accum, int32_t* count, void* stream) {
+  if (!workspace || (P > 0 && (!accum || !count))) return FE_ERR_INVALID_ARG;
+  Layout L;
+  float bg[3];
+  fe_status s = layout_for(P, D, width, height, opts, L, bg);
+  if (s != FE_OK) return s;
+  if (!L.with_backward) return FE_ERR_INVALID_ARG;
+  if (workspace_bytes < L.total) return FE_ERR_WORKSPACE;
+  void* ws = const_cast<void*>(workspace);
+  // psum[g][0..1] hold dL/du and dL/dv of the last fe_render_backward.
+  return cuda_status(launch_screen_stats(at<uint32_t>(ws, L.touched), at<float>(ws, L.psum), P, width, height, accum,
+                                         count, static_cast<cudaStream_t>(stream)));
+}
+
 fe_status fe_debug_dump(const void* workspace, size_t workspace_bytes, int P, int D, int width, int height,
                         const fe_opts* opts, uint64_t* keys, uint32_t* gauss, uint32_t* ranges, uint32_t* n_contrib,
                         float* t_final, float* uv, float* conic, float* opacity, float* depth, float* rgb,

@@ -112,6 +112,10 @@ struct DumpArgs {
 };
 cudaError_t launch_dump(const DumpArgs& d, cudaStream_t st);
 
+// Screen-space gradient statistics of adaptive density control (density.cu).
+cudaError_t launch_screen_stats(const uint32_t* touched, const float* psum, int P, int W, int H, float* accum,
+                                int32_t* count, cudaStream_t st);
+
 cudaError_t probe_fp32(int iters, double* flops, cudaStream_t st);
 cudaError_t launch_l1(const float* pred, const float* target, int64_t n, int64_t rows, float* grad, float* loss,
                       float* scratch, cudaStream_t st);

@@ -41,6 +41,14 @@ class FSTDeform:
         self.d_mlp = torch.zeros_like(self.mlp)
         self._out = None
 
+    def resize(self, P: int):
+        """Workspace for a new Gaussian count (after densification)."""
+        self.P = int(P)
+        self.workspace = None
+        self.workspace = torch.empty(_lib.fe_fst_workspace_size(self.P, self.levels, self.D, self.with_backward),
+                                     dtype=torch.uint8, device=self.planes.device)
+        self._out = None
+
     @classmethod
     def from_numpy(cls, planes, mlp, levels, rs, rt, D, bbox_min, bbox_max, P, device="cuda", **kw):
         return cls(torch.as_tensor(planes), torch.as_tensor(mlp), levels, rs, rt, D, bbox_min, bbox_max, P,

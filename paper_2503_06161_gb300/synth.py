@@ -24,6 +24,9 @@ Recipe (every array float32 unless stated):
                  N(0, 0.01/8) with the d_mu rows (0..2) and the d_o row (10)
                  zero; noise xi [P,3] ~ N(0, 1) scaled by 0.01*t
   targets        rgb U(0,1) [3,H,W]; features N(0,1)
+  density stats  views per Gaussian count ~ U{0..8} (int32); accum = the sum
+                 of count Exp(2e-4) draws (NDC centre-gradient norms);
+                 split normals [P,2,3] ~ N(0, 1)
 """
 from __future__ import annotations
 
@@ -249,6 +252,16 @@ def make_depth_target(height: int, width: int, near: float, far: float, seed: in
     d = near + (far - near) * np.clip(s, 0.0, 1.0)
     d = d * (1.0 + 0.01 * rng.normal(size=d.shape))
     return d.astype(np.float32)
+
+
+def make_density_stats(P: int, seed: int = 6, mean_grad: float = 2e-4, max_views: int = 8):
+    """Statistics that adaptive density control reads after some iterations:
+    (accum float32 [P], count int32 [P], normals float32 [P,2,3])."""
+    rng = np.random.default_rng(seed)
+    count = rng.integers(0, max_views + 1, P).astype(np.int32)
+    accum = np.where(count > 0, rng.gamma(np.maximum(count, 1), mean_grad), 0.0).astype(np.float32)
+    normals = rng.normal(0.0, 1.0, (P, 2, 3)).astype(np.float32)
+    return accum, count, normals
 
 
 def make_decoder(D: int, cout: int = 256, seed: int = 3, w_std: float = 0.05, b_std: float = 0.0):

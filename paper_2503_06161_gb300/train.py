@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import torch
 
-from . import _lib
+from . import _lib, density
 from .decoder import Decoder
 from .fst import FSTDeform
 from .optim import Adam, exp_lr
@@ -39,11 +39,13 @@ SCHEDULE_STEPS = 3000
 class Trainer:
     def __init__(self, masters: dict, sh_degree: int, cam, deform: DeformField | None, decoder: Decoder,
                  bf16_storage: bool = True, max_dups: int | None = None, lr: dict | None = None, device="cuda",
-                 fst: FSTDeform | None = None, schedule: bool = True):
+                 fst: FSTDeform | None = None, schedule: bool = True, density_stats: bool = False):
         """masters: float32 device tensors means [P,3], log_scales [P,3],
         quats [P,4], opacity_logits [P], sh [P,16,3], feat [P,D].  deform:
         the single-level field evaluated inside the renderer, or fst: the
-        full FST module (Sec. 3.2) run around it (not both)."""
+        full FST module (Sec. 3.2) run around it (not both).
+        density_stats: gather the screen-space gradient statistics of
+        adaptive density control every iteration (densify_and_prune)."""
         if deform is not None and fst is not None:
             raise ValueError("one deformation model: deform or fst")
         self.m = masters
@@ -68,12 +70,8 @@ class Trainer:
                                    masters["opacity_logits"], self.sh_store, self.feat_store, sh_degree)
         W, H = self.cam.width, self.cam.height
         self.HW = W * H
-        if max_dups is None:
-            probe = Rasterizer(self.P, self.D, W, H, device=device, max_dups=64 * self.P + 4096, forward_only=True)
-            probe.forward(fst.forward(self.scene, 0.5) if fst is not None else self.scene, self.cam, deform, 0.5)
-            max_dups = int(probe.stats()["num_dups"] * 1.5) + 4096
-            del probe
-        self.rast = Rasterizer(self.P, self.D, W, H, max_dups=max_dups, device=device, auto_grow=False)
+        self.device = device
+        self.rast = self._rasterizer(max_dups)
         kw = dict(dtype=torch.float32, device=device)
         self.out = (torch.empty(3, H, W, **kw), torch.empty(H, W, **kw), torch.empty(H, W, **kw),
                     torch.empty(self.HW, self.D, **kw))
@@ -85,9 +83,7 @@ class Trainer:
         self.scratch = torch.empty(3, 1024, **kw)
         self.dec_out = (self.losses[1:2], torch.empty(self.HW, self.D, **kw), torch.empty(256, self.D, **kw),
                         torch.empty(256, **kw))
-        self.grads = dict(means=torch.empty(P, 3, **kw), log_scales=torch.empty(P, 3, **kw),
-                          quats=torch.empty(P, 4, **kw), opacity_logits=torch.empty(P, **kw),
-                          sh=torch.empty(P, 16, 3, **kw), feat=torch.empty(P, D, **kw))
+        self.grads = self._grad_buffers()
         self.dec_w32 = decoder.weight.float()
         groups = [dict(param=masters[k], lr=lr[k]) for k in ("means", "log_scales", "quats", "opacity_logits")]
         groups.append(dict(param=masters["sh"], lr=lr["sh"], param_bf16=self.sh_store if bf16_storage else None))
@@ -101,6 +97,80 @@ class Trainer:
             self.opt_fst = Adam([dict(param=fst.planes, lr=lr["grid"]), dict(param=fst.mlp, lr=lr["deformation"])])
         self.steps = 0
         self.dec.workspace(self.HW)
+        self.stats = density.DensityStats(self.P, device) if density_stats else None
+
+    def _rasterizer(self, max_dups: int | None) -> Rasterizer:
+        """Rasterizer for the current P; without a capacity, one probe
+        forward at t = 0.5 sizes the duplicate list (1.5x plus slack)."""
+        W, H = self.cam.width, self.cam.height
+        if max_dups is None:
+            probe = Rasterizer(self.P, self.D, W, H, device=self.device, max_dups=64 * self.P + 4096,
+                               forward_only=True)
+            probe.forward(self.fst.forward(self.scene, 0.5) if self.fst is not None else self.scene, self.cam,
+                          self.deform, 0.5)
+            max_dups = int(probe.stats()["num_dups"] * 1.5) + 4096
+            del probe
+        return Rasterizer(self.P, self.D, W, H, max_dups=max_dups, device=self.device, auto_grow=False)
+
+    def _grad_buffers(self) -> dict:
+        P, D = self.P, self.D
+        kw = dict(dtype=torch.float32, device=self.device)
+        return dict(means=torch.empty(P, 3, **kw), log_scales=torch.empty(P, 3, **kw),
+                    quats=torch.empty(P, 4, **kw), opacity_logits=torch.empty(P, **kw),
+                    sh=torch.empty(P, 16, 3, **kw), feat=torch.empty(P, D, **kw))
+
+    GAUSS_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh", "feat")
+
+    def densify_and_prune(self, extent: float, normals: torch.Tensor | None = None,
+                          grad_thresh: float = density.GRAD_THRESH, min_opacity: float = density.MIN_OPACITY,
+                          generator: torch.Generator | None = None, max_dups: int | None = None) -> int:
+        """Adaptive density control from the statistics gathered since the
+        last call: clone / split / prune every parameter, the bf16 render
+        copies and the Adam moments (new Gaussians start with zero moments),
+        then rebuild every buffer sized by P.  dense_scale = percent dense
+        (0.01) x extent.  normals: [P,2,3] N(0,1) draws placing split
+        children (drawn with `generator` when not given).  Returns the new P;
+        reads it back (one host sync)."""
+        if self.stats is None:
+            raise RuntimeError("construct the Trainer with density_stats=True")
+        P = self.P
+        if normals is None:
+            normals = torch.randn(P, 2, 3, generator=generator, device=self.device, dtype=torch.float32)
+        params = {k: self.m[k] for k in self.GAUSS_KEYS}
+        if self.bf16:
+            params["sh_store"], params["feat_store"] = self.sh_store, self.feat_store
+        state = {}
+        for i, k in enumerate(self.GAUSS_KEYS):
+            state[k + ".m"], state[k + ".v"] = self.opt.groups[i]["m"], self.opt.groups[i]["v"]
+        new_p, new_s, n = density.densify(params, state, self.stats, normals, grad_thresh,
+                                          density.PERCENT_DENSE * float(extent), min_opacity)
+        for k in self.GAUSS_KEYS:
+            self.m[k] = new_p[k]
+        if self.bf16:
+            self.sh_store, self.feat_store = new_p["sh_store"], new_p["feat_store"]
+        else:
+            self.sh_store, self.feat_store = self.m["sh"], self.m["feat"]
+        for i, k in enumerate(self.GAUSS_KEYS):
+            g = self.opt.groups[i]
+            g["param"], g["m"], g["v"] = self.m[k], new_s[k + ".m"], new_s[k + ".v"]
+        self.opt.groups[4]["param_bf16"] = self.sh_store if self.bf16 else None
+        self.opt.groups[5]["param_bf16"] = self.feat_store if self.bf16 else None
+        self.P = n
+        self.scene = GaussianScene(self.m["means"], self.m["log_scales"], self.m["quats"], self.m["opacity_logits"],
+                                   self.sh_store, self.feat_store, self.scene.sh_degree)
+        if self.fst is not None:
+            self.fst.resize(n)
+        self.grads = self._grad_buffers()
+        self.rast = None
+        self.rast = self._rasterizer(max_dups)
+        self.stats.reset(n)
+        return n
+
+    def reset_opacity(self, max_opacity: float = density.RESET_OPACITY):
+        """Cap every opacity at max_opacity and restart its Adam moments."""
+        density.reset_opacity(self.m["opacity_logits"], max_opacity)
+        self.opt.groups[3]["m"].zero_()
+        self.opt.groups[3]["v"].zero_()
 
     @classmethod
     def from_numpy(cls, sc, cam, df=None, dec_w=None, dec_b=None, device="cuda", bf16_storage=True, **kw):
@@ -134,6 +204,8 @@ class Trainer:
         rec(1)
         self.rast.backward(scene, self.cam, self.deform, t, self.g_rgb, g_depth, None, self.dec_out[1],
                            grads=self.grads)
+        if self.stats is not None:
+            self.stats.record(self.rast)
         rec(2)
         if self.fst is not None:
             # Deformed-Gaussian gradients -> canonical, planes and weights;

@@ -40,12 +40,14 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_layouts_match_header(tmp_path):
     structs = ["fe_camera", "fe_gaussians", "fe_deform", "fe_opts", "fe_outputs", "fe_output_grads", "fe_grads",
-               "fe_stats", "fe_fst"]
+               "fe_stats", "fe_fst", "fe_attr", "fe_densify_args"]
     c = "#include <stdio.h>\n#include <stddef.h>\n#include \"fe4dgs.h\"\nint main(void){\n"
     for s in structs:
         c += f'printf("{s} %zu\\n", sizeof({s}));\n'
     c += 'printf("fe_opts.max_dups %zu\\n", offsetof(fe_opts, max_dups));\n'
     c += 'printf("fe_deform.bbox_min %zu\\n", offsetof(fe_deform, bbox_min));\n'
+    for f in ("normals", "grad_thresh", "attrs", "capacity"):
+        c += f'printf("fe_densify_args.{f} %zu\\n", offsetof(fe_densify_args, {f}));\n'
     c += "return 0;}\n"
     (tmp_path / "t.c").write_text(c)
     exe = tmp_path / "t"
@@ -55,6 +57,8 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(got[s]) == ctypes.sizeof(getattr(_lib, s)), s
     assert int(got["fe_opts.max_dups"]) == _lib.fe_opts.max_dups.offset
     assert int(got["fe_deform.bbox_min"]) == _lib.fe_deform.bbox_min.offset
+    for f in ("normals", "grad_thresh", "attrs", "capacity"):
+        assert int(got[f"fe_densify_args.{f}"]) == getattr(_lib.fe_densify_args, f).offset, f
 
 
 def test_host_side_status_codes(lib):
@@ -155,3 +159,58 @@ def test_fst_sizes_and_host_side_status_codes(lib):
     f.D = 32
     f.bbox_max[1] = -1.0                                                 # empty box
     assert lib.fe_fst_forward(ctypes.byref(f), 1, *args, 0, 0.5, *args, ws, 1 << 30, 1, None) == 1
+
+
+def test_density_host_side_status_codes(lib):
+    """Every case is refused on the host, before any CUDA call."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    base = (ctypes.addressof(buf) + 255) // 256 * 256
+    ws, n_ws = ctypes.c_void_p(base), 4096
+    assert lib.fe_densify_workspace_size(1000) >= 1000 and lib.fe_densify_workspace_size(-1) == 0
+    attrs = (_lib.fe_attr * 2)()
+    attrs[0].src, attrs[0].dst, attrs[0].width, attrs[0].elem_bytes, attrs[0].role = base, base + 64, 3, 4, 1
+    attrs[1].src, attrs[1].dst, attrs[1].width, attrs[1].elem_bytes, attrs[1].role = base, base + 128, 4, 4, 3
+    a = _lib.fe_densify_args()
+    a.P = 10
+    for f in ("means", "log_scales", "quats", "opacity_logits", "accum", "count", "normals"):
+        setattr(a, f, base)
+    a.grad_thresh, a.dense_scale, a.min_opacity = 2e-4, 0.05, 0.005
+    a.attrs, a.nattrs, a.capacity = ctypes.cast(attrs, ctypes.c_void_p), 2, 20
+    new_p = ctypes.c_void_p(base + 512)
+    assert lib.fe_densify(None, new_p, ws, n_ws, None) == 1
+    assert lib.fe_densify(ctypes.byref(a), None, ws, n_ws, None) == 1
+    a.capacity = 19                                                            # < 2 P
+    assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
+    a.capacity = 20
+    assert lib.fe_densify(ctypes.byref(a), new_p, ws, 16, None) == 3           # workspace
+    a.nattrs = 0
+    assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
+    a.nattrs = 33
+    assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
+    a.nattrs = 2
+    attrs[0].width = 4                                                         # means must be [P][3]
+    assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
+    attrs[0].width, attrs[0].elem_bytes = 3, 2                                 # and float32
+    assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
+    attrs[0].elem_bytes, attrs[0].dst = 4, base                                # dst aliases src
+    assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
+    attrs[0].dst, attrs[1].role = base + 64, 4                                 # unknown role
+    assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
+    attrs[1].role, a.quats = 3, base + 2                                       # unaligned floats
+    assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
+    a.quats, a.normals = base, None
+    assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
+    a.normals, a.dense_scale = base, float("nan")
+    assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
+    for m in (0.0, 1.0, -0.5, float("nan")):
+        assert lib.fe_reset_opacity(ctypes.c_void_p(base), 10, m, None) == 1
+    assert lib.fe_reset_opacity(None, 10, 0.01, None) == 1
+    assert lib.fe_reset_opacity(None, 0, 0.01, None) == 0                     # nothing to do
+    assert lib.fe_reset_opacity(ctypes.c_void_p(base), -1, 0.01, None) == 1
+    opts = _lib.make_opts()
+    assert lib.fe_screen_grad_stats(None, 1 << 30, 10, 32, 64, 64, ctypes.byref(opts), base, base, None) == 1
+    assert lib.fe_screen_grad_stats(ws, 1 << 30, 10, 32, 64, 64, ctypes.byref(opts), None, base, None) == 1
+    assert lib.fe_screen_grad_stats(ws, 16, 10, 32, 64, 64, ctypes.byref(opts), base, base, None) == 3
+    assert lib.fe_screen_grad_stats(ws, 1 << 30, 10, 24, 64, 64, ctypes.byref(opts), base, base, None) == 4
+    fwd = _lib.make_opts(forward_only=True)
+    assert lib.fe_screen_grad_stats(ws, 1 << 30, 10, 32, 64, 64, ctypes.byref(fwd), base, base, None) == 1

@@ -176,3 +176,70 @@ def test_training_with_the_full_fst_module():
         assert np.abs(g).sum() > 0
         ref, _, _ = O.adam_step(before, g, 0.0, 0.0, 1, f32(lr), B1, B2, EPS)
         assert np.max(np.abs(got.cpu().numpy() - ref)) <= TOL_ADAM * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("use_fst", [False, True])
+def test_training_with_density_control(use_fst):
+    """Statistics gathered by the iterations drive clone / split / prune of
+    every parameter, render copy and Adam moment (the Trainer's result equals
+    the densify call on a snapshot of the same buffers); a densify that
+    selects nothing is the identity; training continues on the new set with
+    every P-sized buffer rebuilt; the opacity reset caps every opacity."""
+    from paper_2503_06161_gb300 import density
+    from paper_2503_06161_gb300.fst import FSTDeform
+    sc, cam, df = deformed_case(P=3000, W=150, H=100, D=32, seed=2)
+    w, b = synth.make_decoder(32, seed=5, b_std=0.1)
+    kw = dict(max_dups=200_000, density_stats=True)
+    if use_fst:
+        planes, mlp = synth.make_fst(2, 16, 10, 32, seed=6, plane_std=0.1, head_std=0.05)
+        kw["fst"] = FSTDeform.from_numpy(planes, mlp, 2, 16, 10, 32, (-1.5, -1, 1.5), (1.5, 1, 5), sc.P)
+        df = None
+    tr = Trainer.from_numpy(sc, cam, df, w, b, **kw)
+    H, W = tr.cam.height, tr.cam.width
+    rng = np.random.default_rng(9)
+    tgt_rgb = torch.tensor(rng.random((3, H, W)).astype(np.float32)).cuda()
+    tgt_dec = torch.tensor(rng.normal(size=(H * W, 256)).astype(np.float32)).to(torch.bfloat16).cuda()
+    for t in (0.2, 0.5, 0.8):
+        tr.step(t, tgt_rgb, tgt_dec)
+    torch.cuda.synchronize()
+    cnt = tr.stats.count.cpu().numpy()
+    assert cnt.max() == 3 and (cnt > 0).sum() > 1000 and tr.stats.accum.sum().item() > 0
+    # Nothing selected: the identity.
+    snap = {k: v.clone() for k, v in tr.m.items()}
+    mom = [(g["m"].clone(), g["v"].clone()) for g in tr.opt.groups[:6]]
+    assert tr.densify_and_prune(extent=1.0, grad_thresh=1e30, min_opacity=0.0) == 3000
+    for k in snap:
+        assert torch.equal(snap[k], tr.m[k]), k
+    for (m, v), g in zip(mom, tr.opt.groups[:6]):
+        assert torch.equal(m, g["m"]) and torch.equal(v, g["v"])
+    assert tr.stats.count.sum().item() == 0
+    for t in (0.3, 0.6):
+        tr.step(t, tgt_rgb, tgt_dec)
+    # A selective densify equals the densify call on a snapshot.
+    extent = 1.5
+    params = {k: tr.m[k].clone() for k in Trainer.GAUSS_KEYS}
+    params["sh_store"], params["feat_store"] = tr.sh_store.clone(), tr.feat_store.clone()
+    state = {}
+    for i, k in enumerate(Trainer.GAUSS_KEYS):
+        state[k + ".m"], state[k + ".v"] = tr.opt.groups[i]["m"].clone(), tr.opt.groups[i]["v"].clone()
+    st = density.DensityStats(tr.P)
+    st.accum.copy_(tr.stats.accum)
+    st.count.copy_(tr.stats.count)
+    normals = torch.tensor(np.random.default_rng(1).normal(size=(tr.P, 2, 3)).astype(np.float32)).cuda()
+    ref_p, ref_s, ref_n = density.densify(params, state, st, normals, 1e-4, 0.01 * extent, 0.02)
+    n = tr.densify_and_prune(extent, normals=normals, grad_thresh=1e-4, min_opacity=0.02)
+    assert n == ref_n and n != 3000
+    for k in Trainer.GAUSS_KEYS:
+        assert torch.equal(tr.m[k], ref_p[k]), k
+        g = tr.opt.groups[Trainer.GAUSS_KEYS.index(k)]
+        assert torch.equal(g["m"], ref_s[k + ".m"]) and torch.equal(g["v"], ref_s[k + ".v"]), k
+    assert torch.equal(tr.sh_store, ref_p["sh_store"]) and torch.equal(tr.feat_store, ref_p["feat_store"])
+    assert tr.rast.P == n and tr.stats.P == n and tr.grads["sh"].shape[0] == n
+    for t in (0.25, 0.75):
+        L = tr.step(t, tgt_rgb, tgt_dec)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(L.cpu().numpy())) and tr.rast.stats()["device_errors"] == 0
+    assert tr.stats.count.max().item() == 2
+    tr.reset_opacity(0.01)
+    op = torch.sigmoid(tr.m["opacity_logits"].double()).cpu().numpy()
+    assert op.max() <= 0.01 * (1 + 1e-6) and tr.opt.groups[3]["m"].abs().sum().item() == 0
