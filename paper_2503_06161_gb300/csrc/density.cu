@@ -5,10 +5,10 @@
 //
 // fe_densify runs three kernels: decide (one decision per Gaussian and
 // per-block counts of survivors, clones and splits), scan (one block:
-// exclusive offsets of every block, in block order) and scatter (each
-// Gaussian's rows written to their final places for every attribute
-// stream).  The output order is fixed by the scans, so the result does not
-// depend on scheduling.
+// exclusive offsets of every block, in block order) and scatter (one block
+// per 256 Gaussians and attribute stream, writing each Gaussian's rows to
+// their final places).  The output order is fixed by the scans, so the
+// result does not depend on scheduling.
 #include <cmath>
 
 #include "common.cuh"
@@ -26,6 +26,8 @@ struct AttrDev {
   const void* src;
   void* dst;
   int width, elem_bytes, role;
+  int unit;   // bytes moved per access: 16, 8, 4 or 2 (4 with float arithmetic for MEANS / LOG_SCALES)
+  int wu;     // units per row
 };
 
 struct DensArgs {
@@ -134,56 +136,75 @@ __global__ void __launch_bounds__(1024) densify_scan_kernel(const DensArgs a, in
   }
 }
 
-// Rows of one block's Gaussians: survivor row, clone row and first split
-// child row, the decision, and the split children's centre offsets
-// R(q)(s * n_i), staged in shared memory by the thread that owns the
-// Gaussian; then every attribute is moved with the block's threads laid over
-// (row, element) pairs, elements fastest, so that the reads of the block's
+// One block per (256 Gaussians, attribute): the rows of the block's
+// Gaussians -- survivor row, clone row and first split child row -- and the
+// decision are staged in shared memory by the thread that owns the Gaussian
+// (with the split children's centre offsets R(q)(s * n_i) for the MEANS
+// attribute); then the attribute is moved with the block's threads laid over
+// (row, unit) pairs, units fastest, so that the reads of the block's
 // contiguous source rows and the writes of consecutive destination rows are
-// coalesced whatever the attribute's width.
+// coalesced whatever the attribute's width.  A grid of (tiles x attributes)
+// blocks runs many waves, so the last wave's tail is short.
 struct ScatterSmem {
   uint32_t row[3][kDT];            // survivor, clone, first split child
   float off[kSplitN * 3][kDT];     // child centre offsets
   int8_t d[kDT];
 };
 
-template <typename T>
-__device__ __forceinline__ void move_element(const AttrDev& at, const ScatterSmem& sm, const T* src, T* dst, int j,
-                                             int c, float shrink) {
+// Moves one attribute's rows in units U (16, 8, 4 or 2 bytes); ARITH: the
+// float MEANS / LOG_SCALES roles, whose split children are computed.  Each
+// thread loads up to 64 bytes (rows j, j + R, ...; at most 8 units) before
+// storing any, so that enough bytes are in flight to cover the latency.
+template <typename U>
+constexpr int unroll_of() { return 64 / (int)sizeof(U) > 8 ? 8 : 64 / (int)sizeof(U); }
+
+template <typename U, bool ARITH>
+__device__ __forceinline__ void store_rows(const AttrDev& at, const ScatterSmem& sm, U* dst, int j, int c, U v,
+                                           float shrink) {
   const int d = sm.d[j];
-  if (d < 0) return;
-  const size_t W = (size_t)at.width;
-  const T v = src[(size_t)j * W + c];
+  const size_t WU = (size_t)at.wu;
+  const U z{};
   if (d <= 1) {
-    dst[sm.row[0][j] * W + c] = v;
-    if (d == 1) dst[sm.row[1][j] * W + c] = at.role == FE_ATTR_STATE ? T(0) : v;
+    dst[sm.row[0][j] * WU + c] = v;
+    if (d == 1) dst[sm.row[1][j] * WU + c] = at.role == FE_ATTR_STATE ? z : v;
     return;
   }
 #pragma unroll
   for (int i = 0; i < kSplitN; ++i) {
-    T o = v;
-    if constexpr (sizeof(T) == 4) {
-      if (at.role == FE_ATTR_MEANS) o = v + sm.off[i * 3 + c][j];
-      else if (at.role == FE_ATTR_LOG_SCALES) o = v + shrink;
-    }
-    if (at.role == FE_ATTR_STATE) o = T(0);
-    dst[(sm.row[2][j] + i) * W + c] = o;
+    U o = at.role == FE_ATTR_STATE ? z : v;
+    if constexpr (ARITH) o = at.role == FE_ATTR_MEANS ? v + sm.off[i * 3 + c][j] : v + shrink;
+    dst[(sm.row[2][j] + i) * WU + c] = o;
   }
 }
 
-template <typename T>
+template <typename U, bool ARITH>
 __device__ __forceinline__ void move_attr(const AttrDev& at, const ScatterSmem& sm, int g0, int nrows, float shrink) {
-  const T* src = static_cast<const T*>(at.src) + (size_t)g0 * at.width;
-  T* dst = static_cast<T*>(at.dst);
-  const int W = at.width;
-  if (W <= kDT) {
-    const int R = kDT / W;  // rows per pass
-    const int j0 = threadIdx.x / W, c = threadIdx.x - j0 * W;
+  const int WU = at.wu;
+  const U* src = reinterpret_cast<const U*>(static_cast<const char*>(at.src) + (size_t)g0 * at.width * at.elem_bytes);
+  U* dst = static_cast<U*>(at.dst);
+  if (WU <= kDT) {
+    const int R = kDT / WU;  // rows per pass
+    const int j0 = threadIdx.x / WU, c = threadIdx.x - j0 * WU;
     if (j0 >= R) return;
-    for (int j = j0; j < nrows; j += R) move_element<T>(at, sm, src, dst, j, c, shrink);
+    constexpr int kUnroll = unroll_of<U>();
+    for (int jb = j0; jb < nrows; jb += R * kUnroll) {
+      U v[kUnroll];
+      bool live[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int j = jb + u * R;
+        live[u] = j < nrows && sm.d[j] >= 0;
+        if (live[u]) v[u] = src[(size_t)j * WU + c];
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (live[u]) store_rows<U, ARITH>(at, sm, dst, jb + u * R, c, v[u], shrink);
+    }
   } else {
-    for (int j = 0; j < nrows; ++j)
-      for (int c = threadIdx.x; c < W; c += kDT) move_element<T>(at, sm, src, dst, j, c, shrink);
+    for (int j = 0; j < nrows; ++j) {
+      if (sm.d[j] < 0) continue;
+      for (int c = threadIdx.x; c < WU; c += kDT) store_rows<U, ARITH>(at, sm, dst, j, c, src[(size_t)j * WU + c], shrink);
+    }
   }
 }
 
@@ -202,7 +223,8 @@ __global__ void __launch_bounds__(kDT) densify_scatter_kernel(const DensArgs a) 
   sm.row[0][threadIdx.x] = (uint32_t)(a.blk[blockIdx.x * 3] + ik);
   sm.row[1][threadIdx.x] = K + (uint32_t)(a.blk[blockIdx.x * 3 + 1] + ic);
   sm.row[2][threadIdx.x] = K + C + (uint32_t)kSplitN * (uint32_t)(a.blk[blockIdx.x * 3 + 2] + is);
-  if (d == 2) {
+  const AttrDev& at = a.attrs[blockIdx.y];
+  if (d == 2 && at.role == FE_ATTR_MEANS) {
     // Rotation of the (normalised) quaternion applied to s * n_i.
     const float* q = a.quats + (size_t)g * 4;
     const float n = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
@@ -224,11 +246,11 @@ __global__ void __launch_bounds__(kDT) densify_scatter_kernel(const DensArgs a) 
   __syncthreads();
   const int nrows = min(kDT, a.P - g0);
   const float shrink = logf(1.0f / (0.8f * (float)kSplitN));
-  for (int t = 0; t < a.nattrs; ++t) {
-    const AttrDev& at = a.attrs[t];
-    if (at.elem_bytes == 4) move_attr<float>(at, sm, g0, nrows, shrink);
-    else move_attr<uint16_t>(at, sm, g0, nrows, shrink);
-  }
+  if (at.role == FE_ATTR_MEANS || at.role == FE_ATTR_LOG_SCALES) move_attr<float, true>(at, sm, g0, nrows, shrink);
+  else if (at.unit == 16) move_attr<uint4, false>(at, sm, g0, nrows, shrink);
+  else if (at.unit == 8) move_attr<uint2, false>(at, sm, g0, nrows, shrink);
+  else if (at.unit == 4) move_attr<uint32_t, false>(at, sm, g0, nrows, shrink);
+  else move_attr<uint16_t, false>(at, sm, g0, nrows, shrink);
 }
 
 __global__ void reset_opacity_kernel(float* logits, int64_t P, float cap) {
@@ -308,7 +330,17 @@ extern "C" fe_status fe_densify(const fe_densify_args* args, int64_t* new_P, voi
       return FE_ERR_INVALID_ARG;
     if ((at.role == FE_ATTR_MEANS || at.role == FE_ATTR_LOG_SCALES) && (at.width != 3 || at.elem_bytes != 4))
       return FE_ERR_INVALID_ARG;
-    a.attrs[t] = AttrDev{at.src, at.dst, at.width, at.elem_bytes, at.role};
+    // Widest access that every row start of src and dst allows.
+    const size_t row = (size_t)at.width * at.elem_bytes;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(at.src) | reinterpret_cast<uintptr_t>(at.dst);
+    int unit = at.elem_bytes;
+    if (at.role == FE_ATTR_COPY || at.role == FE_ATTR_STATE)
+      for (int u : {16, 8, 4})
+        if (u > unit && row % u == 0 && base % u == 0) {
+          unit = u;
+          break;
+        }
+    a.attrs[t] = AttrDev{at.src, at.dst, at.width, at.elem_bytes, at.role, unit, (int)(row / unit)};
   }
   const int nblk = ceil_blocks(P, kDT);
   unsigned char* ws = static_cast<unsigned char*>(workspace);
@@ -318,7 +350,7 @@ extern "C" fe_status fe_densify(const fe_densify_args* args, int64_t* new_P, voi
   a.new_P = new_P;
   densify_decide_kernel<<<nblk, kDT, 0, st>>>(a);
   densify_scan_kernel<<<1, 1024, 0, st>>>(a, nblk);
-  densify_scatter_kernel<<<nblk, kDT, 0, st>>>(a);
+  densify_scatter_kernel<<<dim3(nblk, a.nattrs), kDT, 0, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
 
