@@ -700,18 +700,20 @@ def run_micro(args, cfg):
     clk = clocks.stop()
     ms = statistics.median(a.elapsed_time(b) for a, b in ev)
     extra = {}
+    if args.micro in ("densify", "fst") and not args.no_cpu_baseline:
+        extra["cpu_baseline"] = micro_oracle(args.micro, cfg, P, D)
     if args.micro == "densify":
         # Each input row read once, each output row written once, plus the
         # statistics (accum, count) of every Gaussian.
         n = int(new_P.item())
         nbytes = row_bytes * (P + n) + 8 * P
-        extra = {"P": P, "new_P": n, "row_bytes": row_bytes}
+        extra.update({"P": P, "new_P": n, "row_bytes": row_bytes})
     if args.micro == "fst":
         fl = 6.0 * fst_macs(fc["levels"], D) * P   # forward 2 M, reverse 4 M flop per Gaussian
         mhz = clk.get("sm_mhz") or 2070.0
         peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
         tf = fl / (ms * 1e-3) / 1e12
-        print(json.dumps({"micro": "fst", "workload": args.workload, "what": what, "ms": round(ms, 4),
+        print(json.dumps({"micro": "fst", "workload": args.workload, "what": what, "ms": round(ms, 4), **extra,
                           "roofline": {"bound": "alu", "achieved": round(tf, 3), "peak": round(peak, 2),
                                        "unit": "TFLOP/s", "frac": round(tf / peak, 4)},
                           "steps": args.steps, "warmup": args.warmup, "clocks": clk}))
@@ -723,6 +725,43 @@ def run_micro(args, cfg):
                                                         "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
                                                         "peak_basis": basis},
                       "steps": args.steps, "warmup": args.warmup, "clocks": clk}))
+
+
+def micro_oracle(kind: str, cfg, P: int, D: int) -> dict:
+    """The FP64 oracle timed on the host on the micro benchmark's inputs: the
+    whole densify of the P Gaussians' streams (numpy, one thread), or the
+    full FST module's forward + reverse on a bounded sample of Gaussians,
+    scaled to P (numpy; BLAS threads for the layer products)."""
+    from paper_2503_06161_gb300 import synth
+    if kind == "densify":
+        from oracle import density as DN
+        sc = synth.make_scene(P, D, cfg["lo"], cfg["hi"], seed=0)
+        acc, cnt, nrm = synth.make_density_stats(P)
+        params = dict(means=sc.means, log_scales=sc.log_scales, quats=sc.quats, opacity_logits=sc.opacity_logits,
+                      sh=sc.sh.reshape(P, 16, 3), feat=sc.feat, sh_store=sc.sh.reshape(P, 16, 3), feat_store=sc.feat)
+        state = {k + s: params[k] for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "feat")
+                 for s in (".m", ".v")}
+        extent = 0.5 * float(np.linalg.norm(np.subtract(cfg["hi"], cfg["lo"])))
+        t0 = time.perf_counter()
+        DN.densify(params, state, acc, cnt, nrm, 2e-4, 0.01 * extent, 0.005)
+        dt = time.perf_counter() - t0
+        return {"value": round(dt * 1e3, 2), "unit": "ms", "cores": 1, "kind": "oracle",
+                "sample": f"FP64 numpy densify of all {P} Gaussians' streams (same statistics and draws)"}
+    from oracle import fst as OF
+    fc = cfg.get("fst", dict(levels=4, rs=64, rt=100))
+    n = min(P, 4000)
+    sc = synth.make_scene(n, D, cfg["lo"], cfg["hi"], seed=0)
+    planes, mlp = synth.make_fst(fc["levels"], fc["rs"], fc["rt"], D, seed=1)
+    pl = OF.unpack_planes(planes, fc["levels"], fc["rs"], fc["rt"])
+    ly = OF.unpack_mlp(mlp, fc["levels"], D)
+    rng = np.random.default_rng(0)
+    up = [rng.normal(size=s) for s in ((n, 3), (n, 4), (n, 3), (n,), (n, D))]
+    t0 = time.perf_counter()
+    out = OF.forward(pl, ly, sc.means.astype(np.float64), 0.5, cfg["lo"], cfg["hi"], fc["levels"], fc["rs"], fc["rt"])
+    OF.backward(pl, ly, out["state"], *up)
+    dt = (time.perf_counter() - t0) * P / n
+    return {"value": round(dt * 1e3, 1), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 numpy forward + reverse of {n} Gaussians, scaled to {P} (BLAS may use every core)"}
 
 
 # ---------------------------------------------------------------------------
