@@ -519,7 +519,30 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
         }
       }
       __syncwarp();
-      if (jact) {
+      if (K::JPL == 2 && jact && __popc(jact) <= 16) {
+        // At most 16 active entries: lane pair jg takes the jg-th active
+        // entry, so one pass covers them all (P rows of inactive entries
+        // are left unwritten: the combine reads only active ones).
+        constexpr int CP2 = K::CPL / 2;
+        const int jg = lane >> 1, cg = lane & 1;
+        const bool has = jg < __popc(jact);
+        const int jl = has ? (int)__fns(jact, 0, jg + 1) : 0;
+        float2 acc[CP2];
+#pragma unroll
+        for (int c = 0; c < CP2; ++c) acc[c] = make_float2(0.0f, 0.0f);
+#pragma unroll 4
+        for (int p = 0; p < 32; ++p) {
+          const float wv = has ? slice[p * WS + jl] : 0.0f;
+          const float2* gr = reinterpret_cast<const float2*>(s_G + (warp * 32 + p) * GS + cg * K::CPL);
+#pragma unroll
+          for (int c = 0; c < CP2; ++c) acc[c] = __ffma2_rn(make_float2(wv, wv), gr[c], acc[c]);
+        }
+        __syncwarp();
+        if (has) {
+#pragma unroll
+          for (int c = 0; c < CP2; ++c) *reinterpret_cast<float2*>(slice + jl * NC + cg * K::CPL + 2 * c) = acc[c];
+        }
+      } else if (jact) {
         // P[j][c] = sum over the warp's pixels of w[p][j] * G[p][c], channel
         // pairs in packed FMAs.
         constexpr int CP2 = K::CPL / 2;
