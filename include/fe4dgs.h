@@ -392,7 +392,8 @@ fe_status fe_fst_backward(const fe_fst *fst, int P, const float *means, float t,
  * channels of the squared difference of neighbouring nodes along each of
  * its two axes, summed over planes and axes, times `weight`.  Writes the
  * weighted loss to *loss (one device float) and ADDS weight * dL_TV/dplanes
- * to d_planes (so it composes with fe_fst_backward's plane gradients).
+ * to d_planes (so it composes with fe_fst_backward's plane gradients);
+ * d_planes must not overlap the planes (FE_ERR_INVALID_ARG).
  * scratch: device array of at least 1024 floats.  Deterministic.
  * Asynchronous on `stream`. */
 fe_status fe_fst_tv(const fe_fst *fst, float weight, float *loss, float *d_planes, float *scratch, void *stream);

@@ -1318,6 +1318,13 @@ extern "C" fe_status fe_fst_tv(const fe_fst* fst, float weight, float* loss, flo
   FstGeom g;
   if (!fst || !make_geom(fst, 0, g)) return FE_ERR_INVALID_ARG;
   if (!fst->planes || !loss || !d_planes || !scratch) return FE_ERR_INVALID_ARG;
+  {
+    // The gradient array must not overlap the planes (the kernel reads the
+    // planes while it updates the gradient).
+    const uintptr_t p0 = reinterpret_cast<uintptr_t>(fst->planes), d0 = reinterpret_cast<uintptr_t>(d_planes);
+    const uintptr_t n = (uintptr_t)plane_floats(g) * sizeof(float);
+    if (p0 < d0 + n && d0 < p0 + n) return FE_ERR_INVALID_ARG;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   TvArgs a{};
   a.g = g;

@@ -156,7 +156,12 @@ def test_fst_sizes_and_host_side_status_codes(lib):
     assert lib.fe_fst_forward(ctypes.byref(f), 1, *args, 0, 0.5, *args, ws, 1 << 30, 1, None) == 1  # NULLs
     f.D = 24
     assert lib.fe_fst_forward(ctypes.byref(f), 1, *args, 0, 0.5, *args, ws, 1 << 30, 1, None) == 4
-    f.D = 32
+    f.bbox_max[1] = 1.0
+    f.D, f.planes = 32, 1 << 20
+    n_pl = lib.fe_fst_plane_floats(2, 8, 6)
+    for d in (1 << 20, (1 << 20) + 4 * (n_pl - 1), (1 << 20) - 4 * (n_pl - 1)):   # d_planes overlapping the planes
+        assert lib.fe_fst_tv(ctypes.byref(f), 0.03, ws, ctypes.c_void_p(d), ws, None) == 1
+    assert lib.fe_fst_tv(ctypes.byref(f), 0.03, None, ctypes.c_void_p(1 << 24), ws, None) == 1      # NULL loss
     f.bbox_max[1] = -1.0                                                 # empty box
     assert lib.fe_fst_forward(ctypes.byref(f), 1, *args, 0, 0.5, *args, ws, 1 << 30, 1, None) == 1
 
