@@ -390,24 +390,30 @@ def run_ours(args, world, rank, local):
 
     # ---- forward-only FPS (rendering, the paper's speed metric): a
     # forward-only workspace (no reverse-pass state), as inference uses.
-    frast = Rasterizer(P, D, W, H, max_dups=rast.capacity, device=dev, auto_grow=False, forward_only=True)
-    for _ in range(2):
-        frast.forward(scene, cam, deform, t, out=out, feat_bf16=feat_bf)
-    if graph_ms is not None:
-        fwd_only_ms, _ = graphed(lambda: frast.forward(scene, cam, deform, t, out=out, feat_bf16=feat_bf),
-                                 max(3, K_steps))
-    else:
+    def fwd_time(df_obj, capacity):
+        frast = Rasterizer(P, D, W, H, max_dups=capacity, device=dev, auto_grow=False, forward_only=True)
+        for _ in range(2):
+            frast.forward(scene, cam, df_obj, t, out=out, feat_bf16=feat_bf)
+        if frast.stats(raise_on_error=False)["device_errors"]:
+            raise RuntimeError("forward-only rasterizer overflowed its duplicate list")
+        if graph_ms is not None:
+            return graphed(lambda: frast.forward(scene, cam, df_obj, t, out=out, feat_bf16=feat_bf),
+                           max(3, K_steps))[0]
         fwd_only = []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for _ in range(max(3, K_steps)):
             flush.zero_()
             e0.record(stream)
-            frast.forward(scene, cam, deform, t, out=out, feat_bf16=feat_bf)
+            frast.forward(scene, cam, df_obj, t, out=out, feat_bf16=feat_bf)
             e1.record(stream)
             torch.cuda.synchronize()
             fwd_only.append(e0.elapsed_time(e1))
-        fwd_only_ms = statistics.mean(fwd_only)
-    del frast
+        return statistics.mean(fwd_only)
+
+    fwd_only_ms = fwd_time(deform, rast.capacity)
+    # The same forward without the deformation query (the canonical,
+    # static Gaussians): the rendering cost alone.
+    static_ms = fwd_time(None, int(rast.capacity * 1.25) + 4096) if deform is not None else fwd_only_ms
 
     # ---- roofline of the dominant kernel
     clock_mhz = clk.get("sm_mhz") or 2070.0
@@ -587,6 +593,7 @@ def run_ours(args, world, rank, local):
         "timing": "one CUDA-graph replay per step" if graph_ms is not None else "eager launches",
         "eager_ms_per_step": round(eager_ms, 4),
         "fwd_fps": round(world * 1000.0 / fwd_only_ms, 2), "fwd_ms": round(fwd_only_ms, 4),
+        "fwd_fps_no_deform": round(world * 1000.0 / static_ms, 2),
         "fwd_ms_in_step": round(fwd_ms, 4),
         "K": int(K), "visible": nvis, "pairs": {"visits": visits, "blended": contribs,
                                                   "visits_per_pixel": round(visits / HW, 1)},
