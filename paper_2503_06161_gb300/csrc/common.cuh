@@ -172,6 +172,17 @@ __host__ __device__ inline bool pixel_rect(float u, float v, int r, int W, int H
   return true;
 }
 
+// Pixel of thread `tid` inside a tile of tw x th = 256 pixels: each warp
+// covers an 8 x 4 block of pixels (lane l at (l % 8, l / 8)), blocks laid
+// row-major over the tile.  A compact warp footprint means fewer warps that
+// a Gaussian's square only partly covers, so fewer idle lanes when a warp
+// blends or differentiates an entry.
+__device__ __forceinline__ void tile_pixel(int tid, int tw, int& lx, int& ly) {
+  const int w = tid >> 5, l = tid & 31, bpr = tw >> 3;  // 8-wide blocks per tile row
+  lx = ((w % bpr) << 3) + (l & 7);
+  ly = ((w / bpr) << 2) + (l >> 3);
+}
+
 // alpha of record `rec` at pixel centre (pxc, pyc); one evaluation order,
 // shared by the forward and reverse kernels so both take the same skip,
 // clamp and inclusion decisions.  Returns false when the pair is skipped.

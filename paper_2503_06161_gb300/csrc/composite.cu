@@ -82,7 +82,9 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
   float* s_wide = reinterpret_cast<float*>(smem + 2 * (size_t)sbytes);
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-  const int px = tx * a.tw + tid % a.tw, py = ty * a.th + tid / a.tw;
+  int lx, ly;
+  tile_pixel(tid, a.tw, lx, ly);
+  const int px = tx * a.tw + lx, py = ty * a.th + ly;
   const bool inside = px < a.W && py < a.H;
   const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
   const uint2 rg = a.ranges[tile];
@@ -316,7 +318,9 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-  const int px = tx * a.tw + tid % a.tw, py = ty * a.th + tid / a.tw;
+  int lx, ly;
+  tile_pixel(tid, a.tw, lx, ly);
+  const int px = tx * a.tw + lx, py = ty * a.th + ly;
   const bool inside = px < a.W && py < a.H;
   const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
   const size_t HW = (size_t)a.W * a.H, pix = inside ? (size_t)py * a.W + px : 0;
