@@ -301,7 +301,6 @@ template <int D>
 __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kernel(const CompositeArgs a) {
   using K = BwdCfg<D>;
   constexpr int B = K::B, NC = K::NC, GS = K::GS, WS = K::WS, NP = partial_stride(D);
-  constexpr int NV = kPartialScalars + D;  // values per row
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ int s_abort;
@@ -587,23 +586,45 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
     // some pixel of the tile blended (the other rows stay unwritten and
     // unflagged, i.e. zero).
     const uint32_t* se = s_e + (k & 1) * B;
-    uint32_t bm = 0;
+    uint32_t jm[8], bm = 0;
 #pragma unroll
-    for (int w8 = 0; w8 < 8; ++w8) bm |= s_jact[w8];
+    for (int w8 = 0; w8 < 8; ++w8) {
+      jm[w8] = s_jact[w8];
+      bm |= jm[w8];
+    }
     const int nact = __popc(bm);
-    for (int item = tid; item < nact * NV; item += kThreads) {
-      // q: 0..5 geometric terms, 6..9 rgb/depth, 10.. features; row index
-      // puts the features first.
-      const int ja = item / NV, q = item - ja * NV;
+    // One item = four consecutive columns of an active entry's partial row
+    // [features | du dv dA dB dCc dopacity | r g b | depth | 0 0]: the warp
+    // partials summed in warp order, one 16-byte store.
+    constexpr int NQ = D / 4 + 3;
+    for (int item = tid; item < nact * NQ; item += kThreads) {
+      const int ja = item / NQ, q4 = item - ja * NQ;
       const int j = (int)__fns(bm, 0, ja + 1);  // the ja-th active entry
-      float acc = 0.0f;
+      float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
       for (int w8 = 0; w8 < 8; ++w8) {
-        if ((s_jact[w8] >> j) & 1u)
-          acc += q < 6 ? s_geo[(w8 * B + j) * 8 + q] : s_slice[w8 * K::SLICE + j * NC + (q - 6)];
+        if ((jm[w8] >> j) & 1u) {
+          const float* sl = s_slice + w8 * K::SLICE + j * NC;  // rgb, depth, features
+          const float* ge = s_geo + (w8 * B + j) * 8;          // six geometric terms
+          float4 v;
+          if (q4 < D / 4) {
+            v = *reinterpret_cast<const float4*>(sl + 4 + 4 * q4);
+          } else if (q4 == D / 4) {
+            v = *reinterpret_cast<const float4*>(ge);
+          } else if (q4 == D / 4 + 1) {
+            const float2 g2 = *reinterpret_cast<const float2*>(ge + 4), c2 = *reinterpret_cast<const float2*>(sl);
+            v = make_float4(g2.x, g2.y, c2.x, c2.y);
+          } else {
+            const float2 c2 = *reinterpret_cast<const float2*>(sl + 2);
+            v = make_float4(c2.x, c2.y, 0.0f, 0.0f);
+          }
+          acc.x += v.x;
+          acc.y += v.y;
+          acc.z += v.z;
+          acc.w += v.w;
+        }
       }
-      const int col = q < kPartialScalars ? D + q : q - kPartialScalars;
-      if ((int64_t)se[j] < a.cap) a.partials[(size_t)se[j] * NP + col] = acc;
+      if ((int64_t)se[j] < a.cap) *reinterpret_cast<float4*>(a.partials + (size_t)se[j] * NP + 4 * q4) = acc;
     }
     if (tid < nb && ((bm >> tid) & 1u) && (int64_t)se[tid] < a.cap)
       atomicOr(a.pflags + (se[tid] >> 5), 1u << (se[tid] & 31u));
