@@ -612,6 +612,18 @@ __device__ __forceinline__ void outer_tiles(const float* s_d, int ds, const floa
   const int nog = (NO + TO - 1) / TO, ntile = nog * (NI / 8);
   for (int tile = threadIdx.x; tile < ntile; tile += kFThreads) {
     const int o0 = (tile % nog) * TO, i0 = (tile / nog) * 8;
+    // The block's partial rows of this tile are loaded before the product,
+    // so their L2 round trip overlaps it.
+    float4 prev[TO][2];
+#pragma unroll
+    for (int r = 0; r < TO; ++r) {
+      prev[r][0] = prev[r][1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (!first && o0 + r < NO) {
+        const float4* row = reinterpret_cast<const float4*>(pw + (size_t)(o0 + r) * ldw + i0);
+        prev[r][0] = row[0];
+        prev[r][1] = row[1];
+      }
+    }
     float2 acc[TO][4];
 #pragma unroll
     for (int r = 0; r < TO; ++r)
@@ -640,8 +652,8 @@ __device__ __forceinline__ void outer_tiles(const float* s_d, int ds, const floa
         acc[r][3] = __ffma2_rn(dd, make_float2(x1.z, x1.w), acc[r][3]);
       }
     }
-    // Read-modify-write of the block's partial one tile row at a time: the
-    // row's two 16-byte loads are issued together, then added and stored.
+    // Partial += this chunk's sums (the partial loaded above; zero for the
+    // block's first chunk, whose sums are stored as they are).
 #pragma unroll
     for (int r = 0; r < TO; ++r) {
       if (o0 + r < NO) {
@@ -649,7 +661,7 @@ __device__ __forceinline__ void outer_tiles(const float* s_d, int ds, const floa
         float4 v0 = make_float4(acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y);
         float4 v1 = make_float4(acc[r][2].x, acc[r][2].y, acc[r][3].x, acc[r][3].y);
         if (!first) {
-          const float4 a0 = row[0], a1 = row[1];
+          const float4 a0 = prev[r][0], a1 = prev[r][1];
           v0.x += a0.x; v0.y += a0.y; v0.z += a0.z; v0.w += a0.w;
           v1.x += a1.x; v1.y += a1.y; v1.z += a1.z; v1.w += a1.w;
         }
