@@ -453,13 +453,14 @@ typedef struct {
   int64_t capacity;                  /* rows of every dst; must be >= 2 P */
 } fe_densify_args;
 
-/* Device workspace of fe_densify for P Gaussians. */
+/* Device workspace of fe_densify for P Gaussians (pass it 16-byte aligned). */
 size_t fe_densify_workspace_size(int P);
 
 /* Writes every attribute's densified rows to its dst and the new Gaussian
  * count to *new_P (one device int64).  The result is deterministic (fixed
  * scan order).  FE_ERR_INVALID_ARG for NULL pointers, unaligned float
- * arrays or capacity < 2 P; FE_ERR_WORKSPACE for a small workspace.
+ * arrays, a workspace that is not 16-byte aligned or capacity < 2 P;
+ * FE_ERR_WORKSPACE for a small workspace.
  * Asynchronous on `stream`. */
 fe_status fe_densify(const fe_densify_args *args, int64_t *new_P, void *workspace, size_t workspace_bytes,
                      void *stream);

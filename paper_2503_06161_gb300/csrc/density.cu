@@ -297,6 +297,7 @@ extern "C" fe_status fe_densify(const fe_densify_args* args, int64_t* new_P, voi
   const int P = args->P;
   if (args->capacity < (int64_t)kSplitN * P) return FE_ERR_INVALID_ARG;
   if (!workspace || workspace_bytes < fe_densify_workspace_size(P)) return FE_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(workspace) % 16) return FE_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (P == 0) return cudaMemsetAsync(new_P, 0, sizeof(int64_t), st) == cudaSuccess ? FE_OK : FE_ERR_CUDA;
   if (!args->means || !args->log_scales || !args->quats || !args->opacity_logits || !args->accum || !args->count ||

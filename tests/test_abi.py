@@ -188,6 +188,7 @@ def test_density_host_side_status_codes(lib):
     assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
     a.capacity = 20
     assert lib.fe_densify(ctypes.byref(a), new_p, ws, 16, None) == 3           # workspace
+    assert lib.fe_densify(ctypes.byref(a), new_p, ctypes.c_void_p(base + 8), n_ws, None) == 1   # unaligned
     a.nattrs = 0
     assert lib.fe_densify(ctypes.byref(a), new_p, ws, n_ws, None) == 1
     a.nattrs = 33
