@@ -87,6 +87,38 @@ def test_densify_bf16_rows_are_copied_bitwise():
     assert np.array_equal(got_p["feat"], ref_p["feat"])
 
 
+def test_densify_every_access_width():
+    """Streams whose rows take every access width of the scatter: 16-byte
+    (SH), 8-byte (float32 pairs, four bf16), 4-byte (odd float32 widths,
+    including one wider than a block pass of 256 units), 2-byte (three bf16);
+    copies and optimiser state bit-exact against the oracle."""
+    P = 3001
+    params, state, accum, count, normals = _inputs(P, seed=5)
+    rng = np.random.default_rng(11)
+    params["pair"] = rng.normal(size=(P, 2)).astype(np.float32)
+    params["wide"] = rng.normal(size=(P, 257)).astype(np.float32)
+    state["s_pair"] = rng.normal(size=(P, 2)).astype(np.float32)
+    state["s_wide"] = rng.normal(size=(P, 257)).astype(np.float32)
+    dev = "cuda"
+    t = {k: torch.as_tensor(v, device=dev).contiguous() for k, v in params.items()}
+    bf = {"b3": torch.randn(P, 3, generator=torch.Generator().manual_seed(1)).to(torch.bfloat16),
+          "b4": torch.randn(P, 4, generator=torch.Generator().manual_seed(2)).to(torch.bfloat16)}
+    t.update({k: v.to(dev) for k, v in bf.items()})
+    s = {k: torch.as_tensor(v, device=dev).contiguous() for k, v in state.items()}
+    st = density.DensityStats(P, dev)
+    st.accum.copy_(torch.as_tensor(accum))
+    st.count.copy_(torch.as_tensor(count))
+    p2, s2, n = density.densify(t, s, st, torch.as_tensor(normals, device=dev), THRESH, DENSE, MIN_OP)
+    torch.cuda.synchronize()
+    ref_in = dict(params, **{k: v.float().numpy() for k, v in bf.items()})
+    ref_p, ref_s, d = DN.densify(ref_in, state, accum, count, normals, THRESH, DENSE, MIN_OP, precision="f32")
+    assert n == ref_p["means"].shape[0] and set(np.unique(d).tolist()) == {-1, 0, 1, 2}
+    for k in ("pair", "wide", "b3", "b4", "quats", "opacity_logits", "sh", "feat"):
+        assert np.array_equal(p2[k].float().cpu().numpy(), ref_p[k]), k
+    for k in state:
+        assert np.array_equal(s2[k].cpu().numpy(), ref_s[k]), k
+
+
 @pytest.mark.parametrize("case", ["all_pruned", "all_split", "all_cloned", "none_selected"])
 def test_densify_degenerate_cases(case):
     P = 1000
