@@ -80,6 +80,8 @@ def densify(params: dict, state: dict, stats: DensityStats, normals: torch.Tenso
     dev = params["means"].device
     new_P = torch.zeros(1, dtype=torch.int64, device=dev)
     ws = torch.empty(_lib.fe_densify_workspace_size(P), dtype=torch.uint8, device=dev)
+    # One call moves at most 32 streams; more streams take further calls,
+    # each repeating the (deterministic) decision and scan.
     for i in range(0, len(attrs), 32):
         chunk = attrs[i:i + 32]
         _lib.fe_densify(P, params["means"], params["log_scales"], params["quats"], params["opacity_logits"],
