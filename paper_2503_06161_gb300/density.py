@@ -87,6 +87,8 @@ def densify(params: dict, state: dict, stats: DensityStats, normals: torch.Tenso
         _lib.fe_densify(P, params["means"], params["log_scales"], params["quats"], params["opacity_logits"],
                         stats.accum, stats.count, normals.contiguous(), grad_thresh, dense_scale, min_opacity, chunk,
                         2 * P, new_P, ws, stream)
+    if stream is not None and hasattr(stream, "synchronize"):
+        stream.synchronize()  # the count was written on that stream
     n = int(new_P.item())
     return ({k: v[:n] for k, v in out_p.items()}, {k: v[:n] for k, v in out_s.items()}, n)
 
