@@ -1082,7 +1082,7 @@ def oracle_rate(workload: str, budget_s: float):
     sc, cam, df = synth.config_inputs(workload)
     t = 0.5
     fixed = _oracle_sample(O, sc, cam, df, t, 1, 0)
-    n = 64
+    n = 2048  # pixels per step: enough that the per-pixel cost dominates the timing noise of the fixed part
     tn = _oracle_sample(O, sc, cam, df, t, n, 1)
     per_pix = max(tn - fixed, 1e-9) / (n - 1)
     n2 = int(max(64, min(cam.width * cam.height, (budget_s - fixed - tn) / max(per_pix, 1e-9) * 0.5)))
@@ -1108,7 +1108,7 @@ def run_reference(args, world, rank):
     sc, cam, df = synth.config_inputs(args.workload)
     t = args.t
     fixed = _oracle_sample(O, sc, cam, df, t, 1, 0)
-    n = 64
+    n = 2048  # pixels per step: enough that the per-pixel cost dominates the timing noise of the fixed part
     times = []
     for i in range(args.warmup + args.steps):
         dt = _oracle_sample(O, sc, cam, df, t, n, 10 + i)
