@@ -127,6 +127,66 @@ def test_backward_matches_oracle(P, levels, rs, rt, D):
     print(f"dropped {int(drop.sum())} of {P} Gaussians near a decision")
 
 
+def test_full_size_module_on_sampled_gaussians():
+    """The training workload's module and launch configuration (200,000
+    Gaussians, 4 levels of 64^3 x 100, D=32): offsets of a random sample of
+    Gaussians against the oracle, and the reverse pass with upstream
+    gradients on that sample only (the others contribute exact zeros), so the
+    oracle's plane and weight gradients of the sample are the exact
+    reference."""
+    P, levels, rs, rt, D = 200_000, 4, 64, 100, 32
+    sc = synth.make_scene(P, D, LO, HI, seed=0)
+    planes, mlp = synth.make_fst(levels, rs, rt, D, seed=1)
+    scene = GaussianScene.from_numpy(sc, "cuda")
+    fst = FSTDeform.from_numpy(planes, mlp, levels, rs, rt, D, LO, HI, P)
+    pl, ly = OF.unpack_planes(planes, levels, rs, rt), OF.unpack_mlp(mlp, levels, D)
+    t = 0.37
+    st = fst.forward(scene, t)
+    rng = np.random.default_rng(21)
+    idx = np.sort(rng.choice(P, 1500, replace=False))
+    out = OF.forward(pl, ly, np.asarray(sc.means, np.float64)[idx], t, LO, HI, levels, rs, rt)
+    torch.cuda.synchronize()
+    for got, canon, off in ((st.means, sc.means, out["dmu"]), (st.feat, sc.feat, out["dz"])):
+        # deformed = canonical + offset, rounded to float32 once: the offset
+        # is compared at its own scale plus that rounding
+        c = np.asarray(canon, np.float64)[idx]
+        g = got.float().cpu().numpy().astype(np.float64)[idx] - c
+        den = np.maximum(np.abs(off), np.sqrt(np.mean(off ** 2)))
+        assert np.all(np.abs(g - off) <= TOL_FEAT_REL * den + 1.2e-7 * np.abs(c + off))
+    rel, cell = OF.margins(out["state"])
+    keep = (rel >= RELU_MARGIN) & (cell >= CELL_MARGIN)
+    assert keep.sum() > 0.9 * len(idx)
+    up_s = _upstream(len(idx), D, seed=5)
+    for k in up_s:
+        up_s[k][~keep] = 0.0
+    full = {k: np.zeros((P,) + v.shape[1:]) for k, v in up_s.items()}
+    for k in full:
+        full[k][idx] = up_s[k]
+    dev = {k: torch.tensor(v, dtype=torch.float32, device="cuda").contiguous() for k, v in full.items()}
+    grads = dict(dev, means=dev["means"].clone())
+    fst.backward(scene, t, grads)
+    torch.cuda.synchronize()
+    ref = OF.backward(pl, ly, out["state"], up_s["means"], up_s["quats"], up_s["log_scales"],
+                      up_s["opacity_logits"], up_s["feat"])
+    gm = grads["means"].cpu().numpy().astype(np.float64)
+    assert rel_err(gm[idx], up_s["means"] + ref["mu"]) < TOL_GRAD_REL
+    others = np.ones(P, bool)
+    others[idx] = False
+    assert np.all(gm[others] == 0.0)
+    got_pl = fst.d_planes.cpu().numpy().astype(np.float64)
+    ref_pl = np.concatenate([x.ravel() for x in ref["planes"]])
+    # Only the sample's corners are touched (a few hundred thousand of 42.6 M
+    # entries); the others must stay exactly zero.  The touched ones are
+    # compared at the scale of the touched entries (the rms over all entries
+    # would shrink with the sample's sparsity).
+    nz = ref_pl != 0.0
+    assert np.all(got_pl[~nz] == 0.0)
+    assert rel_err(got_pl[nz], ref_pl[nz]) < TOL_GRAD_REL
+    got_w = fst.d_mlp.cpu().numpy().astype(np.float64)
+    ref_w = np.concatenate([np.concatenate([w.ravel(), b]) for w, b in ref["layers"]])
+    assert rel_err(got_w, ref_w) < TOL_GRAD_REL
+
+
 def test_weight_gradients_are_reproducible():
     P, levels, rs, rt, D = 5000, 2, 8, 6, 32
     sc, scene, fst, _, _ = _case(P, levels, rs, rt, D, seed=11)
