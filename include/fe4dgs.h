@@ -215,9 +215,10 @@ fe_status fe_l1_loss_grad(const float *pred, const float *target, int64_t n, int
  * per-block partial sums live in a 64 KiB array inside the library (one
  * per GPU that loads it, kept until the process exits); n may be at most
  * 33,554,432 elements (16384 blocks of 2048), else FE_ERR_WORKSPACE is
- * returned and nothing is launched.  The first call on a device looks up
- * that array's device address with the device current; make that first
- * call before any stream capture.  Every call shares the array: calls whose
+ * returned and nothing is launched.  Every call looks up that array's
+ * device address on the current device (a host-side lookup); the first
+ * lookup on a device may load the library's device code, so make the first
+ * call on each device before any stream capture.  Every call shares the array: calls whose
  * work overlaps on the GPU (different streams, or other threads) race and
  * must be ordered by the caller.  No device memory is allocated or freed. */
 fe_status fe_l1_loss_grad_noalloc(const float *pred, const float *target, int64_t n, int64_t rows, float *grad,

@@ -624,19 +624,24 @@ cudaError_t probe_fp32(int iters, double* flops, cudaStream_t st) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int blocks = sms * 8;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  // The sink's address first: nothing to release if the lookup fails.
   float* sink = nullptr;
-  cudaGetSymbolAddress(reinterpret_cast<void**>(&sink), g_probe_sink);
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&sink), g_probe_sink);
+  if (e != cudaSuccess) return e;
   if (!sink) return cudaErrorInvalidSymbol;
+  cudaEvent_t e0, e1;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
   fma_probe_kernel<<<blocks, 256, 0, st>>>(iters / 8 + 1, 1.0f, sink);  // warm-up
   cudaEventRecord(e0, st);
   fma_probe_kernel<<<blocks, 256, 0, st>>>(iters, 1.0f, sink);
   cudaEventRecord(e1, st);
-  cudaError_t e = cudaEventSynchronize(e1);
+  e = cudaEventSynchronize(e1);
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return e;

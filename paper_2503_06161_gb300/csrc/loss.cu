@@ -110,27 +110,19 @@ namespace {
 
 constexpr int kNoAllocBlocks = 16384;
 constexpr int64_t kNoAllocPerBlock = 2048;
-constexpr int kMaxDevices = 64;
-
 __device__ __align__(256) float g_l1_noalloc_scratch[kNoAllocBlocks];
 
-// Device address of g_l1_noalloc_scratch per device, looked up once per
-// device with that device current (the host-side name of the array is only
-// a stand-in, not a device address).
-float* g_scratch_addr[kMaxDevices] = {};
-
+// Device address of g_l1_noalloc_scratch on the current device.  The
+// host-side name of the array is only a stand-in, not a device address, so
+// every call asks the runtime (a host-side lookup; nothing is cached, so a
+// device reset or another thread cannot leave a stale address behind).  The
+// first lookup on a device may load the module: make the first call before
+// any stream capture.
 cudaError_t noalloc_scratch(float** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  float* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_l1_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_scratch_addr[dev]) {
-    float* p = nullptr;
-    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_l1_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

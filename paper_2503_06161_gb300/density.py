@@ -71,26 +71,50 @@ def densify(params: dict, state: dict, stats: DensityStats, normals: torch.Tenso
     if normals.shape != (P, 2, 3) or normals.dtype != torch.float32:
         raise ValueError("normals must be float32 [P, 2, 3]")
     role = dict(means=_lib.FE_ATTR_MEANS, log_scales=_lib.FE_ATTR_LOG_SCALES)
-    out_p = {k: torch.empty((2 * P,) + tuple(v.shape[1:]), dtype=v.dtype, device=v.device)
-             for k, v in params.items()}
-    out_s = {k: torch.empty((2 * P,) + tuple(v.shape[1:]), dtype=v.dtype, device=v.device)
-             for k, v in state.items()}
-    attrs = [(v, out_p[k], role.get(k, _lib.FE_ATTR_COPY)) for k, v in params.items()]
-    attrs += [(v, out_s[k], _lib.FE_ATTR_STATE) for k, v in state.items()]
     dev = params["means"].device
-    new_P = torch.zeros(1, dtype=torch.int64, device=dev)
-    ws = torch.empty(_lib.fe_densify_workspace_size(P), dtype=torch.uint8, device=dev)
-    # One call moves at most 32 streams; more streams take further calls,
-    # each repeating the (deterministic) decision and scan.
-    for i in range(0, len(attrs), 32):
-        chunk = attrs[i:i + 32]
-        _lib.fe_densify(P, params["means"], params["log_scales"], params["quats"], params["opacity_logits"],
-                        stats.accum, stats.count, normals.contiguous(), grad_thresh, dense_scale, min_opacity, chunk,
-                        2 * P, new_P, ws, stream)
-    if stream is not None and hasattr(stream, "synchronize"):
-        stream.synchronize()  # the count was written on that stream
+    st = _as_stream(stream, dev)
+    # The inputs were produced on the caller's current stream: the densify
+    # stream waits for it, and every buffer of this call is allocated and
+    # zeroed on the densify stream itself, so the zero fill of the count is
+    # ordered before the scan that writes it and no buffer returns to a pool
+    # while the scatter may still use it.
+    st.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(st):
+        out_p = {k: torch.empty((2 * P,) + tuple(v.shape[1:]), dtype=v.dtype, device=v.device)
+                 for k, v in params.items()}
+        out_s = {k: torch.empty((2 * P,) + tuple(v.shape[1:]), dtype=v.dtype, device=v.device)
+                 for k, v in state.items()}
+        attrs = [(v, out_p[k], role.get(k, _lib.FE_ATTR_COPY)) for k, v in params.items()]
+        attrs += [(v, out_s[k], _lib.FE_ATTR_STATE) for k, v in state.items()]
+        new_P = torch.zeros(1, dtype=torch.int64, device=dev)
+        ws = torch.empty(_lib.fe_densify_workspace_size(P), dtype=torch.uint8, device=dev)
+        nrm = normals.contiguous()
+        # One call moves at most 32 streams; more streams take further calls,
+        # each repeating the (deterministic) decision and scan.
+        for i in range(0, len(attrs), 32):
+            chunk = attrs[i:i + 32]
+            _lib.fe_densify(P, params["means"], params["log_scales"], params["quats"], params["opacity_logits"],
+                            stats.accum, stats.count, nrm, grad_thresh, dense_scale, min_opacity, chunk, 2 * P,
+                            new_P, ws, st)
+    st.synchronize()  # the count was written on the densify stream
+    cur = torch.cuda.current_stream(dev)
+    if st != cur:
+        # The outputs belong to the densify stream's pool; the caller goes on
+        # using them on its current stream.
+        for v in list(out_p.values()) + list(out_s.values()):
+            v.record_stream(cur)
     n = int(new_P.item())
     return ({k: v[:n] for k, v in out_p.items()}, {k: v[:n] for k, v in out_s.items()}, n)
+
+
+def _as_stream(stream, device):
+    """torch stream object for None (the current stream), a torch stream, or
+    a raw cudaStream_t handle (int)."""
+    if stream is None:
+        return torch.cuda.current_stream(device)
+    if isinstance(stream, torch.cuda.Stream):
+        return stream
+    return torch.cuda.ExternalStream(int(stream), device=device)
 
 
 def reset_opacity(logits: torch.Tensor, max_opacity: float = RESET_OPACITY, stream=None):

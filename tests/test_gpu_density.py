@@ -79,6 +79,40 @@ def test_densify_matches_oracle(P):
         assert (d64 != d).sum() <= P // 10000                       # the FP64 definition agrees
 
 
+@pytest.mark.parametrize("raw_handle", [False, True])
+def test_densify_on_a_side_stream_while_the_current_stream_is_busy(raw_handle):
+    # The inputs are written on the current stream, which is then kept busy;
+    # densify runs on another stream (a torch stream or its raw handle) and
+    # must see the finished inputs and return the right count and rows.
+    P = 20_000
+    params, state, accum, count, normals = _inputs(P, seed=4)
+    dev = "cuda"
+    src = {k: torch.as_tensor(v, device=dev).contiguous() for k, v in list(params.items()) + list(state.items())}
+    src_a, src_c = torch.as_tensor(accum, device=dev), torch.as_tensor(count, device=dev)
+    t = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
+    s = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in state.items()}
+    st = density.DensityStats(P, dev)
+    big = torch.randn(4096, 4096, device=dev)
+    torch.cuda.synchronize()
+    for _ in range(20):          # keep the current stream busy
+        big = big @ big
+        big = big / big.norm()
+    # The inputs land (device to device, on the current stream) after the busy work.
+    for k in t:
+        t[k].copy_(src[k])
+    for k in s:
+        s[k].copy_(src[k])
+    st.accum.copy_(src_a)
+    st.count.copy_(src_c)
+    side = torch.cuda.Stream()
+    p2, s2, n = density.densify(t, s, st, torch.as_tensor(normals, device=dev), THRESH, DENSE, MIN_OP,
+                                stream=side.cuda_stream if raw_handle else side)
+    torch.cuda.synchronize()
+    got_p = {k: v.float().cpu().numpy() for k, v in p2.items()}
+    got_s = {k: v.cpu().numpy() for k, v in s2.items()}
+    _check(params, state, accum, count, normals, got_p, got_s, n)
+
+
 def test_densify_bf16_rows_are_copied_bitwise():
     params, state, accum, count, normals = _inputs(3000)
     got_p, _, n, t, _ = _gpu(params, state, accum, count, normals, feat_bf16=True)

@@ -37,6 +37,30 @@ def test_noalloc_l1_matches_allocating_entry_point_twice():
         assert abs(a - b) <= REL_TOL * abs(b), (a, b)
 
 
+@pytest.mark.parametrize("rows,ch,offset", [(640 * 512 + 1, 3, 0), (1000, 3, 1), (5, 1, 0)])
+def test_noalloc_l1_tail_and_unaligned_inputs(rows, ch, offset):
+    # n not a multiple of 4 (scalar tail) and inputs one float past a 16-byte
+    # boundary (the scalar path throughout), against the allocating entry point.
+    rng = np.random.default_rng(rows + offset)
+    n = rows * ch
+    base_p = torch.as_tensor(rng.normal(size=n + offset).astype(np.float32), device="cuda")
+    base_t = torch.as_tensor(rng.normal(size=n + offset).astype(np.float32), device="cuda")
+    pred, tgt = base_p[offset:], base_t[offset:]
+    base_g = torch.empty(n + offset, device="cuda")
+    g = base_g[offset:]
+    g_ref = torch.empty(n, device="cuda")
+    l_ref = torch.zeros(1, device="cuda")
+    _lib.fe_l1_loss_grad(pred, tgt, rows, g_ref, l_ref, torch.empty(1024, device="cuda"))
+    for _ in range(2):
+        g.fill_(float("nan"))
+        l = torch.full((1,), float("nan"), device="cuda")
+        _lib.fe_l1_loss_grad_noalloc(pred, tgt, rows, g, l)
+        torch.cuda.synchronize()
+        assert torch.equal(g, g_ref)
+        a, b = float(l.item()), float(l_ref.item())
+        assert abs(a - b) <= REL_TOL * abs(b), (a, b)
+
+
 def test_noalloc_l1_rejects_sizes_past_its_array():
     L = _lib.load()
     x = torch.zeros(4, device="cuda")
