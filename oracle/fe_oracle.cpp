@@ -78,6 +78,7 @@ typedef struct {
   int *rect;         // [P,4] inclusive pixel rect x0,y0,x1,y1 (x0>x1: empty)
   double *rmargin;   // [P] distance of 3*sqrt(lambda) to the nearest integer, relative
   int *gflags;       // [P] bit0 rgb clamp, bit1 J clamp, bit2 relu, bit3 grid cell
+  int *gndec;        // [P] number of near-threshold gradient-only decisions (may be NULL)
 } or_gauss;
 
 }  // extern "C"
@@ -233,19 +234,32 @@ void deform_forward(const or_deform& df, const double mu[3], double t, DeformSta
   }
 }
 
+// Gradient-only decisions of the reverse pass that a caller takes the other
+// way (all false: the FP64 decisions).  flip_cell at an interior grid node
+// differentiates through the neighbouring cell; at a border node it toggles
+// the clamp (which zeroes the coordinate's gradient).
+struct DeformFlips {
+  const bool* relu1;
+  const bool* relu2;
+  const bool (*cell)[2];
+};
+
 // Gradient of the head outputs (ddelta[11]) back to the canonical mean.
-void deform_backward(const or_deform& df, const DeformState& s, const double ddelta[11], double dmu[3]) {
+void deform_backward(const or_deform& df, const DeformState& s, const double ddelta[11], double dmu[3],
+                     const DeformFlips* fl = nullptr) {
   const int C = df.C, R = df.R;
   double dh2[kHidden], dh1[kHidden], dfv[kMaxC];
   for (int c = 0; c < kHidden; ++c) {
     double acc = 0;
     for (int o = 0; o < 11; ++o) acc += df.wh[o * kHidden + c] * ddelta[o];
-    dh2[c] = s.pre2[c] > 0 ? acc : 0;
+    const bool on = (s.pre2[c] > 0) != (fl && fl->relu2[c]);
+    dh2[c] = on ? acc : 0;
   }
   for (int c = 0; c < kHidden; ++c) {
     double acc = 0;
     for (int o = 0; o < kHidden; ++o) acc += df.w2[o * kHidden + c] * dh2[o];
-    dh1[c] = s.pre1[c] > 0 ? acc : 0;
+    const bool on = (s.pre1[c] > 0) != (fl && fl->relu1[c]);
+    dh1[c] = on ? acc : 0;
   }
   for (int c = 0; c < C; ++c) {
     double acc = 0;
@@ -254,8 +268,22 @@ void deform_backward(const or_deform& df, const DeformState& s, const double dde
   }
   double dcoord[4] = {0, 0, 0, 0};
   for (int k = 0; k < 6; ++k) {
-    const double f1 = s.fr[k][0], f2 = s.fr[k][1];
-    const int i = s.i0[k][0], j = s.i0[k][1];
+    double f1 = s.fr[k][0], f2 = s.fr[k][1];
+    int i = s.i0[k][0], j = s.i0[k][1];
+    int clamped[2] = {s.clamped[k][0], s.clamped[k][1]};
+    for (int e = 0; e < 2; ++e) {
+      if (!(fl && fl->cell[k][e])) continue;
+      const double gp = s.pos[k][e];
+      const int n = (int)std::nearbyint(gp);
+      if (n <= 0 || n >= R - 1) {
+        clamped[e] = !clamped[e];
+      } else {
+        int& ie = e == 0 ? i : j;
+        double& fe = e == 0 ? f1 : f2;
+        ie = ie == n ? n - 1 : n;
+        fe = gp - ie;
+      }
+    }
     const double* P00 = df.planes + ((size_t)(k * R + i) * R + j) * C;
     const double* P10 = df.planes + ((size_t)(k * R + i + 1) * R + j) * C;
     const double* P01 = df.planes + ((size_t)(k * R + i) * R + j + 1) * C;
@@ -269,8 +297,8 @@ void deform_backward(const or_deform& df, const DeformState& s, const double dde
       dg1 += ds * ((1 - f2) * (P10[c] - P00[c]) + f2 * (P11[c] - P01[c]));
       dg2 += ds * ((1 - f1) * (P01[c] - P00[c]) + f1 * (P11[c] - P10[c]));
     }
-    if (!s.clamped[k][0]) dcoord[kPair[k][0]] += dg1 * 0.5 * (R - 1);
-    if (!s.clamped[k][1]) dcoord[kPair[k][1]] += dg2 * 0.5 * (R - 1);
+    if (!clamped[0]) dcoord[kPair[k][0]] += dg1 * 0.5 * (R - 1);
+    if (!clamped[1]) dcoord[kPair[k][1]] += dg2 * 0.5 * (R - 1);
   }
   for (int a = 0; a < 3; ++a) dmu[a] = dcoord[a] * 2.0 / (df.bbox_max[a] - df.bbox_min[a]);
 }
@@ -303,7 +331,25 @@ struct GState {
   double zerr;         // bound on the binary32 error of the camera-space depth
   int gflags;
   int visible;
+  double rnear;        // nearest integer to 3 sqrt(lambda_max) (radius-ceil decision)
+  // Gradient-only decisions within rounding of their threshold (rgb clamp,
+  // J clamp, ReLU, grid cell), in a fixed order: their number, and which of
+  // them the reverse pass takes the other way (bit k of gflip flips the
+  // k-th).  A binary32 evaluation may take either branch there.
+  int gndec;
+  uint64_t gflip;
+  bool flip_rgb[3], flip_jx, flip_jy;
+  bool flip_relu1[kHidden], flip_relu2[kHidden];
+  bool flip_cell[6][2];
 };
+
+// Records a near-threshold gradient decision; true when gflip takes it the
+// other way.
+bool gdecision(GState& st) {
+  const bool f = ((st.gflip >> st.gndec) & 1ull) != 0;
+  ++st.gndec;
+  return f;
+}
 
 void quat_to_rot(const double q[4], double Rm[9]) {
   const double w = q[0], x = q[1], y = q[2], z = q[3];
@@ -313,8 +359,9 @@ void quat_to_rot(const double q[4], double Rm[9]) {
 }
 
 void gaussian_forward(const or_scene& sc, const or_deform* df, const or_camera& cam, double t, int g,
-                      const double* geps, GState& st) {
+                      const double* geps, GState& st, uint64_t gflip = 0) {
   double delta[11] = {0};
+  st.gflip = gflip;
   st.has_deform = df && df->enabled;
   if (st.has_deform) {
     deform_forward(*df, sc.means + 3 * g, t, st.ds);
@@ -324,6 +371,11 @@ void gaussian_forward(const or_scene& sc, const or_deform* df, const or_camera& 
   }
   std::memcpy(st.ds.delta, delta, sizeof(delta));
   st.gflags = 0;
+  st.gndec = 0;
+  st.flip_rgb[0] = st.flip_rgb[1] = st.flip_rgb[2] = false;
+  st.flip_jx = st.flip_jy = false;
+  for (int o = 0; o < kHidden; ++o) st.flip_relu1[o] = st.flip_relu2[o] = false;
+  for (int k = 0; k < 6; ++k) st.flip_cell[k][0] = st.flip_cell[k][1] = false;
   // Eq. 6 reading: mu + d_mu; quaternion + d_q renormalised; log-scale + d_s;
   // opacity logit + d_o.
   for (int a = 0; a < 3; ++a) st.mu[a] = sc.means[3 * g + a] + delta[a];
@@ -387,7 +439,10 @@ void gaussian_forward(const or_scene& sc, const or_deform* df, const or_camera& 
     for (int k = 0; k < nb; ++k) acc += sc.sh[(size_t)g * 48 + 3 * k + ch] * st.Y[k];
     st.rgb_raw[ch] = acc;
     st.rgb[ch] = acc > 0 ? acc : 0;
-    if (geps && std::fabs(acc) < geps[0]) st.gflags |= 1;
+    if (geps && std::fabs(acc) < geps[0]) {
+      st.gflags |= 1;
+      st.flip_rgb[ch] = gdecision(st);
+    }
   }
   if (!(z > cam.znear)) return;
   // EWA (Eq. 9 of Sec. 3.3) with the affine Jacobian of the pinhole model at
@@ -399,8 +454,14 @@ void gaussian_forward(const or_scene& sc, const or_deform* df, const or_camera& 
   st.cly = st.ty < -limy || st.ty > limy;
   st.txc = std::min(limx, std::max(-limx, st.tx));
   st.tyc = std::min(limy, std::max(-limy, st.ty));
-  if (geps && (std::fabs(std::fabs(st.tx) - limx) < geps[1] * limx || std::fabs(std::fabs(st.ty) - limy) < geps[1] * limy))
+  if (geps && std::fabs(std::fabs(st.tx) - limx) < geps[1] * limx) {
     st.gflags |= 2;
+    st.flip_jx = gdecision(st);
+  }
+  if (geps && std::fabs(std::fabs(st.ty) - limy) < geps[1] * limy) {
+    st.gflags |= 2;
+    st.flip_jy = gdecision(st);
+  }
   st.J[0] = cam.fx / z; st.J[1] = 0; st.J[2] = -cam.fx * st.txc / z;
   st.J[3] = 0; st.J[4] = cam.fy / z; st.J[5] = -cam.fy * st.tyc / z;
   for (int r = 0; r < 2; ++r)
@@ -430,7 +491,8 @@ void gaussian_forward(const or_scene& sc, const or_deform* df, const or_camera& 
   const double lam = mid + std::sqrt(std::max(0.1, mid * mid - st.det));
   const double xr = 3.0 * std::sqrt(lam);
   st.radius = (int)std::ceil(xr);
-  st.rmargin = std::fabs(xr - std::nearbyint(xr)) / xr;
+  st.rnear = std::nearbyint(xr);
+  st.rmargin = std::fabs(xr - st.rnear) / xr;
   st.u = cam.fx * st.tx + cam.cx;
   st.v = cam.fy * st.ty + cam.cy;
   st.visible = 1;
@@ -448,14 +510,25 @@ void gaussian_forward(const or_scene& sc, const or_deform* df, const or_camera& 
     for (int o = 0; o < kHidden; ++o) { rms1 += st.ds.pre1[o] * st.ds.pre1[o]; rms2 += st.ds.pre2[o] * st.ds.pre2[o]; }
     rms1 = std::sqrt(rms1 / kHidden) + 1e-30; rms2 = std::sqrt(rms2 / kHidden) + 1e-30;
     for (int o = 0; o < kHidden; ++o)
-      if (std::fabs(st.ds.pre1[o]) < geps[2] * rms1 || std::fabs(st.ds.pre2[o]) < geps[2] * rms2) st.gflags |= 4;
+      if (std::fabs(st.ds.pre1[o]) < geps[2] * rms1) {
+        st.gflags |= 4;
+        st.flip_relu1[o] = gdecision(st);
+      }
+    for (int o = 0; o < kHidden; ++o)
+      if (std::fabs(st.ds.pre2[o]) < geps[2] * rms2) {
+        st.gflags |= 4;
+        st.flip_relu2[o] = gdecision(st);
+      }
     // Only the spatial coordinates carry a gradient (to the canonical mean);
     // the time coordinate of the xt, yt, zt planes does not.
     for (int k = 0; k < 6; ++k)
       for (int e = 0; e < 2; ++e) {
         if (kPair[k][e] == 3) continue;
         const double gp = st.ds.pos[k][e];
-        if (std::fabs(gp - std::nearbyint(gp)) < geps[3] * (df->R - 1)) st.gflags |= 8;
+        if (std::fabs(gp - std::nearbyint(gp)) < geps[3] * (df->R - 1)) {
+          st.gflags |= 8;
+          st.flip_cell[k][e] = gdecision(st);
+        }
       }
   }
 }
@@ -486,37 +559,88 @@ struct PixelResult {
   double T;
   int ncontrib, flags;
   uint64_t sig;
+  int ndec;  // near-threshold decisions met (see composite_pixel)
 };
 
+// Near-threshold decisions of one pixel, counted in the order they are met;
+// bit k of `flip` takes the k-th one the other way.
+struct PixelDecisions {
+  uint64_t flip;
+  int n;
+  bool take(bool natural) {
+    const bool f = ((flip >> n) & 1ull) != 0;
+    ++n;
+    return natural != f;
+  }
+};
+
+// Composites pixel (x, y).  With eps, every decision whose FP64 margin is
+// inside the binary32 error model is flagged and counted as a decision, in
+// this order: (1) inclusion of Gaussians near the edge of their square (by
+// index; the other branch puts a Gaussian inside the square out and one
+// outside in -- for a radius ceil near an integer n the ring n < m <= n + 1
+// is the part that changes); (2) the order of two possible contributors
+// (alpha >= 1/255 up to the skip margin) that are adjacent in depth order
+// with depths inside their binary32 error bounds (the other branch swaps
+// them); (3) per candidate, front to back, the alpha skip and then the
+// termination test.  A binary32 evaluation may take either branch of each;
+// `flip` (bit k: the k-th decision the other way) selects one of the
+// resulting results.  flip = 0 is the FP64 result.
 void composite_pixel(const or_scene& sc, const std::vector<GState>& gs, const or_camera& cam, const double* bg,
                      int x, int y, const double* eps, PixelResult& res, double* feat_out,
-                     std::vector<Contrib>* contribs) {
+                     std::vector<Contrib>* contribs, uint64_t flip = 0) {
   (void)cam;
   const double px = x + 0.5, py = y + 0.5;
   const int P = sc.P, D = sc.D;
   std::vector<int> cand;
   int flags = 0;
+  PixelDecisions dec{flip, 0};
   for (int g = 0; g < P; ++g) {
     const GState& s = gs[g];
     if (!s.visible) continue;
     const double dx = px - s.u, dy = py - s.v;
     const double m = std::max(std::fabs(dx), std::fabs(dy));
     const double r = s.radius;
-    if (m <= r) cand.push_back(g);
+    bool in = m <= r;
     if (eps) {
       // An inclusion decision only matters where the Gaussian would contribute.
       const bool near_edge = std::fabs(m - r) < eps[0] * (std::fabs(s.u) + std::fabs(s.v) + r);
-      const bool ring = s.rmargin < eps[1] && m > r - 1.0 - 1e-9 && m <= r + 1.0;
+      const bool ring = s.rmargin < eps[1] && m > s.rnear && m <= s.rnear + 1.0;
       if (near_edge || ring) {
         const double power = -0.5 * (s.conic[0] * dx * dx + s.conic[2] * dy * dy) - s.conic[1] * dx * dy;
-        if (s.o * std::exp(power) >= kAlphaMin * (1 - 1e-3)) flags |= kFlagIncl;
+        if (s.o * std::exp(power) >= kAlphaMin * (1 - 1e-3)) {
+          flags |= kFlagIncl;
+          in = dec.take(in);
+        }
       }
     }
+    if (in) cand.push_back(g);
   }
   std::sort(cand.begin(), cand.end(), [&](int i, int k) {
     if (gs[i].p[2] != gs[k].p[2]) return gs[i].p[2] < gs[k].p[2];
     return i < k;
   });
+  auto alpha_at = [&](int g) {
+    const GState& s = gs[g];
+    const double dx = px - s.u, dy = py - s.v;
+    const double power = -0.5 * (s.conic[0] * dx * dx + s.conic[2] * dy * dy) - s.conic[1] * dx * dy;
+    return power > 0 ? 0.0 : std::min(kAlphaMax, s.o * std::exp(power));
+  };
+  if (eps) {
+    // Order decisions among the possible contributors, front to back.
+    int prev = -1;
+    for (size_t ci = 0; ci < cand.size(); ++ci) {
+      if (alpha_at(cand[ci]) < kAlphaMin * (1 - eps[2])) continue;
+      if (prev >= 0) {
+        const GState& a = gs[cand[prev]];
+        const GState& b = gs[cand[ci]];
+        if (std::fabs(b.p[2] - a.p[2]) <= eps[4] * (a.zerr + b.zerr) && dec.take(false)) {
+          std::swap(cand[prev], cand[ci]);
+        }
+      }
+      prev = (int)ci;
+    }
+  }
   double T = 1.0, C[3] = {0, 0, 0}, Z = 0, sumw = 0;
   for (int k = 0; k < D; ++k) feat_out[k] = 0;
   int n = 0;
@@ -531,11 +655,19 @@ void composite_pixel(const or_scene& sc, const std::vector<GState>& gs, const or
     const double G = std::exp(power);
     const double oG = s.o * G;
     const double alpha = std::min(kAlphaMax, oG);
-    if (eps && std::fabs(alpha - kAlphaMin) < eps[2] * kAlphaMin) flags |= kFlagSkip;
-    if (alpha < kAlphaMin) continue;
+    bool skip = alpha < kAlphaMin;
+    if (eps && std::fabs(alpha - kAlphaMin) < eps[2] * kAlphaMin) {
+      flags |= kFlagSkip;
+      skip = dec.take(skip);
+    }
+    if (skip) continue;
     const double Tn = T * (1 - alpha);
-    if (eps && std::fabs(Tn - kTMin) < eps[3] * kTMin) flags |= kFlagTerm;
-    if (Tn < kTMin) break;
+    bool stop = Tn < kTMin;
+    if (eps && std::fabs(Tn - kTMin) < eps[3] * kTMin) {
+      flags |= kFlagTerm;
+      stop = dec.take(stop);
+    }
+    if (stop) break;
     if (eps && std::fabs(oG - kAlphaMax) < eps[5] * kAlphaMax) flags |= kFlagClamp;
     if (eps && prev_contrib >= 0) {
       // Two depths closer than their binary32 error bounds (times eps[4]) may
@@ -564,6 +696,7 @@ void composite_pixel(const or_scene& sc, const std::vector<GState>& gs, const or
   res.ncontrib = n;
   res.flags = flags;
   res.sig = sig;
+  res.ndec = dec.n;
 }
 
 void fill_gauss_out(const std::vector<GState>& gs, or_gauss* out) {
@@ -581,14 +714,15 @@ void fill_gauss_out(const std::vector<GState>& gs, or_gauss* out) {
     if (out->rect) for (int k = 0; k < 4; ++k) out->rect[4 * g + k] = s.rect[k];
     if (out->rmargin) out->rmargin[g] = s.rmargin;
     if (out->gflags) out->gflags[g] = s.gflags;
+    if (out->gndec) out->gndec[g] = s.gndec;
   }
 }
 
 void all_gaussians(const or_scene& sc, const or_deform* df, const or_camera& cam, double t, const double* geps,
-                   std::vector<GState>& gs) {
+                   std::vector<GState>& gs, const uint64_t* gflip = nullptr) {
   gs.resize(sc.P);
 #pragma omp parallel for schedule(dynamic, 256)
-  for (int g = 0; g < sc.P; ++g) gaussian_forward(sc, df, cam, t, g, geps, gs[g]);
+  for (int g = 0; g < sc.P; ++g) gaussian_forward(sc, df, cam, t, g, geps, gs[g], gflip ? gflip[g] : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -610,7 +744,7 @@ void gaussian_backward(const or_scene& sc, const or_deform* df, const or_camera&
   const int nb = (sc.sh_degree + 1) * (sc.sh_degree + 1);
   double ddir[3] = {0, 0, 0};
   for (int ch = 0; ch < 3; ++ch) {
-    const double gch = s.rgb_raw[ch] >= 0 ? drgb[ch] : 0.0;
+    const double gch = (s.rgb_raw[ch] >= 0) != s.flip_rgb[ch] ? drgb[ch] : 0.0;
     for (int k = 0; k < 16; ++k) {
       const double v = k < nb ? gch * s.Y[k] : 0.0;
       d_sh[(size_t)g * 48 + 3 * k + ch] = v;
@@ -663,7 +797,7 @@ void gaussian_backward(const or_scene& sc, const or_deform* df, const or_camera&
     dp[2] += -cam.fx / (z * z) * dJ[0] - cam.fy / (z * z) * dJ[4];
     dp[2] += cam.fx * s.txc / (z * z) * dJ[2] + cam.fy * s.tyc / (z * z) * dJ[5];
     double dtxc = -cam.fx / z * dJ[2], dtyc = -cam.fy / z * dJ[5];
-    double dtx = s.clx ? 0.0 : dtxc, dty = s.cly ? 0.0 : dtyc;
+    double dtx = (s.clx != 0) != s.flip_jx ? 0.0 : dtxc, dty = (s.cly != 0) != s.flip_jy ? 0.0 : dtyc;
     // Projected centre u = fx x/z + cx, v = fy y/z + cy.
     dtx += cam.fx * du;
     dty += cam.fy * dv;
@@ -707,7 +841,8 @@ void gaussian_backward(const or_scene& sc, const or_deform* df, const or_camera&
     for (int a = 0; a < 3; ++a) ddelta[7 + a] = dlogs[a];
     ddelta[10] = dlogit;
     double dgrid[3];
-    deform_backward(*df, s.ds, ddelta, dgrid);
+    const DeformFlips fl{s.flip_relu1, s.flip_relu2, s.flip_cell};
+    deform_backward(*df, s.ds, ddelta, dgrid, &fl);
     for (int a = 0; a < 3; ++a) dmu_total[a] += dgrid[a];
   }
   for (int a = 0; a < 3; ++a) d_means[3 * g + a] = dmu_total[a];
@@ -763,6 +898,54 @@ int or_render(const or_scene* sc, const or_deform* df, const or_camera* cam, dou
   return 0;
 }
 
+// Every result a binary32 evaluation may legitimately produce at each listed
+// pixel: the pixel is composited once per combination of its near-threshold
+// decisions (composite_pixel, eps required), at most 2^max_bits
+// combinations, and the distinct results (by contributor sequence) are
+// written, the FP64 one (flip = 0) first.  Per pixel i and result a <
+// max_alts: rgb [i][a][3] (with bg T), depth, alpha, feat [i][a][D], the
+// flip mask that produced it; nalts[i] = number written; ndec[i] = decisions
+// met by the FP64 result.
+int or_render_alts(const or_scene* sc, const or_deform* df, const or_camera* cam, double t, const double* bg,
+                   int npix, const int* pix, const double* eps, int max_bits, int max_alts, double* out_rgb,
+                   double* out_depth, double* out_alpha, double* out_feat, uint64_t* out_flip, int* out_nalts,
+                   int* out_ndec) {
+  if (!sc || !cam || !eps || sc->D > kMaxD || (df && df->enabled && df->C > kMaxC) || max_alts < 1 ||
+      max_bits < 0 || max_bits > 16)
+    return 1;
+  std::vector<GState> gs;
+  all_gaussians(*sc, df, *cam, t, nullptr, gs);
+  const int D = sc->D;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < npix; ++i) {
+    std::vector<double> f(D > 0 ? D : 1);
+    std::vector<uint64_t> sigs;
+    int seen = 0, na = 0, ndec0 = 0;
+    for (uint64_t mask = 0; mask < (1ull << std::min(seen, max_bits)) || mask == 0; ++mask) {
+      PixelResult r;
+      composite_pixel(*sc, gs, *cam, bg, pix[2 * i], pix[2 * i + 1], eps, r, f.data(), nullptr, mask);
+      if (mask == 0) ndec0 = r.ndec;
+      seen = std::max(seen, r.ndec);
+      // Bits past the decisions this combination met change nothing.
+      if (r.ndec < 64 && (mask >> r.ndec) != 0) continue;
+      if (std::find(sigs.begin(), sigs.end(), r.sig) != sigs.end()) continue;
+      sigs.push_back(r.sig);
+      if (na < max_alts) {
+        const size_t a = (size_t)i * max_alts + na;
+        for (int ch = 0; ch < 3; ++ch) out_rgb[3 * a + ch] = r.rgb[ch];
+        out_depth[a] = r.depth;
+        out_alpha[a] = r.alpha;
+        for (int k = 0; k < D; ++k) out_feat[a * D + k] = f[k];
+        out_flip[a] = mask;
+        ++na;
+      }
+    }
+    out_nalts[i] = na;
+    out_ndec[i] = ndec0;
+  }
+  return 0;
+}
+
 // Gradients of L = sum over the listed pixels of
 //   g_rgb . rgb + g_depth * depth + g_alpha * alpha + g_feat . feat
 // with respect to every canonical parameter (overwritten, all P rows).
@@ -770,15 +953,22 @@ int or_render(const or_scene* sc, const or_deform* df, const or_camera* cam, dou
 // [npix], g_feat [npix,D].
 // d_uv (optional, [P][2]): the gradient of the loss with respect to each
 // Gaussian's projected centre (u, v) in pixels.
+// Decision overrides (all optional): flip [npix] with eps takes pixel i's
+// near-threshold decisions the other way as in or_render_alts; gflip [P]
+// with geps takes Gaussian g's near-threshold gradient-only decisions (rgb
+// clamp, J clamp, ReLU, grid cell; counted by or_preprocess's gndec) the
+// other way, bit k for the k-th.
 int or_backward(const or_scene* sc, const or_deform* df, const or_camera* cam, double t, const double* bg,
                 int npix, const int* pix, const double* g_rgb, const double* g_depth, const double* g_alpha,
                 const double* g_feat, double* d_means, double* d_log_scales, double* d_quats, double* d_logits,
-                double* d_sh, double* d_feat, double* d_uv) {
+                double* d_sh, double* d_feat, double* d_uv, const double* eps, const uint64_t* flip,
+                const double* geps, const uint64_t* gflip) {
   if (!sc || !cam || sc->D > kMaxD || (df && df->enabled && df->C > kMaxC)) return 1;
+  if ((flip && !eps) || (gflip && !geps)) return 1;
   const int P = sc->P, D = sc->D;
   const int NS = 10;  // du dv dA dB dC dop drgb[3] ddepth
   std::vector<GState> gs;
-  all_gaussians(*sc, df, *cam, t, nullptr, gs);
+  all_gaussians(*sc, df, *cam, t, gflip ? geps : nullptr, gs, gflip);
   struct PixGrad { int g; double w; double v[NS]; };
   std::vector<std::vector<PixGrad>> per_pix(npix);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -786,7 +976,8 @@ int or_backward(const or_scene* sc, const or_deform* df, const or_camera* cam, d
     PixelResult r;
     std::vector<double> f(D > 0 ? D : 1);
     std::vector<Contrib> cs;
-    composite_pixel(*sc, gs, *cam, bg, pix[2 * i], pix[2 * i + 1], nullptr, r, f.data(), &cs);
+    composite_pixel(*sc, gs, *cam, bg, pix[2 * i], pix[2 * i + 1], flip ? eps : nullptr, r, f.data(), &cs,
+                    flip ? flip[i] : 0);
     const double* gr = g_rgb + 3 * i;
     const double* gf = g_feat + (size_t)i * D;
     const double gz = g_depth[i], ga = g_alpha[i];

@@ -94,7 +94,7 @@ class _Camera(ctypes.Structure):
 class _Gauss(ctypes.Structure):
     _fields_ = [("delta", _dp), ("uv", _dp), ("conic", _dp), ("opacity", _dp), ("depth", _dp),
                 ("rgb", _dp), ("rgb_raw", _dp), ("radius", _ip), ("rect", _ip),
-                ("rmargin", _dp), ("gflags", _ip)]
+                ("rmargin", _dp), ("gflags", _ip), ("gndec", _ip)]
 
 
 def _setup(L):
@@ -103,16 +103,21 @@ def _setup(L):
     L.or_render.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Deform), ctypes.POINTER(_Camera),
                             ctypes.c_double, _dp, ctypes.c_int, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _ip, _ip,
                             ctypes.POINTER(ctypes.c_uint64)]
+    _u64p = ctypes.POINTER(ctypes.c_uint64)
     L.or_backward.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Deform), ctypes.POINTER(_Camera),
                               ctypes.c_double, _dp, ctypes.c_int, _ip, _dp, _dp, _dp, _dp,
-                              _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+                              _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _u64p, _dp, _u64p]
+    L.or_render_alts.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Deform), ctypes.POINTER(_Camera),
+                                 ctypes.c_double, _dp, ctypes.c_int, _ip, _dp, ctypes.c_int, ctypes.c_int,
+                                 _dp, _dp, _dp, _dp, _u64p, _ip, _ip]
     L.or_tile_bin.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_float), _ip, ctypes.POINTER(ctypes.c_float),
                               ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
                               ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_longlong)]
     L.or_sh_eval.argtypes = [ctypes.c_int, _dp, _dp, _dp]
     L.or_deform_eval.argtypes = [ctypes.POINTER(_Deform), ctypes.c_int, _dp, ctypes.c_double, _dp, _dp]
-    for f in (L.or_preprocess, L.or_render, L.or_backward, L.or_tile_bin, L.or_sh_eval, L.or_deform_eval):
+    for f in (L.or_preprocess, L.or_render, L.or_render_alts, L.or_backward, L.or_tile_bin, L.or_sh_eval,
+              L.or_deform_eval):
         f.restype = ctypes.c_int
     L.or_num_threads.restype = ctypes.c_int
 
@@ -177,7 +182,8 @@ def _marshal(scene, camera, deform, keep: _Keep):
 
 def gaussians(scene, camera, deform=None, t: float = 0.0, geps=DEFAULT_GEPS) -> dict:
     """Per-Gaussian FP64 state: delta[P,11], uv, conic, opacity, depth, rgb,
-    rgb_raw, radius, rect, rmargin, gflags."""
+    rgb_raw, radius, rect, rmargin, gflags, gndec (number of near-threshold
+    gradient-only decisions, the bits a backward gflip may set)."""
     L = lib()
     keep = _Keep()
     sc, cam, df = _marshal(scene, camera, deform, keep)
@@ -187,10 +193,11 @@ def gaussians(scene, camera, deform=None, t: float = 0.0, geps=DEFAULT_GEPS) -> 
     out["radius"] = np.zeros(P, np.int32)
     out["rect"] = np.zeros((P, 4), np.int32)
     out["gflags"] = np.zeros(P, np.int32)
+    out["gndec"] = np.zeros(P, np.int32)
     g = _Gauss()
     for k in ("delta", "uv", "conic", "opacity", "depth", "rgb", "rgb_raw", "rmargin"):
         setattr(g, k, _ptr(out[k]))
-    for k in ("radius", "rect", "gflags"):
+    for k in ("radius", "rect", "gflags", "gndec"):
         setattr(g, k, _ptr(out[k], _ip))
     ge = keep.d(np.asarray(geps)) if geps is not None else None
     rc = L.or_preprocess(ctypes.byref(sc), ctypes.byref(df), ctypes.byref(cam), float(t), _ptr(ge), ctypes.byref(g))
@@ -228,12 +235,43 @@ def render(scene, camera, deform=None, t: float = 0.0, bg=(0.0, 0.0, 0.0), pixel
     return out
 
 
+def render_alternatives(scene, camera, deform=None, t: float = 0.0, bg=(0.0, 0.0, 0.0), pixels=None,
+                        eps=DEFAULT_EPS, max_bits: int = 6, max_alts: int = 16) -> dict:
+    """Every result a binary32 evaluation may legitimately give at the listed
+    pixels: each combination of a pixel's near-threshold decisions (flags of
+    ``render``) taken either way, at most 2**max_bits combinations, distinct
+    results kept (the FP64 one first).  Returns rgb [n,A,3], depth [n,A],
+    alpha [n,A], feat [n,A,D], flip [n,A] (uint64 decision mask for
+    ``backward``), nalts [n], ndec [n]."""
+    L = lib()
+    keep = _Keep()
+    sc, cam, df = _marshal(scene, camera, deform, keep)
+    pix = all_pixels(camera.width, camera.height) if pixels is None else np.ascontiguousarray(pixels, np.int32)
+    n, A, D = pix.shape[0], int(max_alts), scene.D
+    out = dict(rgb=np.zeros((n, A, 3)), depth=np.zeros((n, A)), alpha=np.zeros((n, A)), feat=np.zeros((n, A, D)),
+               flip=np.zeros((n, A), np.uint64), nalts=np.zeros(n, np.int32), ndec=np.zeros(n, np.int32))
+    bgv = keep.d(np.asarray(bg))
+    ep = keep.d(np.asarray(eps))
+    u64 = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    rc = L.or_render_alts(ctypes.byref(sc), ctypes.byref(df), ctypes.byref(cam), float(t), _ptr(bgv), n,
+                          _ptr(pix, _ip), _ptr(ep), int(max_bits), A, _ptr(out["rgb"]), _ptr(out["depth"]),
+                          _ptr(out["alpha"]), _ptr(out["feat"]), u64(out["flip"]), _ptr(out["nalts"], _ip),
+                          _ptr(out["ndec"], _ip))
+    if rc:
+        raise RuntimeError(f"or_render_alts failed: {rc}")
+    return out
+
+
 def backward(scene, camera, deform=None, t: float = 0.0, bg=(0.0, 0.0, 0.0), pixels=None,
-             g_rgb=None, g_depth=None, g_alpha=None, g_feat=None, want_uv: bool = False) -> dict:
+             g_rgb=None, g_depth=None, g_alpha=None, g_feat=None, want_uv: bool = False, flip=None,
+             gflip=None, eps=DEFAULT_EPS, geps=DEFAULT_GEPS) -> dict:
     """FP64 gradients of sum(g . outputs) over the listed pixels w.r.t.
     means, log_scales, quats, opacity_logits, sh [P,16,3], feat [P,D]; with
     want_uv also "uv" [P,2], the gradient w.r.t. each projected centre
-    (pixels)."""
+    (pixels).  flip [npix] (uint64, see ``render_alternatives``) takes a
+    pixel's near-threshold decisions the other way; gflip [P] (uint64) takes
+    a Gaussian's near-threshold gradient-only decisions (``gaussians``'
+    gndec) the other way, bit k for the k-th."""
     L = lib()
     keep = _Keep()
     sc, cam, df = _marshal(scene, camera, deform, keep)
@@ -249,10 +287,16 @@ def backward(scene, camera, deform=None, t: float = 0.0, bg=(0.0, 0.0, 0.0), pix
     bgv = keep.d(np.asarray(bg))
     if want_uv:
         out["uv"] = np.zeros((P, 2))
+    u64 = lambda a: None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    fl = None if flip is None else np.ascontiguousarray(np.asarray(flip).reshape(n), np.uint64)
+    gfl = None if gflip is None else np.ascontiguousarray(np.asarray(gflip).reshape(P), np.uint64)
+    ep = keep.d(np.asarray(eps)) if fl is not None else None
+    gep = keep.d(np.asarray(geps)) if gfl is not None else None
     rc = L.or_backward(ctypes.byref(sc), ctypes.byref(df), ctypes.byref(cam), float(t), _ptr(bgv), n,
                        _ptr(pix, _ip), _ptr(gr), _ptr(gz), _ptr(ga), _ptr(gf), _ptr(out["means"]),
                        _ptr(out["log_scales"]), _ptr(out["quats"]), _ptr(out["opacity_logits"]),
-                       _ptr(out["sh"]), _ptr(out["feat"]), _ptr(out["uv"]) if want_uv else None)
+                       _ptr(out["sh"]), _ptr(out["feat"]), _ptr(out["uv"]) if want_uv else None,
+                       _ptr(ep), u64(fl), _ptr(gep), u64(gfl))
     if rc:
         raise RuntimeError(f"or_backward failed: {rc}")
     return out
