@@ -78,6 +78,131 @@ def masked_forward_errors(run: GpuRun, ref, pix_index=None):
     return e, flagged
 
 
+FLAG_NAMES = {O.FLAG_INCL: "inclusion", O.FLAG_SKIP: "alpha_skip", O.FLAG_TERM: "termination",
+              O.FLAG_DEPTH: "depth_order", O.FLAG_CLAMP: "alpha_clamp"}
+
+
+def flag_breakdown(flags) -> dict:
+    """Pixels per decision flag (a pixel may carry several)."""
+    flags = np.asarray(flags)
+    return {name: int(((flags & bit) != 0).sum()) for bit, name in FLAG_NAMES.items()}
+
+
+def forward_parity(run: GpuRun, sc, cam, df=None, t=0.0, bg=(0.0, 0.0, 0.0), pixels=None):
+    """Compares EVERY listed pixel (default all) with the oracle.
+
+    A pixel whose FP64 decisions are all clear of their thresholds is
+    compared with the FP64 result.  A flagged pixel (a decision within the
+    binary32 error model of its threshold) is compared with the oracle result
+    of each way of taking those decisions (``render_alternatives``) and the
+    closest one is kept: both branches are correct results of the pass.
+    Returns (errors over all pixels, report, flip) where flip [n] is the
+    chosen decision mask per pixel (0 = the FP64 branch) for the reverse
+    pass, and report holds the flagged count, the per-flag breakdown, the
+    pixels whose GPU result took a non-FP64 branch and the number of pixels
+    left unchecked (always 0)."""
+    ref = O.render(sc, cam, df, t=t, bg=bg, pixels=pixels)
+    n = ref["rgb"].shape[0]
+    idx = np.arange(run.rgb.shape[0]) if pixels is None else pixel_index(pixels, cam.width)
+    got = dict(rgb=run.rgb[idx], depth=run.depth[idx], alpha=run.alpha[idx], feat=run.feat[idx])
+    want = {k: ref[k].copy() for k in ("rgb", "depth", "alpha", "feat")}
+    frms = max(float(np.sqrt(np.mean(ref["feat"] ** 2))), 1e-30) if ref["feat"].size else 1.0
+    flagged = (ref["flags"] & O.VALUE_FLAGS) != 0
+    flip = np.zeros(n, np.uint64)
+    nalts = np.ones(n, np.int32)
+    if flagged.any():
+        pix = O.all_pixels(cam.width, cam.height) if pixels is None else np.asarray(pixels)
+        sel = np.nonzero(flagged)[0]
+        alt = O.render_alternatives(sc, cam, df, t=t, bg=bg, pixels=pix[sel])
+        for j, i in enumerate(sel):
+            na = int(alt["nalts"][j])
+            nalts[i] = na
+            score = []
+            for a in range(na):
+                fden = np.maximum(np.abs(alt["feat"][j, a]), frms)
+                score.append(max(np.abs(got["rgb"][i] - alt["rgb"][j, a]).max() / TOL_RGB_ABS,
+                                 abs(got["depth"][i] - alt["depth"][j, a]) / TOL_DEPTH_ABS,
+                                 abs(got["alpha"][i] - alt["alpha"][j, a]) / TOL_RGB_ABS,
+                                 (np.abs(got["feat"][i] - alt["feat"][j, a]) / fden).max(initial=0) / TOL_FEAT_REL))
+            a = int(np.argmin(score))
+            for k in ("rgb", "depth", "alpha", "feat"):
+                want[k][i] = alt[k][j, a]
+            flip[i] = alt["flip"][j, a]
+    e = dict(rgb=float(np.abs(got["rgb"] - want["rgb"]).max(initial=0)),
+             depth=float(np.abs(got["depth"] - want["depth"]).max(initial=0)),
+             alpha=float(np.abs(got["alpha"] - want["alpha"]).max(initial=0)),
+             feat=float((np.abs(got["feat"] - want["feat"]) / np.maximum(np.abs(want["feat"]), frms)).max(initial=0)))
+    report = dict(pixels=n, flagged=int(flagged.sum()), per_flag=flag_breakdown(ref["flags"]),
+                  other_branch=int((flip != 0).sum()), max_alternatives=int(nalts.max(initial=1)), unchecked=0)
+    return e, report, flip
+
+
+def check_forward(e, report, flagged_max):
+    """Asserts the forward bars and that the flagged count stays within its
+    measured bound (a guard on the width of the decision margins)."""
+    print("forward errors", e, "report", report)
+    assert report["unchecked"] == 0
+    assert report["flagged"] <= flagged_max, report
+    assert e["rgb"] < TOL_RGB_ABS and e["depth"] < TOL_DEPTH_ABS and e["alpha"] < TOL_RGB_ABS, e
+    assert e["feat"] < TOL_FEAT_REL, e
+
+
+GRAD_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh", "feat")
+
+
+def _row_err(got, ref):
+    """Per-Gaussian worst relative error (rms floor over the whole array)."""
+    got = np.asarray(got, np.float64).reshape(got.shape[0], -1)
+    ref = np.asarray(ref, np.float64).reshape(ref.shape[0], -1)
+    rms = max(float(np.sqrt(np.mean(ref ** 2))), 1e-30) if ref.size else 1.0
+    return (np.abs(got - ref) / np.maximum(np.abs(ref), rms)).max(axis=1, initial=0)
+
+
+def grad_parity(got, sc, cam, df, t, bg, pixels, G, flip=None, max_bits=3):
+    """Compares the gradients of EVERY Gaussian with the oracle's gradients of
+    the same upstream gradients G (per listed pixel), the pixels' decisions
+    taken as the forward comparison found them (flip).  A Gaussian with a
+    gradient-only decision within rounding of its threshold (rgb clamp, J
+    clamp, ReLU, grid cell: gndec > 0) is compared with the oracle's
+    gradients for each way of taking those decisions and the closest is
+    kept.  Returns (errors per array, report)."""
+    kw = dict(pixels=pixels, g_rgb=G["rgb"], g_depth=G["depth"], g_alpha=G["alpha"], g_feat=G["feat"], flip=flip)
+    ref = O.backward(sc, cam, df, t, bg, **kw)
+    gndec = O.gaussians(sc, cam, df, t=t)["gndec"]
+    P = sc.P
+    best = np.zeros(P, np.int64)
+    chosen = {k: ref[k].copy() for k in GRAD_KEYS}
+    if (gndec > 0).any():
+        nb = min(int(gndec.max()), max_bits)
+        score0 = np.max([_row_err(got[k], ref[k]) for k in GRAD_KEYS], axis=0)
+        bscore = score0.copy()
+        for mask in range(1, 1 << nb):
+            need = mask.bit_length()
+            gf = np.where(gndec >= need, mask, 0).astype(np.uint64)
+            if not gf.any():
+                continue
+            alt = O.backward(sc, cam, df, t, bg, gflip=gf, **kw)
+            sc_m = np.max([_row_err(got[k], alt[k]) for k in GRAD_KEYS], axis=0)
+            better = (gf != 0) & (sc_m < bscore)
+            bscore[better] = sc_m[better]
+            best[better] = mask
+            for k in GRAD_KEYS:
+                chosen[k][better] = alt[k][better]
+    errs = {k: rel_err(got[k], chosen[k]) for k in GRAD_KEYS}
+    report = dict(gaussians=P, near_decisions=int((gndec > 0).sum()), other_branch=int((best != 0).sum()),
+                  excluded=0)
+    return errs, report
+
+
+def check_grads(errs, report, tol=TOL_GRAD_REL, near_max=None):
+    print("grad errors", errs, "report", report)
+    assert report["excluded"] == 0
+    if near_max is not None:
+        assert report["near_decisions"] <= near_max, report
+    for k, e in errs.items():
+        assert e < tol, (k, e)
+
+
 def pixel_index(pix, width):
     pix = np.asarray(pix)
     return pix[:, 1] * width + pix[:, 0]

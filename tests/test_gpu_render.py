@@ -1,11 +1,13 @@
 """GPU parity of the FE-4DGS pass against the FP64 oracle, through the C ABI.
 
 Forward: RGB and depth within 1e-4 absolute, features within 1e-4 relative,
-on pixels whose oracle decisions are not within rounding distance of a
-threshold (those are counted and masked).  Integer stage: keys, per-entry
-Gaussian ids and tile ranges bit-exact.  Reverse: gradients within 1e-3
-relative of the oracle's analytic FP64 gradients and 1e-2 of central finite
-differences of the oracle forward."""
+on EVERY pixel: a pixel whose oracle decisions are within rounding distance
+of a threshold is compared with the oracle result of the branch the GPU
+took (each branch is a correct result), and the flagged count stays within
+its measured bound.  Integer stage: keys, per-entry Gaussian ids and tile
+ranges bit-exact.  Reverse: gradients of EVERY Gaussian within 1e-3
+relative of the oracle's analytic FP64 gradients (decisions as the GPU took
+them) and 1e-2 of central finite differences of the oracle forward."""
 import dataclasses
 
 import numpy as np
@@ -14,8 +16,8 @@ import torch
 
 from oracle import oracle as O
 from paper_2503_06161_gb300 import synth, _lib
-from tests.gpu_helpers import (TOL_DEPTH_ABS, TOL_FD_REL, TOL_FEAT_REL, TOL_GRAD_REL, TOL_RGB_ABS, deformed_case,
-                               gpu_backward, gpu_forward, masked_forward_errors, pixel_index, rel_err)
+from tests.gpu_helpers import (TOL_FD_REL, TOL_FEAT_REL, TOL_RGB_ABS, check_forward, check_grads, deformed_case,
+                               forward_parity, gpu_backward, gpu_forward, grad_parity, pixel_index, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -80,27 +82,23 @@ def test_tile_bin_bit_exact_endonerf_scene():
 # --------------------------------------------------------------------------
 
 def test_forward_static_1k_64x64():
+    # Three pixels carry an alpha-skip decision within 1e-4 of 1/255; they
+    # are checked against the branch the GPU took.
     sc, cam, _ = synth.config_inputs("static_1k_64x64")
     run = gpu_forward(sc, cam)
-    ref = O.render(sc, cam)
-    e, flagged = masked_forward_errors(run, ref)
-    print("static_1k_64x64 errors", e, "flagged", flagged)
-    assert flagged <= 0.02 * cam.width * cam.height
-    assert e["rgb"] < TOL_RGB_ABS and e["depth"] < TOL_DEPTH_ABS and e["alpha"] < TOL_RGB_ABS
-    assert e["feat"] < TOL_FEAT_REL
+    e, rep, _ = forward_parity(run, sc, cam)
+    check_forward(e, rep, flagged_max=4)
 
 
 @pytest.mark.parametrize("D", [16, 32, 64, 128])
 def test_forward_deformed_ragged(D):
+    # 192 of 15000 pixels flagged: 161 depth-order ties, 22 alpha skips, 11
+    # terminations; all checked.
     sc, cam, df = deformed_case(D=D)
     bg = (0.1, 0.2, 0.3)
     run = gpu_forward(sc, cam, df, t=0.3, bg=bg)
-    ref = O.render(sc, cam, df, t=0.3, bg=bg)
-    e, flagged = masked_forward_errors(run, ref)
-    print(f"D={D} errors", e, "flagged", flagged)
-    assert flagged <= 0.02 * cam.width * cam.height
-    assert e["rgb"] < TOL_RGB_ABS and e["depth"] < TOL_DEPTH_ABS and e["alpha"] < TOL_RGB_ABS
-    assert e["feat"] < TOL_FEAT_REL
+    e, rep, _ = forward_parity(run, sc, cam, df, t=0.3, bg=bg)
+    check_forward(e, rep, flagged_max=230)
 
 
 def test_per_gaussian_state():
@@ -169,10 +167,8 @@ def test_forward_bf16_storage():
     sc, cam, df = deformed_case(seed=3)
     sc16 = dataclasses.replace(sc, sh=synth.bf16_round(sc.sh), feat=synth.bf16_round(sc.feat))
     run = gpu_forward(sc, cam, df, t=0.6, bf16=True)
-    ref = O.render(sc16, cam, df, t=0.6)
-    e, flagged = masked_forward_errors(run, ref)
-    print("bf16 errors", e, "flagged", flagged)
-    assert e["rgb"] < TOL_RGB_ABS and e["depth"] < TOL_DEPTH_ABS and e["feat"] < TOL_FEAT_REL
+    e, rep, _ = forward_parity(run, sc16, cam, df, t=0.6)
+    check_forward(e, rep, flagged_max=170)
 
 
 @pytest.mark.parametrize("deg", [0, 1, 2])
@@ -180,17 +176,15 @@ def test_forward_lower_sh_degree(deg):
     sc, cam, df = deformed_case(P=1500, seed=4)
     sc = dataclasses.replace(sc, sh_degree=deg)
     run = gpu_forward(sc, cam, df, t=0.2)
-    ref = O.render(sc, cam, df, t=0.2)
-    e, _ = masked_forward_errors(run, ref)
-    assert e["rgb"] < TOL_RGB_ABS
+    e, rep, _ = forward_parity(run, sc, cam, df, t=0.2)
+    check_forward(e, rep, flagged_max=18)
 
 
 def test_forward_deform_c64():
     sc, cam, df = deformed_case(P=2000, C=64, R=8, seed=5)
     run = gpu_forward(sc, cam, df, t=0.9)
-    ref = O.render(sc, cam, df, t=0.9)
-    e, _ = masked_forward_errors(run, ref)
-    assert e["rgb"] < TOL_RGB_ABS and e["feat"] < TOL_FEAT_REL
+    e, rep, _ = forward_parity(run, sc, cam, df, t=0.9)
+    check_forward(e, rep, flagged_max=85)
 
 
 # --------------------------------------------------------------------------
@@ -207,30 +201,23 @@ def _upstream(n, D, seed=0, mask=None):
     return g
 
 
-def _compare_grads(got, ref, gflags, tol=TOL_GRAD_REL):
-    keep = gflags == 0
-    errs = {}
-    for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "feat"):
-        a, b = got[k][keep], ref[k][keep]
-        errs[k] = rel_err(a, b)
-    print("grad errors", errs)
-    for k, e in errs.items():
-        assert e < tol, (k, e)
-
-
-@pytest.mark.parametrize("D,deform", [(16, False), (32, True), (64, True)])
-def test_backward_matches_oracle(D, deform):
+@pytest.mark.parametrize("D,deform,flagged_max", [(16, False, 8), (32, True, 75), (64, True, 75)])
+def test_backward_matches_oracle(D, deform, flagged_max):
+    # Upstream gradients on every pixel; the oracle's reverse takes each
+    # flagged pixel's decisions as the GPU forward took them, and each
+    # Gaussian's near-threshold gradient-only decisions as its GPU gradient
+    # shows: no pixel and no Gaussian is left out.
     sc, cam, df = deformed_case(P=1500, W=96, H=72, D=D, seed=7)
     df = df if deform else None
     t, bg = 0.4, (0.2, 0.1, 0.3)
     run = gpu_forward(sc, cam, df, t=t, bg=bg)
     pix = O.all_pixels(cam.width, cam.height)
-    fl = O.render(sc, cam, df, t=t, bg=bg)["flags"]
-    G = _upstream(len(pix), D, mask=fl == 0)
+    e, rep, flip = forward_parity(run, sc, cam, df, t=t, bg=bg)
+    check_forward(e, rep, flagged_max=flagged_max)
+    G = _upstream(len(pix), D)
     got = gpu_backward(run, t, G["rgb"], G["depth"], G["alpha"], G["feat"])
-    ref = O.backward(sc, cam, df, t, bg, pix, G["rgb"], G["depth"], G["alpha"], G["feat"])
-    gflags = O.gaussians(sc, cam, df, t=t)["gflags"]
-    _compare_grads(got, ref, gflags)
+    errs, grep = grad_parity(got, sc, cam, df, t, bg, pix, G, flip)
+    check_grads(errs, grep, near_max=2)
 
 
 def test_backward_matches_central_differences():
@@ -298,6 +285,12 @@ def test_forward_and_backward_deterministic():
 # --------------------------------------------------------------------------
 
 def test_endonerf_200k_640x512_sampled():
+    # Full-size workload and launch configuration, sampled pixels (the FP64
+    # oracle composites each one exactly): every sampled pixel checked (10 of
+    # 306 flagged: 8 depth-order ties, 2 alpha skips), then the reverse pass
+    # with upstream gradients on the sampled pixels only, so the oracle's
+    # gradient of every Gaussian is exact; no Gaussian is left out (185 have
+    # a gradient-only decision within rounding of its threshold).
     sc, cam, df = synth.config_inputs("endonerf_200k_640x512")
     t = 0.5
     run = gpu_forward(sc, cam, df, t=t)
@@ -307,26 +300,21 @@ def test_endonerf_200k_640x512_sampled():
     pix = np.c_[rng.integers(0, W, 300), rng.integers(0, H, 300)].astype(np.int32)
     corners = np.array([[0, 0], [W - 1, H - 1], [15, 15], [16, 16], [W - 1, 0], [0, H - 1]], np.int32)
     pix = np.r_[pix, corners]
-    ref = O.render(sc, cam, df, t=t, pixels=pix)
-    e, flagged = masked_forward_errors(run, ref, pixel_index(pix, W))
-    print("endonerf sampled errors", e, "flagged", flagged, "K", st["num_dups"])
-    assert flagged <= 0.05 * len(pix)
-    assert e["rgb"] < TOL_RGB_ABS and e["depth"] < TOL_DEPTH_ABS and e["feat"] < TOL_FEAT_REL
-    # Reverse pass with upstream gradients on the sampled pixels only.
-    ok = (ref["flags"] == 0)
-    n = len(pix)
-    Gs = _upstream(n, sc.D, seed=9, mask=ok)
+    idx = pixel_index(pix, W)
+    uniq, first = np.unique(idx, return_index=True)
+    pix = pix[np.sort(first)]
+    idx = pixel_index(pix, W)
+    print("K", st["num_dups"])
+    e, rep, flip = forward_parity(run, sc, cam, df, t=t, pixels=pix)
+    check_forward(e, rep, flagged_max=14)
+    Gs = _upstream(len(pix), sc.D, seed=9)
     HW = W * H
     full = dict(rgb=np.zeros((HW, 3)), depth=np.zeros(HW), alpha=np.zeros(HW), feat=np.zeros((HW, sc.D)))
-    idx = pixel_index(pix, W)
     for k in full:
         full[k][idx] = Gs[k]
     got = gpu_backward(run, t, full["rgb"], full["depth"], full["alpha"], full["feat"])
-    uniq, first = np.unique(idx, return_index=True)
-    refg = O.backward(sc, cam, df, t, (0, 0, 0), pix[first], Gs["rgb"][first], Gs["depth"][first],
-                      Gs["alpha"][first], Gs["feat"][first])
-    gflags = O.gaussians(sc, cam, df, t=t)["gflags"]
-    _compare_grads(got, refg, gflags)
+    errs, grep = grad_parity(got, sc, cam, df, t, (0, 0, 0), pix, Gs, flip)
+    check_grads(errs, grep, near_max=230)
 
 
 # --------------------------------------------------------------------------
@@ -348,9 +336,8 @@ def test_all_behind_camera_and_single_pixel_image():
     sc2 = synth.make_scene(50, 16, (-0.1, -0.1, 2), (0.1, 0.1, 3), seed=2)
     cam2 = synth.make_camera(1, 1, 10.0)
     run2 = gpu_forward(sc2, cam2)
-    ref2 = O.render(sc2, cam2)
-    e, _ = masked_forward_errors(run2, ref2)
-    assert e["rgb"] < TOL_RGB_ABS
+    e, rep, _ = forward_parity(run2, sc2, cam2)
+    check_forward(e, rep, flagged_max=1)
 
 
 def test_huge_gaussian_covers_every_tile():
@@ -359,9 +346,8 @@ def test_huge_gaussian_covers_every_tile():
     cam = synth.make_camera(130, 90, 60.0)
     run = gpu_forward(sc, cam)
     assert run.rast.dump()["touched"].cpu().numpy()[0] == 9 * 6
-    ref = O.render(sc, cam)
-    e, _ = masked_forward_errors(run, ref)
-    assert e["rgb"] < TOL_RGB_ABS and e["feat"] < TOL_FEAT_REL
+    e, rep, _ = forward_parity(run, sc, cam)
+    check_forward(e, rep, flagged_max=40)
 
 
 def test_duplicate_capacity_overflow_is_reported():
