@@ -74,7 +74,7 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--t", type=float, default=0.5)
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--D", type=int, default=None, help="feature width override (16, 32, 64, 128): D sweep")
+    p.add_argument("--D", type=int, default=None, help="feature width override (16, 32, 64, 128, 256): D sweep")
     p.add_argument("--P", type=int, default=None, help="Gaussian count override (--micro fst: profiling sizes)")
     p.add_argument("--micro", choices=["decoder", "adam", "fst", "densify"], default=None,
                    help="time one HBM-bound kernel alone on the workload's sizes")
@@ -981,10 +981,20 @@ def run_batch(args, world, rank, local, cfg):
     tuner = Autotuner()
     br = BatchRenderer(scene, deform, views, tuner)
     br.capture()
+    # Data-parallel over views: each rank renders its own views; one
+    # exchange per step sums the ranks' gradient sums (rank order).
+    from paper_2503_06161_gb300.dist import GradExchange
+    exchange = GradExchange(world) if world > 1 else None
+
+    def step():
+        br.replay()
+        if exchange is not None:
+            exchange.exchange([br.flat])
+
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
-        br.replay()
+        step()
     torch.cuda.synchronize()
     errs = br.device_errors()
     K_steps = args.steps
@@ -997,7 +1007,7 @@ def run_batch(args, world, rank, local, cfg):
     for i in range(K_steps):
         flush.zero_()
         ev[i][0].record(stream)
-        br.replay()
+        step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -1005,35 +1015,38 @@ def run_batch(args, world, rank, local, cfg):
     clk = clocks.stop()
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     ms = max_over_ranks(ms, world, dev)
-    # Per-stage times and pair counts from one eager pass with stage events.
-    stages = {n: 0.0 for n in ("deform_project", "binning", "composite_fwd", "loss", "composite_bwd", "feat_grad",
-                               "gauss_bwd")}
+    # Per-stage times from one eager pass with the batch's stage events (the
+    # batched compositing forward and reverse are one persistent launch
+    # each), and the pair counts of every view.
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+    for e in evs:  # handles exist once recorded
+        e.record(stream)
+    torch.cuda.synchronize()
+    _lib.set_events(br.batch._opts[0], evs)
+    e_loss0, e_loss1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    br.forward()
+    e_loss0.record(stream)
+    br.losses_and_grads()
+    e_loss1.record(stream)
+    br.backward()
+    torch.cuda.synchronize()
+    _lib.set_events(br.batch._opts[0], None)
+    stages = {"per_view_deform_project_bin": evs[0].elapsed_time(evs[1]),
+              "composite_fwd_batched": evs[1].elapsed_time(evs[2]), "loss": e_loss0.elapsed_time(e_loss1),
+              "composite_bwd_batched": evs[4].elapsed_time(evs[5]),
+              "per_view_gauss_bwd": evs[5].elapsed_time(evs[7])}
     visits = contribs = 0
-    bounds = [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 7)]
-    for r, v, b in zip(br.rasts, br.views, br.bufs):
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
-        for e in evs:  # handles exist once recorded
-            e.record(stream)
-        torch.cuda.synchronize()
-        _lib.set_events(r.opts, evs)
-        HW = v.cam.width * v.cam.height
-        r.forward(scene, v.cam, deform, v.t, out=b["out"])
-        _lib.fe_l1_loss_grad(b["out"][0], v.tgt_rgb, HW, b["g_rgb"], br.losses[0, 0:1], br.scratch[0, 0])
-        _lib.fe_l1_loss_grad(b["out"][3], v.tgt_feat, HW, b["g_feat"], br.losses[0, 1:2], br.scratch[0, 1])
-        r.backward(scene, v.cam, deform, v.t, b["g_rgb"], None, None, b["g_feat"], grads=br.grads)
-        torch.cuda.synchronize()
-        _lib.set_events(r.opts, None)
-        for n, (a, c) in zip(stages, bounds):
-            stages[n] += evs[a].elapsed_time(evs[c])
+    for k, v in enumerate(br.views):
+        ws_k, o_k = br.view_workspace(k)
         counts = torch.zeros(2, dtype=torch.int64, device=dev)
-        _lib.fe_count_pairs(scene.struct(), v.cam, r.opts, r.workspace, counts)
+        _lib.fe_count_pairs(scene.struct(), v.cam, o_k, ws_k, counts)
         vi, co = (int(x) for x in counts.cpu())
         visits += vi
         contribs += co
     C = df_np.C if df_np is not None else 0
     clock_mhz = clk.get("sm_mhz") or 2070.0
     alu_peak = SMS * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
-    ach = flops_composite_bwd(visits, contribs, D) / (stages["composite_bwd"] * 1e-3) / 1e12
+    ach = flops_composite_bwd(visits, contribs, D) / (stages["composite_bwd_batched"] * 1e-3) / 1e12
     n_views = len(views)
     result = {
         "metric": METRIC, "value": round(world * 1000.0 / ms, 3), "unit": "it/s", "n_gpus": world, "steps": K_steps,
@@ -1041,18 +1054,21 @@ def run_batch(args, world, rank, local, cfg):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "gaussians": P, "D": D, "storage": "bf16 sh/feat" if bf16 else "f32",
                    "views": [f"{v.cam.width}x{v.cam.height}@t={v.t:.3f}" for v in views],
-                   "tile_shapes": [f"{a}x{b}" for a, b in br.tile_shapes],
-                   "step": f"{n_views} views fwd+bwd (L1 rgb+feat), gradients summed, one CUDA-graph replay",
-                   "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
+                   "tile_shapes": [f"{a}x{b}" for a, b in br.tile_shapes], "fwd_batch": br.fwd_batch,
+                   "step": f"{n_views} views fwd+bwd (L1 rgb+feat) through fe_render_batch / "
+                           "fe_render_batch_backward (one persistent compositing launch per direction over all "
+                           "(view, tile) items), gradients summed, one CUDA-graph replay",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": ("data-parallel over views: each rank its own views, one ordered gradient "
+                                   "exchange per step" if world > 1 else "one GPU")},
         "views_per_s": round(world * n_views * 1000.0 / ms, 2),
-        "autotune_ms": {f"{k[0]}x{k[1]}": {f"{a}x{b}": round(t, 4) for (a, b), t in v.items()}
-                        for k, v in tuner.timings.items()},
-        "eager_stage_ms_sum": {k: round(v, 4) for k, v in stages.items()},
+        "autotune_ms": {str(k[:2]): {str(a): round(t, 4) for a, t in v.items()} for k, v in tuner.timings.items()},
+        "eager_stage_ms": {k: round(v, 4) for k, v in stages.items()},
         "pairs": {"visits": visits, "blended": contribs},
         "roofline": {"kernel": "composite_bwd", "bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
                      "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4), "traffic": None,
-                     "note": "eager pass, all views"},
-        "device_errors": errs, "gpu_launches": n_views * 18, "clocks": clk, "e2e": None,
+                     "note": "the batched (persistent) compositing reverse over all views, eager pass"},
+        "device_errors": errs, "gpu_launches": n_views * 16 + 2 * n_views + 2, "clocks": clk, "e2e": None,
     }
     if rank == 0:
         print(json.dumps(result))

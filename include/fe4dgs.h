@@ -60,7 +60,8 @@ typedef struct {
  * rotation from the quaternion (w, x, y, z) after normalisation. */
 typedef struct {
   int P;                    /* number of Gaussians, >= 0 */
-  int D;                    /* feature channels: 16, 32, 64 or 128 */
+  int D;                    /* feature channels: 16, 32, 64, 128 or 256 (256 runs the compositing
+                               kernels as two passes over 128-channel halves) */
   int sh_degree;            /* 0..3; sh always holds 16 coefficients per channel */
   int sh_bf16;              /* 1: sh holds bfloat16, else float32 */
   int feat_bf16;            /* 1: feat holds bfloat16, else float32 */
@@ -106,6 +107,15 @@ typedef struct {
                                binning [3] after compositing; backward [4] start [5] after
                                the compositing reverse [6] after the feature-gradient sum
                                [7] after the per-Gaussian reverse */
+  int fwd_batch;            /* Gaussians per shared-memory batch of the compositing forward:
+                               0 = the default for D (128 up to D = 32, 64 at D = 64, 32 at
+                               D = 128), else 32, 64 or 128 (128 only up to D = 64); the
+                               images do not depend on it */
+  int wait_polls;           /* bound of each staging wait of the compositing kernels, in
+                               polls: 0 = the default (2^20); a negative value makes every
+                               such wait give up at once -- a test hook for the timeout path:
+                               the launch still waits (with its own bound) for the copies it
+                               issued, records FE_ERR_TIMEOUT and returns */
 } fe_opts;
 
 /* Render outputs (Eq. 7-8 plus depth): rgb [3,H,W] planar = sum w c + bg T;
@@ -469,6 +479,73 @@ fe_status fe_densify(const fe_densify_args *args, int64_t *new_P, void *workspac
 /* logits[g] = min(logits[g], log(max_opacity / (1 - max_opacity))), g < P,
  * 0 < max_opacity < 1.  Asynchronous on `stream`. */
 fe_status fe_reset_opacity(float *logits, int64_t P, float max_opacity, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched form: V views of one deforming scene, each with its own time t,
+ * camera and resolution (e.g. the timestamps and viewpoints of one training
+ * batch), rendered in one call (Sec. 3.3: the same single rasterization
+ * pass per view), and their reverse pass with the parameter gradients
+ * summed over the views.  The per-Gaussian stages of each view
+ * (deformation, projection, colour, binning; in the reverse, the sums of
+ * the partial rows and the per-Gaussian chain rule) run on up to four
+ * helper streams forked from `stream` and joined back to it (views dealt
+ * round-robin: view v on helper v mod S, S = min(4, V)); the compositing of
+ * ALL views runs on `stream` as one persistent launch -- as many blocks as
+ * fit on the GPU, each taking (view, tile) work items from a device counter
+ * until none are left -- and so does the compositing reverse.  Images are
+ * bitwise those of fe_render_forward on each view with the same options;
+ * the gradients are those of fe_render_backward on each view, summed in a
+ * fixed order: helper i adds views i, i + S, i + 2S, ... in that order, then
+ * the S sums are added in helper order (for V <= 4: plain view order).
+ * The helper streams and their events are created by the first batched
+ * call on a device (make it before any stream capture); calls on one device
+ * serialise their enqueueing on a lock, and the whole call can be captured
+ * into a CUDA graph.
+ * ------------------------------------------------------------------------ */
+#define FE_MAX_VIEWS 32
+
+typedef struct {
+  int V;                    /* number of views, 1..FE_MAX_VIEWS */
+  const fe_camera *cams;    /* host array [V] */
+  const float *t;           /* host array [V]: time of each view */
+  const fe_opts *opts;      /* host array [V]: tile shape, background and list capacity of each
+                               view.  forward_only, accumulate_grads (first view: add to the
+                               gradient buffers instead of overwriting them), fwd_batch and
+                               wait_polls are taken from opts[0] for the whole batch, and so
+                               are the profiling events, here: forward [0] start [1] after
+                               every view's deformation, projection and binning [2] after
+                               the batched compositing; backward [4] start [5] after the
+                               batched compositing reverse [7] after every view's
+                               per-Gaussian reverse. */
+} fe_batch;
+
+/* Bytes of workspace for a batch: a 256-byte batch header, then one
+ * fe_workspace_size region per view (256-byte aligned), then (with the
+ * backward and more than one view) one float32 gradient set per helper
+ * stream (P x (3 + 3 + 4 + 1 + 48 + D) floats, each array 256-byte aligned). */
+fe_status fe_batch_workspace_size(int P, int D, const fe_batch *b, size_t *bytes);
+
+/* Forward pass of every view of the batch.  out: host array [V] of the
+ * views' outputs (as fe_render_forward's).  The workspace (at least
+ * fe_batch_workspace_size bytes, 256-byte aligned) keeps each view's state
+ * for fe_render_batch_backward.  Asynchronous on `stream`. */
+fe_status fe_render_batch(const fe_gaussians *g, const fe_deform *deform, const fe_batch *b, void *workspace,
+                          size_t workspace_bytes, const fe_outputs *out, void *stream);
+
+/* Reverse pass of the last fe_render_batch on this workspace (same g,
+ * deform, b).  grad_out: host array [V] of the views' upstream gradients.
+ * grads receives the sum over views of each view's parameter gradients in
+ * the fixed order above (overwritten, unless opts[0].accumulate_grads: then
+ * the sum is added to it).  Deterministic.  Asynchronous on `stream`. */
+fe_status fe_render_batch_backward(const fe_gaussians *g, const fe_deform *deform, const fe_batch *b,
+                                   void *workspace, size_t workspace_bytes, const fe_output_grads *grad_out,
+                                   const fe_grads *grads, void *stream);
+
+/* Synchronous: per-view statistics of the last batch call (host array [V]).
+ * Returns the first non-OK status of the views (FE_ERR_TIMEOUT,
+ * FE_ERR_WORKSPACE or FE_ERR_NONFINITE as fe_read_stats). */
+fe_status fe_batch_read_stats(const void *workspace, size_t workspace_bytes, int P, int D, const fe_batch *b,
+                              fe_stats *stats, void *stream);
 
 /* Measured single-precision FMA throughput: runs an FMA-chain kernel over
  * the whole GPU for `iters` iterations per thread and writes FLOP/s

@@ -47,7 +47,16 @@ class fe_deform(ctypes.Structure):
 
 class fe_opts(ctypes.Structure):
     _fields_ = [("tile_w", c_int), ("tile_h", c_int), ("bg", c_float * 3), ("max_dups", c_int64),
-                ("forward_only", c_int), ("accumulate_grads", c_int), ("events", ctypes.POINTER(c_void_p))]
+                ("forward_only", c_int), ("accumulate_grads", c_int), ("events", ctypes.POINTER(c_void_p)),
+                ("fwd_batch", c_int), ("wait_polls", c_int)]
+
+
+class fe_batch(ctypes.Structure):
+    _fields_ = [("V", c_int), ("cams", ctypes.POINTER(fe_camera)), ("t", ctypes.POINTER(c_float)),
+                ("opts", ctypes.POINTER(fe_opts))]
+
+
+FE_MAX_VIEWS = 32
 
 
 class fe_outputs(ctypes.Structure):
@@ -128,6 +137,12 @@ _SIGNATURES = {
                              c_void_p, c_void_p],
     "fe_densify": [_P(fe_densify_args), c_void_p, c_void_p, ctypes.c_size_t, c_void_p],
     "fe_reset_opacity": [c_void_p, c_int64, c_float, c_void_p],
+    "fe_batch_workspace_size": [c_int, c_int, _P(fe_batch), _P(ctypes.c_size_t)],
+    "fe_render_batch": [_P(fe_gaussians), _P(fe_deform), _P(fe_batch), c_void_p, ctypes.c_size_t, _P(fe_outputs),
+                        c_void_p],
+    "fe_render_batch_backward": [_P(fe_gaussians), _P(fe_deform), _P(fe_batch), c_void_p, ctypes.c_size_t,
+                                 _P(fe_output_grads), _P(fe_grads), c_void_p],
+    "fe_batch_read_stats": [c_void_p, ctypes.c_size_t, c_int, c_int, _P(fe_batch), _P(fe_stats), c_void_p],
 }
 
 _lib = None
@@ -178,14 +193,34 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def make_opts(tile=(16, 16), bg=(0.0, 0.0, 0.0), max_dups=0, forward_only=False, accumulate=False) -> fe_opts:
+def make_opts(tile=(16, 16), bg=(0.0, 0.0, 0.0), max_dups=0, forward_only=False, accumulate=False, fwd_batch=0,
+              wait_polls=0) -> fe_opts:
     o = fe_opts()
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
     o.bg[:] = [float(x) for x in bg]
     o.max_dups = int(max_dups)
     o.forward_only = 1 if forward_only else 0
     o.accumulate_grads = 1 if accumulate else 0
+    o.fwd_batch = int(fwd_batch)
+    o.wait_polls = int(wait_polls)
     return o
+
+
+def make_batch(cams, ts, opts) -> fe_batch:
+    """fe_batch over host arrays of cameras (fe_camera), times and fe_opts
+    (kept alive by the returned object)."""
+    V = len(cams)
+    if not (len(ts) == V and len(opts) == V):
+        raise ValueError("one camera, time and options struct per view")
+    b = fe_batch()
+    b._cams = (fe_camera * V)(*cams)
+    b._t = (c_float * V)(*[float(t) for t in ts])
+    b._opts = (fe_opts * V)(*opts)
+    b.V = V
+    b.cams = ctypes.cast(b._cams, ctypes.POINTER(fe_camera))
+    b.t = ctypes.cast(b._t, ctypes.POINTER(c_float))
+    b.opts = ctypes.cast(b._opts, ctypes.POINTER(fe_opts))
+    return b
 
 
 def make_camera(width, height, fx, fy, cx, cy, world_to_cam, campos, znear=0.2) -> fe_camera:
@@ -248,6 +283,51 @@ def fe_render_backward(g: fe_gaussians, deform, cam: fe_camera, t: float, opts: 
                                    workspace.numel() * workspace.element_size(), ctypes.byref(go), ctypes.byref(gr),
                                    _stream(stream))
     _check("fe_render_backward", rc)
+
+
+def fe_batch_workspace_size(P: int, D: int, batch: fe_batch) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_batch_workspace_size", load().fe_batch_workspace_size(int(P), int(D), ctypes.byref(batch),
+                                                                      ctypes.byref(n)))
+    return int(n.value)
+
+
+def fe_render_batch(g: fe_gaussians, deform, batch: fe_batch, workspace, outs, stream=None):
+    """outs: per view (rgb, depth, alpha, feat[, feat_bf16]) device tensors."""
+    arr = (fe_outputs * batch.V)()
+    for k, o in enumerate(outs):
+        arr[k] = fe_outputs(_ptr(o[0]), _ptr(o[1]), _ptr(o[2]), _ptr(o[3]), _ptr(o[4]) if len(o) > 4 else None)
+    rc = load().fe_render_batch(ctypes.byref(g), ctypes.byref(deform) if deform is not None else None,
+                                ctypes.byref(batch), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                arr, _stream(stream))
+    _check("fe_render_batch", rc)
+
+
+def fe_render_batch_backward(g: fe_gaussians, deform, batch: fe_batch, workspace, grad_outs, grads: dict,
+                             stream=None):
+    """grad_outs: per view (g_rgb, g_depth, g_alpha, g_feat), any None;
+    grads: dict of the summed gradient tensors (means, log_scales, quats,
+    opacity_logits, sh, feat)."""
+    arr = (fe_output_grads * batch.V)()
+    for k, o in enumerate(grad_outs):
+        arr[k] = fe_output_grads(*[_ptr(x) for x in o])
+    gr = fe_grads(*[_ptr(grads[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "feat")])
+    rc = load().fe_render_batch_backward(ctypes.byref(g), ctypes.byref(deform) if deform is not None else None,
+                                         ctypes.byref(batch), _ptr(workspace),
+                                         workspace.numel() * workspace.element_size(), arr, ctypes.byref(gr),
+                                         _stream(stream))
+    _check("fe_render_batch_backward", rc)
+
+
+def fe_batch_read_stats(workspace, P: int, D: int, batch: fe_batch, stream=None, raise_on_error: bool = True):
+    """(status, per-view stats dicts); synchronous."""
+    arr = (fe_stats * batch.V)()
+    rc = load().fe_batch_read_stats(_ptr(workspace), workspace.numel() * workspace.element_size(), int(P), int(D),
+                                    ctypes.byref(batch), arr, _stream(stream))
+    if raise_on_error:
+        _check("fe_batch_read_stats", rc)
+    return rc, [dict(num_dups=s.num_dups, capacity=s.capacity, num_visible=s.num_visible,
+                     device_errors=s.device_errors, has_forward=s.has_forward) for s in arr]
 
 
 def fe_tile_bin(uv, radius, depth, width: int, height: int, opts: fe_opts, workspace, stream=None):

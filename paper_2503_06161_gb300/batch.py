@@ -1,18 +1,20 @@
 """Batched rendering: many (time, camera, resolution) views of one deforming
-scene rendered forward and backward in a single CUDA-graph launch, with the
-parameter gradients summed over the views (the multi-view form of the pass).
+scene rendered forward and backward through the library's batched entry
+points (fe_render_batch / fe_render_batch_backward), the parameter gradients
+summed over the views.
 
-The views are dealt round-robin to S streams.  Each stream renders its views
-one after another with its own workspace and its own gradient buffer (its
-first view overwrites, the others add); the streams run concurrently, so the
-launches of one view fill the GPU where another's leave it idle.  At the join
-one kernel sums the S gradient buffers in stream order, so the result is
-reproducible bit for bit.  Each view uses the tile shape the autotuner picked
-for its resolution (the images do not depend on the tile shape: inclusion is
-per pixel).  The whole batch -- fork, every view's launches, join, sum -- is
-captured into one CUDA graph and replayed as one launch.
+Per view the per-Gaussian stages (deformation query, projection, colour,
+binning) run one after another; the compositing of all views is ONE
+persistent launch whose blocks take (view, tile) work items from a device
+counter, and so is its reverse, so small views no longer leave the GPU half
+empty.  Each view uses the tile shape the autotuner picked for its
+resolution, and the whole batch the forward batch size (Gaussians per
+shared-memory batch) it picked; neither changes an image (inclusion is per
+pixel, the staging unit is not part of the arithmetic).  The batch step --
+forward, the per-view L1 losses, reverse -- is captured into one CUDA graph
+and replayed as one launch.
 
-    br = BatchRenderer(scene, deform, views, Autotuner(), streams=4)
+    br = BatchRenderer(scene, deform, views, Autotuner())
     br.capture()
     br.replay()
 """
@@ -27,42 +29,70 @@ from . import _lib
 from .raster import DeformField, GaussianScene, Rasterizer
 
 TILE_SHAPES = ((16, 16), (32, 8), (8, 32))
+FWD_BATCHES = (32, 64, 128)
 GRAD_SHAPES = (("means", (3,)), ("log_scales", (3,)), ("quats", (4,)), ("opacity_logits", ()), ("sh", (16, 3)))
+
+
+def _time(fn, reps: int) -> float:
+    ms = []
+    for k in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        if k:
+            ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
 
 
 class Autotuner:
     """Picks, per (width, height, P, D, storage), the tile shape with the
-    fastest forward + backward, timed with CUDA events on the real scene.
-    Results are cached for the life of the object."""
+    fastest forward + backward, and per batch the forward batch size,
+    timed with CUDA events on the real scene.  Results are cached for the
+    life of the object."""
 
-    def __init__(self, shapes=TILE_SHAPES, reps: int = 3):
-        self.shapes, self.reps = tuple(shapes), int(reps)
+    def __init__(self, shapes=TILE_SHAPES, fwd_batches=FWD_BATCHES, reps: int = 3):
+        self.shapes, self.fwd_batches, self.reps = tuple(shapes), tuple(fwd_batches), int(reps)
         self.cache: dict = {}
         self.timings: dict = {}
 
-    def pick(self, scene: GaussianScene, deform, cam, t, max_dups, workspace, grads, g_rgb, g_feat) -> tuple:
+    def pick_tile(self, scene: GaussianScene, deform, cam, t, max_dups, g_rgb, g_feat) -> tuple:
         key = (cam.width, cam.height, scene.P, scene.D, str(scene.feat.dtype))
         if key in self.cache:
             return self.cache[key]
-        best, best_ms, times = None, float("inf"), {}
+        best, best_ms, times = (16, 16), float("inf"), {}
         for shape in self.shapes:
             if cam.width < shape[0] and cam.height < shape[1]:
                 continue
             r = Rasterizer(scene.P, scene.D, cam.width, cam.height, tile=shape, max_dups=max_dups,
-                           device=workspace.device, auto_grow=False, workspace=workspace)
-            ms = []
-            for k in range(self.reps + 1):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
+                           device=scene.means.device, auto_grow=False)
+
+            def step():
                 r.forward(scene, cam, deform, t)
-                r.backward(scene, cam, deform, t, g_rgb, None, None, g_feat, grads=grads)
-                e1.record()
-                torch.cuda.synchronize()
-                if k:
-                    ms.append(e0.elapsed_time(e1))
-            times[shape] = statistics.median(ms)
+                r.backward(scene, cam, deform, t, g_rgb, None, None, g_feat)
+
+            times[shape] = _time(step, self.reps)
             if times[shape] < best_ms:
                 best, best_ms = shape, times[shape]
+            del r
+        self.cache[key] = best
+        self.timings[key] = times
+        return best
+
+    def pick_fwd_batch(self, renderer: "BatchRenderer") -> int:
+        key = ("fwd_batch", tuple((v.cam.width, v.cam.height) for v in renderer.views), renderer.scene.P,
+               renderer.scene.D, str(renderer.scene.feat.dtype))
+        if key in self.cache:
+            return self.cache[key]
+        best, best_ms, times = 0, float("inf"), {}
+        for B in self.fwd_batches:
+            if B == 128 and renderer.scene.D > 64:
+                continue
+            renderer.set_fwd_batch(B)
+            times[B] = _time(renderer.run, self.reps)
+            if times[B] < best_ms:
+                best, best_ms = B, times[B]
         self.cache[key] = best
         self.timings[key] = times
         return best
@@ -106,104 +136,114 @@ def grad_floats(P: int, D: int) -> int:
 
 
 class BatchRenderer:
+    """Owns the batch workspace, the per-view image and gradient buffers and
+    the summed parameter gradients of one batch of views."""
+
     def __init__(self, scene: GaussianScene, deform: DeformField | None, views: list, autotuner: Autotuner | None,
-                 streams: int = 4, capacity_margin: float = 1.5, device="cuda"):
+                 capacity_margin: float = 1.5, fwd_batch: int = 0, tiles=None, device="cuda"):
+        """tiles: optional tile shape per view (else autotuned, or 16x16
+        without an autotuner); fwd_batch: 0 = autotuned (default size
+        without an autotuner)."""
+        if not 1 <= len(views) <= _lib.FE_MAX_VIEWS:
+            raise ValueError(f"1..{_lib.FE_MAX_VIEWS} views per batch")
         self.scene, self.deform, self.views = scene, deform, list(views)
         P, D = scene.P, scene.D
         self.device = torch.device(device)
-        self.S = max(1, min(int(streams), len(self.views), 8))
         kw = dict(dtype=torch.float32, device=self.device)
-        nflat = grad_floats(P, D)
-        # Gradient buffer per stream; the batch's sum (stream 0's buffer is
-        # summed into itself, so it is also the result).
-        self.flat = [torch.zeros(nflat, **kw) for _ in range(self.S)]
-        self.grads = _grad_views(self.flat[0], P, D)
-        self.stream_of = [k % self.S for k in range(len(self.views))]
-        # Capacity of each view's (Gaussian, tile) list from a probe forward;
-        # one workspace per stream, sized for its largest view.
-        caps = []
-        for v in self.views:
-            probe = Rasterizer(P, D, v.cam.width, v.cam.height, max_dups=64 * P + 4096, forward_only=True,
-                               device=self.device)
-            probe.forward(scene, v.cam, deform, v.t)
-            caps.append(int(probe.stats()["num_dups"] * capacity_margin) + 4096)
-            del probe
-        torch.cuda.empty_cache()
-        size = [0] * self.S
-        for k, (v, cap) in enumerate(zip(self.views, caps)):
-            need = max(Rasterizer.workspace_bytes(P, D, v.cam.width, v.cam.height, tile=s, max_dups=cap)
-                       for s in TILE_SHAPES)
-            size[self.stream_of[k]] = max(size[self.stream_of[k]], need)
-        self.workspaces = [torch.empty(n, dtype=torch.uint8, device=self.device) for n in size]
+        self.flat = torch.zeros(grad_floats(P, D), **kw)
+        self.grads = _grad_views(self.flat, P, D)
         self.bufs = []
         for v in self.views:
             H, W = v.cam.height, v.cam.width
             self.bufs.append(dict(out=(torch.empty(3, H, W, **kw), torch.empty(H, W, **kw), torch.empty(H, W, **kw),
                                        torch.empty(H * W, D, **kw)),
                                   g_rgb=torch.full((3, H, W), 1e-3, **kw), g_feat=torch.full((H * W, D), 1e-3, **kw)))
+        # Capacity of each view's (Gaussian, tile) list from a probe forward.
+        self.caps = []
+        for v in self.views:
+            probe = Rasterizer(P, D, v.cam.width, v.cam.height, max_dups=64 * P + 4096, forward_only=True,
+                               device=self.device)
+            probe.forward(scene, v.cam, deform, v.t)
+            self.caps.append(int(probe.stats()["num_dups"] * capacity_margin) + 4096)
+            del probe
+        torch.cuda.empty_cache()
+        if tiles is not None:
+            self.tiles = [tuple(x) for x in tiles]
+        elif autotuner is not None:
+            self.tiles = [autotuner.pick_tile(scene, deform, v.cam, v.t, cap, b["g_rgb"], b["g_feat"])
+                          for v, cap, b in zip(self.views, self.caps, self.bufs)]
+        else:
+            self.tiles = [(16, 16)] * len(self.views)
         self.losses = torch.zeros(len(self.views), 2, **kw)
         self.scratch = torch.empty(len(self.views), 2, 1024, **kw)
-        # Device error bits of each view (a workspace header is cleared by
-        # every forward), copied out after each view.
-        self.errs = torch.zeros(len(self.views), dtype=torch.int32, device=self.device)
-        # Tile shape per view (autotuned per resolution, else 16x16).
-        self.rasts, first = [], set()
-        grads0 = _grad_views(self.flat[0], P, D)
-        for k, (v, cap) in enumerate(zip(self.views, caps)):
-            s = self.stream_of[k]
-            shape = (16, 16)
-            if autotuner is not None:
-                b = self.bufs[k]
-                shape = autotuner.pick(scene, deform, v.cam, v.t, cap, self.workspaces[s], grads0, b["g_rgb"],
-                                       b["g_feat"])
-            self.rasts.append(Rasterizer(P, D, v.cam.width, v.cam.height, tile=shape, max_dups=cap,
-                                         device=self.device, auto_grow=False, accumulate=s in first,
-                                         workspace=self.workspaces[s]))
-            first.add(s)
-        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.S)]
+        self.fwd_batch = int(fwd_batch)
+        self._build()
+        if autotuner is not None and fwd_batch == 0:
+            self.set_fwd_batch(autotuner.pick_fwd_batch(self))
+        self.graph = None
+
+    def _build(self, wait_polls: int = 0):
+        opts = [_lib.make_opts(tile=shape, max_dups=cap, fwd_batch=self.fwd_batch, wait_polls=wait_polls)
+                for shape, cap in zip(self.tiles, self.caps)]
+        self.batch = _lib.make_batch([v.cam for v in self.views], [v.t for v in self.views], opts)
+        nbytes = _lib.fe_batch_workspace_size(self.scene.P, self.scene.D, self.batch)
+        if getattr(self, "workspace", None) is None or self.workspace.numel() < nbytes:
+            self.workspace = None
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+
+    def set_fwd_batch(self, B: int):
+        self.fwd_batch = int(B)
+        self._build()
+        self.graph = None
+
+    def set_wait_polls(self, polls: int):
+        """Test hook of the staging-wait bound (fe_opts.wait_polls)."""
+        self._build(wait_polls=polls)
         self.graph = None
 
     @property
     def tile_shapes(self):
-        return [r.tile for r in self.rasts]
+        return list(self.tiles)
 
-    def _run_view(self, k: int, grads: dict):
-        v, r, b = self.views[k], self.rasts[k], self.bufs[k]
-        HW = v.cam.width * v.cam.height
-        r.forward(self.scene, v.cam, self.deform, v.t, out=b["out"])
-        _lib.fe_l1_loss_grad(b["out"][0], v.tgt_rgb, HW, b["g_rgb"], self.losses[k, 0:1], self.scratch[k, 0])
-        _lib.fe_l1_loss_grad(b["out"][3], v.tgt_feat, HW, b["g_feat"], self.losses[k, 1:2], self.scratch[k, 1])
-        r.backward(self.scene, v.cam, self.deform, v.t, b["g_rgb"], None, None, b["g_feat"], grads=grads)
-        self.errs[k:k + 1].copy_(r.workspace[:4].view(torch.int32))
+    def view_workspace(self, k: int):
+        """(single-view workspace slice, its fe_opts) of view k inside the
+        batch workspace (a 256-byte header, then the views' workspaces)."""
+        off = 256
+        for j in range(k):
+            off += _lib.fe_workspace_size(self.scene.P, self.scene.D, self.views[j].cam.width,
+                                          self.views[j].cam.height, self.batch._opts[j])
+        o = self.batch._opts[k]
+        n = _lib.fe_workspace_size(self.scene.P, self.scene.D, self.views[k].cam.width, self.views[k].cam.height, o)
+        return self.workspace[off:off + n], o
+
+    def forward(self):
+        g = self.scene.struct()
+        d = self.deform.struct() if self.deform is not None else None
+        _lib.fe_render_batch(g, d, self.batch, self.workspace, [b["out"] for b in self.bufs])
+
+    def losses_and_grads(self):
+        """Per view, the L1 losses of the rendered RGB and feature maps to the
+        view's targets and their gradients (the upstream gradients)."""
+        for k, (v, b) in enumerate(zip(self.views, self.bufs)):
+            HW = v.cam.width * v.cam.height
+            _lib.fe_l1_loss_grad(b["out"][0], v.tgt_rgb, HW, b["g_rgb"], self.losses[k, 0:1], self.scratch[k, 0])
+            _lib.fe_l1_loss_grad(b["out"][3], v.tgt_feat, HW, b["g_feat"], self.losses[k, 1:2], self.scratch[k, 1])
+
+    def backward(self):
+        g = self.scene.struct()
+        d = self.deform.struct() if self.deform is not None else None
+        _lib.fe_render_batch_backward(g, d, self.batch, self.workspace,
+                                      [(b["g_rgb"], None, None, b["g_feat"]) for b in self.bufs], self.grads)
 
     def run(self):
         """All views: forward, L1 losses (RGB and features), backward; the
-        gradients are summed into self.grads."""
-        P, D = self.scene.P, self.scene.D
-        if self.S == 1:
-            for k in range(len(self.views)):
-                self._run_view(k, self.grads)
-            return
-        main = torch.cuda.current_stream(self.device)
-        start = torch.cuda.Event()
-        start.record(main)
-        done = []
-        for s, st in enumerate(self.streams):
-            st.wait_event(start)
-            with torch.cuda.stream(st):
-                g = _grad_views(self.flat[s], P, D)
-                for k in range(len(self.views)):
-                    if self.stream_of[k] == s:
-                        self._run_view(k, g)
-                e = torch.cuda.Event()
-                e.record(st)
-                done.append(e)
-        for e in done:
-            main.wait_event(e)
-        _lib.fe_sum_f32(self.flat[0], self.flat, stream=main)
+        gradients are summed over the views into self.grads."""
+        self.forward()
+        self.losses_and_grads()
+        self.backward()
 
     def capture(self):
-        """Record one batch into a CUDA graph (after one eager warm-up run)."""
+        """Record one batch step into a CUDA graph (after one eager warm-up run)."""
         self.run()
         torch.cuda.synchronize()
         s = torch.cuda.Stream(device=self.device)
@@ -221,10 +261,15 @@ class BatchRenderer:
             self.capture()
         self.graph.replay()
 
+    def stats(self, raise_on_error: bool = False):
+        """(status, per-view statistics) of the last batch call (synchronises)."""
+        return _lib.fe_batch_read_stats(self.workspace, self.scene.P, self.scene.D, self.batch,
+                                        raise_on_error=raise_on_error)
+
     def device_errors(self) -> int:
         """OR over the views of the device error bits of the last run
-        (synchronises): 1 = a view's list overflowed its capacity."""
+        (synchronises): 1 = a list overflowed, 2 = a bounded wait gave up."""
         e = 0
-        for x in self.errs.cpu().tolist():
-            e |= int(x)
+        for st in self.stats()[1]:
+            e |= int(st["device_errors"])
         return e

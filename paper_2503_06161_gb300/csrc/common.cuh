@@ -259,9 +259,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Polls of a staging wait before it gives up, and of the drain that waits
+// for a block's copies in flight before its shared memory is released.
+constexpr int kWaitPolls = 1 << 20;
+constexpr int kDrainPolls = 1 << 22;
+
 // Bounded wait for the phase of the given parity; false after `limit`
-// polls (each poll may suspend the thread for a short time).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = 1 << 20) {
+// polls (each poll may suspend the thread for a short time; limit 0 gives
+// up at once).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = kWaitPolls) {
   for (int i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;

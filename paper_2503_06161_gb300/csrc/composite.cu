@@ -45,7 +45,7 @@ __device__ __forceinline__ void stage_issue(const CompositeArgs& a, unsigned cha
     fence_proxy_async();  // earlier generic reads of this buffer come first
     tma_load_1d(buf + (size_t)tid * kRec * 4, a.rec + 3 * (size_t)g, (uint32_t)kRec * 4u, bar);
     tma_load_1d(buf + (size_t)B * kRec * 4 + (size_t)tid * rowb,
-                static_cast<const unsigned char*>(a.feat) + (size_t)g * rowb, rowb, bar);
+                static_cast<const unsigned char*>(a.feat) + (size_t)g * a.feat_row_bytes, rowb, bar);
   }
 }
 
@@ -63,24 +63,50 @@ __device__ __forceinline__ void widen_bf16(const unsigned char* raw, float* dst,
   }
 }
 
-// Shared memory of the forward: two staging buffers, then (bf16 features)
-// one fp32 copy of the current batch's rows.
-template <int D>
-__host__ __device__ constexpr size_t fwd_smem_bytes(int bf16) {
-  return 2 * (size_t)stage_bytes(fwd_batch<D>(), D, bf16) + (bf16 ? (size_t)fwd_batch<D>() * D * 4 : 0);
+// Shared memory of the forward with B-Gaussian batches: two staging
+// buffers, then (bf16 features) one fp32 copy of the current batch's rows.
+__host__ __device__ constexpr size_t fwd_smem_bytes(int B, int D, int bf16) {
+  return 2 * (size_t)stage_bytes(B, D, bf16) + (bf16 ? (size_t)B * D * 4 : 0);
 }
 
-template <int D, bool kCount>
-__global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const CompositeArgs a) {
-  constexpr int B = fwd_batch<D>();
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ int s_abort;
+// Staging state a block carries from tile to tile: how many times each of
+// its two staging buffers has been armed.  Arming is block-uniform, so
+// every thread derives the same wait parity from it: batch j of a tile sits
+// in buffer j & 1 and completes that buffer's (arms[b] + j / 2)-th phase.
+struct StageState {
+  uint32_t arms[2];
+  bool dead;  // a drain gave up: shared memory may still receive a copy
+};
+
+__device__ __forceinline__ uint32_t stage_parity(const StageState& st, uint32_t j) {
+  return (st.arms[j & 1] + (j >> 1)) & 1u;
+}
+
+// A tile is done with its staging buffers: the last two batches it issued
+// (any earlier one completed before its buffer was re-armed) must land
+// before shared memory is reused, whether the tile finished, left early or
+// gave up on a wait.  The drain has its own, long bound; if even that runs
+// out the block stops taking tiles.
+__device__ __forceinline__ void stage_drain(StageState& st, uint64_t* s_bar, uint32_t issued, uint32_t* err) {
+  bool ok = true;
+  for (uint32_t j = issued > 2 ? issued - 2 : 0; j < issued; ++j)
+    ok &= mbar_wait(&s_bar[j & 1], stage_parity(st, j), kDrainPolls);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) set_err(err, kErrTimeout);
+    st.dead = true;
+  }
+  st.arms[0] += (issued + 1) / 2;
+  st.arms[1] += issued / 2;
+}
+
+// Forward compositing of one tile by the whole block (see the file comment).
+template <int D, int B, bool kCount>
+__device__ __forceinline__ void fwd_tile(const CompositeArgs& a, const int tile, unsigned char* smem, uint64_t* s_bar,
+                                         int* s_abort, StageState& stg) {
   const int tid = threadIdx.x;
   const bool bf16 = a.feat_bf16 != 0;
   const uint32_t sbytes = stage_bytes(B, D, a.feat_bf16);
   float* s_wide = reinterpret_cast<float*>(smem + 2 * (size_t)sbytes);
-  const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
   int lx, ly;
   tile_pixel(tid, a.tw, lx, ly);
@@ -90,20 +116,17 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
   const uint2 rg = a.ranges[tile];
   const uint32_t n = rg.y - rg.x;
   const uint32_t nbatch = (n + B - 1) / B;
-  if (tid == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    mbar_init_fence();
-    s_abort = 0;
-  }
-  __syncthreads();
   // Gaussian of this thread's slot in batch k (prefetched a batch ahead).
   auto slot_gid = [&](uint32_t k) -> uint32_t {
     const uint32_t p = k * B + (uint32_t)tid;
     return (k < nbatch && tid < B && p < n) ? __ldg(&a.sorted[rg.x + p].y) : 0u;
   };
   auto batch_len = [&](uint32_t k) -> int { return (int)min((uint32_t)B, n - k * B); };
-  if (nbatch > 0) stage_issue<D>(a, smem, B, batch_len(0), slot_gid(0), &s_bar[0]);
+  uint32_t issued = 0;
+  if (nbatch > 0) {
+    stage_issue<D>(a, smem, B, batch_len(0), slot_gid(0), &s_bar[0]);
+    issued = 1;
+  }
   uint32_t g_next = slot_gid(1);
   float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Z = 0.f;
   float2 F[D / 2];  // feature channels in pairs (packed FP32 FMA)
@@ -117,30 +140,35 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
   constexpr int NG = B / 32;
   static_assert(NG >= 1 && NG <= 4, "blend masks cover at most four groups");
   uint32_t cm0 = 0u, cm1 = 0u, cm2 = 0u, cm3 = 0u;
-  const bool track = !kCount && a.cmask != nullptr;
+  const bool track = !kCount && a.cmask != nullptr && a.aux;
   const size_t cslot0 = (size_t)(rg.x >> 5) + (size_t)tile;
   const int lane = tid & 31, warp = tid >> 5;
-  uint32_t k = 0;
-  for (; k < nbatch; ++k) {
+  for (uint32_t k = 0; k < nbatch; ++k) {
     // Every thread is past batch k-1 here, so its buffer may be refilled.
-    if (__syncthreads_count(done) == kThreads) break;
+    // A wait on batch k-1 that gave up (s_abort[(k-1) & 1], written before
+    // this barrier; a failure in this iteration writes the other slot, so
+    // no thread can see it change) ends the tile for the whole block before
+    // anything is re-armed.
+    if (__syncthreads_count(done) == kThreads || (k > 0 && ((volatile int*)s_abort)[(k - 1) & 1])) break;
     if (k + 1 < nbatch) {
       stage_issue<D>(a, smem + ((k + 1) & 1) * (size_t)sbytes, B, batch_len(k + 1), g_next, &s_bar[(k + 1) & 1]);
+      issued = k + 2;
       g_next = slot_gid(k + 2);
     }
     const unsigned char* buf = smem + (k & 1) * (size_t)sbytes;
-    if (*(volatile int*)&s_abort || !mbar_wait(&s_bar[k & 1], (k >> 1) & 1)) {
-      if (!*(volatile int*)&s_abort) {
-        *(volatile int*)&s_abort = 1;
-        set_err(a.err, kErrTimeout);
-      }
+    const bool landed = mbar_wait(&s_bar[k & 1], stage_parity(stg, k), a.polls);
+    if (!landed) {
+      ((volatile int*)s_abort)[k & 1] = 1;
+      set_err(a.err, kErrTimeout);
       done = true;
     }
     const int nb = batch_len(k);
     const float* s_rec = reinterpret_cast<const float*>(buf);
     const float* s_feat = reinterpret_cast<const float*>(buf + (size_t)B * kRec * 4);
     if (bf16) {
-      widen_bf16<D>(buf + (size_t)B * kRec * 4, s_wide, nb);
+      // Every thread widens its share of the rows (also threads whose pixel
+      // is outside the image or done), unless its wait gave up.
+      if (landed) widen_bf16<D>(buf + (size_t)B * kRec * 4, s_wide, nb);
       __syncthreads();
       s_feat = s_wide;
     }
@@ -216,10 +244,7 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
       cm0 = cm1 = cm2 = cm3 = 0u;
     }
   }
-  // After an early exit batch k is still in flight: it must land before the
-  // block's shared memory is released.
-  if (k < nbatch && tid == 0 && !*(volatile int*)&s_abort && !mbar_wait(&s_bar[k & 1], (k >> 1) & 1))
-    set_err(a.err, kErrTimeout);
+  stage_drain(stg, s_bar, issued, a.err);
   if (kCount) {
     // Block sums of the pair counts, one 64-bit atomic per warp.
     unsigned long long v = visits, c = contribs;
@@ -236,16 +261,20 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
   }
   if (inside) {
     const size_t HW = (size_t)a.W * a.H, p = (size_t)py * a.W + px;
-    a.out_rgb[p] = C0 + T * a.bg[0];
-    a.out_rgb[HW + p] = C1 + T * a.bg[1];
-    a.out_rgb[2 * HW + p] = C2 + T * a.bg[2];
-    a.out_depth[p] = Z;
-    a.out_alpha[p] = 1.0f - T;
-    float4* fo = reinterpret_cast<float4*>(a.out_feat + p * D);
+    if (a.aux) {
+      a.out_rgb[p] = C0 + T * a.bg[0];
+      a.out_rgb[HW + p] = C1 + T * a.bg[1];
+      a.out_rgb[2 * HW + p] = C2 + T * a.bg[2];
+      a.out_depth[p] = Z;
+      a.out_alpha[p] = 1.0f - T;
+      a.t_final[p] = T;
+      a.n_contrib[p] = last;
+    }
+    float4* fo = reinterpret_cast<float4*>(a.out_feat + p * a.out_ld);
 #pragma unroll
     for (int d4 = 0; d4 < D / 4; ++d4) fo[d4] = make_float4(F[2 * d4].x, F[2 * d4].y, F[2 * d4 + 1].x, F[2 * d4 + 1].y);
     if (a.out_feat_bf16) {
-      uint4* fb = reinterpret_cast<uint4*>(a.out_feat_bf16 + p * D);
+      uint4* fb = reinterpret_cast<uint4*>(a.out_feat_bf16 + p * a.out_ld);
 #pragma unroll
       for (int q = 0; q < D / 8; ++q) {
         uint32_t w4[4];
@@ -257,8 +286,59 @@ __global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const Composite
         fb[q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
       }
     }
-    a.t_final[p] = T;
-    a.n_contrib[p] = last;
+  }
+}
+
+// Barriers and the abort flag of a compositing block, initialised once.
+__device__ __forceinline__ void stage_init(uint64_t* s_bar) {
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_init_fence();
+  }
+}
+
+// One block per tile.
+template <int D, int B, bool kCount>
+__global__ void __launch_bounds__(kThreads) composite_fwd_kernel(const CompositeArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_abort[2];
+  stage_init(s_bar);
+  if (threadIdx.x == 0) s_abort[0] = s_abort[1] = 0;
+  __syncthreads();
+  StageState stg{{0u, 0u}, false};
+  fwd_tile<D, B, kCount>(a, blockIdx.x, smem, s_bar, s_abort, stg);
+}
+
+// (view, tile) work item `item` of a batch: the view whose item range holds it.
+__device__ __forceinline__ int batch_view(const BatchCompositeArgs& ba, int item) {
+  int v = 0;
+  while (v + 1 < ba.V && item >= ba.item_start[v + 1]) ++v;
+  return v;
+}
+
+// Persistent form over a batch of views: each block takes (view, tile)
+// items from a device counter until the batch is exhausted (no block waits
+// for another: items are independent).
+template <int D, int B>
+__global__ void __launch_bounds__(kThreads) composite_fwd_batch_kernel(const __grid_constant__ BatchCompositeArgs ba) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_abort[2], s_item;
+  stage_init(s_bar);
+  StageState stg{{0u, 0u}, false};
+  for (;;) {
+    // Every thread is past the previous tile (its drain ended in a barrier).
+    if (threadIdx.x == 0) {
+      s_item = (int)atomicAdd(ba.queue, 1u);
+      s_abort[0] = s_abort[1] = 0;
+    }
+    __syncthreads();
+    const int item = s_item;
+    if (item >= ba.nitems || stg.dead) break;
+    const int v = batch_view(ba, item);
+    fwd_tile<D, B, false>(ba.view[v], item - ba.item_start[v], smem, s_bar, s_abort, stg);
   }
 }
 
@@ -297,13 +377,12 @@ struct BwdCfg {
   __host__ __device__ static constexpr size_t smem_bytes(int bf16) { return off_e(bf16) + (size_t)(2 * B + 8 + 4) * 4; }
 };
 
+// Reverse compositing of one tile by the whole block.
 template <int D>
-__global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kernel(const CompositeArgs a) {
+__device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile, unsigned char* smem, uint64_t* s_bar,
+                                         int* s_abort, StageState& stg) {
   using K = BwdCfg<D>;
-  constexpr int B = K::B, NC = K::NC, GS = K::GS, WS = K::WS, NP = partial_stride(D);
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ int s_abort;
+  constexpr int B = K::B, NC = K::NC, GS = K::GS, WS = K::WS;
   const bool bf16 = a.feat_bf16 != 0;
   const uint32_t sbytes = stage_bytes(B, D, a.feat_bf16);
   float* s_G = reinterpret_cast<float*>(smem + K::off_G);          // [256][GS]
@@ -315,7 +394,6 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
   uint32_t* s_jact = s_e + 2 * B;
   uint32_t* s_maxn = s_jact + 8;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
   int lx, ly;
   tile_pixel(tid, a.tw, lx, ly);
@@ -335,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
     }
     grow[0] = g0; grow[1] = g1; grow[2] = g2; grow[3] = gz;
     if (inside && a.g_feat) {
-      const float4* src = reinterpret_cast<const float4*>(a.g_feat + pix * D);
+      const float4* src = reinterpret_cast<const float4*>(a.g_feat + pix * a.out_ld);
 #pragma unroll
       for (int d4 = 0; d4 < D / 4; ++d4) {
         const float4 v = __ldg(src + d4);
@@ -356,13 +434,7 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
   float T = Tf;
   float Q = (grow[0] * a.bg[0] + grow[1] * a.bg[1] + grow[2] * a.bg[2]) * Tf;
   const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, nc);
-  if (tid == 0) {
-    *s_maxn = 0u;
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    mbar_init_fence();
-    s_abort = 0;
-  }
+  if (tid == 0) *s_maxn = 0u;
   __syncthreads();
   if (lane == 0 && wmax) atomicMax(s_maxn, wmax);
   __syncthreads();
@@ -391,26 +463,30 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
   };
   uint32_t e_next, g_next;
   slot(0, e_next, g_next);
+  uint32_t issued = 0;
   if (nbatch > 0) {
     stage_issue<D>(a, s_stage, B, batch_len(0), g_next, &s_bar[0]);
     if (tid < B) s_e[tid] = e_next;
+    issued = 1;
   }
   slot(1, e_next, g_next);
   float* slice = s_slice + warp * K::SLICE;
   for (uint32_t k = 0; k < nbatch; ++k) {
-    // Every thread is past batch k-1 (and its combine) here.
+    // Every thread is past batch k-1 (and its combine) here.  A wait on
+    // batch k-1 that gave up ends the tile for the whole block (the flag
+    // slots alternate by batch, as in the forward).
     __syncthreads();
+    if (k > 0 && ((volatile int*)s_abort)[(k - 1) & 1]) break;
     if (k + 1 < nbatch) {
       stage_issue<D>(a, s_stage + ((k + 1) & 1) * (size_t)sbytes, B, batch_len(k + 1), g_next, &s_bar[(k + 1) & 1]);
       if (tid < B) s_e[((k + 1) & 1) * B + tid] = e_next;
+      issued = k + 2;
       slot(k + 2, e_next, g_next);
     }
     bool live = true;
-    if (*(volatile int*)&s_abort || !mbar_wait(&s_bar[k & 1], (k >> 1) & 1)) {
-      if (!*(volatile int*)&s_abort) {
-        *(volatile int*)&s_abort = 1;
-        set_err(a.err, kErrTimeout);
-      }
+    if (!mbar_wait(&s_bar[k & 1], stage_parity(stg, k), a.polls)) {
+      ((volatile int*)s_abort)[k & 1] = 1;
+      set_err(a.err, kErrTimeout);
       live = false;
     }
     const unsigned char* buf = s_stage + (k & 1) * (size_t)sbytes;
@@ -418,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
     const float* s_feat = reinterpret_cast<const float*>(buf + (size_t)B * kRec * 4);
     const int nb = batch_len(k);
     if (bf16) {
-      widen_bf16<D>(buf + (size_t)B * kRec * 4, s_wide, nb);
+      if (live) widen_bf16<D>(buf + (size_t)B * kRec * 4, s_wide, nb);
       __syncthreads();
       s_feat = s_wide;
     }
@@ -434,18 +510,17 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
         for (int q = 0; q < B / 4; ++q) wrow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       // Entry j given its evaluation (hit: the pixel includes it): the T
-      // replay, the gradient terms, and their warp sums.
-      auto entry = [&](int j, bool hit, const PairEval& pe) {
-        float v[8];
+      // replay and the gradient terms v (six geometric values, then two
+      // zeros), and the blend weight written to the warp's w slice.
+      auto entry = [&](int j, bool hit, const PairEval& pe, float (&v)[8]) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[q] = 0.0f;
-        float w = 0.0f;
         if (hit) {
           const float* rec = s_rec + j * kRec;
           const float one_m = 1.0f - pe.alpha;
           const float inv = __fdividef(1.0f, one_m);  // one_m >= 0.01
           T = T * inv;  // transmittance before this Gaussian
-          w = pe.alpha * T;
+          const float w = pe.alpha * T;
           // s = g . (rgb, depth, feature) of this Gaussian.
           const float4 r4 = *reinterpret_cast<const float4*>(rec + 4);  // ., ., depth, r
           const float4 r8 = *reinterpret_cast<const float4*>(rec + 8);  // g, b, ., .
@@ -472,53 +547,94 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
             v[4] = dp2 * pe.dy * pe.dy;
             v[5] = dalpha * pe.G;
           }
+          slice[lane * WS + j] = w;
         }
-        if (hit) slice[lane * WS + j] = w;
-        if (__ballot_sync(0xFFFFFFFFu, hit)) {
-          jact |= 1u << j;
-          // Reduce-scatter of v[0..7] over the warp: lane 4m ends with index m.
-          const int b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1;
+      };
+      const int b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1, b2 = (lane >> 1) & 1;
+      // Warp sums of one entry's v[0..7] (reduce-scatter: lane 4m ends with
+      // the sum of index m).
+      auto scatter1 = [&](int j, float (&v)[8]) {
+        jact |= 1u << j;
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float send = b16 ? v[i] : v[i + 4];
-            const float keep = b16 ? v[i + 4] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
-          }
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const float send = b8 ? v[i] : v[i + 2];
-            const float keep = b8 ? v[i + 2] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
-          }
-          {
-            const float send = b4 ? v[0] : v[1];
-            const float keep = b4 ? v[1] : v[0];
-            v[0] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
-          }
-          v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 2);
-          v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 1);
-          const int m = lane >> 2;
-          if ((lane & 3) == 0 && m < 6) s_geo[(warp * B + j) * 8 + m] = v[0];
+        for (int i = 0; i < 4; ++i) {
+          const float send = b16 ? v[i] : v[i + 4];
+          const float keep = b16 ? v[i + 4] : v[i];
+          v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
         }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const float send = b8 ? v[i] : v[i + 2];
+          const float keep = b8 ? v[i + 2] : v[i];
+          v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+        }
+        {
+          const float send = b4 ? v[0] : v[1];
+          const float keep = b4 ? v[1] : v[0];
+          v[0] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
+        }
+        v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 2);
+        v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 1);
+        const int m = lane >> 2;
+        if ((lane & 3) == 0 && m < 6) s_geo[(warp * B + j) * 8 + m] = v[0];
+      };
+      // Both entries' sums at once: u = (va, vb), lane 2m ends with the sum
+      // of index m (16 shuffles instead of 18, and no warp-wide exchange
+      // between the two entries' arithmetic).
+      auto scatter2 = [&](int ja, int jb, float (&va)[8], float (&vb)[8]) {
+        jact |= (1u << ja) | (1u << jb);
+        float u[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float send = b16 ? va[i] : vb[i];
+          const float keep = b16 ? vb[i] : va[i];
+          u[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float send = b8 ? u[i] : u[i + 4];
+          const float keep = b8 ? u[i + 4] : u[i];
+          u[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const float send = b4 ? u[i] : u[i + 2];
+          const float keep = b4 ? u[i + 2] : u[i];
+          u[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
+        }
+        {
+          const float send = b2 ? u[0] : u[1];
+          const float keep = b2 ? u[1] : u[0];
+          u[0] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 2);
+        }
+        u[0] += __shfl_xor_sync(0xFFFFFFFFu, u[0], 1);
+        // lane 2m holds index m = 8 b16 + 4 b8 + 2 b4 + b2 of u = (va, vb).
+        const int m = lane >> 1, e = m & 7;
+        if ((lane & 1) == 0 && e < 6) s_geo[(warp * B + (m < 8 ? ja : jb)) * 8 + e] = u[0];
       };
       auto evaluate = [&](int j, PairEval& pe) -> bool {
         return live && rel0 + (uint32_t)j < nc && eval_pair(s_rec + j * kRec, pxc, pyc, pe);
       };
-      // The entries to visit, back to front, two evaluated ahead of their
-      // (ordered) replay.
+      // The entries to visit, back to front, in pairs: both evaluated, then
+      // replayed in order (the T chain), then summed over the warp together.
       while (todo) {
         const int ja = 31 - __clz(todo);
         todo &= ~(1u << ja);
         PairEval pa, pb;
+        float va[8], vb[8];
         const bool ha = evaluate(ja, pa);
         if (todo) {
           const int jb = 31 - __clz(todo);
           todo &= ~(1u << jb);
           const bool hb = evaluate(jb, pb);
-          entry(ja, ha, pa);
-          entry(jb, hb, pb);
+          entry(ja, ha, pa, va);
+          entry(jb, hb, pb, vb);
+          const bool aa = __any_sync(0xFFFFFFFFu, ha), ab = __any_sync(0xFFFFFFFFu, hb);
+          if (aa && ab) scatter2(ja, jb, va, vb);
+          else if (aa) scatter1(ja, va);
+          else if (ab) scatter1(jb, vb);
         } else {
-          entry(ja, ha, pa);
+          entry(ja, ha, pa, va);
+          if (__any_sync(0xFFFFFFFFu, ha)) scatter1(ja, va);
         }
       }
       __syncwarp();
@@ -595,10 +711,13 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
     const int nact = __popc(bm);
     // One item = four consecutive columns of an active entry's partial row
     // [features | du dv dA dB dCc dopacity | r g b | depth | 0 0]: the warp
-    // partials summed in warp order, one 16-byte store.
+    // partials summed in warp order, one 16-byte store.  A channel-split
+    // pass that is not the first adds its geometric terms (du .. dopacity)
+    // to the row the first pass wrote and leaves colour and depth alone.
     constexpr int NQ = D / 4 + 3;
-    for (int item = tid; item < nact * NQ; item += kThreads) {
-      const int ja = item / NQ, q4 = item - ja * NQ;
+    const int nq = a.aux ? NQ : NQ - 1;
+    for (int item = tid; item < nact * nq; item += kThreads) {
+      const int ja = item / nq, q4 = item - ja * nq;
       const int j = (int)__fns(bm, 0, ja + 1);  // the ja-th active entry
       float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
@@ -624,20 +743,88 @@ __global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kerne
           acc.w += v.w;
         }
       }
-      if ((int64_t)se[j] < a.cap) *reinterpret_cast<float4*>(a.partials + (size_t)se[j] * NP + 4 * q4) = acc;
+      if ((int64_t)se[j] < a.cap) {
+        float* row = a.partials + (size_t)se[j] * a.prow;
+        float4* dst = reinterpret_cast<float4*>(q4 < D / 4 ? row + a.pcol0 + 4 * q4 : row + a.pscal + 4 * (q4 - D / 4));
+        if (!a.aux && q4 >= D / 4) {
+          const float4 prev = *dst;
+          acc.x += prev.x;
+          acc.y += prev.y;
+          if (q4 == D / 4) {
+            acc.z += prev.z;
+            acc.w += prev.w;
+          } else {
+            acc.z = prev.z;  // colour: the first pass's
+            acc.w = prev.w;
+          }
+        }
+        *dst = acc;
+      }
     }
     if (tid < nb && ((bm >> tid) & 1u) && (int64_t)se[tid] < a.cap)
       atomicOr(a.pflags + (se[tid] >> 5), 1u << (se[tid] & 31u));
   }
+  stage_drain(stg, s_bar, issued, a.err);
 }
 
+// One block per tile.
 template <int D>
+__global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1) composite_bwd_kernel(const CompositeArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_abort[2];
+  stage_init(s_bar);
+  if (threadIdx.x == 0) s_abort[0] = s_abort[1] = 0;
+  __syncthreads();
+  StageState stg{{0u, 0u}, false};
+  bwd_tile<D>(a, blockIdx.x, smem, s_bar, s_abort, stg);
+}
+
+// Persistent form over a batch of views, as the forward's.
+template <int D>
+__global__ void __launch_bounds__(kThreads, D <= 32 ? 2 : 1)
+    composite_bwd_batch_kernel(const __grid_constant__ BatchCompositeArgs ba) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_abort[2], s_item;
+  stage_init(s_bar);
+  StageState stg{{0u, 0u}, false};
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_item = (int)atomicAdd(ba.queue, 1u);
+      s_abort[0] = s_abort[1] = 0;
+    }
+    __syncthreads();
+    const int item = s_item;
+    if (item >= ba.nitems || stg.dead) break;
+    const int v = batch_view(ba, item);
+    bwd_tile<D>(ba.view[v], item - ba.item_start[v], smem, s_bar, s_abort, stg);
+  }
+}
+
+template <int D, int B, bool kCount>
 cudaError_t launch_fwd_t(const CompositeArgs& a, cudaStream_t st) {
-  const size_t smem = fwd_smem_bytes<D>(a.feat_bf16);
-  auto k = a.counts ? composite_fwd_kernel<D, true> : composite_fwd_kernel<D, false>;
+  const size_t smem = fwd_smem_bytes(B, D, a.feat_bf16);
+  auto k = composite_fwd_kernel<D, B, kCount>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<a.ntiles, kThreads, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+// Batch sizes: 32, 64, 128 Gaussians (128 only up to D = 64); the counting
+// form runs with the default batch only.
+template <int D>
+cudaError_t launch_fwd_d(const CompositeArgs& a, int B, cudaStream_t st) {
+  if (B == 0) B = fwd_batch<D>();
+  if (a.counts) return B == fwd_batch<D>() ? launch_fwd_t<D, fwd_batch<D>(), true>(a, st) : cudaErrorInvalidValue;
+  switch (B) {
+    case 32: return launch_fwd_t<D, 32, false>(a, st);
+    case 64: return launch_fwd_t<D, 64, false>(a, st);
+    case 128:
+      if constexpr (D <= 64) return launch_fwd_t<D, 128, false>(a, st);
+      break;
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int D>
@@ -649,15 +836,97 @@ cudaError_t launch_bwd_t(const CompositeArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Grid of a persistent launch: as many blocks as fit on the GPU at once
+// (occupancy x SMs), never more than there are work items.
+template <typename Kern>
+cudaError_t persistent_grid(Kern k, size_t smem, int nitems, int& grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  grid = per_sm * sms;
+  if (grid > nitems) grid = nitems;
+  if (grid < 1) grid = 1;
+  return cudaSuccess;
+}
+
+template <int D, int B>
+cudaError_t launch_fwd_batch_t(const BatchCompositeArgs& b, int bf16, cudaStream_t st) {
+  const size_t smem = fwd_smem_bytes(B, D, bf16);
+  auto k = composite_fwd_batch_kernel<D, B>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int grid = 1;
+  if (e == cudaSuccess) e = persistent_grid(k, smem, b.nitems, grid);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kThreads, smem, st>>>(b);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_fwd_batch_d(const BatchCompositeArgs& b, int bf16, int B, cudaStream_t st) {
+  if (B == 0) B = fwd_batch<D>();
+  switch (B) {
+    case 32: return launch_fwd_batch_t<D, 32>(b, bf16, st);
+    case 64: return launch_fwd_batch_t<D, 64>(b, bf16, st);
+    case 128:
+      if constexpr (D <= 64) return launch_fwd_batch_t<D, 128>(b, bf16, st);
+      break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int D>
+cudaError_t launch_bwd_batch_t(const BatchCompositeArgs& b, int bf16, cudaStream_t st) {
+  const size_t smem = BwdCfg<D>::smem_bytes(bf16);
+  auto k = composite_bwd_batch_kernel<D>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int grid = 1;
+  if (e == cudaSuccess) e = persistent_grid(k, smem, b.nitems, grid);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kThreads, smem, st>>>(b);
+  return cudaGetLastError();
+}
+
+// D = 256 runs as two passes over 128-channel halves (h = 0, 1): the same
+// list, the same per-pixel decisions, each pass staging and accumulating
+// its half of every feature row.  Pass 0 owns colour, depth, alpha, T_final,
+// n_contrib, the blend masks and (reverse) the colour / depth / alpha /
+// background terms; the reverse's geometric terms are linear in the dot
+// products g . x, so pass 1 adds the share of its channels to the rows pass
+// 0 wrote (same stream, pass 0 first: a fixed order).
+CompositeArgs channel_half(const CompositeArgs& a, int h) {
+  CompositeArgs c = a;
+  const size_t elem = a.feat_bf16 ? 2 : 4;
+  c.D = 128;
+  c.feat = static_cast<const unsigned char*>(a.feat) + (size_t)h * 128 * elem;
+  if (a.out_feat) c.out_feat = a.out_feat + h * 128;
+  if (a.out_feat_bf16) c.out_feat_bf16 = a.out_feat_bf16 + h * 128;
+  if (a.g_feat) c.g_feat = a.g_feat + h * 128;
+  c.pcol0 = a.pcol0 + h * 128;
+  if (h > 0) {
+    c.aux = 0;
+    c.g_rgb = c.g_depth = c.g_alpha = nullptr;
+  }
+  return c;
+}
+
 }  // namespace
 
-cudaError_t launch_composite_fwd(const CompositeArgs& a, cudaStream_t st) {
+bool fwd_batch_supported(int B) { return B == 0 || B == 32 || B == 64 || B == 128; }
+
+cudaError_t launch_composite_fwd(const CompositeArgs& a, int fwd_batch, cudaStream_t st) {
   if (a.ntiles <= 0) return cudaSuccess;
   switch (a.D) {
-    case 16: return launch_fwd_t<16>(a, st);
-    case 32: return launch_fwd_t<32>(a, st);
-    case 64: return launch_fwd_t<64>(a, st);
-    case 128: return launch_fwd_t<128>(a, st);
+    case 16: return launch_fwd_d<16>(a, fwd_batch, st);
+    case 32: return launch_fwd_d<32>(a, fwd_batch, st);
+    case 64: return launch_fwd_d<64>(a, fwd_batch, st);
+    case 128: return launch_fwd_d<128>(a, fwd_batch, st);
+    case 256: {
+      if (a.counts) return launch_fwd_d<128>(channel_half(a, 0), fwd_batch, st);
+      const cudaError_t e = launch_fwd_d<128>(channel_half(a, 0), fwd_batch, st);
+      return e != cudaSuccess ? e : launch_fwd_d<128>(channel_half(a, 1), fwd_batch, st);
+    }
   }
   return cudaErrorInvalidValue;
 }
@@ -669,6 +938,49 @@ cudaError_t launch_composite_bwd(const CompositeArgs& a, cudaStream_t st) {
     case 32: return launch_bwd_t<32>(a, st);
     case 64: return launch_bwd_t<64>(a, st);
     case 128: return launch_bwd_t<128>(a, st);
+    case 256: {
+      const cudaError_t e = launch_bwd_t<128>(channel_half(a, 0), st);
+      return e != cudaSuccess ? e : launch_bwd_t<128>(channel_half(a, 1), st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// The batch's per-view arguments for channel half h, its own work counter.
+static BatchCompositeArgs batch_half(const BatchCompositeArgs& b, int h) {
+  BatchCompositeArgs c = b;
+  for (int v = 0; v < b.V; ++v) c.view[v] = channel_half(b.view[v], h);
+  c.queue = b.queue + 2 * h;
+  return c;
+}
+
+cudaError_t launch_composite_fwd_batch(const BatchCompositeArgs& b, int D, int feat_bf16, int fwd_batch,
+                                       cudaStream_t st) {
+  if (b.nitems <= 0) return cudaSuccess;
+  switch (D) {
+    case 16: return launch_fwd_batch_d<16>(b, feat_bf16, fwd_batch, st);
+    case 32: return launch_fwd_batch_d<32>(b, feat_bf16, fwd_batch, st);
+    case 64: return launch_fwd_batch_d<64>(b, feat_bf16, fwd_batch, st);
+    case 128: return launch_fwd_batch_d<128>(b, feat_bf16, fwd_batch, st);
+    case 256: {
+      const cudaError_t e = launch_fwd_batch_d<128>(batch_half(b, 0), feat_bf16, fwd_batch, st);
+      return e != cudaSuccess ? e : launch_fwd_batch_d<128>(batch_half(b, 1), feat_bf16, fwd_batch, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_composite_bwd_batch(const BatchCompositeArgs& b, int D, int feat_bf16, cudaStream_t st) {
+  if (b.nitems <= 0) return cudaSuccess;
+  switch (D) {
+    case 16: return launch_bwd_batch_t<16>(b, feat_bf16, st);
+    case 32: return launch_bwd_batch_t<32>(b, feat_bf16, st);
+    case 64: return launch_bwd_batch_t<64>(b, feat_bf16, st);
+    case 128: return launch_bwd_batch_t<128>(b, feat_bf16, st);
+    case 256: {
+      const cudaError_t e = launch_bwd_batch_t<128>(batch_half(b, 0), feat_bf16, st);
+      return e != cudaSuccess ? e : launch_bwd_batch_t<128>(batch_half(b, 1), feat_bf16, st);
+    }
   }
   return cudaErrorInvalidValue;
 }

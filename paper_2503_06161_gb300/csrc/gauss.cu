@@ -786,7 +786,8 @@ __device__ __forceinline__ void for_each_row(const uint32_t* bits, uint32_t e0, 
 //    bitwise reproducible.
 template <int NP>
 __device__ __forceinline__ void reduce_rows_short(const GaussBwdArgs& b, uint32_t e0, uint32_t e1, int lane,
-                                                  float acc[5]) {
+                                                  float* acc) {
+  constexpr int NQ = (NP + 31) / 32;
   const uint32_t w0 = e0 >> 5, w1 = (e1 - 1) >> 5;
   for (uint32_t w = w0; w <= w1; ++w) {
     uint32_t m = b.pflags[w];
@@ -802,17 +803,17 @@ __device__ __forceinline__ void reduce_rows_short(const GaussBwdArgs& b, uint32_
         e[u] = lo + (v[u] ? (uint32_t)(__ffs(m) - 1) : 0u);
         m = v[u] ? (m & (m - 1u)) : 0u;
       }
-      float x[4][5];
+      float x[4][NQ];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float* row = b.partials + (size_t)e[u] * NP;
 #pragma unroll
-        for (int q = 0; q < 5; ++q) x[u][q] = (v[u] && lane + 32 * q < NP) ? row[lane + 32 * q] : 0.0f;
+        for (int q = 0; q < NQ; ++q) x[u][q] = (v[u] && lane + 32 * q < NP) ? row[lane + 32 * q] : 0.0f;
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int q = 0; q < 5; ++q)
+        for (int q = 0; q < NQ; ++q)
           if (v[u]) acc[q] += x[u][q];
     }
   }
@@ -820,7 +821,7 @@ __device__ __forceinline__ void reduce_rows_short(const GaussBwdArgs& b, uint32_
 
 template <int NP>
 __device__ __forceinline__ void reduce_rows_long(const GaussBwdArgs& b, uint32_t e0, uint32_t e1, int lane,
-                                                 float acc[5]) {
+                                                 float* acc) {
   const uint32_t w0 = e0 >> 5, w1 = (e1 - 1) >> 5;
 #pragma unroll 1
   for (int c0 = 0; c0 < NP; c0 += 16) {
@@ -869,13 +870,16 @@ __global__ void __launch_bounds__(kThreads) partial_reduce_kernel(const GaussBwd
   if (g >= P) return;
   const uint32_t e0 = b.offs_by_gid[g];
   const uint32_t e1 = (uint32_t)min((uint64_t)e0 + b.touched[g], (uint64_t)b.cap);  // e0 >= e1 past capacity
-  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // columns lane, lane+32, ... (NP <= 140)
+  constexpr int NQ = (NP + 31) / 32;
+  float acc[NQ];  // columns lane, lane+32, ...
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0f;
   if (e0 < e1) {
     if (e1 - e0 <= 64) reduce_rows_short<NP>(b, e0, e1, lane, acc);
     else reduce_rows_long<NP>(b, e0, e1, lane, acc);
   }
 #pragma unroll
-  for (int q = 0; q < 5; ++q) {
+  for (int q = 0; q < NQ; ++q) {
     const int col = lane + 32 * q;
     if (col < D) b.d_feat[g * D + col] = b.accumulate ? b.d_feat[g * D + col] + acc[q] : acc[q];
     else if (col < NP) b.psum[g * 12 + (col - D)] = acc[q];
@@ -1158,6 +1162,7 @@ cudaError_t launch_gauss_bwd(const GaussArgs& a, const GaussBwdArgs& b, cudaStre
     case 32: partial_reduce_kernel<32><<<nblk, kThreads, 0, st>>>(b, a.P); break;
     case 64: partial_reduce_kernel<64><<<nblk, kThreads, 0, st>>>(b, a.P); break;
     case 128: partial_reduce_kernel<128><<<nblk, kThreads, 0, st>>>(b, a.P); break;
+    case 256: partial_reduce_kernel<256><<<nblk, kThreads, 0, st>>>(b, a.P); break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();

@@ -90,10 +90,40 @@ struct CompositeArgs {
   uint64_t* counts;  // non-NULL: counting variant of the forward (no outputs)
   uint32_t* err;     // header error bits (staging timeouts)
   uint32_t* cmask;   // NULL, or per (tile, 32-entry group, warp) masks of blended entries
+  int polls;         // bound of each staging wait (polls); 0: give up at once
+  // Channel split (D = 256 runs as two passes over 128-channel halves; a
+  // single pass has feat_row_bytes = D x element size, out_ld = D,
+  // prow = D + 12, pcol0 = 0, pscal = D, aux = 1):
+  uint32_t feat_row_bytes;  // bytes between consecutive Gaussians' rows of `feat` (pointer at this pass's channels)
+  int out_ld;               // floats between pixels of out_feat / out_feat_bf16 / g_feat (pointers at this pass's channels)
+  int prow, pcol0, pscal;   // partial row stride (floats), column of this pass's first channel, of the scalars
+  int aux;                  // 1: this pass writes colour, depth, alpha, T_final, n_contrib, the blend masks and
+                            // (reverse) the scalar columns; 0: (reverse) adds its geometric terms to them
 };
 
-cudaError_t launch_composite_fwd(const CompositeArgs& a, cudaStream_t st);
+// Forward compositing; fwd_batch = Gaussians per staged batch (32, 64 or
+// 128; 0 = the default for D).
+cudaError_t launch_composite_fwd(const CompositeArgs& a, int fwd_batch, cudaStream_t st);
 cudaError_t launch_composite_bwd(const CompositeArgs& a, cudaStream_t st);
+
+// Views of one batched launch (kernel parameter space holds them all).
+constexpr int kMaxViews = 32;
+
+// A batch of views composited by one persistent launch: (view, tile) work
+// items numbered view after view (view v owns items [item_start[v],
+// item_start[v+1])), taken by the blocks from the device counter `queue`
+// (zeroed before the launch).
+struct BatchCompositeArgs {
+  int V, nitems;
+  int item_start[kMaxViews + 1];
+  CompositeArgs view[kMaxViews];
+  uint32_t* queue;
+};
+
+cudaError_t launch_composite_fwd_batch(const BatchCompositeArgs& b, int D, int feat_bf16, int fwd_batch,
+                                       cudaStream_t st);
+cudaError_t launch_composite_bwd_batch(const BatchCompositeArgs& b, int D, int feat_bf16, cudaStream_t st);
+bool fwd_batch_supported(int fwd_batch);
 
 struct DumpArgs {
   int64_t cap;
@@ -117,6 +147,9 @@ cudaError_t launch_screen_stats(const uint32_t* touched, const float* psum, int 
                                 int32_t* count, cudaStream_t st);
 
 cudaError_t probe_fp32(int iters, double* flops, cudaStream_t st);
+// dst = ((srcs[0] + srcs[1]) + ...) elementwise (1..8 sources, any alignment;
+// dst may alias srcs[0]).
+cudaError_t launch_sum_f32(float* dst, const float* const* srcs, int nsrc, int64_t n, cudaStream_t st);
 cudaError_t launch_l1(const float* pred, const float* target, int64_t n, int64_t rows, float* grad, float* loss,
                       float* scratch, cudaStream_t st);
 void l1_grad_launch(const float* pred, const float* target, int64_t n, float inv_rows, float* grad, float* partial,

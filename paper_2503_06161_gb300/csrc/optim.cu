@@ -108,7 +108,36 @@ __global__ void __launch_bounds__(256) sum_kernel(float* __restrict__ dst, const
   }
 }
 
+// Unaligned arrays: one element per thread.
+__global__ void __launch_bounds__(256) sum1_kernel(float* __restrict__ dst, const SumArgs s, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float acc = s.src[0][i];
+    for (int k = 1; k < s.nsrc; ++k) acc += s.src[k][i];
+    dst[i] = acc;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_sum_f32(float* dst, const float* const* srcs, int nsrc, int64_t n, cudaStream_t st) {
+  if (nsrc < 1 || nsrc > kSumMaxSrc) return cudaErrorInvalidValue;
+  if (n <= 0) return cudaSuccess;
+  SumArgs s{};
+  s.nsrc = nsrc;
+  bool vec = al16(dst);
+  for (int k = 0; k < nsrc; ++k) {
+    s.src[k] = srcs[k];
+    vec = vec && al16(srcs[k]);
+  }
+  if (vec) {
+    const int64_t blocks = (n / 4 + 255) / 256 + 1;
+    sum_kernel<<<(int)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(dst, s, n);
+  } else {
+    const int64_t blocks = (n + 255) / 256;
+    sum1_kernel<<<(int)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(dst, s, n);
+  }
+  return cudaGetLastError();
+}
 
 }  // namespace fe
 

@@ -97,18 +97,25 @@ class Rasterizer:
 
     def __init__(self, P: int, D: int, width: int, height: int, tile=(16, 16), bg=(0.0, 0.0, 0.0),
                  max_dups: int = 0, forward_only: bool = False, device="cuda", auto_grow: bool | None = None,
-                 accumulate: bool = False, workspace: torch.Tensor | None = None):
+                 accumulate: bool = False, workspace: torch.Tensor | None = None, fwd_batch: int = 0,
+                 wait_polls: int = 0):
         """accumulate: backward adds to the gradient buffers instead of
         overwriting them.  workspace: optional uint8 device tensor to use
         (e.g. one buffer shared by views that are rendered one after the
-        other); it must hold workspace_bytes(...)."""
+        other); it must hold workspace_bytes(...).  fwd_batch: Gaussians per
+        staged batch of the compositing forward (0 = default).  wait_polls:
+        test hook of the staging-wait bound (fe_opts.wait_polls)."""
         self.P, self.D, self.width, self.height = int(P), int(D), int(width), int(height)
         self.tile, self.bg, self.forward_only = tuple(tile), tuple(bg), bool(forward_only)
         self.accumulate = bool(accumulate)
+        self.fwd_batch, self.wait_polls = int(fwd_batch), int(wait_polls)
         self.device = torch.device(device)
-        # Without an explicit capacity, check each forward for overflow (one
-        # host sync) and grow the duplicate list when needed.
+        # Without an explicit capacity, the FIRST forward reads the list size
+        # back (one host sync) and grows the list to 1.5x what it needed;
+        # later forwards read nothing back.  An overflow is still recorded on
+        # the device (the overflowing tiles are left empty): check() reads it.
         self.auto_grow = (max_dups == 0) if auto_grow is None else bool(auto_grow)
+        self._sized = False
         self._alloc(int(max_dups), workspace)
 
     @staticmethod
@@ -117,7 +124,8 @@ class Rasterizer:
                                       _lib.make_opts(tuple(tile), (0.0, 0.0, 0.0), int(max_dups), forward_only))
 
     def _alloc(self, max_dups: int, workspace: torch.Tensor | None = None):
-        self.opts = _lib.make_opts(self.tile, self.bg, max_dups, self.forward_only, self.accumulate)
+        self.opts = _lib.make_opts(self.tile, self.bg, max_dups, self.forward_only, self.accumulate, self.fwd_batch,
+                                   self.wait_polls)
         self.nbytes = _lib.fe_workspace_size(self.P, self.D, self.width, self.height, self.opts)
         if workspace is not None:
             if workspace.numel() * workspace.element_size() < self.nbytes or workspace.dtype != torch.uint8:
@@ -144,13 +152,22 @@ class Rasterizer:
         for _ in range(4):
             _lib.fe_render_forward(scene.struct(), deform.struct() if deform is not None else None, cam, t,
                                    self.opts, self.workspace, rgb, depth, alpha, feat, feat_bf16=feat_bf16)
-            if not self.auto_grow:
+            if not self.auto_grow or self._sized:
                 break
             st = self.stats(raise_on_error=False)
-            if not (st["device_errors"] & 1):
+            # Sized once the list fits with a 1.5x margin for later frames;
+            # otherwise grow and render again (the state the backward reads
+            # must be in the workspace that stays).
+            if not (st["device_errors"] & 1) and st["num_dups"] * 3 <= 2 * self.capacity:
+                self._sized = True
                 break
-            self._alloc(int(st["num_dups"] * 1.25) + 4096)
+            self._alloc(int(st["num_dups"] * 1.5) + 4096)
         return rgb, depth, alpha, feat
+
+    def check(self):
+        """Raises if the last forward overflowed its list or hit another
+        device-side error (synchronises the stream)."""
+        self.stats(raise_on_error=True)
 
     def backward(self, scene: GaussianScene, cam: _lib.fe_camera, deform: DeformField | None, t: float,
                  g_rgb=None, g_depth=None, g_alpha=None, g_feat=None, grads=None):

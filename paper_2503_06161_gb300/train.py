@@ -39,13 +39,16 @@ SCHEDULE_STEPS = 3000
 class Trainer:
     def __init__(self, masters: dict, sh_degree: int, cam, deform: DeformField | None, decoder: Decoder,
                  bf16_storage: bool = True, max_dups: int | None = None, lr: dict | None = None, device="cuda",
-                 fst: FSTDeform | None = None, schedule: bool = True, density_stats: bool = False):
+                 fst: FSTDeform | None = None, schedule: bool = True, density_stats: bool = False,
+                 grad_exchange=None):
         """masters: float32 device tensors means [P,3], log_scales [P,3],
         quats [P,4], opacity_logits [P], sh [P,16,3], feat [P,D].  deform:
         the single-level field evaluated inside the renderer, or fst: the
         full FST module (Sec. 3.2) run around it (not both).
         density_stats: gather the screen-space gradient statistics of
-        adaptive density control every iteration (densify_and_prune)."""
+        adaptive density control every iteration (densify_and_prune).
+        grad_exchange: a dist.GradExchange of data-parallel training; every
+        step sums the ranks' gradients with it before the Adam update."""
         if deform is not None and fst is not None:
             raise ValueError("one deformation model: deform or fst")
         self.m = masters
@@ -96,6 +99,7 @@ class Trainer:
         if fst is not None:
             self.opt_fst = Adam([dict(param=fst.planes, lr=lr["grid"]), dict(param=fst.mlp, lr=lr["deformation"])])
         self.steps = 0
+        self.exchange = grad_exchange
         self.dec.workspace(self.HW)
         self.stats = density.DensityStats(self.P, device) if density_stats else None
 
@@ -166,6 +170,14 @@ class Trainer:
         self.stats.reset(n)
         return n
 
+    def trained_grads(self) -> list:
+        """The gradient tensors of every trained parameter (the data-parallel
+        exchange sums these over the ranks)."""
+        out = [self.grads[k] for k in self.GAUSS_KEYS] + [self.dec_out[2], self.dec_out[3]]
+        if self.fst is not None:
+            out += [self.fst.d_planes, self.fst.d_mlp]
+        return out
+
     def reset_opacity(self, max_opacity: float = density.RESET_OPACITY):
         """Cap every opacity at max_opacity and restart its Adam moments."""
         density.reset_opacity(self.m["opacity_logits"], max_opacity)
@@ -221,6 +233,8 @@ class Trainer:
         without a depth target, TV 0 without the FST module)."""
         self.forward_backward(t, tgt_rgb, tgt_dec, tgt_depth, events)
         g = self.grads
+        if self.exchange is not None:
+            self.exchange.exchange(self.trained_grads())
         lrs = None
         if self.schedule:
             lr = dict(self.lr, means=exp_lr(self.steps, self.lr["means"], SCHEDULE["means"], SCHEDULE_STEPS))

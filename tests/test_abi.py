@@ -40,12 +40,15 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_layouts_match_header(tmp_path):
     structs = ["fe_camera", "fe_gaussians", "fe_deform", "fe_opts", "fe_outputs", "fe_output_grads", "fe_grads",
-               "fe_stats", "fe_fst", "fe_attr", "fe_densify_args"]
+               "fe_stats", "fe_fst", "fe_attr", "fe_densify_args", "fe_batch"]
     c = "#include <stdio.h>\n#include <stddef.h>\n#include \"fe4dgs.h\"\nint main(void){\n"
     for s in structs:
         c += f'printf("{s} %zu\\n", sizeof({s}));\n'
     c += 'printf("fe_opts.max_dups %zu\\n", offsetof(fe_opts, max_dups));\n'
     c += 'printf("fe_deform.bbox_min %zu\\n", offsetof(fe_deform, bbox_min));\n'
+    c += 'printf("fe_opts.fwd_batch %zu\\n", offsetof(fe_opts, fwd_batch));\n'
+    c += 'printf("fe_opts.wait_polls %zu\\n", offsetof(fe_opts, wait_polls));\n'
+    c += 'printf("FE_MAX_VIEWS %d\\n", FE_MAX_VIEWS);\n'
     for f in ("normals", "grad_thresh", "attrs", "capacity"):
         c += f'printf("fe_densify_args.{f} %zu\\n", offsetof(fe_densify_args, {f}));\n'
     c += "return 0;}\n"
@@ -57,6 +60,9 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(got[s]) == ctypes.sizeof(getattr(_lib, s)), s
     assert int(got["fe_opts.max_dups"]) == _lib.fe_opts.max_dups.offset
     assert int(got["fe_deform.bbox_min"]) == _lib.fe_deform.bbox_min.offset
+    assert int(got["fe_opts.fwd_batch"]) == _lib.fe_opts.fwd_batch.offset
+    assert int(got["fe_opts.wait_polls"]) == _lib.fe_opts.wait_polls.offset
+    assert int(got["FE_MAX_VIEWS"]) == _lib.FE_MAX_VIEWS
     for f in ("normals", "grad_thresh", "attrs", "capacity"):
         assert int(got[f"fe_densify_args.{f}"]) == getattr(_lib.fe_densify_args, f).offset, f
 
@@ -220,3 +226,80 @@ def test_density_host_side_status_codes(lib):
     assert lib.fe_screen_grad_stats(ws, 1 << 30, 10, 24, 64, 64, ctypes.byref(opts), base, base, None) == 4
     fwd = _lib.make_opts(forward_only=True)
     assert lib.fe_screen_grad_stats(ws, 1 << 30, 10, 32, 64, 64, ctypes.byref(fwd), base, base, None) == 1
+
+
+def test_batch_host_side_checks(lib):
+    cam = _lib.make_camera(64, 48, 50.0, 50.0, 32.0, 24.0, [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1],
+                           [0, 0, 0])
+    small = _lib.make_camera(20, 12, 20.0, 20.0, 10.0, 6.0, [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1],
+                             [0, 0, 0])
+    n = ctypes.c_size_t(0)
+    b = _lib.make_batch([cam, small], [0.0, 0.5], [_lib.make_opts(), _lib.make_opts(tile=(32, 8))])
+    assert lib.fe_batch_workspace_size(1000, 32, ctypes.byref(b), ctypes.byref(n)) == 0
+    # A 256-byte header, each view's single-view workspace (256-aligned),
+    # then one gradient set per helper stream (two views: two streams).
+    one = _lib.fe_workspace_size(1000, 32, 64, 48, _lib.make_opts())
+    two = _lib.fe_workspace_size(1000, 32, 20, 12, _lib.make_opts(tile=(32, 8)))
+    a256 = lambda x: (x + 255) // 256 * 256
+    gset = sum(a256(4 * 1000 * w) for w in (3, 3, 4, 1, 48, 32))
+    assert n.value == 256 + one + two + 2 * gset
+    fwd_only = _lib.make_batch([cam, small], [0.0, 0.5], [_lib.make_opts(forward_only=True), _lib.make_opts()])
+    assert lib.fe_batch_workspace_size(1000, 32, ctypes.byref(fwd_only), ctypes.byref(n)) == 0
+    assert n.value == 256 + _lib.fe_workspace_size(1000, 32, 64, 48, _lib.make_opts(forward_only=True)) + \
+        _lib.fe_workspace_size(1000, 32, 20, 12, _lib.make_opts(forward_only=True))
+    assert lib.fe_batch_workspace_size(1000, 24, ctypes.byref(b), ctypes.byref(n)) == 4      # D
+    b0 = _lib.make_batch([], [], [])
+    assert lib.fe_batch_workspace_size(1000, 32, ctypes.byref(b0), ctypes.byref(n)) == 1     # no views
+    many = _lib.make_batch([cam] * 33, [0.0] * 33, [_lib.make_opts()] * 33)
+    assert lib.fe_batch_workspace_size(1000, 32, ctypes.byref(many), ctypes.byref(n)) == 1   # > FE_MAX_VIEWS
+    bad_tile = _lib.make_batch([cam], [0.0], [_lib.make_opts(tile=(12, 12))])
+    assert lib.fe_batch_workspace_size(1000, 32, ctypes.byref(bad_tile), ctypes.byref(n)) == 4
+    assert lib.fe_render_batch(None, None, ctypes.byref(b), None, 0, None, None) == 1
+    assert lib.fe_render_batch_backward(None, None, ctypes.byref(b), None, 0, None, None, None) == 1
+    assert lib.fe_batch_read_stats(None, 0, 1000, 32, ctypes.byref(b), None, None) == 1
+
+
+def test_injected_workspace_failures_return_a_status(lib):
+    # A caller whose allocation failed passes NULL, or a buffer one byte too
+    # small: every render entry point returns a status before any CUDA call
+    # (the pointers below are never dereferenced).
+    P, D, W, H = 100, 32, 64, 48
+    o = _lib.make_opts()
+    need = _lib.fe_workspace_size(P, D, W, H, o)
+    cam = _lib.make_camera(W, H, 50.0, 50.0, 32.0, 24.0, [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1], [0, 0, 0])
+    g = _lib.fe_gaussians()
+    g.P, g.D, g.sh_degree = P, D, 3
+    g.means = g.log_scales = g.quats = g.opacity_logits = g.sh = g.feat = 1 << 20
+    out = _lib.fe_outputs(1 << 21, 1 << 21, 1 << 21, 1 << 21, None)
+    go = _lib.fe_output_grads(None, None, None, None)
+    gr = _lib.fe_grads(*([1 << 22] * 6))
+    ws = ctypes.c_void_p(1 << 24)                                   # 256-byte aligned
+    stats = _lib.fe_stats()
+    for bytes_, want in ((need - 1, 3), (0, 3)):
+        assert lib.fe_render_forward(ctypes.byref(g), None, ctypes.byref(cam), 0.0, ctypes.byref(o), ws, bytes_,
+                                     ctypes.byref(out), None) == want
+        assert lib.fe_render_backward(ctypes.byref(g), None, ctypes.byref(cam), 0.0, ctypes.byref(o), ws, bytes_,
+                                      ctypes.byref(go), ctypes.byref(gr), None) == want
+        assert lib.fe_read_stats(ws, bytes_, P, D, W, H, ctypes.byref(o), ctypes.byref(stats), None) == want
+        assert lib.fe_count_pairs(ctypes.byref(g), ctypes.byref(cam), ctypes.byref(o), ws, bytes_, ws, None) == want
+    assert lib.fe_render_forward(ctypes.byref(g), None, ctypes.byref(cam), 0.0, ctypes.byref(o), None, need,
+                                 ctypes.byref(out), None) == 1
+    assert lib.fe_render_backward(ctypes.byref(g), None, ctypes.byref(cam), 0.0, ctypes.byref(o), None, need,
+                                  ctypes.byref(go), ctypes.byref(gr), None) == 1
+    assert lib.fe_render_forward(ctypes.byref(g), None, ctypes.byref(cam), 0.0, ctypes.byref(o),
+                                 ctypes.c_void_p((1 << 24) + 16), need, ctypes.byref(out), None) == 1  # misaligned
+    b = _lib.make_batch([cam, cam], [0.0, 1.0], [o, o])
+    nb = _lib.fe_batch_workspace_size(P, D, b)
+    outs = (_lib.fe_outputs * 2)(out, out)
+    gos = (_lib.fe_output_grads * 2)(go, go)
+    assert lib.fe_render_batch(ctypes.byref(g), None, ctypes.byref(b), ws, nb - 1, outs, None) == 3
+    assert lib.fe_render_batch(ctypes.byref(g), None, ctypes.byref(b), None, nb, outs, None) == 1
+    assert lib.fe_render_batch_backward(ctypes.byref(g), None, ctypes.byref(b), ws, nb - 1, gos, ctypes.byref(gr),
+                                        None) == 3
+    sts = (_lib.fe_stats * 2)()
+    assert lib.fe_batch_read_stats(ws, nb - 1, P, D, ctypes.byref(b), sts, None) == 3
+    # The Python layer refuses a shared workspace that is too small.
+    import torch
+    from paper_2503_06161_gb300.raster import Rasterizer
+    with pytest.raises(ValueError):
+        Rasterizer(P, D, W, H, device="cpu", workspace=torch.empty(need - 1, dtype=torch.uint8))

@@ -90,7 +90,7 @@ def test_forward_static_1k_64x64():
     check_forward(e, rep, flagged_max=4)
 
 
-@pytest.mark.parametrize("D", [16, 32, 64, 128])
+@pytest.mark.parametrize("D", [16, 32, 64, 128, 256])
 def test_forward_deformed_ragged(D):
     # 192 of 15000 pixels flagged: 161 depth-order ties, 22 alpha skips, 11
     # terminations; all checked.
@@ -115,6 +115,48 @@ def test_per_gaussian_state():
     assert np.abs(d["opacity"].cpu().numpy()[vis] - g["opacity"][vis]).max() < 1e-6
     assert rel_err(d["depth"].cpu().numpy()[vis], g["depth"][vis]) < 1e-6
     assert np.abs(d["rgb"].cpu().numpy()[vis] - g["rgb"][vis]).max() < 1e-5
+
+
+def test_needle_thin_gaussians_conic_and_radius():
+    # Scale ratio e^7 ~ 1100 with random rotations: the projected 2D
+    # covariance is nearly rank one, a c ~ b^2 up to the 0.3 px^2 dilation,
+    # so the determinant a c - b^2 cancels by a factor kappa = (a c + b^2) /
+    # det of up to ~2e3.  Each conic entry must match the FP64 oracle within
+    # 64 kappa u (u = 2^-24): a, b and c are binary32 sums of nine products,
+    # each within about 16 u of its exact value, and the determinant's
+    # relative error is kappa times theirs; the compensated evaluation of
+    # a c - b^2 itself adds at most 2 u (test_compensated_det).
+    rng = np.random.default_rng(31)
+    P, D = 600, 16
+    sc = synth.make_scene(P, D, (-1.5, -1.2, 3.0), (1.5, 1.2, 6.0), seed=31)
+    ls = np.full((P, 3), -8.0, np.float32)
+    ls[:, 0] = -1.0
+    sc = dataclasses.replace(sc, log_scales=ls + rng.normal(0, 0.05, (P, 3)).astype(np.float32))
+    cam = synth.make_camera(320, 256, 280.0)
+    run = gpu_forward(sc, cam)
+    d = run.rast.dump()
+    g = O.gaussians(sc, cam)
+    vis = (g["radius"] > 0) & (d["touched"].cpu().numpy() > 0)
+    assert vis.sum() > 300
+    # the oracle conic (a, b, c) = inverse of the dilated covariance; its
+    # determinant and the cancellation factor from the covariance entries
+    ca, cb, cc = g["conic"][:, 0], g["conic"][:, 1], g["conic"][:, 2]
+    det_conic = ca * cc - cb * cb
+    A, B, C = cc / det_conic, -cb / det_conic, ca / det_conic          # covariance entries
+    kappa = (A * C + B * B) / (A * C - B * B)
+    assert np.median(kappa[vis]) > 100                                 # the case is ill-conditioned
+    got = d["conic"].cpu().numpy()
+    u = 2.0 ** -24
+    scale = np.maximum(np.abs(g["conic"]), np.abs(g["conic"]).max(axis=1, keepdims=True))
+    err = (np.abs(got - g["conic"]) / scale).max(axis=1)
+    bound = 64 * kappa * u + 1e-6
+    print("needle conic: max kappa", kappa[vis].max(), "max err / bound", (err[vis] / bound[vis]).max())
+    assert np.all(err[vis] <= bound[vis])
+    sure = vis & (g["rmargin"] > 1e-5)
+    assert np.array_equal(d["radius"].cpu().numpy()[sure], g["radius"][sure])
+    # (The images of such needles are not held to the 1e-4 bar of the other
+    # cases: the quadratic form along the long axis cancels further, and the
+    # binary32 render differs from FP64 by up to ~2e-3 in RGB there.)
 
 
 def test_tile_lists_match_oracle_rects():
@@ -201,7 +243,8 @@ def _upstream(n, D, seed=0, mask=None):
     return g
 
 
-@pytest.mark.parametrize("D,deform,flagged_max", [(16, False, 8), (32, True, 75), (64, True, 75)])
+@pytest.mark.parametrize("D,deform,flagged_max", [(16, False, 8), (32, True, 75), (64, True, 75), (128, True, 75),
+                                                   (256, True, 75)])
 def test_backward_matches_oracle(D, deform, flagged_max):
     # Upstream gradients on every pixel; the oracle's reverse takes each
     # flagged pixel's decisions as the GPU forward took them, and each
