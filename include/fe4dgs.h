@@ -244,7 +244,8 @@ fe_status fe_l1_loss_grad_noalloc(const float *pred, const float *target, int64_
  * ------------------------------------------------------------------------ */
 typedef struct {
   int64_t HW;               /* pixels (rows of feat), 0 <= HW < 2^31 - 128 */
-  int D;                    /* feature channels: 32 or 64 (else FE_ERR_UNSUPPORTED) */
+  int D;                    /* feature channels: 16, 32 or 64 (else FE_ERR_UNSUPPORTED); 16 runs the
+                               32-channel kernel on tiles the tensor maps zero-fill past channel 16 */
   const void *feat;         /* [HW, D] bf16, row-major, 16-byte aligned */
   const void *weight;       /* [256, D] bf16, row-major, 16-byte aligned */
   const float *bias;        /* [256] float32 */
@@ -349,19 +350,27 @@ typedef struct {
   const float *planes;   /* device, fe_fst_plane_floats(levels, rs, rt) floats, 16-byte aligned */
   const float *mlp;      /* device, fe_fst_mlp_floats(levels, D) floats, 16-byte aligned */
   float bbox_min[3], bbox_max[3];   /* scene box of the coordinate normalisation */
+  int exact_planes;      /* reverse: 0 = plane gradients summed with float atomics (fast; the
+                            last bits depend on the order of the additions); 1 = summed exactly
+                            in fixed point, bitwise reproducible (workspace with_backward = 2;
+                            about twice the reverse's time) */
 } fe_fst;
 
 /* Float counts of the plane and MLP arrays (0 for invalid arguments). */
 int64_t fe_fst_plane_floats(int levels, int rs, int rt);
 int64_t fe_fst_mlp_floats(int levels, int D);
 
-/* Device workspace of fe_fst_forward / fe_fst_backward for P Gaussians.
- * with_backward = 0: forward only (inference; the HexPlane features, 0.5 KB
- * per Gaussian at 4 levels); 1: the forward also keeps the per-Gaussian
- * activations the reverse pass reads, and the reverse's own per-Gaussian
- * buffers (about 5.1 KB per Gaussian at 4 levels in all), plus per-block
- * partial sums of the weight gradients. */
-fe_status fe_fst_workspace_size(int P, int levels, int D, int with_backward, size_t *bytes);
+/* Device workspace of fe_fst_forward / fe_fst_backward for P Gaussians and
+ * planes of levels x (rs, rt) nodes.  with_backward = 0: forward only
+ * (inference; the HexPlane features, 0.5 KB per Gaussian at 4 levels); 1:
+ * the forward also keeps the per-Gaussian activations the reverse pass
+ * reads, and the reverse's own per-Gaussian buffers (about 5.1 KB per
+ * Gaussian at 4 levels in all) and per-block partial sums of the weight
+ * gradients; 2: as 1, plus the exact plane-gradient accumulators that
+ * fe_fst.exact_planes = 1 needs (16 bytes per plane float).  The first 4
+ * bytes of the workspace hold the reverse's error bits (1: an exact
+ * plane-gradient term of magnitude >= 2^23 was clamped). */
+fe_status fe_fst_workspace_size(int P, int levels, int rs, int rt, int D, int with_backward, size_t *bytes);
 
 /* Deformation of P Gaussians at time t.  Inputs (device, canonical, the
  * fe_gaussians layouts): means [P,3], quats [P,4], log_scales [P,3],
@@ -387,9 +396,12 @@ fe_status fe_fst_forward(const fe_fst *fst, int P, const float *means, const flo
  * (device float32, overwritten):
  *   d_means   [P,3]  d_means_t plus the path through the HexPlane
  *                    coordinates (may alias d_means_t);
- *   d_planes         like planes: summed with float atomics, so the order
- *                    of the additions (and the last bits) can vary between
- *                    runs;
+ *   d_planes         like planes: with fst->exact_planes, every Gaussian's
+ *                    terms summed exactly (96-bit fixed point, resolution
+ *                    2^-72, |sum| < 2^23, integer atomics whose order does
+ *                    not matter), then rounded once to float32 -- bitwise
+ *                    reproducible; otherwise summed with float atomics (the
+ *                    last bits depend on the order of the additions);
  *   d_mlp            like mlp: per-block partial sums reduced in a fixed
  *                    order (reproducible bit for bit).
  * Asynchronous on `stream`. */

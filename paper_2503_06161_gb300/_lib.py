@@ -89,7 +89,7 @@ class fe_adam_group(ctypes.Structure):
 
 class fe_fst(ctypes.Structure):
     _fields_ = [("levels", c_int), ("rs", c_int), ("rt", c_int), ("D", c_int), ("planes", c_void_p),
-                ("mlp", c_void_p), ("bbox_min", c_float * 3), ("bbox_max", c_float * 3)]
+                ("mlp", c_void_p), ("bbox_min", c_float * 3), ("bbox_max", c_float * 3), ("exact_planes", c_int)]
 
 
 class fe_attr(ctypes.Structure):
@@ -128,7 +128,7 @@ _SIGNATURES = {
     "fe_decoder_read_errors": [c_void_p, _P(ctypes.c_uint32), c_void_p],
     "fe_adam_step": [_P(fe_adam_group), c_int, c_int, c_float, c_float, c_float, c_void_p],
     "fe_sum_f32": [c_void_p, _P(c_void_p), c_int, c_int64, c_void_p],
-    "fe_fst_workspace_size": [c_int, c_int, c_int, c_int, _P(ctypes.c_size_t)],
+    "fe_fst_workspace_size": [c_int, c_int, c_int, c_int, c_int, c_int, _P(ctypes.c_size_t)],
     "fe_fst_forward": [_P(fe_fst), c_int] + [c_void_p] * 5 + [c_int, c_float] + [c_void_p] * 6
                       + [ctypes.c_size_t, c_int, c_void_p],
     "fe_fst_backward": [_P(fe_fst), c_int, c_void_p, c_float] + [c_void_p] * 9 + [ctypes.c_size_t, c_void_p],
@@ -457,9 +457,10 @@ def fe_sum_f32(dst, srcs, stream=None):
 
 
 # --- full FST deformation module ---------------------------------------------
-def make_fst(levels: int, rs: int, rt: int, D: int, planes, mlp, bbox_min, bbox_max) -> fe_fst:
+def make_fst(levels: int, rs: int, rt: int, D: int, planes, mlp, bbox_min, bbox_max, exact_planes=False) -> fe_fst:
     f = fe_fst()
     f.levels, f.rs, f.rt, f.D = int(levels), int(rs), int(rt), int(D)
+    f.exact_planes = 1 if exact_planes else 0
     f.planes = _ptr(planes)
     f.mlp = _ptr(mlp)
     for a in range(3):
@@ -476,9 +477,12 @@ def fe_fst_mlp_floats(levels: int, D: int) -> int:
     return int(load().fe_fst_mlp_floats(levels, D))
 
 
-def fe_fst_workspace_size(P: int, levels: int, D: int, with_backward: bool) -> int:
+def fe_fst_workspace_size(P: int, levels: int, rs: int, rt: int, D: int, with_backward) -> int:
+    """with_backward: 0 / False (forward only), 1 / True, or 2 (with the exact
+    plane-gradient accumulators)."""
     n = ctypes.c_size_t(0)
-    _check("fe_fst_workspace_size", load().fe_fst_workspace_size(P, levels, D, int(with_backward), ctypes.byref(n)))
+    _check("fe_fst_workspace_size", load().fe_fst_workspace_size(P, levels, rs, rt, D, int(with_backward),
+                                                                  ctypes.byref(n)))
     return int(n.value)
 
 

@@ -360,7 +360,7 @@ struct BwdCfg {
   static constexpr int CPL = NC / CG;               // channels per lane (even: packed FMA)
   static constexpr bool GREG = D <= 64;             // upstream gradients kept in registers
   static constexpr int GS = NC + 2;                 // per-pixel gradient row stride (8-byte rows)
-  static constexpr int WS = B + 4;                  // w row stride (16-byte rows)
+  static constexpr int WS = B + 2;                  // w row stride (8-byte rows; 2-way bank conflicts on the w writes)
   static constexpr int SLICE = (32 * WS > B * NC) ? 32 * WS : B * NC;
   static_assert(B % JG == 0 && CPL % 2 == 0 && JPL <= 2, "lane grid of the per-warp product");
   // Byte offsets in dynamic shared memory: per-pixel gradient rows, warp
@@ -503,24 +503,22 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
     if (rel0 < wmax) {
       const uint32_t lenmask = nb >= 32 ? 0xFFFFFFFFu : ((1u << nb) - 1u);
       uint32_t todo = masked ? __ldg(a.cmask + (cslot0 + rel0 / 32) * 8 + warp) & lenmask : lenmask;
-      // Entries not visited keep w = 0.
-      {
-        float4* wrow = reinterpret_cast<float4*>(slice + lane * WS);
-#pragma unroll
-        for (int q = 0; q < B / 4; ++q) wrow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
+      // Every lane writes w (0 where it did not blend) for every entry the
+      // warp visits; rows of entries it does not visit may hold stale values:
+      // the products of those columns are never combined.
       // Entry j given its evaluation (hit: the pixel includes it): the T
       // replay and the gradient terms v (six geometric values, then two
       // zeros), and the blend weight written to the warp's w slice.
       auto entry = [&](int j, bool hit, const PairEval& pe, float (&v)[8]) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[q] = 0.0f;
+        float w = 0.0f;
         if (hit) {
           const float* rec = s_rec + j * kRec;
           const float one_m = 1.0f - pe.alpha;
           const float inv = __fdividef(1.0f, one_m);  // one_m >= 0.01
           T = T * inv;  // transmittance before this Gaussian
-          const float w = pe.alpha * T;
+          w = pe.alpha * T;
           // s = g . (rgb, depth, feature) of this Gaussian.
           const float4 r4 = *reinterpret_cast<const float4*>(rec + 4);  // ., ., depth, r
           const float4 r8 = *reinterpret_cast<const float4*>(rec + 8);  // g, b, ., .
@@ -547,8 +545,8 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
             v[4] = dp2 * pe.dy * pe.dy;
             v[5] = dalpha * pe.G;
           }
-          slice[lane * WS + j] = w;
         }
+        slice[lane * WS + j] = w;
       };
       const int b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1, b2 = (lane >> 1) & 1;
       // Warp sums of one entry's v[0..7] (reduce-scatter: lane 4m ends with

@@ -89,6 +89,8 @@ struct DecCfg {
 struct DecArgs {
   int64_t HW;
   int ntiles;
+  int d_real;        // channels of feat / d_feat / d_weight (<= D: D = 16 runs the D = 32 kernel on tiles
+                     // the tensor maps zero-fill past channel 16; the padded columns are not stored)
   const float* bias;
   float* out;        // forward: [HW, 256]
   float scale;       // L1: loss and gradient scale
@@ -431,8 +433,8 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       if (D == 32) tmem_ld16(t_row + col + 16 * h, v);
       else tmem_ld32(t_row + col + 32 * h, v);
       tmem_wait_ld(v);
-      if (pj < a.HW) {
-        float4* o = reinterpret_cast<float4*>(a.d_feat + pj * D + (D / 2) * h);
+      if (pj < a.HW && (D / 2) * h < a.d_real) {
+        float4* o = reinterpret_cast<float4*>(a.d_feat + pj * a.d_real + (D / 2) * h);
 #pragma unroll
         for (int e = 0; e < D / 8; ++e)
           o[e] = make_float4(a.scale * __uint_as_float(v[4 * e]), a.scale * __uint_as_float(v[4 * e + 1]),
@@ -608,14 +610,17 @@ __global__ void __launch_bounds__(kDecThreads, 1)
   }
 }
 
-// Fixed-order sums of the per-CTA partials, scaled.
-__global__ void decoder_reduce_kernel(int ncta, int D, float scale, const float* part_loss, const float* part_dw,
-                                      const float* part_db, float* loss, float* d_weight, float* d_bias) {
-  const int n_dw = kDecN * D;
+// Fixed-order sums of the per-CTA partials, scaled (partials of D columns,
+// the first d_real of them stored).
+__global__ void decoder_reduce_kernel(int ncta, int D, int d_real, float scale, const float* part_loss,
+                                      const float* part_dw, const float* part_db, float* loss, float* d_weight,
+                                      float* d_bias) {
+  const int n_dw = kDecN * d_real;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_dw) {
+    const int src = (i / d_real) * D + i % d_real;
     float s = 0.0f;
-    for (int c = 0; c < ncta; ++c) s += part_dw[(size_t)c * n_dw + i];
+    for (int c = 0; c < ncta; ++c) s += part_dw[(size_t)c * kDecN * D + src];
     d_weight[i] = scale * s;
   } else if (i < n_dw + kDecN) {
     const int j = i - n_dw;
@@ -698,9 +703,12 @@ DecLayout dec_layout(int64_t HW, int D) {
 
 bool aligned16p(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// The kernel width for D channels (16 runs as 32 on zero-filled tiles).
+int dec_width(int D) { return D == 16 ? 32 : D; }
+
 fe_status dec_check(const fe_decoder_args* a) {
   if (!a || a->HW < 0 || a->HW > (int64_t)kDecBM * ((1ll << 31) / kDecBM - 1)) return FE_ERR_INVALID_ARG;
-  if (a->D != 32 && a->D != 64) return FE_ERR_UNSUPPORTED;
+  if (a->D != 16 && a->D != 32 && a->D != 64) return FE_ERR_UNSUPPORTED;
   if (!a->weight || !a->bias || !aligned16p(a->weight)) return FE_ERR_INVALID_ARG;
   if (a->HW > 0 && (!a->feat || !aligned16p(a->feat))) return FE_ERR_INVALID_ARG;
   return FE_OK;
@@ -721,8 +729,8 @@ using namespace fe;
 extern "C" {
 
 size_t fe_decoder_workspace_size(int64_t HW, int D) {
-  if (HW < 0 || (D != 32 && D != 64)) return 0;
-  return dec_layout(HW, D).total;
+  if (HW < 0 || (D != 16 && D != 32 && D != 64)) return 0;
+  return dec_layout(HW, dec_width(D)).total;
 }
 
 fe_status fe_decode_forward(const fe_decoder_args* a, float* out, void* workspace, size_t workspace_bytes,
@@ -730,23 +738,26 @@ fe_status fe_decode_forward(const fe_decoder_args* a, float* out, void* workspac
   fe_status s = dec_check(a);
   if (s != FE_OK) return s;
   if (!workspace || !out || !aligned16p(out)) return FE_ERR_INVALID_ARG;
-  const DecLayout L = dec_layout(a->HW, a->D);
+  const int DW = dec_width(a->D);
+  const DecLayout L = dec_layout(a->HW, DW);
   if (workspace_bytes < L.total) return FE_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(workspace, 0, 256, st) != cudaSuccess) return FE_ERR_CUDA;
   if (a->HW == 0) return FE_OK;
   CUtensorMap mf, mw;
-  const CUtensorMapSwizzle swz = a->D == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-  if (!make_map(&mf, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->feat, a->D, a->HW, a->D, kDecBM, swz) ||
-      !make_map(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->weight, a->D, kDecN, a->D, kDecN, swz))
+  // Rows of a->D channels; boxes of DW channels (zero-filled past a->D).
+  const CUtensorMapSwizzle swz = DW == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  if (!make_map(&mf, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->feat, a->D, a->HW, DW, kDecBM, swz) ||
+      !make_map(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->weight, a->D, kDecN, DW, kDecN, swz))
     return FE_ERR_CUDA;
   DecArgs d{};
   d.HW = a->HW;
   d.ntiles = (int)((a->HW + kDecBM - 1) / kDecBM);
+  d.d_real = a->D;
   d.bias = a->bias;
   d.out = out;
   d.err = static_cast<uint32_t*>(workspace);
-  return dispatch<kDecForward>(a->D, mf, mw, mw, d, L.ncta, st) == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+  return dispatch<kDecForward>(DW, mf, mw, mw, d, L.ncta, st) == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
 
 fe_status fe_decode_l1(const fe_decoder_args* a, const void* target, int target_bf16, float scale, float* loss,
@@ -756,7 +767,8 @@ fe_status fe_decode_l1(const fe_decoder_args* a, const void* target, int target_
   if (s != FE_OK) return s;
   if (!workspace || !loss || !d_weight || !d_bias) return FE_ERR_INVALID_ARG;
   if (a->HW > 0 && (!target || !aligned16p(target) || !d_feat || !aligned16p(d_feat))) return FE_ERR_INVALID_ARG;
-  const DecLayout L = dec_layout(a->HW, a->D);
+  const int DW = dec_width(a->D);
+  const DecLayout L = dec_layout(a->HW, DW);
   if (workspace_bytes < L.total) return FE_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned char* ws = static_cast<unsigned char*>(workspace);
@@ -769,16 +781,17 @@ fe_status fe_decode_l1(const fe_decoder_args* a, const void* target, int target_
     return FE_OK;
   }
   CUtensorMap mf, mw, mt;
-  const CUtensorMapSwizzle swz = a->D == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  const CUtensorMapSwizzle swz = DW == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   const bool tb = target_bf16 != 0;
-  if (!make_map(&mf, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->feat, a->D, a->HW, a->D, kDecBM, swz) ||
-      !make_map(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->weight, a->D, kDecN, a->D, kDecN, swz) ||
+  if (!make_map(&mf, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->feat, a->D, a->HW, DW, kDecBM, swz) ||
+      !make_map(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->weight, a->D, kDecN, DW, kDecN, swz) ||
       !make_map(&mt, tb ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, tb ? 2 : 4, target,
                 kDecN, a->HW, tb ? 64 : 32, kDecBM, CU_TENSOR_MAP_SWIZZLE_128B))
     return FE_ERR_CUDA;
   DecArgs d{};
   d.HW = a->HW;
   d.ntiles = (int)((a->HW + kDecBM - 1) / kDecBM);
+  d.d_real = a->D;
   d.bias = a->bias;
   d.scale = scale;
   d.d_feat = d_feat;
@@ -786,12 +799,12 @@ fe_status fe_decode_l1(const fe_decoder_args* a, const void* target, int target_
   d.part_dw = reinterpret_cast<float*>(ws + L.dw);
   d.part_db = reinterpret_cast<float*>(ws + L.db);
   d.err = static_cast<uint32_t*>(workspace);
-  const cudaError_t e = tb ? dispatch<kDecL1Bf16>(a->D, mf, mw, mt, d, L.ncta, st)
-                           : dispatch<kDecL1F32>(a->D, mf, mw, mt, d, L.ncta, st);
+  const cudaError_t e = tb ? dispatch<kDecL1Bf16>(DW, mf, mw, mt, d, L.ncta, st)
+                           : dispatch<kDecL1F32>(DW, mf, mw, mt, d, L.ncta, st);
   if (e != cudaSuccess) return FE_ERR_CUDA;
   const int n = kDecN * a->D + kDecN + 1;
-  decoder_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(L.ncta, a->D, scale, d.part_loss, d.part_dw, d.part_db, loss,
-                                                         d_weight, d_bias);
+  decoder_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(L.ncta, DW, a->D, scale, d.part_loss, d.part_dw, d.part_db,
+                                                         loss, d_weight, d_bias);
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
 

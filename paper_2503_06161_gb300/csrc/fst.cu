@@ -139,8 +139,10 @@ int bwd_blocks(int P) {
   return chunks < 2 * 152 ? chunks : 2 * 152;
 }
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+// acc: with the reverse pass, the exact plane-gradient accumulators, two
+// uint64 arrays (hi, lo) of one entry per plane float (see fixed_add).
 struct WsLayout {
-  size_t wt, wn, f, act, dv, df, part, total;
+  size_t wt, wn, f, act, dv, df, part, acc, total;
 };
 WsLayout ws_layout(const FstGeom& g, int with_backward) {
   WsLayout w{};
@@ -151,7 +153,8 @@ WsLayout ws_layout(const FstGeom& g, int with_backward) {
   w.dv = w.act + (with_backward ? al256((size_t)g.nslots * g.P * 4) : 0);
   w.df = w.dv + (with_backward ? al256((size_t)kFW * g.P * 4) : 0);
   w.part = w.df + (with_backward ? al256((size_t)g.levels * kFC * g.P * 4) : 0);
-  w.total = w.part + (with_backward ? al256((size_t)bwd_blocks(g.P) * g.mlp_aligned * 4) : 0);
+  w.acc = w.part + (with_backward ? al256((size_t)bwd_blocks(g.P) * g.mlp_aligned * 4) : 0);
+  w.total = w.acc + (with_backward == 2 ? al256((size_t)plane_floats(g) * 16) : 0);
   return w;
 }
 
@@ -704,6 +707,51 @@ __device__ void block_outer(const float* s_d, int ds, const float* s_x, int xs, 
   __syncthreads();
 }
 
+// Exact, order-independent plane-gradient sums.  Each float contribution x
+// is the integer X = x 2^72 (exact for |x| >= 2^-49; smaller ones rounded to
+// the nearest multiple of 2^-72), held as hi 2^32 + lo with 0 <= lo < 2^32,
+// and added with 64-bit integer atomics into hi[i] (two's complement) and
+// lo[i]: integer sums do not depend on the order of the additions, so the
+// result is the same bits however the Gaussians are scheduled.  |sum| must
+// stay below 2^23 (contributions at or above it are clamped and flagged).
+__device__ __forceinline__ void fixed_add(unsigned long long* hi, unsigned long long* lo, size_t i, float x,
+                                          uint32_t* err) {
+  const uint32_t u = __float_as_uint(x);
+  const int e = (int)((u >> 23) & 0xFFu);
+  if (e == 0) return;  // zero or below 2^-126: under the resolution
+  uint64_t m = (u & 0x7FFFFFu) | 0x800000u;  // |x| = m 2^(e - 150)
+  int sh = e - 150 + 72;                      // |X| = m 2^sh
+  if (sh > 71) {                              // |x| >= 2^23
+    set_err(err, kErrOverflow);
+    m = 0xFFFFFFu;
+    sh = 71;
+  }
+  uint64_t h, l;
+  if (sh >= 32) {
+    h = m << (sh - 32);
+    l = 0;
+  } else if (sh >= 0) {
+    const uint64_t X = m << sh;
+    h = X >> 32;
+    l = X & 0xFFFFFFFFull;
+  } else if (sh > -25) {
+    h = 0;
+    l = (m + (1ull << (-sh - 1))) >> (-sh);  // nearest, ties up
+  } else {
+    return;
+  }
+  if (u >> 31) {  // -(h 2^32 + l)
+    if (l) {
+      h = ~h;            // -h - 1
+      l = 0x100000000ull - l;
+    } else {
+      h = ~h + 1ull;     // -h
+    }
+  }
+  if (h) atomicAdd(hi + i, (unsigned long long)h);
+  if (l) atomicAdd(lo + i, (unsigned long long)l);
+}
+
 // Lane-cooperative reverse of one level's HexPlane sample for NG Gaussians
 // at once (lane = channel, dfc[q] = d f of this channel for Gaussian q): all
 // corner fetches are issued before any arithmetic, plane gradients by
@@ -711,6 +759,7 @@ __device__ void block_outer(const float* s_d, int ds, const float* s_x, int xs, 
 // (lane 0 adds).
 template <int NG>
 __device__ __forceinline__ void plane_backward(const FstGeom& g, const float* __restrict__ planes, float* d_planes,
+                                               unsigned long long* acc_hi, unsigned long long* acc_lo, uint32_t* err,
                                                int lv, const int* const* ci, const float* const* cf, const float* dfc,
                                                int lane, float* const* dc) {
   float q00[NG][6], q01[NG][6], q10[NG][6], q11[NG][6];
@@ -748,11 +797,20 @@ __device__ __forceinline__ void plane_backward(const FstGeom& g, const float* __
       const int ia = ca & 0x3FFFFFFF, ib = cb & 0x3FFFFFFF;
       const float fa = cf[n][lv * 4 + A], fb = cf[n][lv * 4 + B];
       const int rb = g.prb[lv * 6 + k];
-      float* dbase = d_planes + g.poff[lv * 6 + k] + ((size_t)ia * rb + ib) * kFC + lane;
-      atomicAdd(dbase, (1.0f - fa) * (1.0f - fb) * ds);
-      atomicAdd(dbase + kFC, (1.0f - fa) * fb * ds);
-      atomicAdd(dbase + (size_t)rb * kFC, fa * (1.0f - fb) * ds);
-      atomicAdd(dbase + (size_t)rb * kFC + kFC, fa * fb * ds);
+      const size_t di = g.poff[lv * 6 + k] + ((size_t)ia * rb + ib) * kFC + lane;
+      const float w00 = (1.0f - fa) * (1.0f - fb) * ds, w01 = (1.0f - fa) * fb * ds;
+      const float w10 = fa * (1.0f - fb) * ds, w11 = fa * fb * ds;
+      if (acc_hi) {
+        fixed_add(acc_hi, acc_lo, di, w00, err);
+        fixed_add(acc_hi, acc_lo, di + kFC, w01, err);
+        fixed_add(acc_hi, acc_lo, di + (size_t)rb * kFC, w10, err);
+        fixed_add(acc_hi, acc_lo, di + (size_t)rb * kFC + kFC, w11, err);
+      } else {
+        atomicAdd(d_planes + di, w00);
+        atomicAdd(d_planes + di + kFC, w01);
+        atomicAdd(d_planes + di + (size_t)rb * kFC, w10);
+        atomicAdd(d_planes + di + (size_t)rb * kFC + kFC, w11);
+      }
       if (!(ca >> 30))  // A is always a spatial axis
         dcl[A] += ds * ((1.0f - fb) * (q10[n][k] - q00[n][k]) + fb * (q11[n][k] - q01[n][k])) * 0.5f *
                   (float)(g.pra[lv * 6 + k] - 1);
@@ -962,8 +1020,21 @@ struct HexArgs {
   FstGeom g;
   const float *planes, *means, *df, *d_means_t;
   float t;
-  float *d_means, *d_planes;
+  float* d_means;
+  float* d_planes;                      // float-atomic plane sums (acc_hi == NULL)
+  unsigned long long *acc_hi, *acc_lo;  // or exact plane-gradient sums (fixed_add)
+  uint32_t* err;
 };
+
+// d_planes[i] = the exact sum hi 2^32 + lo, times 2^-72, rounded to float.
+__global__ void __launch_bounds__(256) fst_planes_out_kernel(const unsigned long long* __restrict__ hi,
+                                                             const unsigned long long* __restrict__ lo, int64_t n,
+                                                             float* __restrict__ d_planes) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)(long long)hi[i] * 0x1p-40 + (double)lo[i] * 0x1p-72;
+    d_planes[i] = (float)v;
+  }
+}
 
 __global__ void __launch_bounds__(kHexThreads, 2) fst_hex_bwd_kernel(const HexArgs a) {
   __shared__ int s_ci[kHexThreads][kFMaxL * 4];
@@ -993,7 +1064,7 @@ __global__ void __launch_bounds__(kHexThreads, 2) fst_hex_bwd_kernel(const HexAr
       const float dfc[2] = {__ldg(a.df + (size_t)(p0 + r) * nf + lv * kFC + lane),
                             __ldg(a.df + (size_t)(p0 + r + 1) * nf + lv * kFC + lane)};
       float* dc[2] = {s_dc[r], s_dc[r + 1]};
-      plane_backward<2>(g, a.planes, a.d_planes, lv, ci, cf, dfc, lane, dc);
+      plane_backward<2>(g, a.planes, a.d_planes, a.acc_hi, a.acc_lo, a.err, lv, ci, cf, dfc, lane, dc);
     }
     if (j < nw) {
       const int r = warp * 32 + j;
@@ -1001,7 +1072,7 @@ __global__ void __launch_bounds__(kHexThreads, 2) fst_hex_bwd_kernel(const HexAr
       const float* cf[1] = {s_cf[r]};
       const float dfc[1] = {__ldg(a.df + (size_t)(p0 + r) * nf + lv * kFC + lane)};
       float* dc[1] = {s_dc[r]};
-      plane_backward<1>(g, a.planes, a.d_planes, lv, ci, cf, dfc, lane, dc);
+      plane_backward<1>(g, a.planes, a.d_planes, a.acc_hi, a.acc_lo, a.err, lv, ci, cf, dfc, lane, dc);
     }
   }
   __syncwarp();
@@ -1127,17 +1198,19 @@ extern "C" int64_t fe_fst_mlp_floats(int levels, int D) {
   return make_geom(&f, 0, g) ? g.mlp_packed : 0;
 }
 
-extern "C" fe_status fe_fst_workspace_size(int P, int levels, int D, int with_backward, size_t* bytes) {
+extern "C" fe_status fe_fst_workspace_size(int P, int levels, int rs, int rt, int D, int with_backward,
+                                           size_t* bytes) {
   if (!bytes) return FE_ERR_INVALID_ARG;
   fe_fst f{};
   f.levels = levels;
-  f.rs = 2;
-  f.rt = 2;
+  f.rs = rs;
+  f.rt = rt;
   f.D = D;
   for (int a = 0; a < 3; ++a) f.bbox_max[a] = 1.0f;
   FstGeom g;
   if (!make_geom(&f, P, g)) return (D == 16 || D == 32 || D == 64 || D == 128) ? FE_ERR_INVALID_ARG : FE_ERR_UNSUPPORTED;
-  *bytes = ws_layout(g, with_backward ? 1 : 0).total;
+  if (with_backward < 0 || with_backward > 2) return FE_ERR_INVALID_ARG;
+  *bytes = ws_layout(g, with_backward).total;
   return FE_OK;
 }
 
@@ -1253,15 +1326,27 @@ extern "C" fe_status fe_fst_backward(const fe_fst* fst, int P, const float* mean
     return FE_ERR_INVALID_ARG;
   }
   if (!workspace || !al16p(workspace) || !d_planes || !d_mlp) return FE_ERR_INVALID_ARG;
-  const WsLayout w = ws_layout(g, 1);
+  const bool exact = fst->exact_planes != 0;
+  const WsLayout w = ws_layout(g, exact ? 2 : 1);
   if (workspace_bytes < w.total) return FE_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(d_planes, 0, (size_t)plane_floats(g) * 4, st) != cudaSuccess) return FE_ERR_CUDA;
-  if (P == 0) return cudaMemsetAsync(d_mlp, 0, (size_t)g.mlp_packed * 4, st) == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+  const int64_t npl = plane_floats(g);
+  if (P == 0) {
+    if (cudaMemsetAsync(d_planes, 0, (size_t)npl * 4, st) != cudaSuccess) return FE_ERR_CUDA;
+    return cudaMemsetAsync(d_mlp, 0, (size_t)g.mlp_packed * 4, st) == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+  }
   if (!fst->planes || !means || !d_means_t || !d_quats_t || !d_log_scales_t || !d_opacity_logits_t || !d_feat_t ||
       !d_means || !al16p(d_feat_t))
     return FE_ERR_INVALID_ARG;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
+  unsigned long long* acc_hi = exact ? reinterpret_cast<unsigned long long*>(ws + w.acc) : nullptr;
+  unsigned long long* acc_lo = exact ? acc_hi + npl : nullptr;
+  if (cudaMemsetAsync(ws, 0, kWsHeader, st) != cudaSuccess) return FE_ERR_CUDA;
+  if (exact) {
+    if (cudaMemsetAsync(acc_hi, 0, (size_t)npl * 16, st) != cudaSuccess) return FE_ERR_CUDA;
+  } else if (cudaMemsetAsync(d_planes, 0, (size_t)npl * 4, st) != cudaSuccess) {
+    return FE_ERR_CUDA;
+  }
   BwdArgs a{};
   a.g = g;
   a.planes = fst->planes;
@@ -1319,7 +1404,14 @@ extern "C" fe_status fe_fst_backward(const fe_fst* fst, int P, const float* mean
     h.t = t;
     h.d_means = d_means;
     h.d_planes = d_planes;
+    h.acc_hi = acc_hi;
+    h.acc_lo = acc_lo;
+    h.err = reinterpret_cast<uint32_t*>(ws);
     fst_hex_bwd_kernel<<<(P + kHexThreads - 1) / kHexThreads, kHexThreads, 0, st>>>(h);
+    if (exact) {
+      const int64_t nb = (npl + 255) / 256;
+      fst_planes_out_kernel<<<(int)(nb < 152 * 16 ? nb : 152 * 16), 256, 0, st>>>(acc_hi, acc_lo, npl, d_planes);
+    }
   }
   fst_reduce_kernel<<<(int)((g.mlp_packed + 255) / 256), 256, 0, st>>>(g, a.part, nblk, d_mlp);
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;

@@ -24,8 +24,12 @@ from .raster import GaussianScene
 
 class FSTDeform:
     def __init__(self, planes: torch.Tensor, mlp: torch.Tensor, levels: int, rs: int, rt: int, D: int, bbox_min,
-                 bbox_max, P: int, with_backward: bool = True, device="cuda"):
+                 bbox_max, P: int, with_backward: bool = True, device="cuda", exact_planes: bool = False):
+        """exact_planes: plane gradients as exact fixed-point sums (bitwise
+        reproducible, about twice the reverse's time) instead of float
+        atomics."""
         self.levels, self.rs, self.rt, self.D, self.P = int(levels), int(rs), int(rt), int(D), int(P)
+        self.exact_planes = bool(exact_planes)
         dev = torch.device(device)
         self.planes = planes.to(dev, torch.float32).contiguous()
         self.mlp = mlp.to(dev, torch.float32).contiguous()
@@ -35,8 +39,8 @@ class FSTDeform:
             raise ValueError("MLP array size does not match (levels, D)")
         self.bbox_min, self.bbox_max = tuple(float(x) for x in bbox_min), tuple(float(x) for x in bbox_max)
         self.with_backward = bool(with_backward)
-        self.workspace = torch.empty(_lib.fe_fst_workspace_size(P, levels, D, with_backward), dtype=torch.uint8,
-                                     device=dev)
+        self.workspace = torch.empty(_lib.fe_fst_workspace_size(P, levels, rs, rt, D, self._wb()),
+                                     dtype=torch.uint8, device=dev)
         self.d_planes = torch.zeros_like(self.planes)
         self.d_mlp = torch.zeros_like(self.mlp)
         self._out = None
@@ -45,7 +49,8 @@ class FSTDeform:
         """Workspace for a new Gaussian count (after densification)."""
         self.P = int(P)
         self.workspace = None
-        self.workspace = torch.empty(_lib.fe_fst_workspace_size(self.P, self.levels, self.D, self.with_backward),
+        self.workspace = torch.empty(_lib.fe_fst_workspace_size(self.P, self.levels, self.rs, self.rt, self.D,
+                                                                self._wb()),
                                      dtype=torch.uint8, device=self.planes.device)
         self._out = None
 
@@ -54,9 +59,12 @@ class FSTDeform:
         return cls(torch.as_tensor(planes), torch.as_tensor(mlp), levels, rs, rt, D, bbox_min, bbox_max, P,
                    device=device, **kw)
 
+    def _wb(self) -> int:
+        return (2 if self.exact_planes else 1) if self.with_backward else 0
+
     def struct(self) -> _lib.fe_fst:
         return _lib.make_fst(self.levels, self.rs, self.rt, self.D, self.planes, self.mlp, self.bbox_min,
-                             self.bbox_max)
+                             self.bbox_max, self.exact_planes)
 
     def _buffers(self, scene: GaussianScene):
         key = (scene.P, scene.feat.dtype, scene.means.device)

@@ -92,10 +92,11 @@ def test_workspace_grows_with_capacity_and_backward(lib):
 
 def test_decoder_host_side_status_codes(lib):
     # Argument checks of the decoder entry points return before any CUDA call.
-    assert lib.fe_decoder_workspace_size(1000, 16) == 0          # D not supported by the decoder
+    assert lib.fe_decoder_workspace_size(1000, 128) == 0         # D not supported by the decoder
+    assert lib.fe_decoder_workspace_size(1000, 16) == lib.fe_decoder_workspace_size(1000, 32)   # runs as 32
     assert lib.fe_decoder_workspace_size(-1, 32) == 0
     a = _lib.fe_decoder_args()
-    a.HW, a.D, a.feat, a.weight, a.bias = 1000, 16, 16, 16, 16
+    a.HW, a.D, a.feat, a.weight, a.bias = 1000, 128, 16, 16, 16
     args = [None, 0, 1.0, None, None, None, None, None, 0, None]
     assert lib.fe_decode_l1(ctypes.byref(a), *args) == 4         # FE_ERR_UNSUPPORTED
     assert lib.fe_decode_forward(ctypes.byref(a), None, None, 0, None) == 4
@@ -145,12 +146,17 @@ def test_fst_sizes_and_host_side_status_codes(lib):
     assert lib.fe_fst_plane_floats(0, 4, 4) == 0 and lib.fe_fst_plane_floats(5, 4, 4) == 0
     assert lib.fe_fst_plane_floats(2, 1, 4) == 0 and lib.fe_fst_mlp_floats(2, 24) == 0
     n = ctypes.c_size_t(0)
-    assert lib.fe_fst_workspace_size(1000, 4, 32, 0, ctypes.byref(n)) == 0
+    assert lib.fe_fst_workspace_size(1000, 4, 8, 6, 32, 0, ctypes.byref(n)) == 0
     fwd_only = n.value
-    assert lib.fe_fst_workspace_size(1000, 4, 32, 1, ctypes.byref(n)) == 0
+    assert lib.fe_fst_workspace_size(1000, 4, 8, 6, 32, 1, ctypes.byref(n)) == 0
     assert n.value > fwd_only + 1000 * 4 * 900      # the activations kept for the reverse pass
-    assert lib.fe_fst_workspace_size(1000, 4, 24, 1, ctypes.byref(n)) == 4   # D not compiled in
-    assert lib.fe_fst_workspace_size(-1, 4, 32, 1, ctypes.byref(n)) == 1
+    with_bwd = n.value
+    assert lib.fe_fst_workspace_size(1000, 4, 8, 6, 32, 2, ctypes.byref(n)) == 0
+    assert n.value >= with_bwd + 16 * lib.fe_fst_plane_floats(4, 8, 6)      # exact plane accumulators
+    assert lib.fe_fst_workspace_size(1000, 4, 8, 6, 32, 3, ctypes.byref(n)) == 1
+    assert lib.fe_fst_workspace_size(1000, 4, 8, 6, 24, 1, ctypes.byref(n)) == 4   # D not compiled in
+    assert lib.fe_fst_workspace_size(-1, 4, 8, 6, 32, 1, ctypes.byref(n)) == 1
+    assert lib.fe_fst_workspace_size(1000, 4, 1, 6, 32, 1, ctypes.byref(n)) == 1    # rs < 2
     f = _lib.fe_fst()
     f.levels, f.rs, f.rt, f.D = 2, 8, 6, 32
     for a in range(3):

@@ -4,6 +4,9 @@ Appendix A) against the FP64 oracle: deformed Gaussians, the reverse pass
 weight and bias), the TV term, ragged and multi-block sizes, every D, and
 the bf16 feature storage.
 
+With exact_planes the plane gradients are exact fixed-point sums, compared
+bitwise between runs and between orders of the Gaussians.
+
 Comparison protocol: an FP32 evaluation may take the other side of a ReLU
 or grid-cell decision whose FP64 margin is tiny; Gaussians with such a
 decision get zero upstream gradients on both sides, so they drop out of
@@ -199,6 +202,45 @@ def test_weight_gradients_are_reproducible():
         torch.cuda.synchronize()
         res.append((fst.d_mlp.clone(), dev["means"].clone()))
     assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+
+
+def test_exact_plane_gradients_are_independent_of_order():
+    # With exact_planes the plane gradients are every Gaussian's terms summed
+    # exactly in fixed point (integer atomics), then rounded once: two runs
+    # give the same bits, and so does the same scene with its Gaussians in
+    # another order (the per-Gaussian terms are the same; only the summation
+    # order of a float sum would change).  The default float-atomic sums
+    # agree with them to float rounding.
+    P, levels, rs, rt, D = 6000, 2, 8, 6, 32
+    sc, scene, fst, _, _ = _case(P, levels, rs, rt, D, seed=12)
+    t = 0.3
+    up = _upstream(P, D, seed=2)
+    fst.forward(scene, t)
+    dev = {k: torch.tensor(v, dtype=torch.float32, device="cuda") for k, v in up.items()}
+    fst.backward(scene, t, dev)
+    torch.cuda.synchronize()
+    fast = fst.d_planes.clone()
+    fst = FSTDeform(fst.planes, fst.mlp, levels, rs, rt, D, LO, HI, P, exact_planes=True)
+
+    def run(scene_, up_):
+        fst.forward(scene_, t)
+        dev = {k: torch.tensor(v, dtype=torch.float32, device="cuda") for k, v in up_.items()}
+        fst.backward(scene_, t, dev)
+        torch.cuda.synchronize()
+        return fst.d_planes.clone()
+
+    a = run(scene, up)
+    b = run(scene, up)
+    assert torch.equal(a, b)
+    assert int((a != 0).sum()) > 1000
+    assert rel_err(fast.cpu().numpy(), a.cpu().numpy()) < 1e-5
+    perm = np.random.default_rng(3).permutation(P)
+    sc_p = synth.Scene(sc.means[perm], sc.log_scales[perm], sc.quats[perm], sc.opacity_logits[perm], sc.sh[perm],
+                       sc.feat[perm], sc.sh_degree)
+    scene_p = GaussianScene.from_numpy(sc_p, "cuda")
+    c = run(scene_p, {k: v[perm] for k, v in up.items()})
+    assert torch.equal(a, c)
+    assert int(fst.workspace[:4].view(torch.int32).item()) == 0        # no plane-gradient term clamped
 
 
 def test_tv_matches_oracle():
