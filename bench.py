@@ -625,7 +625,8 @@ def run_micro(args, cfg):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     g = torch.Generator().manual_seed(0)
-    HW, D, P = cfg["W"] * cfg["H"], cfg["D"], cfg["P"] if args.P is None else args.P
+    HW, P = cfg["W"] * cfg["H"], cfg["P"] if args.P is None else args.P
+    D = cfg["D"] if args.D is None else args.D
     if args.micro == "fst":
         # The full FST module alone: forward (keeping the reverse state) and
         # reverse from random deformed-Gaussian gradients.

@@ -244,8 +244,10 @@ fe_status fe_l1_loss_grad_noalloc(const float *pred, const float *target, int64_
  * ------------------------------------------------------------------------ */
 typedef struct {
   int64_t HW;               /* pixels (rows of feat), 0 <= HW < 2^31 - 128 */
-  int D;                    /* feature channels: 16, 32 or 64 (else FE_ERR_UNSUPPORTED); 16 runs the
-                               32-channel kernel on tiles the tensor maps zero-fill past channel 16 */
+  int D;                    /* feature channels: 16, 32, 64 or 128 (else FE_ERR_UNSUPPORTED); 16 runs
+                               the 32-channel kernel on tiles the tensor maps zero-fill past channel
+                               16; 128 runs as two launches over the output channels 0-127 and
+                               128-255 (the second adds its share of d_feat to the first's) */
   const void *feat;         /* [HW, D] bf16, row-major, 16-byte aligned */
   const void *weight;       /* [256, D] bf16, row-major, 16-byte aligned */
   const float *bias;        /* [256] float32 */

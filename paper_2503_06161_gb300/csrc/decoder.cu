@@ -45,11 +45,8 @@ constexpr int kEpiWarps = 8;
 constexpr int kWarpMma = kEpiWarps, kWarpF = kEpiWarps + 1, kWarpT0 = kEpiWarps + 2;
 constexpr int kDecThreads = 32 * (kEpiWarps + 4);
 constexpr uint32_t kBoxBytes = 16384;   // one target box: 128 rows x 128 bytes
-constexpr int kTSlots = 8;               // boxes staged: 2 tiles (bf16) or 1 tile (fp32)
-constexpr uint32_t kTBufBytes = 65536;   // one tile buffer of bf16 targets
 constexpr uint32_t kTmemCols = 512;
-// Tensor-memory columns of the accumulators.
-constexpr uint32_t kColAcc = 0, kColDF = 256, kColDW = 320, kColDB = 448;
+constexpr uint32_t kColAcc = 0;
 
 enum DecMode : int { kDecForward = 0, kDecL1Bf16 = 1, kDecL1F32 = 2 };
 
@@ -58,20 +55,38 @@ constexpr uint64_t kLayoutNone = 0, kLayout128B = 2, kLayout64B = 4;
 
 template <int D>
 struct DecCfg {
-  // F tiles in flight (D = 64: two, its larger tiles fill shared memory).
+  // Output channels per launch: 256, or (D = 128) 128 -- the D = 128 decoder
+  // runs as two launches over output-channel halves, because the sign of
+  // each output channel depends on that channel alone and the tensor memory
+  // of one CTA holds the accumulators of only half the channels at D = 128.
+  static constexpr int NO = D == 128 ? 128 : kDecN;
+  // F tiles in flight (D = 64, 128: two, their larger tiles fill shared memory).
   static constexpr int kFStages = D == 32 ? 3 : 2;
   static_assert(kFStages <= 3, "barrier slots for three F stages");
-  static constexpr uint32_t row_bytes = D * 2;  // one F / W row in bf16
-  static constexpr uint64_t layout = D == 64 ? kLayout128B : kLayout64B;
-  static constexpr uint32_t sbo = 8 * row_bytes;  // stride of 8-row groups
-  static constexpr uint32_t w_bytes = kDecN * row_bytes;
+  static constexpr uint32_t row_bytes = D * 2;              // one F / W row in bf16
+  static constexpr int KP = D <= 64 ? 1 : D / 64;           // 128-byte K panels of a row (128B swizzle)
+  static constexpr uint32_t prow = D <= 64 ? row_bytes : 128u;  // bytes of a row within one panel
+  static constexpr uint64_t layout = D >= 64 ? kLayout128B : kLayout64B;
+  static constexpr uint32_t sbo = 8 * prow;  // stride of 8-row groups
+  static constexpr uint32_t w_bytes = NO * row_bytes;
+  static constexpr uint32_t w_panel = NO * prow;
   static constexpr uint32_t f_bytes = kDecBM * row_bytes;
-  // D = 32: each F stage is followed by an all-ones panel of the same
-  // shape, so one product (N = D + 16) yields dW and, in its extra columns,
-  // db; and dF is double-buffered in tensor memory.  D = 64 has no room for
-  // either (shared memory, tensor-memory columns).
-  static constexpr bool merged = D == 32;
-  static constexpr uint32_t f_stride = merged ? 2 * f_bytes : f_bytes;
+  static constexpr uint32_t f_panel = kDecBM * prow;
+  // D = 32, 128: each F stage is followed by an all-ones panel of one
+  // panel's shape, so one product (N = D + 16) yields dW and, in its extra
+  // columns, db.  D = 64 has no room in shared memory for it.
+  static constexpr bool merged = D == 32 || D == 128;
+  // D = 32: dF double-buffered in tensor memory (no room at D = 64, 128).
+  static constexpr bool dfdb = D == 32;
+  static constexpr uint32_t f_stride = merged ? f_bytes + f_panel : f_bytes;
+  // Tensor-memory columns: accumulators of the NO outputs, dF, dW (+ db).
+  static constexpr uint32_t col_df = NO;
+  static constexpr uint32_t col_dw = D == 128 ? 256u : 320u;  // per M half h: + 64 h (NO = 256)
+  static constexpr uint32_t col_db = 448;                     // not merged: per M half + 16 h
+  static_assert(D != 128 || col_dw + D + 16 <= kTmemCols, "tensor-memory columns");
+  // Target boxes staged: 2 tiles of bf16 (64-channel boxes) or 1 tile of fp32 (32-channel boxes).
+  static constexpr int kTSlots = NO / 32;
+  static constexpr uint32_t kTBufBytes = (NO / 64) * kBoxBytes;  // one tile buffer of bf16 targets
   static constexpr uint32_t off_w = 0;
   static constexpr uint32_t off_f = off_w + w_bytes;                  // kFStages stages
   static constexpr uint32_t off_t = off_f + kFStages * f_stride;      // target boxes / S panels
@@ -80,22 +95,32 @@ struct DecCfg {
   static constexpr uint32_t off_bar = off_bias + kDecN * 4;
   static constexpr uint32_t bytes = off_bar + 256;
   static constexpr size_t launch_bytes = bytes + 1024;  // slack for 1024-byte alignment
-  static_assert(D == 32 || D == 64, "decoder feature width");
-  static_assert(off_f % 1024 == 0 && off_t % 1024 == 0,
+  static_assert(D == 32 || D == 64 || D == 128, "decoder feature width");
+  static_assert(off_f % 1024 == 0 && off_t % 1024 == 0 && f_stride % 1024 == 0 && w_panel % 1024 == 0,
                 "swizzled operands need 1024-byte aligned buffers");
   static_assert(launch_bytes <= 232448, "shared memory per block");
 };
 
+// Byte offset of the k-th 16-channel K step within a row-major operand of
+// D channels (K-major, 32 bytes per step; at D = 128 the second 64 channels
+// are the second 128-byte panel).
+template <int D>
+__device__ __forceinline__ uint32_t kstep(int k, uint32_t panel) {
+  return D <= 64 ? 32u * k : (uint32_t)(k >> 2) * panel + 32u * (k & 3);
+}
+
 struct DecArgs {
   int64_t HW;
   int ntiles;
+  int c0;            // first output channel of this launch (D = 128: 0 or 128)
+  int df_add;        // 1: add dF to d_feat (the second launch at D = 128)
   int d_real;        // channels of feat / d_feat / d_weight (<= D: D = 16 runs the D = 32 kernel on tiles
                      // the tensor maps zero-fill past channel 16; the padded columns are not stored)
   const float* bias;
   float* out;        // forward: [HW, 256]
   float scale;       // L1: loss and gradient scale
   float* d_feat;     // [HW, D]
-  float* part_loss;  // [ncta]
+  float* part_loss;  // [ncta] (this launch's)
   float* part_dw;    // [ncta][256][D]
   float* part_db;    // [ncta][256]
   uint32_t* err;
@@ -104,7 +129,7 @@ struct DecArgs {
 // Barrier slots (8 bytes each) after off_bar.
 enum : int {
   kBarW = 0, kBarFFull = 1, kBarFEmpty = kBarFFull + 3, kBarTFull = kBarFEmpty + 3,  // up to 3 F stages
-  kBarTEmpty = kBarTFull + kTSlots,
+  kBarTEmpty = kBarTFull + 8,  // up to 8 target slots
   kBarAccFull = kBarTEmpty + 2, kBarAccEmpty,
   kBarSFull,                // [2] and
   kBarBwd = kBarSFull + 2,  // [2]: tiles alternate, so no wait can see its barrier two phases on
@@ -246,8 +271,11 @@ __global__ void __launch_bounds__(kDecThreads, 1)
   using C = DecCfg<D>;
   constexpr bool kL1 = MODE != kDecForward;
   constexpr bool kTF32 = MODE == kDecL1F32;
+  constexpr int NO = C::NO;
   constexpr int kBoxCh = kTF32 ? 32 : 64;         // target channels per box
-  constexpr int kNumBoxes = kDecN / kBoxCh;       // boxes per tile
+  constexpr int kNumBoxes = NO / kBoxCh;          // boxes per tile
+  constexpr int CPH = NO / 64;                    // 32-channel chunks per epilogue half
+  constexpr uint32_t kTBufBytes = C::kTBufBytes;
   constexpr int kBufs = kTF32 ? 1 : 2;            // tile buffers
   constexpr uint32_t kPanel = kTF32 ? 2 * kBoxBytes : kBoxBytes;  // S panel stride
   extern __shared__ unsigned char dsmem_raw[];
@@ -272,7 +300,7 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       mbar_init(&bars[kBarFEmpty + s], 1);
     }
     for (int s = 0; s < 2; ++s) mbar_init(&bars[kBarTEmpty + s], 1);  // commit after the reverse products
-    for (int s = 0; s < kTSlots; ++s) mbar_init(&bars[kBarTFull + s], 1);
+    for (int s = 0; s < C::kTSlots; ++s) mbar_init(&bars[kBarTFull + s], 1);
     mbar_init(&bars[kBarAccFull], 1);
     mbar_init(&bars[kBarAccEmpty], kEpiWarps);
     mbar_init(&bars[kBarSFull], kEpiWarps);
@@ -291,10 +319,10 @@ __global__ void __launch_bounds__(kDecThreads, 1)
     if (C::merged)
       for (int s = 0; s < C::kFStages; ++s) {
         uint4* op = reinterpret_cast<uint4*>(sm + C::off_f + s * C::f_stride + C::f_bytes);
-        for (int i = tid; i < (int)(C::f_bytes / 16); i += 32 * kEpiWarps)
+        for (int i = tid; i < (int)(C::f_panel / 16); i += 32 * kEpiWarps)
           op[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
       }
-    for (int i = tid; i < kDecN; i += 32 * kEpiWarps) s_bias[i] = a.bias[i];
+    for (int i = tid; i < NO; i += 32 * kEpiWarps) s_bias[i] = a.bias[a.c0 + i];
     fence_proxy_async();
   }
   if (warp == kWarpMma) {
@@ -313,13 +341,14 @@ __global__ void __launch_bounds__(kDecThreads, 1)
     if (lane == 0) {
       uint32_t f_uses = 0;
       mbar_arrive_expect_tx(&bars[kBarW], C::w_bytes);
-      tma_2d(sm + C::off_w, &tm_w, 0, 0, &bars[kBarW]);
+      for (int pnl = 0; pnl < C::KP; ++pnl) tma_2d(sm + C::off_w + pnl * C::w_panel, &tm_w, 64 * pnl, a.c0, &bars[kBarW]);
       for (int i = 0; i < n_mine; ++i) {
         const int f = i % C::kFStages;
         if (!dec_wait(&bars[kBarFEmpty + f], ((i / C::kFStages) & 1) ^ 1, s_abort, a.err)) break;
         mbar_arrive_expect_tx(&bars[kBarFFull + f], C::f_bytes);
-        tma_2d(sm + C::off_f + f * C::f_stride, &tm_f, 0, ((int)blockIdx.x + i * (int)gridDim.x) * kDecBM,
-               &bars[kBarFFull + f]);
+        for (int pnl = 0; pnl < C::KP; ++pnl)
+          tma_2d(sm + C::off_f + f * C::f_stride + pnl * C::f_panel, &tm_f, 64 * pnl,
+                 ((int)blockIdx.x + i * (int)gridDim.x) * kDecBM, &bars[kBarFFull + f]);
         ++f_uses;
       }
       // Every copy issued must have landed before the block leaves.
@@ -339,7 +368,7 @@ __global__ void __launch_bounds__(kDecThreads, 1)
         for (int b = h * (kNumBoxes / 2); b < (h + 1) * (kNumBoxes / 2); ++b) {
           const int slot = buf * kNumBoxes + b;
           mbar_arrive_expect_tx(&bars[kBarTFull + slot], kBoxBytes);
-          tma_2d(sm + C::off_t + slot * kBoxBytes, &tm_t, b * kBoxCh,
+          tma_2d(sm + C::off_t + slot * kBoxBytes, &tm_t, a.c0 + b * kBoxCh,
                  ((int)blockIdx.x + i * (int)gridDim.x) * kDecBM, &bars[kBarTFull + slot]);
         }
         issued = i + 1;
@@ -354,7 +383,7 @@ __global__ void __launch_bounds__(kDecThreads, 1)
     // ---------------- tensor-core issue ----------------
     if (lane == 0) {
       const uint32_t s_w = sb + C::off_w, s_t = sb + C::off_t, s_ones = sb + C::off_ones;
-      constexpr uint32_t id_fwd = mma_idesc(128, kDecN, 0, 0);
+      constexpr uint32_t id_fwd = mma_idesc(128, NO, 0, 0);
       constexpr uint32_t id_df = mma_idesc(128, D, 0, 1);
       constexpr uint32_t id_dw = mma_idesc(128, C::merged ? D + 16 : D, 1, 1);
       constexpr uint32_t id_db = mma_idesc(128, 16, 1, 1);
@@ -362,14 +391,14 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       // 32 bytes along each swizzled row.
       auto forward = [&](int i) -> bool {
         const int f = i % C::kFStages;
-        if (!dec_spin<C::merged>(&bars[kBarFFull + f], (i / C::kFStages) & 1, s_abort, a.err)) return false;
-        if (i > 0 && !dec_spin<C::merged>(&bars[kBarAccEmpty], (i - 1) & 1, s_abort, a.err)) return false;
+        if (!dec_spin<C::dfdb>(&bars[kBarFFull + f], (i / C::kFStages) & 1, s_abort, a.err)) return false;
+        if (i > 0 && !dec_spin<C::dfdb>(&bars[kBarAccEmpty], (i - 1) & 1, s_abort, a.err)) return false;
         tc_fence_after();
         const uint32_t s_f = sb + C::off_f + f * C::f_stride;
 #pragma unroll
         for (int k = 0; k < D / 16; ++k)
-          mma_bf16(tmem + kColAcc, smem_desc(s_f + 32 * k, 16, C::sbo, C::layout),
-                   smem_desc(s_w + 32 * k, 16, C::sbo, C::layout), id_fwd, k > 0);
+          mma_bf16(tmem + kColAcc, smem_desc(s_f + kstep<D>(k, C::f_panel), 16, C::sbo, C::layout),
+                   smem_desc(s_w + kstep<D>(k, C::w_panel), 16, C::sbo, C::layout), id_fwd, k > 0);
         mma_commit(&bars[kBarAccFull]);
         return true;
       };
@@ -383,31 +412,32 @@ __global__ void __launch_bounds__(kDecThreads, 1)
         }
         // The next tile's forward product goes ahead of this tile's reverse.
         if (i + 1 < n_mine && !forward(i + 1)) break;
-        if (!dec_spin<C::merged>(&bars[kBarSFull + (i & 1)], (i >> 1) & 1, s_abort, a.err)) break;
+        if (!dec_spin<C::dfdb>(&bars[kBarSFull + (i & 1)], (i >> 1) & 1, s_abort, a.err)) break;
         tc_fence_after();
         const uint32_t s_s = s_t + (i % kBufs) * kTBufBytes;  // S panels of this tile
         const uint32_t s_f = sb + C::off_f + f * C::f_stride;
-        const uint32_t col_df = kColDF + (C::merged ? (i & 1) * D : 0);  // dF buffer of this tile
+        const uint32_t col_df = C::col_df + (C::dfdb ? (i & 1) * D : 0);  // dF buffer of this tile
         // dF = S W: A = S (K-major, 128B swizzle, 64-channel panels),
-        // B = W read MN-major (K = channel rows, N = D along each row).
+        // B = W read MN-major (K = channel rows, N = D along each row; at
+        // D = 128 the row's second 64 channels are the next panel: LBO).
 #pragma unroll
-        for (int k = 0; k < kDecN / 16; ++k)
+        for (int k = 0; k < NO / 16; ++k)
           mma_bf16(tmem + col_df, smem_desc(s_s + (k >> 2) * kPanel + (k & 3) * 32, 16, 1024, kLayout128B),
-                   smem_desc(s_w + k * 16 * C::row_bytes, 16, C::sbo, C::layout), id_df, k > 0);
+                   smem_desc(s_w + k * 16 * C::prow, C::KP > 1 ? C::w_panel : 16, C::sbo, C::layout), id_df, k > 0);
         // dW += S^T F and db += S^T 1: A = S read MN-major (M = channels,
         // two 64-channel panels per half), B = F read MN-major / all ones.
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < NO / 128; ++h) {
 #pragma unroll
           for (int k = 0; k < kDecBM / 16; ++k) {
             const uint64_t ad = smem_desc(s_s + h * 2 * kPanel + k * 2048, kPanel, 1024, kLayout128B);
             const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
-            // Merged: B = [F | ones] along N (the ones panel one stride on).
-            mma_bf16(tmem + kColDW + 64 * h, ad,
-                     smem_desc(s_f + k * 16 * C::row_bytes, C::merged ? C::f_bytes : 16, C::sbo, C::layout), id_dw,
-                     acc);
+            // Merged: B = [F | ones] along N (the ones panel one panel on).
+            mma_bf16(tmem + C::col_dw + 64 * h, ad,
+                     smem_desc(s_f + k * 16 * C::prow, (C::merged || C::KP > 1) ? C::f_panel : 16, C::sbo, C::layout),
+                     id_dw, acc);
             if (!C::merged)
-              mma_bf16(tmem + kColDB + 16 * h, ad, smem_desc(s_ones, 256, 128, kLayoutNone), id_db, acc);
+              mma_bf16(tmem + C::col_db + 16 * h, ad, smem_desc(s_ones, 256, 128, kLayoutNone), id_db, acc);
           }
         }
         mma_commit(&bars[kBarBwd + (i & 1)]);
@@ -428,17 +458,29 @@ __global__ void __launch_bounds__(kDecThreads, 1)
     // This half's D/2 columns of dF for the rows of tile j, scaled, to d_feat.
     auto store_df = [&](int j) {
       const int64_t pj = ((int64_t)blockIdx.x + (int64_t)j * gridDim.x) * kDecBM + r;
-      uint32_t v[32];
-      const uint32_t col = kColDF + (C::merged ? (j & 1) * D : 0);  // dF buffer of tile j
-      if (D == 32) tmem_ld16(t_row + col + 16 * h, v);
-      else tmem_ld32(t_row + col + 32 * h, v);
-      tmem_wait_ld(v);
-      if (pj < a.HW && (D / 2) * h < a.d_real) {
-        float4* o = reinterpret_cast<float4*>(a.d_feat + pj * a.d_real + (D / 2) * h);
+      const uint32_t col = C::col_df + (C::dfdb ? (j & 1) * D : 0);  // dF buffer of tile j
+      // This half's D/2 columns, 32 (or 16) at a time.
 #pragma unroll
-        for (int e = 0; e < D / 8; ++e)
-          o[e] = make_float4(a.scale * __uint_as_float(v[4 * e]), a.scale * __uint_as_float(v[4 * e + 1]),
-                             a.scale * __uint_as_float(v[4 * e + 2]), a.scale * __uint_as_float(v[4 * e + 3]));
+      for (int part = 0; part < (D >= 64 ? D / 64 : 1); ++part) {
+        uint32_t v[32];
+        const int c_lo = (D / 2) * h + 32 * part;  // first column of this part
+        if (D == 32) tmem_ld16(t_row + col + 16 * h, v);
+        else tmem_ld32(t_row + col + c_lo, v);
+        tmem_wait_ld(v);
+        if (pj < a.HW && c_lo < a.d_real) {
+          float4* o = reinterpret_cast<float4*>(a.d_feat + pj * a.d_real + c_lo);
+          constexpr int NE = D == 32 ? 4 : 8;
+#pragma unroll
+          for (int e = 0; e < NE; ++e) {
+            float4 x = make_float4(a.scale * __uint_as_float(v[4 * e]), a.scale * __uint_as_float(v[4 * e + 1]),
+                                   a.scale * __uint_as_float(v[4 * e + 2]), a.scale * __uint_as_float(v[4 * e + 3]));
+            if (a.df_add) {
+              const float4 y = o[e];
+              x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
+            }
+            o[e] = x;
+          }
+        }
       }
     };
     int i = 0;
@@ -452,22 +494,22 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       const int64_t p = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * kDecBM + r;
       const bool valid = p < a.HW;
       unsigned char* tbuf = sm + C::off_t + (i % kBufs) * kTBufBytes;
-      // Four 32-channel chunks; the load of chunk c+1 is in flight while
+      // CPH 32-channel chunks; the load of chunk c+1 is in flight while
       // chunk c is processed.
       uint32_t va[32], vb[32];
-      tmem_ld32(t_row + kColAcc + 32 * (4 * h), va);
+      tmem_ld32(t_row + kColAcc + 32 * (CPH * h), va);
       tmem_wait_ld(va);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < CPH; ++c) {
         uint32_t(&cur)[32] = (c & 1) ? vb : va;
         uint32_t(&nxt)[32] = (c & 1) ? va : vb;
         if (c > 0) tmem_wait_ld(cur);
-        if (c < 3) tmem_ld32(t_row + kColAcc + 32 * (4 * h + c + 1), nxt);
-        const int ch = 4 * h + c;
+        if (c < CPH - 1) tmem_ld32(t_row + kColAcc + 32 * (CPH * h + c + 1), nxt);
+        const int ch = CPH * h + c;
         const float2* bias2 = reinterpret_cast<const float2*>(s_bias + 32 * ch);
         if (!kL1) {
           if (valid) {
-            float4* o = reinterpret_cast<float4*>(a.out + p * kDecN + 32 * ch);
+            float4* o = reinterpret_cast<float4*>(a.out + p * kDecN + a.c0 + 32 * ch);
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const float2 lo = __fadd2_rn(make_float2(__uint_as_float(cur[4 * e]), __uint_as_float(cur[4 * e + 1])),
@@ -529,7 +571,7 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       if (lane == 0) mbar_arrive(&bars[kBarAccEmpty]);
       if (!ok) break;
       if (!kL1) continue;
-      if (C::merged) {
+      if (C::dfdb) {
         // dF is double-buffered: release this tile's S at once, then store
         // the previous tile's dF (its reverse products ran meanwhile).
         fence_proxy_async();  // S stores -> tensor-core reads
@@ -572,14 +614,19 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       asm volatile("bar.sync 1, 256;" ::: "memory");  // epilogue warps only
       if (!*s_abort && n_mine > 0) {
         // The last backward barrier covers every product of this CTA.
+        // NO = 256: M half h = channels 128 h + r, its D columns; NO = 128
+        // (D = 128): one M tile of channels c0 + r, its columns split between
+        // the two warps of each lane quarter (h: columns 64 h .. 64 h + 63).
         tc_fence_after();
-        const int c = h * 128 + r;
+        const int c = a.c0 + (NO == 256 ? h * 128 : 0) + r;
+        constexpr int KW = NO == 256 ? D / 32 : D / 64;  // 32-column loads per warp
 #pragma unroll
-        for (int k = 0; k < D / 32; ++k) {
+        for (int k = 0; k < KW; ++k) {
+          const int c_lo = NO == 256 ? 32 * k : 64 * h + 32 * k;
           uint32_t v[32];
-          tmem_ld32(t_row + kColDW + 64 * h + 32 * k, v);
+          tmem_ld32(t_row + C::col_dw + (NO == 256 ? 64 * h : 0) + c_lo, v);
           tmem_wait_ld(v);
-          float4* o = reinterpret_cast<float4*>(a.part_dw + ((size_t)blockIdx.x * kDecN + c) * D + 32 * k);
+          float4* o = reinterpret_cast<float4*>(a.part_dw + ((size_t)blockIdx.x * kDecN + c) * D + c_lo);
 #pragma unroll
           for (int e = 0; e < 8; ++e)
             o[e] = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
@@ -587,9 +634,9 @@ __global__ void __launch_bounds__(kDecThreads, 1)
         }
         uint32_t vb1;
         // db: a column of its own, or (merged) column D of the dW product.
-        tmem_ld1(t_row + (C::merged ? kColDW + 64 * h + D : kColDB + 16 * h), vb1);
+        tmem_ld1(t_row + (C::merged ? C::col_dw + (NO == 256 ? 64 * h : 0) + D : C::col_db + 16 * h), vb1);
         tmem_wait_ld1(vb1);
-        a.part_db[(size_t)blockIdx.x * kDecN + c] = __uint_as_float(vb1);
+        if (NO == 256 || h == 0) a.part_db[(size_t)blockIdx.x * kDecN + c] = __uint_as_float(vb1);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
@@ -611,8 +658,8 @@ __global__ void __launch_bounds__(kDecThreads, 1)
 }
 
 // Fixed-order sums of the per-CTA partials, scaled (partials of D columns,
-// the first d_real of them stored).
-__global__ void decoder_reduce_kernel(int ncta, int D, int d_real, float scale, const float* part_loss,
+// the first d_real of them stored; nloss loss partials).
+__global__ void decoder_reduce_kernel(int ncta, int nloss, int D, int d_real, float scale, const float* part_loss,
                                       const float* part_dw, const float* part_db, float* loss, float* d_weight,
                                       float* d_bias) {
   const int n_dw = kDecN * d_real;
@@ -629,7 +676,7 @@ __global__ void decoder_reduce_kernel(int ncta, int D, int d_real, float scale, 
     d_bias[j] = scale * s;
   } else if (i == n_dw + kDecN) {
     float s = 0.0f;
-    for (int c = 0; c < ncta; ++c) s += part_loss[c];
+    for (int c = 0; c < nloss; ++c) s += part_loss[c];
     *loss = scale * s;
   }
 }
@@ -688,6 +735,9 @@ struct DecLayout {
   size_t loss, dw, db, total;
 };
 
+// Launches of one decoder call: D = 128 runs over two output-channel halves.
+int dec_passes(int DW) { return DW == 128 ? 2 : 1; }
+
 DecLayout dec_layout(int64_t HW, int D) {
   DecLayout L{};
   const int64_t ntiles = (HW + kDecBM - 1) / kDecBM;
@@ -695,7 +745,7 @@ DecLayout dec_layout(int64_t HW, int D) {
   L.ncta = (int)(ntiles < sms ? ntiles : sms);
   if (L.ncta < 1) L.ncta = 1;
   L.loss = 256;
-  L.dw = align_up(L.loss + (size_t)L.ncta * 4, 256);
+  L.dw = align_up(L.loss + (size_t)dec_passes(D) * L.ncta * 4, 256);
   L.db = align_up(L.dw + (size_t)L.ncta * kDecN * D * 4, 256);
   L.total = align_up(L.db + (size_t)L.ncta * kDecN * 4, 256);
   return L;
@@ -708,7 +758,7 @@ int dec_width(int D) { return D == 16 ? 32 : D; }
 
 fe_status dec_check(const fe_decoder_args* a) {
   if (!a || a->HW < 0 || a->HW > (int64_t)kDecBM * ((1ll << 31) / kDecBM - 1)) return FE_ERR_INVALID_ARG;
-  if (a->D != 16 && a->D != 32 && a->D != 64) return FE_ERR_UNSUPPORTED;
+  if (a->D != 16 && a->D != 32 && a->D != 64 && a->D != 128) return FE_ERR_UNSUPPORTED;
   if (!a->weight || !a->bias || !aligned16p(a->weight)) return FE_ERR_INVALID_ARG;
   if (a->HW > 0 && (!a->feat || !aligned16p(a->feat))) return FE_ERR_INVALID_ARG;
   return FE_OK;
@@ -717,7 +767,23 @@ fe_status dec_check(const fe_decoder_args* a) {
 template <int MODE>
 cudaError_t dispatch(int D, const CUtensorMap& mf, const CUtensorMap& mw, const CUtensorMap& mt, const DecArgs& a,
                      int grid, cudaStream_t st) {
-  return D == 32 ? launch_dec<32, MODE>(mf, mw, mt, a, grid, st) : launch_dec<64, MODE>(mf, mw, mt, a, grid, st);
+  switch (D) {
+    case 32: return launch_dec<32, MODE>(mf, mw, mt, a, grid, st);
+    case 64: return launch_dec<64, MODE>(mf, mw, mt, a, grid, st);
+    case 128: return launch_dec<128, MODE>(mf, mw, mt, a, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Tensor maps of the feature map and the weights: rows of D channels, boxes
+// of DW channels (zero-filled past D) or, at D = 128, of one 64-channel
+// panel; weight boxes of the rows one launch reads.
+bool dec_maps(const fe_decoder_args* a, int DW, CUtensorMap* mf, CUtensorMap* mw) {
+  const CUtensorMapSwizzle swz = DW >= 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  const uint32_t box = DW <= 64 ? (uint32_t)DW : 64u;
+  const uint32_t wrows = DW == 128 ? 128u : (uint32_t)kDecN;
+  return make_map(mf, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->feat, a->D, a->HW, box, kDecBM, swz) &&
+         make_map(mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->weight, a->D, kDecN, box, wrows, swz);
 }
 
 }  // namespace
@@ -729,7 +795,7 @@ using namespace fe;
 extern "C" {
 
 size_t fe_decoder_workspace_size(int64_t HW, int D) {
-  if (HW < 0 || (D != 16 && D != 32 && D != 64)) return 0;
+  if (HW < 0 || (D != 16 && D != 32 && D != 64 && D != 128)) return 0;
   return dec_layout(HW, dec_width(D)).total;
 }
 
@@ -745,11 +811,7 @@ fe_status fe_decode_forward(const fe_decoder_args* a, float* out, void* workspac
   if (cudaMemsetAsync(workspace, 0, 256, st) != cudaSuccess) return FE_ERR_CUDA;
   if (a->HW == 0) return FE_OK;
   CUtensorMap mf, mw;
-  // Rows of a->D channels; boxes of DW channels (zero-filled past a->D).
-  const CUtensorMapSwizzle swz = DW == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-  if (!make_map(&mf, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->feat, a->D, a->HW, DW, kDecBM, swz) ||
-      !make_map(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->weight, a->D, kDecN, DW, kDecN, swz))
-    return FE_ERR_CUDA;
+  if (!dec_maps(a, DW, &mf, &mw)) return FE_ERR_CUDA;
   DecArgs d{};
   d.HW = a->HW;
   d.ntiles = (int)((a->HW + kDecBM - 1) / kDecBM);
@@ -757,7 +819,11 @@ fe_status fe_decode_forward(const fe_decoder_args* a, float* out, void* workspac
   d.bias = a->bias;
   d.out = out;
   d.err = static_cast<uint32_t*>(workspace);
-  return dispatch<kDecForward>(DW, mf, mw, mw, d, L.ncta, st) == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+  for (int pass = 0; pass < dec_passes(DW); ++pass) {
+    d.c0 = 128 * pass;
+    if (dispatch<kDecForward>(DW, mf, mw, mw, d, L.ncta, st) != cudaSuccess) return FE_ERR_CUDA;
+  }
+  return FE_OK;
 }
 
 fe_status fe_decode_l1(const fe_decoder_args* a, const void* target, int target_bf16, float scale, float* loss,
@@ -781,10 +847,8 @@ fe_status fe_decode_l1(const fe_decoder_args* a, const void* target, int target_
     return FE_OK;
   }
   CUtensorMap mf, mw, mt;
-  const CUtensorMapSwizzle swz = DW == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   const bool tb = target_bf16 != 0;
-  if (!make_map(&mf, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->feat, a->D, a->HW, DW, kDecBM, swz) ||
-      !make_map(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a->weight, a->D, kDecN, DW, kDecN, swz) ||
+  if (!dec_maps(a, DW, &mf, &mw) ||
       !make_map(&mt, tb ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, tb ? 2 : 4, target,
                 kDecN, a->HW, tb ? 64 : 32, kDecBM, CU_TENSOR_MAP_SWIZZLE_128B))
     return FE_ERR_CUDA;
@@ -799,12 +863,21 @@ fe_status fe_decode_l1(const fe_decoder_args* a, const void* target, int target_
   d.part_dw = reinterpret_cast<float*>(ws + L.dw);
   d.part_db = reinterpret_cast<float*>(ws + L.db);
   d.err = static_cast<uint32_t*>(workspace);
-  const cudaError_t e = tb ? dispatch<kDecL1Bf16>(DW, mf, mw, mt, d, L.ncta, st)
-                           : dispatch<kDecL1F32>(DW, mf, mw, mt, d, L.ncta, st);
-  if (e != cudaSuccess) return FE_ERR_CUDA;
+  // D = 128: the second launch (channels 128-255) adds its dF to the
+  // first's (same stream: a fixed order) and has loss partials of its own.
+  const int npass = dec_passes(DW);
+  for (int pass = 0; pass < npass; ++pass) {
+    DecArgs dp = d;
+    dp.c0 = 128 * pass;
+    dp.df_add = pass > 0 ? 1 : 0;
+    dp.part_loss = d.part_loss + (size_t)pass * L.ncta;
+    const cudaError_t e = tb ? dispatch<kDecL1Bf16>(DW, mf, mw, mt, dp, L.ncta, st)
+                             : dispatch<kDecL1F32>(DW, mf, mw, mt, dp, L.ncta, st);
+    if (e != cudaSuccess) return FE_ERR_CUDA;
+  }
   const int n = kDecN * a->D + kDecN + 1;
-  decoder_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(L.ncta, DW, a->D, scale, d.part_loss, d.part_dw, d.part_db,
-                                                         loss, d_weight, d_bias);
+  decoder_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(L.ncta, npass * L.ncta, DW, a->D, scale, d.part_loss,
+                                                         d.part_dw, d.part_db, loss, d_weight, d_bias);
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
 

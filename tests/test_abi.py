@@ -92,11 +92,11 @@ def test_workspace_grows_with_capacity_and_backward(lib):
 
 def test_decoder_host_side_status_codes(lib):
     # Argument checks of the decoder entry points return before any CUDA call.
-    assert lib.fe_decoder_workspace_size(1000, 128) == 0         # D not supported by the decoder
+    assert lib.fe_decoder_workspace_size(1000, 256) == 0         # D not supported by the decoder
     assert lib.fe_decoder_workspace_size(1000, 16) == lib.fe_decoder_workspace_size(1000, 32)   # runs as 32
     assert lib.fe_decoder_workspace_size(-1, 32) == 0
     a = _lib.fe_decoder_args()
-    a.HW, a.D, a.feat, a.weight, a.bias = 1000, 128, 16, 16, 16
+    a.HW, a.D, a.feat, a.weight, a.bias = 1000, 256, 16, 16, 16
     args = [None, 0, 1.0, None, None, None, None, None, 0, None]
     assert lib.fe_decode_l1(ctypes.byref(a), *args) == 4         # FE_ERR_UNSUPPORTED
     assert lib.fe_decode_forward(ctypes.byref(a), None, None, 0, None) == 4

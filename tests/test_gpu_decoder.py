@@ -64,7 +64,7 @@ def _l1_check(feat, w, b, tgt, got, rows=None):
     return n_und
 
 
-@pytest.mark.parametrize("D", [16, 32, 64])
+@pytest.mark.parametrize("D", [16, 32, 64, 128])
 def test_decoder_forward_matches_oracle(D):
     HW = 1000  # 7 full 128-pixel tiles and a ragged tail of 104
     feat, w, b, tgt, dec, ft, tt = _inputs(HW, D)
@@ -76,7 +76,8 @@ def test_decoder_forward_matches_oracle(D):
 
 
 @pytest.mark.parametrize("D,tdtype", [(16, torch.bfloat16), (32, torch.bfloat16), (64, torch.bfloat16),
-                                      (16, torch.float32), (32, torch.float32), (64, torch.float32)])
+                                      (128, torch.bfloat16), (16, torch.float32), (32, torch.float32),
+                                      (64, torch.float32), (128, torch.float32)])
 def test_decoder_l1_matches_oracle(D, tdtype):
     HW = 1000
     feat, w, b, tgt, dec, ft, tt = _inputs(HW, D, seed=D, target_dtype=tdtype)
@@ -87,7 +88,7 @@ def test_decoder_l1_matches_oracle(D, tdtype):
     assert n_und <= 1e-4 * HW * 256  # ~2 * MARGIN * density of out - target near 0
 
 
-@pytest.mark.parametrize("D", [16, 32])
+@pytest.mark.parametrize("D", [16, 32, 128])
 def test_decoder_l1_many_tiles_per_cta(D):
     # More tiles than SMs: every CTA walks several tiles, so the weight and
     # bias gradients accumulate across tiles in tensor memory.
