@@ -332,10 +332,12 @@ def test_forward_and_backward_deterministic():
 SAMPLED_WORKLOADS = [
     # 10 of 306 flagged (8 depth-order ties, 2 alpha skips); 185 near.
     ("endonerf_200k_640x512", 300, 14, 230),
-    # BF16 storage of SH and features (FP32 compositing).
+    # BF16 storage of SH and features (FP32 compositing): 10 of 306 flagged
+    # (8 depth-order ties, 2 alpha skips); 190 near.
     ("endonerf_200k_640x512_bf16", 300, 14, 230),
-    # 1M Gaussians, 1280x1024, D=64, BF16 storage.
-    ("scared_1m_1280x1024", 200, 30, 2000),
+    # 1M Gaussians, 1280x1024, D=64, BF16 storage: 22 of 206 flagged (19
+    # depth-order ties, 2 inclusion, 1 termination); 1005 near.
+    ("scared_1m_1280x1024", 200, 30, 1500),
 ]
 
 
