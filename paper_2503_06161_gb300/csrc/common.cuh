@@ -200,21 +200,46 @@ __device__ __forceinline__ float fast_exp2(float x) {
   return y;
 }
 
+// rec: a 16-byte aligned render record (u, v, A, B | Cc, opacity, ...,
+// radius at word 10), read as two 16-byte and one 4-byte shared loads.
 __device__ __forceinline__ bool eval_pair(const float* rec, float pxc, float pyc, PairEval& e) {
+  const float4 q0 = *reinterpret_cast<const float4*>(rec);      // u, v, A, B
+  const float2 q1 = *reinterpret_cast<const float2*>(rec + 4);  // Cc, opacity
   const float r = rec[10];
-  e.dx = __fsub_rn(pxc, rec[0]);
-  e.dy = __fsub_rn(pyc, rec[1]);
+  e.dx = __fsub_rn(pxc, q0.x);
+  e.dy = __fsub_rn(pyc, q0.y);
   if (fabsf(e.dx) > r || fabsf(e.dy) > r) return false;
   // power2 = A dx^2 + B dx dy + Cc dy^2 = (A dx + B dy) dx + Cc dy dy, with
   // explicit FMAs so the forward and reverse kernels round identically.
-  const float t = __fmaf_rn(rec[2], e.dx, __fmul_rn(rec[3], e.dy));
-  const float p2 = __fmaf_rn(t, e.dx, __fmul_rn(__fmul_rn(rec[4], e.dy), e.dy));
+  const float t = __fmaf_rn(q0.z, e.dx, __fmul_rn(q0.w, e.dy));
+  const float p2 = __fmaf_rn(t, e.dx, __fmul_rn(__fmul_rn(q1.x, e.dy), e.dy));
   if (p2 > 0.0f) return false;
   e.G = fast_exp2(p2);
-  const float oG = __fmul_rn(rec[5], e.G);
+  const float oG = __fmul_rn(q1.y, e.G);
   e.clamped = oG > kAlphaMax;
   e.alpha = e.clamped ? kAlphaMax : oG;
   return e.alpha >= kAlphaMin;
+}
+
+// The same evaluation without early exits (every lane runs every step, so
+// the evaluations of several entries interleave): identical arithmetic, so
+// identical decisions and values wherever it returns true.  Lanes that
+// return false leave e with values that are not used.
+__device__ __forceinline__ bool eval_pair_flat(const float* rec, float pxc, float pyc, PairEval& e) {
+  const float4 q0 = *reinterpret_cast<const float4*>(rec);      // u, v, A, B
+  const float2 q1 = *reinterpret_cast<const float2*>(rec + 4);  // Cc, opacity
+  const float r = rec[10];
+  e.dx = __fsub_rn(pxc, q0.x);
+  e.dy = __fsub_rn(pyc, q0.y);
+  const bool inside = !(fabsf(e.dx) > r) && !(fabsf(e.dy) > r);
+  const float t = __fmaf_rn(q0.z, e.dx, __fmul_rn(q0.w, e.dy));
+  const float p2 = __fmaf_rn(t, e.dx, __fmul_rn(__fmul_rn(q1.x, e.dy), e.dy));
+  const bool below = !(p2 > 0.0f);
+  e.G = fast_exp2(below ? p2 : 0.0f);
+  const float oG = __fmul_rn(q1.y, e.G);
+  e.clamped = oG > kAlphaMax;
+  e.alpha = e.clamped ? kAlphaMax : oG;
+  return inside && below && e.alpha >= kAlphaMin;
 }
 
 __device__ __forceinline__ void set_err(uint32_t* err, uint32_t bits) { atomicOr(err, bits); }

@@ -461,6 +461,13 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
       g = eg.y;
     }
   };
+  // The forward's blend-mask word of this warp for batch k (read a batch
+  // ahead, so its global latency overlaps the previous batch).
+  auto mask_word = [&](uint32_t k) -> uint32_t {
+    return (masked && k < nbatch && batch_lo(k) < wmax) ? __ldg(a.cmask + (cslot0 + batch_lo(k) / 32) * 8 + warp)
+                                                         : 0xFFFFFFFFu;
+  };
+  uint32_t mask_next = mask_word(0);
   uint32_t e_next, g_next;
   slot(0, e_next, g_next);
   uint32_t issued = 0;
@@ -499,10 +506,12 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
       s_feat = s_wide;
     }
     const uint32_t rel0 = batch_lo(k);
+    const uint32_t mask_k = mask_next;
+    mask_next = mask_word(k + 1);
     uint32_t jact = 0;
     if (rel0 < wmax) {
       const uint32_t lenmask = nb >= 32 ? 0xFFFFFFFFu : ((1u << nb) - 1u);
-      uint32_t todo = masked ? __ldg(a.cmask + (cslot0 + rel0 / 32) * 8 + warp) & lenmask : lenmask;
+      uint32_t todo = mask_k & lenmask;
       // Every lane writes w (0 where it did not blend) for every entry the
       // warp visits; rows of entries it does not visit may hold stale values:
       // the products of those columns are never combined.
@@ -510,42 +519,51 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
       // replay and the gradient terms v (six geometric values, then two
       // zeros), and the blend weight written to the warp's w slice.
       auto entry = [&](int j, bool hit, const PairEval& pe, float (&v)[8]) {
+        // Without branches, so that the two entries of a pair interleave:
+        // a lane that did not blend takes alpha = 0, which leaves T and Q
+        // exactly as they were (1 / (1 - 0) = 1, w = 0), and zero terms.
+        const float* rec = s_rec + j * kRec;
+        const float al = hit ? pe.alpha : 0.0f;
+        const float one_m = 1.0f - al;
+        const float inv = __fdividef(1.0f, one_m);  // one_m >= 0.01
+        T = T * inv;  // transmittance before this Gaussian
+        const float w = al * T;
+        // s = g . (rgb, depth, feature) of this Gaussian, in four
+        // independent chains of channel pairs (pair i in chain i mod 4).
+        const float4 r0 = *reinterpret_cast<const float4*>(rec);      // ., ., A, B
+        const float4 r4 = *reinterpret_cast<const float4*>(rec + 4);  // Cc, ., depth, r
+        const float4 r8 = *reinterpret_cast<const float4*>(rec + 8);  // g, b, ., .
+        const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * D);
+        const float2* g2 = reinterpret_cast<const float2*>(grow);
+        float2 sc[4];
+        sc[0] = __fmul2_rn(K::GREG ? G[0] : g2[0], make_float2(r4.w, r8.x));
+        sc[1] = __fmul2_rn(K::GREG ? G[1] : g2[1], make_float2(r8.y, r4.z));
+        sc[2] = make_float2(0.0f, 0.0f);
+        sc[3] = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = 0.0f;
-        float w = 0.0f;
-        if (hit) {
-          const float* rec = s_rec + j * kRec;
-          const float one_m = 1.0f - pe.alpha;
-          const float inv = __fdividef(1.0f, one_m);  // one_m >= 0.01
-          T = T * inv;  // transmittance before this Gaussian
-          w = pe.alpha * T;
-          // s = g . (rgb, depth, feature) of this Gaussian.
-          const float4 r4 = *reinterpret_cast<const float4*>(rec + 4);  // ., ., depth, r
-          const float4 r8 = *reinterpret_cast<const float4*>(rec + 8);  // g, b, ., .
-          const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * D);
-          // Even and odd channels summed in the two halves of a pair.
-          const float2* g2 = reinterpret_cast<const float2*>(grow);
-          float2 s2 = __fmul2_rn(K::GREG ? G[0] : g2[0], make_float2(r4.w, r8.x));
-          s2 = __ffma2_rn(K::GREG ? G[1] : g2[1], make_float2(r8.y, r4.z), s2);
-#pragma unroll
-          for (int d4 = 0; d4 < D / 4; ++d4) {
-            const float4 xv = f4[d4];
-            s2 = __ffma2_rn(K::GREG ? G[2 + 2 * d4] : g2[2 + 2 * d4], make_float2(xv.x, xv.y), s2);
-            s2 = __ffma2_rn(K::GREG ? G[3 + 2 * d4] : g2[3 + 2 * d4], make_float2(xv.z, xv.w), s2);
-          }
-          const float s = s2.x + s2.y;
-          const float dalpha = T * s - (Q - ga * Tf) * inv;
-          Q = fmaf(w, s, Q);
-          if (!pe.clamped) {
-            const float dp2 = dalpha * pe.alpha * kLn2;
-            v[0] = -dp2 * (2.0f * rec[2] * pe.dx + rec[3] * pe.dy);
-            v[1] = -dp2 * (2.0f * rec[4] * pe.dy + rec[3] * pe.dx);
-            v[2] = dp2 * pe.dx * pe.dx;
-            v[3] = dp2 * pe.dx * pe.dy;
-            v[4] = dp2 * pe.dy * pe.dy;
-            v[5] = dalpha * pe.G;
-          }
+        for (int d4 = 0; d4 < D / 4; ++d4) {
+          const float4 xv = f4[d4];
+          const int c0 = 2 + 2 * d4;  // channel pair of xv.x, xv.y
+          sc[c0 & 3] = __ffma2_rn(K::GREG ? G[c0] : g2[c0], make_float2(xv.x, xv.y), sc[c0 & 3]);
+          sc[(c0 + 1) & 3] = __ffma2_rn(K::GREG ? G[c0 + 1] : g2[c0 + 1], make_float2(xv.z, xv.w), sc[(c0 + 1) & 3]);
         }
+        const float2 s01 = __fadd2_rn(sc[0], sc[1]), s23 = __fadd2_rn(sc[2], sc[3]);
+        const float2 s2 = __fadd2_rn(s01, s23);
+        const float s = s2.x + s2.y;
+        const float dalpha = T * s - (Q - ga * Tf) * inv;
+        Q = fmaf(w, s, Q);
+        // Geometric terms: zero where the pixel did not blend, and all but
+        // the opacity term zero where alpha was clamped.
+        const bool geo = hit && !pe.clamped;
+        const float dp2 = geo ? dalpha * pe.alpha * kLn2 : 0.0f;
+        v[0] = -dp2 * (2.0f * r0.z * pe.dx + r0.w * pe.dy);
+        v[1] = -dp2 * (2.0f * r4.x * pe.dy + r0.w * pe.dx);
+        v[2] = dp2 * pe.dx * pe.dx;
+        v[3] = dp2 * pe.dx * pe.dy;
+        v[4] = dp2 * pe.dy * pe.dy;
+        v[5] = hit ? dalpha * pe.G : 0.0f;
+        v[6] = 0.0f;
+        v[7] = 0.0f;
         slice[lane * WS + j] = w;
       };
       const int b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1, b2 = (lane >> 1) & 1;
@@ -610,7 +628,8 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
         if ((lane & 1) == 0 && e < 6) s_geo[(warp * B + (m < 8 ? ja : jb)) * 8 + e] = u[0];
       };
       auto evaluate = [&](int j, PairEval& pe) -> bool {
-        return live && rel0 + (uint32_t)j < nc && eval_pair(s_rec + j * kRec, pxc, pyc, pe);
+        const bool h = eval_pair_flat(s_rec + j * kRec, pxc, pyc, pe);
+        return h && live && rel0 + (uint32_t)j < nc;
       };
       // The entries to visit, back to front, in pairs: both evaluated, then
       // replayed in order (the T chain), then summed over the warp together.

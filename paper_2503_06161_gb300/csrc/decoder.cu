@@ -63,6 +63,10 @@ struct DecCfg {
   // F tiles in flight (D = 64, 128: two, their larger tiles fill shared memory).
   static constexpr int kFStages = D == 32 ? 3 : 2;
   static_assert(kFStages <= 3, "barrier slots for three F stages");
+  // Tile buffers of bf16 targets (and S).  (A third buffer at D = 32, in
+  // place of the third F stage and the merged db product, measured slower:
+  // the epilogue, not the target loads, sets the tile period.)
+  static constexpr int kTBufs = 2;
   static constexpr uint32_t row_bytes = D * 2;              // one F / W row in bf16
   static constexpr int KP = D <= 64 ? 1 : D / 64;           // 128-byte K panels of a row (128B swizzle)
   static constexpr uint32_t prow = D <= 64 ? row_bytes : 128u;  // bytes of a row within one panel
@@ -84,8 +88,10 @@ struct DecCfg {
   static constexpr uint32_t col_dw = D == 128 ? 256u : 320u;  // per M half h: + 64 h (NO = 256)
   static constexpr uint32_t col_db = 448;                     // not merged: per M half + 16 h
   static_assert(D != 128 || col_dw + D + 16 <= kTmemCols, "tensor-memory columns");
-  // Target boxes staged: 2 tiles of bf16 (64-channel boxes) or 1 tile of fp32 (32-channel boxes).
-  static constexpr int kTSlots = NO / 32;
+  // Target boxes staged: kTBufs tiles of bf16 (64-channel boxes) or 1 tile
+  // of fp32 (32-channel boxes).
+  static constexpr int kTSlots = kTBufs * NO / 64 > NO / 32 ? kTBufs * NO / 64 : NO / 32;
+  static_assert(kTSlots <= 12, "barrier slots for twelve target boxes");
   static constexpr uint32_t kTBufBytes = (NO / 64) * kBoxBytes;  // one tile buffer of bf16 targets
   static constexpr uint32_t off_w = 0;
   static constexpr uint32_t off_f = off_w + w_bytes;                  // kFStages stages
@@ -93,7 +99,7 @@ struct DecCfg {
   static constexpr uint32_t off_ones = off_t + kTSlots * kBoxBytes;
   static constexpr uint32_t off_bias = off_ones + 512;  // one 16 x 16 all-ones operand
   static constexpr uint32_t off_bar = off_bias + kDecN * 4;
-  static constexpr uint32_t bytes = off_bar + 256;
+  static constexpr uint32_t bytes = off_bar + 320;
   static constexpr size_t launch_bytes = bytes + 1024;  // slack for 1024-byte alignment
   static_assert(D == 32 || D == 64 || D == 128, "decoder feature width");
   static_assert(off_f % 1024 == 0 && off_t % 1024 == 0 && f_stride % 1024 == 0 && w_panel % 1024 == 0,
@@ -129,12 +135,13 @@ struct DecArgs {
 // Barrier slots (8 bytes each) after off_bar.
 enum : int {
   kBarW = 0, kBarFFull = 1, kBarFEmpty = kBarFFull + 3, kBarTFull = kBarFEmpty + 3,  // up to 3 F stages
-  kBarTEmpty = kBarTFull + 8,  // up to 8 target slots
-  kBarAccFull = kBarTEmpty + 2, kBarAccEmpty,
+  kBarTEmpty = kBarTFull + 12,  // up to 12 target slots
+  kBarAccFull = kBarTEmpty + 3, kBarAccEmpty,  // up to 3 tile buffers
   kBarSFull,                // [2] and
   kBarBwd = kBarSFull + 2,  // [2]: tiles alternate, so no wait can see its barrier two phases on
   kBarDrain = kBarBwd + 2, kNumBars
 };
+static_assert(kNumBars * 8 + 40 <= 320, "barrier area: barriers, tensor-memory base, abort flag, 8 warp sums");
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint64_t layout) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
@@ -276,7 +283,7 @@ __global__ void __launch_bounds__(kDecThreads, 1)
   constexpr int kNumBoxes = NO / kBoxCh;          // boxes per tile
   constexpr int CPH = NO / 64;                    // 32-channel chunks per epilogue half
   constexpr uint32_t kTBufBytes = C::kTBufBytes;
-  constexpr int kBufs = kTF32 ? 1 : 2;            // tile buffers
+  constexpr int kBufs = kTF32 ? 1 : C::kTBufs;    // tile buffers
   constexpr uint32_t kPanel = kTF32 ? 2 * kBoxBytes : kBoxBytes;  // S panel stride
   extern __shared__ unsigned char dsmem_raw[];
   // Swizzled operands are addressed by shared-memory address bits: align the
@@ -299,7 +306,7 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       mbar_init(&bars[kBarFFull + s], 1);
       mbar_init(&bars[kBarFEmpty + s], 1);
     }
-    for (int s = 0; s < 2; ++s) mbar_init(&bars[kBarTEmpty + s], 1);  // commit after the reverse products
+    for (int s = 0; s < kBufs; ++s) mbar_init(&bars[kBarTEmpty + s], 1);  // commit after the reverse products
     for (int s = 0; s < C::kTSlots; ++s) mbar_init(&bars[kBarTFull + s], 1);
     mbar_init(&bars[kBarAccFull], 1);
     mbar_init(&bars[kBarAccEmpty], kEpiWarps);
@@ -417,15 +424,9 @@ __global__ void __launch_bounds__(kDecThreads, 1)
         const uint32_t s_s = s_t + (i % kBufs) * kTBufBytes;  // S panels of this tile
         const uint32_t s_f = sb + C::off_f + f * C::f_stride;
         const uint32_t col_df = C::col_df + (C::dfdb ? (i & 1) * D : 0);  // dF buffer of this tile
-        // dF = S W: A = S (K-major, 128B swizzle, 64-channel panels),
-        // B = W read MN-major (K = channel rows, N = D along each row; at
-        // D = 128 the row's second 64 channels are the next panel: LBO).
-#pragma unroll
-        for (int k = 0; k < NO / 16; ++k)
-          mma_bf16(tmem + col_df, smem_desc(s_s + (k >> 2) * kPanel + (k & 3) * 32, 16, 1024, kLayout128B),
-                   smem_desc(s_w + k * 16 * C::prow, C::KP > 1 ? C::w_panel : 16, C::sbo, C::layout), id_df, k > 0);
         // dW += S^T F and db += S^T 1: A = S read MN-major (M = channels,
         // two 64-channel panels per half), B = F read MN-major / all ones.
+        // Issued first: F's stage is released once they complete.
 #pragma unroll
         for (int h = 0; h < NO / 128; ++h) {
 #pragma unroll
@@ -440,8 +441,15 @@ __global__ void __launch_bounds__(kDecThreads, 1)
               mma_bf16(tmem + C::col_db + 16 * h, ad, smem_desc(s_ones, 256, 128, kLayoutNone), id_db, acc);
           }
         }
-        mma_commit(&bars[kBarBwd + (i & 1)]);
         mma_commit(&bars[kBarFEmpty + f]);
+        // dF = S W: A = S (K-major, 128B swizzle, 64-channel panels),
+        // B = W read MN-major (K = channel rows, N = D along each row; at
+        // D = 128 the row's second 64 channels are the next panel: LBO).
+#pragma unroll
+        for (int k = 0; k < NO / 16; ++k)
+          mma_bf16(tmem + col_df, smem_desc(s_s + (k >> 2) * kPanel + (k & 3) * 32, 16, 1024, kLayout128B),
+                   smem_desc(s_w + k * 16 * C::prow, C::KP > 1 ? C::w_panel : 16, C::sbo, C::layout), id_df, k > 0);
+        mma_commit(&bars[kBarBwd + (i & 1)]);
         mma_commit(&bars[kBarTEmpty + (i % kBufs)]);
       }
       // Drain: every issued tensor-core operation completes before the
@@ -495,7 +503,9 @@ __global__ void __launch_bounds__(kDecThreads, 1)
       const bool valid = p < a.HW;
       unsigned char* tbuf = sm + C::off_t + (i % kBufs) * kTBufBytes;
       // CPH 32-channel chunks; the load of chunk c+1 is in flight while
-      // chunk c is processed.
+      // chunk c is processed.  Once the last chunk is in registers the
+      // accumulator is released, so the next tile's forward product runs
+      // while that chunk is processed.
       uint32_t va[32], vb[32];
       tmem_ld32(t_row + kColAcc + 32 * (CPH * h), va);
       tmem_wait_ld(va);
@@ -505,6 +515,11 @@ __global__ void __launch_bounds__(kDecThreads, 1)
         uint32_t(&nxt)[32] = (c & 1) ? va : vb;
         if (c > 0) tmem_wait_ld(cur);
         if (c < CPH - 1) tmem_ld32(t_row + kColAcc + 32 * (CPH * h + c + 1), nxt);
+        if (c == CPH - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars[kBarAccEmpty]);
+        }
         const int ch = CPH * h + c;
         const float2* bias2 = reinterpret_cast<const float2*>(s_bias + 32 * ch);
         if (!kL1) {
@@ -547,17 +562,18 @@ __global__ void __launch_bounds__(kDecThreads, 1)
           }
         }
         uint32_t sg[16];
-        float part = 0.0f;
+        // |o - t| of even and odd channels in two chains (then one sum).
+        float part_e = 0.0f, part_o = 0.0f;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const float2 o =
               __fadd2_rn(make_float2(__uint_as_float(cur[2 * k]), __uint_as_float(cur[2 * k + 1])), bias2[k]);
           const float2 d = __ffma2_rn(t2[k], make_float2(-1.0f, -1.0f), o);  // o - t, one rounding
-          part += fabsf(d.x);
-          part += fabsf(d.y);
+          part_e += fabsf(d.x);
+          part_o += fabsf(d.y);
           sg[k] = sign_pair_bf16(d, valid);
         }
-        if (valid) loss += part;
+        if (valid) loss += part_e + part_o;
         // S row r, channels 32ch .. 32ch+31: panel ch/2 of this tile buffer,
         // logical chunks 4 (ch & 1) .. +3 -- over targets already consumed.
         unsigned char* srow = tbuf + (ch >> 1) * kPanel + r * 128;
@@ -566,9 +582,6 @@ __global__ void __launch_bounds__(kDecThreads, 1)
           *reinterpret_cast<uint4*>(srow + (((4 * (ch & 1) + e) ^ (r & 7)) << 4)) =
               make_uint4(sg[4 * e], sg[4 * e + 1], sg[4 * e + 2], sg[4 * e + 3]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bars[kBarAccEmpty]);
       if (!ok) break;
       if (!kL1) continue;
       if (C::dfdb) {
@@ -658,26 +671,49 @@ __global__ void __launch_bounds__(kDecThreads, 1)
 }
 
 // Fixed-order sums of the per-CTA partials, scaled (partials of D columns,
-// the first d_real of them stored; nloss loss partials).
-__global__ void decoder_reduce_kernel(int ncta, int nloss, int D, int d_real, float scale, const float* part_loss,
-                                      const float* part_dw, const float* part_db, float* loss, float* d_weight,
-                                      float* d_bias) {
+// the first d_real of them stored; nloss loss partials).  A block sums 32
+// outputs (one per lane): warp w adds the partials c = w, w + 8, ... in
+// order, then the eight warp sums are added in warp order.
+constexpr int kRedWarps = 8;
+
+__global__ void __launch_bounds__(32 * kRedWarps) decoder_reduce_kernel(int ncta, int nloss, int D, int d_real,
+                                                                        float scale, const float* part_loss,
+                                                                        const float* part_dw, const float* part_db,
+                                                                        float* loss, float* d_weight, float* d_bias) {
+  __shared__ float s_part[kRedWarps][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n_dw = kDecN * d_real;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * 32 + lane;
+  const float* src = nullptr;
+  size_t stride = 0;
+  int count = 0;
+  float* dst = nullptr;
   if (i < n_dw) {
-    const int src = (i / d_real) * D + i % d_real;
-    float s = 0.0f;
-    for (int c = 0; c < ncta; ++c) s += part_dw[(size_t)c * kDecN * D + src];
-    d_weight[i] = scale * s;
+    src = part_dw + (size_t)(i / d_real) * D + i % d_real;
+    stride = (size_t)kDecN * D;
+    count = ncta;
+    dst = d_weight + i;
   } else if (i < n_dw + kDecN) {
-    const int j = i - n_dw;
-    float s = 0.0f;
-    for (int c = 0; c < ncta; ++c) s += part_db[(size_t)c * kDecN + j];
-    d_bias[j] = scale * s;
+    src = part_db + (i - n_dw);
+    stride = kDecN;
+    count = ncta;
+    dst = d_bias + (i - n_dw);
   } else if (i == n_dw + kDecN) {
-    float s = 0.0f;
-    for (int c = 0; c < nloss; ++c) s += part_loss[c];
-    *loss = scale * s;
+    src = part_loss;
+    stride = 1;
+    count = nloss;
+    dst = loss;
+  }
+  float s = 0.0f;
+#pragma unroll 4
+  for (int c = warp; c < count; c += kRedWarps) s += src[(size_t)c * stride];
+  s_part[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && dst) {
+    float t = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kRedWarps; ++w) t += s_part[w][lane];
+    *dst = scale * t;
   }
 }
 
@@ -876,7 +912,7 @@ fe_status fe_decode_l1(const fe_decoder_args* a, const void* target, int target_
     if (e != cudaSuccess) return FE_ERR_CUDA;
   }
   const int n = kDecN * a->D + kDecN + 1;
-  decoder_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(L.ncta, npass * L.ncta, DW, a->D, scale, d.part_loss,
+  decoder_reduce_kernel<<<(n + 31) / 32, 32 * kRedWarps, 0, st>>>(L.ncta, npass * L.ncta, DW, a->D, scale, d.part_loss,
                                                          d.part_dw, d.part_db, loss, d_weight, d_bias);
   return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
