@@ -362,6 +362,10 @@ struct BwdCfg {
   static constexpr int GS = NC + 2;                 // per-pixel gradient row stride (8-byte rows)
   static constexpr int WS = B + 2;                  // w row stride (8-byte rows; 2-way bank conflicts on the w writes)
   static constexpr int SLICE = (32 * WS > B * NC) ? 32 * WS : B * NC;
+  // Scalar row of a warp's entry: du dv dA dB dCc dopacity | r g b | depth | 0 0
+  // (the layout of the partial row's scalar columns); B + 1 rows per warp,
+  // the last one a sink for the sums of no entry.
+  static constexpr int GR = 12;
   static_assert(B % JG == 0 && CPL % 2 == 0 && JPL <= 2, "lane grid of the per-warp product");
   // Byte offsets in dynamic shared memory: per-pixel gradient rows, warp
   // slices, geometric warp partials, two staging buffers, the fp32 copy of
@@ -369,13 +373,19 @@ struct BwdCfg {
   static constexpr size_t off_G = 0;
   static constexpr size_t off_slice = off_G + (size_t)kThreads * GS * 4;
   static constexpr size_t off_geo = off_slice + (size_t)8 * SLICE * 4;
-  static constexpr size_t off_stage = (off_geo + (size_t)8 * B * 8 * 4 + 127) / 128 * 128;
+  static constexpr size_t off_stage = (off_geo + (size_t)8 * (B + 1) * GR * 4 + 127) / 128 * 128;
   __host__ __device__ static constexpr size_t off_wide(int bf16) { return off_stage + 2 * (size_t)stage_bytes(B, D, bf16); }
   __host__ __device__ static constexpr size_t off_e(int bf16) {
     return off_wide(bf16) + (bf16 ? (size_t)B * D * 4 : 0);
   }
   __host__ __device__ static constexpr size_t smem_bytes(int bf16) { return off_e(bf16) + (size_t)(2 * B + 8 + 4) * 4; }
 };
+
+static_assert(BwdCfg<16>::smem_bytes(1) <= 232448 && BwdCfg<32>::smem_bytes(1) <= 232448 &&
+                  BwdCfg<64>::smem_bytes(1) <= 232448 && BwdCfg<128>::smem_bytes(1) <= 232448 &&
+                  BwdCfg<128>::smem_bytes(0) <= 232448,
+              "reverse compositing shared memory per block");
+static_assert(2 * (BwdCfg<32>::smem_bytes(1) + 1024) <= 233472, "two reverse blocks per SM at D <= 32");
 
 // Reverse compositing of one tile by the whole block.
 template <int D>
@@ -387,7 +397,7 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
   const uint32_t sbytes = stage_bytes(B, D, a.feat_bf16);
   float* s_G = reinterpret_cast<float*>(smem + K::off_G);          // [256][GS]
   float* s_slice = reinterpret_cast<float*>(smem + K::off_slice);  // [8][SLICE]: w[p][j], then P[j][c]
-  float* s_geo = reinterpret_cast<float*>(smem + K::off_geo);      // [8][B][8]
+  float* s_geo = reinterpret_cast<float*>(smem + K::off_geo);      // [8][B + 1][GR]
   unsigned char* s_stage = smem + K::off_stage;                     // [2][sbytes]
   float* s_wide = reinterpret_cast<float*>(smem + K::off_wide(a.feat_bf16));
   uint32_t* s_e = reinterpret_cast<uint32_t*>(smem + K::off_e(a.feat_bf16));  // [2][B]
@@ -423,6 +433,10 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
 #pragma unroll
       for (int d = 0; d < D; ++d) grow[4 + d] = 0.0f;
     }
+  }
+  for (int i = tid; i < 8 * (B + 1); i += kThreads) {
+    s_geo[i * K::GR + 10] = 0.0f;
+    s_geo[i * K::GR + 11] = 0.0f;
   }
   float2 G[K::GREG ? NC / 2 : 1];
   if (K::GREG) {
@@ -570,7 +584,6 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
       // Warp sums of one entry's v[0..7] (reduce-scatter: lane 4m ends with
       // the sum of index m).
       auto scatter1 = [&](int j, float (&v)[8]) {
-        jact |= 1u << j;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const float send = b16 ? v[i] : v[i + 4];
@@ -591,13 +604,12 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
         v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 2);
         v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 1);
         const int m = lane >> 2;
-        if ((lane & 3) == 0 && m < 6) s_geo[(warp * B + j) * 8 + m] = v[0];
+        if ((lane & 3) == 0 && m < 6) s_geo[(warp * (B + 1) + j) * K::GR + m] = v[0];
       };
       // Both entries' sums at once: u = (va, vb), lane 2m ends with the sum
       // of index m (16 shuffles instead of 18, and no warp-wide exchange
       // between the two entries' arithmetic).
-      auto scatter2 = [&](int ja, int jb, float (&va)[8], float (&vb)[8]) {
-        jact |= (1u << ja) | (1u << jb);
+      auto scatter2 = [&](int ja, int jb, const float (&va)[8], const float (&vb)[8]) {
         float u[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -625,35 +637,56 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
         u[0] += __shfl_xor_sync(0xFFFFFFFFu, u[0], 1);
         // lane 2m holds index m = 8 b16 + 4 b8 + 2 b4 + b2 of u = (va, vb).
         const int m = lane >> 1, e = m & 7;
-        if ((lane & 1) == 0 && e < 6) s_geo[(warp * B + (m < 8 ? ja : jb)) * 8 + e] = u[0];
+        if ((lane & 1) == 0 && e < 6) s_geo[(warp * (B + 1) + (m < 8 ? ja : jb)) * K::GR + e] = u[0];
       };
       auto evaluate = [&](int j, PairEval& pe) -> bool {
         const bool h = eval_pair_flat(s_rec + j * kRec, pxc, pyc, pe);
         return h && live && rel0 + (uint32_t)j < nc;
       };
-      // The entries to visit, back to front, in pairs: both evaluated, then
-      // replayed in order (the T chain), then summed over the warp together.
-      while (todo) {
+      // The entries to visit, back to front: with an odd count the first
+      // (the latest in list order) alone, then pairs -- both evaluated, then
+      // replayed in order (the T chain).  A pair's warp sums are formed
+      // after the next pair's arithmetic (the first time, zeros go to the
+      // sink row), so the shuffles overlap independent work.
+      const int cnt = __popc(todo);
+      if (cnt & 1) {
         const int ja = 31 - __clz(todo);
         todo &= ~(1u << ja);
+        PairEval pa;
+        float va[8];
+        const bool ha = evaluate(ja, pa);
+        entry(ja, ha, pa, va);
+        if (__any_sync(0xFFFFFFFFu, ha)) {
+          jact |= 1u << ja;
+          scatter1(ja, va);
+        }
+      }
+      float qa[8], qb[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) qa[i] = qb[i] = 0.0f;
+      int qja = B, qjb = B;
+      for (int n = 0; n < cnt / 2; ++n) {
+        const int ja = 31 - __clz(todo);
+        todo &= ~(1u << ja);
+        const int jb = 31 - __clz(todo);
+        todo &= ~(1u << jb);
         PairEval pa, pb;
         float va[8], vb[8];
         const bool ha = evaluate(ja, pa);
-        if (todo) {
-          const int jb = 31 - __clz(todo);
-          todo &= ~(1u << jb);
-          const bool hb = evaluate(jb, pb);
-          entry(ja, ha, pa, va);
-          entry(jb, hb, pb, vb);
-          const bool aa = __any_sync(0xFFFFFFFFu, ha), ab = __any_sync(0xFFFFFFFFu, hb);
-          if (aa && ab) scatter2(ja, jb, va, vb);
-          else if (aa) scatter1(ja, va);
-          else if (ab) scatter1(jb, vb);
-        } else {
-          entry(ja, ha, pa, va);
-          if (__any_sync(0xFFFFFFFFu, ha)) scatter1(ja, va);
+        const bool hb = evaluate(jb, pb);
+        entry(ja, ha, pa, va);
+        entry(jb, hb, pb, vb);
+        jact |= (__any_sync(0xFFFFFFFFu, ha) ? 1u << ja : 0u) | (__any_sync(0xFFFFFFFFu, hb) ? 1u << jb : 0u);
+        scatter2(qja, qjb, qa, qb);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          qa[i] = va[i];
+          qb[i] = vb[i];
         }
+        qja = ja;
+        qjb = jb;
       }
+      if (cnt >= 2) scatter2(qja, qjb, qa, qb);
       __syncwarp();
       if (K::JPL == 2 && jact && __popc(jact) <= 16) {
         // At most 16 active entries: lane pair jg takes the jg-th active
@@ -676,7 +709,12 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
         __syncwarp();
         if (has) {
 #pragma unroll
-          for (int c = 0; c < CP2; ++c) *reinterpret_cast<float2*>(slice + jl * NC + cg * K::CPL + 2 * c) = acc[c];
+          for (int c = 0; c < CP2; ++c) {
+            // Colour and depth (the first two pairs) go to the scalar row.
+            float* dst = (cg == 0 && c < 2) ? s_geo + (warp * (B + 1) + jl) * K::GR + 6 + 2 * c
+                                            : slice + jl * NC + cg * K::CPL + 2 * c;
+            *reinterpret_cast<float2*>(dst) = acc[c];
+          }
         }
       } else if (jact) {
         // P[j][c] = sum over the warp's pixels of w[p][j] * G[p][c], channel
@@ -710,7 +748,12 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
         for (int jj = 0; jj < K::JPL; ++jj)
 #pragma unroll
           for (int c = 0; c < CP2; ++c)
-            *reinterpret_cast<float2*>(slice + (jg * K::JPL + jj) * NC + cg * K::CPL + 2 * c) = acc[jj][c];
+          {
+            const int jj2 = jg * K::JPL + jj;
+            float* dst = (cg == 0 && c < 2) ? s_geo + (warp * (B + 1) + jj2) * K::GR + 6 + 2 * c
+                                            : slice + jj2 * NC + cg * K::CPL + 2 * c;
+            *reinterpret_cast<float2*>(dst) = acc[jj][c];
+          }
       }
     }
     if (lane == 0) s_jact[warp] = jact;
@@ -728,32 +771,24 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
     const int nact = __popc(bm);
     // One item = four consecutive columns of an active entry's partial row
     // [features | du dv dA dB dCc dopacity | r g b | depth | 0 0]: the warp
-    // partials summed in warp order, one 16-byte store.  A channel-split
-    // pass that is not the first adds its geometric terms (du .. dopacity)
-    // to the row the first pass wrote and leaves colour and depth alone.
+    // partials (feature columns from the warp slices, the rest from the
+    // warps' scalar rows, which have that layout) summed in warp order, one
+    // 16-byte store.  A channel-split pass that is not the first adds its
+    // geometric terms (du .. dopacity) to the row the first pass wrote and
+    // leaves colour and depth alone.
     constexpr int NQ = D / 4 + 3;
     const int nq = a.aux ? NQ : NQ - 1;
     for (int item = tid; item < nact * nq; item += kThreads) {
       const int ja = item / nq, q4 = item - ja * nq;
       const int j = (int)__fns(bm, 0, ja + 1);  // the ja-th active entry
+      const bool fcol = q4 < D / 4;
+      const float* src = fcol ? s_slice + j * NC + 4 + 4 * q4 : s_geo + j * K::GR + 4 * (q4 - D / 4);
+      const int wstride = fcol ? K::SLICE : (B + 1) * K::GR;
       float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
       for (int w8 = 0; w8 < 8; ++w8) {
         if ((jm[w8] >> j) & 1u) {
-          const float* sl = s_slice + w8 * K::SLICE + j * NC;  // rgb, depth, features
-          const float* ge = s_geo + (w8 * B + j) * 8;          // six geometric terms
-          float4 v;
-          if (q4 < D / 4) {
-            v = *reinterpret_cast<const float4*>(sl + 4 + 4 * q4);
-          } else if (q4 == D / 4) {
-            v = *reinterpret_cast<const float4*>(ge);
-          } else if (q4 == D / 4 + 1) {
-            const float2 g2 = *reinterpret_cast<const float2*>(ge + 4), c2 = *reinterpret_cast<const float2*>(sl);
-            v = make_float4(g2.x, g2.y, c2.x, c2.y);
-          } else {
-            const float2 c2 = *reinterpret_cast<const float2*>(sl + 2);
-            v = make_float4(c2.x, c2.y, 0.0f, 0.0f);
-          }
+          const float4 v = *reinterpret_cast<const float4*>(src + w8 * wstride);
           acc.x += v.x;
           acc.y += v.y;
           acc.z += v.z;
