@@ -218,8 +218,10 @@ __device__ __forceinline__ void fwd_tile(const CompositeArgs& a, const int tile,
           cur = 0u;
           for (; j + 1 < je; j += 2) {
             PairEval p0, p1;
-            const bool h0 = eval_pair(s_rec + j * kRec, pxc, pyc, p0);
-            const bool h1 = eval_pair(s_rec + (j + 1) * kRec, pxc, pyc, p1);
+            // Both evaluations without early exits, so that they interleave
+            // (identical arithmetic and decisions to eval_pair).
+            const bool h0 = eval_pair_flat(s_rec + j * kRec, pxc, pyc, p0);
+            const bool h1 = eval_pair_flat(s_rec + (j + 1) * kRec, pxc, pyc, p1);
             if (h0 && blend(j, p0)) break;
             if (h1 && blend(j + 1, p1)) break;
           }
