@@ -267,26 +267,37 @@ __device__ __forceinline__ void mlp_hidden2(const float* sw, const float f[C], f
 #pragma unroll
   for (int o = 0; o < kHidden / 2; ++o) h2p[o] = make_float2(sw[L::kB2 + 2 * o], sw[L::kB2 + 2 * o + 1]);
   m1 = 0;
+  // First-layer units G at a time: their dots are independent chains
+  // (each unit's own sequence of FMAs is unchanged), then the second-layer
+  // updates in unit order.  (C = 64 keeps one unit: more would spill.)
+  constexpr int G = C <= 32 ? 4 : 1;
 #pragma unroll 1
-  for (int o1 = 0; o1 < kHidden; ++o1) {
-    const float4* w1r = reinterpret_cast<const float4*>(sw + L::kW1 + o1 * C);
-    float2 acc2 = make_float2(sw[L::kB1 + o1], 0.0f);
+  for (int o0 = 0; o0 < kHidden; o0 += G) {
+    float2 acc2[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) acc2[u] = make_float2(sw[L::kB1 + o0 + u], 0.0f);
 #pragma unroll
     for (int c4 = 0; c4 < C / 4; ++c4) {
-      const float4 w = w1r[c4];
-      acc2 = __ffma2_rn(make_float2(w.x, w.y), make_float2(f[4 * c4], f[4 * c4 + 1]), acc2);
-      acc2 = __ffma2_rn(make_float2(w.z, w.w), make_float2(f[4 * c4 + 2], f[4 * c4 + 3]), acc2);
-    }
-    const float acc = acc2.x + acc2.y;
-    m1 |= (uint64_t)(acc > 0.0f) << o1;
-    const float h = fmaxf(acc, 0.0f);
-    const float2 hh = make_float2(h, h);
-    const float4* w2r = reinterpret_cast<const float4*>(sw + L::kW2t + o1 * kHidden);
 #pragma unroll
-    for (int o4 = 0; o4 < kHidden / 4; ++o4) {
-      const float4 w = w2r[o4];
-      h2p[2 * o4] = __ffma2_rn(make_float2(w.x, w.y), hh, h2p[2 * o4]);
-      h2p[2 * o4 + 1] = __ffma2_rn(make_float2(w.z, w.w), hh, h2p[2 * o4 + 1]);
+      for (int u = 0; u < G; ++u) {
+        const float4 w = reinterpret_cast<const float4*>(sw + L::kW1 + (o0 + u) * C)[c4];
+        acc2[u] = __ffma2_rn(make_float2(w.x, w.y), make_float2(f[4 * c4], f[4 * c4 + 1]), acc2[u]);
+        acc2[u] = __ffma2_rn(make_float2(w.z, w.w), make_float2(f[4 * c4 + 2], f[4 * c4 + 3]), acc2[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const float acc = acc2[u].x + acc2[u].y;
+      m1 |= (uint64_t)(acc > 0.0f) << (o0 + u);
+      const float h = fmaxf(acc, 0.0f);
+      const float2 hh = make_float2(h, h);
+      const float4* w2r = reinterpret_cast<const float4*>(sw + L::kW2t + (o0 + u) * kHidden);
+#pragma unroll
+      for (int o4 = 0; o4 < kHidden / 4; ++o4) {
+        const float4 w = w2r[o4];
+        h2p[2 * o4] = __ffma2_rn(make_float2(w.x, w.y), hh, h2p[2 * o4]);
+        h2p[2 * o4 + 1] = __ffma2_rn(make_float2(w.z, w.w), hh, h2p[2 * o4 + 1]);
+      }
     }
   }
 #pragma unroll
