@@ -462,9 +462,10 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
   // processed, the last in list order, may be short).
   auto batch_lo = [&](uint32_t k) -> uint32_t { return (nbatch - 1 - k) * (uint32_t)B; };
   auto batch_len = [&](uint32_t k) -> int { return (int)min((uint32_t)B, n - batch_lo(k)); };
-  // With 32-entry batches the forward's masks say which entries blended in
-  // some pixel of this warp; the others are skipped.
-  const bool masked = B == 32 && a.cmask != nullptr;
+  // The forward's masks say which entries of each 32-entry group blended in
+  // some pixel of this warp; the others are skipped (a 16-entry batch takes
+  // its half of the group's word).
+  const bool masked = a.cmask != nullptr;
   const size_t cslot0 = (size_t)(rg.x >> 5) + (size_t)tile;
   // List entry and Gaussian of this thread's slot in batch k.
   auto slot = [&](uint32_t k, uint32_t& e, uint32_t& g) {
@@ -480,8 +481,9 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
   // The forward's blend-mask word of this warp for batch k (read a batch
   // ahead, so its global latency overlaps the previous batch).
   auto mask_word = [&](uint32_t k) -> uint32_t {
-    return (masked && k < nbatch && batch_lo(k) < wmax) ? __ldg(a.cmask + (cslot0 + batch_lo(k) / 32) * 8 + warp)
-                                                         : 0xFFFFFFFFu;
+    return (masked && k < nbatch && batch_lo(k) < wmax)
+               ? __ldg(a.cmask + (cslot0 + batch_lo(k) / 32) * 8 + warp) >> (batch_lo(k) & 31u)
+               : 0xFFFFFFFFu;
   };
   uint32_t mask_next = mask_word(0);
   uint32_t e_next, g_next;
@@ -676,9 +678,13 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
         float va[8], vb[8];
         const bool ha = evaluate(ja, pa);
         const bool hb = evaluate(jb, pb);
+        const bool aa = __any_sync(0xFFFFFFFFu, ha), ab = __any_sync(0xFFFFFFFFu, hb);
+        // Neither entry blends in this warp (only without the forward's
+        // masks): nothing changes, nothing to sum.
+        if (!(aa || ab)) continue;
         entry(ja, ha, pa, va);
         entry(jb, hb, pb, vb);
-        jact |= (__any_sync(0xFFFFFFFFu, ha) ? 1u << ja : 0u) | (__any_sync(0xFFFFFFFFu, hb) ? 1u << jb : 0u);
+        jact |= (aa ? 1u << ja : 0u) | (ab ? 1u << jb : 0u);
         scatter2(qja, qjb, qa, qb);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {

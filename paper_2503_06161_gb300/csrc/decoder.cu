@@ -239,6 +239,12 @@ __device__ __forceinline__ uint32_t sign_pair_bf16(float2 d, bool valid) {
   return valid ? (s & keep) : 0u;
 }
 
+// Programmatic dependent launch: wait until the kernels this one may have
+// started beside have finished (their memory visible), and let the next
+// kernel of the stream start its set-up while this one runs.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ bool dec_wait(uint64_t* bar, uint32_t parity, volatile int* abort, uint32_t* err) {
   if (*abort) return false;
   if (mbar_wait(bar, parity)) return true;
@@ -329,7 +335,6 @@ __global__ void __launch_bounds__(kDecThreads, 1)
         for (int i = tid; i < (int)(C::f_panel / 16); i += 32 * kEpiWarps)
           op[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
       }
-    for (int i = tid; i < NO; i += 32 * kEpiWarps) s_bias[i] = a.bias[a.c0 + i];
     fence_proxy_async();
   }
   if (warp == kWarpMma) {
@@ -342,6 +347,10 @@ __global__ void __launch_bounds__(kDecThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
+  // Set-up above touches no global memory; everything below may read what
+  // the previous kernel of the stream wrote.
+  grid_dep_wait();
+  grid_dep_launch();
 
   if (warp == kWarpF) {
     // ---------------- W (once) and F tiles ----------------
@@ -459,6 +468,8 @@ __global__ void __launch_bounds__(kDecThreads, 1)
     }
   } else {
     // ---------------- epilogue: warps 0-7, one pixel row per thread ----------------
+    for (int i = tid; i < NO; i += 32 * kEpiWarps) s_bias[i] = a.bias[a.c0 + i];
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // epilogue warps only: the bias is in place
     const int q = warp & 3, h = warp >> 2;  // lane quarter, channel half
     const int r = q * 32 + lane;            // tile row = tensor-memory lane
     const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
@@ -681,6 +692,7 @@ __global__ void __launch_bounds__(32 * kRedWarps) decoder_reduce_kernel(int ncta
                                                                         const float* part_dw, const float* part_db,
                                                                         float* loss, float* d_weight, float* d_bias) {
   __shared__ float s_part[kRedWarps][33];
+  grid_dep_wait();  // the decoder launches that wrote the partials
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n_dw = kDecN * d_real;
   const int i = blockIdx.x * 32 + lane;
@@ -754,6 +766,24 @@ int num_sms() {
   return n;
 }
 
+// A launch that may start while the previous kernel of the stream finishes
+// (programmatic stream serialization); the kernel orders itself with
+// griddepcontrol.wait.
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*k)(Params...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <int D, int MODE>
 cudaError_t launch_dec(const CUtensorMap& mf, const CUtensorMap& mw, const CUtensorMap& mt, const DecArgs& a, int grid,
                        cudaStream_t st) {
@@ -761,8 +791,7 @@ cudaError_t launch_dec(const CUtensorMap& mf, const CUtensorMap& mw, const CUten
   const size_t smem = DecCfg<D>::launch_bytes;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<grid, kDecThreads, smem, st>>>(mf, mw, mt, a);
-  return cudaGetLastError();
+  return launch_pdl(k, grid, kDecThreads, smem, st, mf, mw, mt, a);
 }
 
 // Workspace: 256-byte header (error bits), then per-CTA partial loss, dW, db.
@@ -912,9 +941,10 @@ fe_status fe_decode_l1(const fe_decoder_args* a, const void* target, int target_
     if (e != cudaSuccess) return FE_ERR_CUDA;
   }
   const int n = kDecN * a->D + kDecN + 1;
-  decoder_reduce_kernel<<<(n + 31) / 32, 32 * kRedWarps, 0, st>>>(L.ncta, npass * L.ncta, DW, a->D, scale, d.part_loss,
-                                                         d.part_dw, d.part_db, loss, d_weight, d_bias);
-  return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+  const cudaError_t e = launch_pdl(decoder_reduce_kernel, (n + 31) / 32, 32 * kRedWarps, 0, st, L.ncta, npass * L.ncta,
+                                   DW, a->D, scale, (const float*)d.part_loss, (const float*)d.part_dw,
+                                   (const float*)d.part_db, loss, d_weight, d_bias);
+  return e == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
 
 fe_status fe_decoder_read_errors(const void* workspace, uint32_t* err, void* stream) {
