@@ -119,6 +119,8 @@ GaussBwdArgs gauss_bwd_args(const Layout& L, void* ws, const fe_grads* grads, in
   gb.cap = L.cap;
   gb.touched = at<uint32_t>(ws, L.touched);
   gb.offs_by_gid = at<uint32_t>(ws, L.offs_by_gid);
+  gb.order = at<uint32_t>(ws, L.dval[0]);
+  gb.offs = at<uint32_t>(ws, L.offs);
   gb.partials = at<float>(ws, L.partials);
   gb.pflags = at<uint32_t>(ws, L.pflags);
   gb.d_means = grads->means;

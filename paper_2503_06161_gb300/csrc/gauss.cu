@@ -768,133 +768,107 @@ __global__ void __launch_bounds__(kThreads, 2) gauss_fwd_kernel(const GaussArgs 
 }
 
 // ---------------------------------------------------------------------------
-// Iterates the written partial rows of emission range [e0, e1) in increasing
-// order (fixed summation order), reading the bitmask a word at a time.
-template <typename F>
-__device__ __forceinline__ void for_each_row(const uint32_t* bits, uint32_t e0, uint32_t e1, F&& f) {
-  if (e0 >= e1) return;
-  for (uint32_t w = e0 >> 5; w <= (e1 - 1) >> 5; ++w) {
-    uint32_t m = bits[w];
-    const uint32_t lo = w << 5;
-    if (lo < e0) m &= ~0u << (e0 - lo);
-    if (e1 - lo < 32) m &= (1u << (e1 - lo)) - 1u;
-    while (m) {
-      const int b = __ffs(m) - 1;
-      m &= m - 1;
-      f(lo + (uint32_t)b);
-    }
-  }
-}
-
-// Sum of each Gaussian's partial rows, one warp per Gaussian, in a fixed
-// order, writing d_feat[g] and the ten scalar sums to psum[g].
-//  * short ranges (<= 64 emission entries): lane c adds column c of every
-//    written row in increasing order, loading four rows before adding;
-//  * long ranges (a large Gaussian near the camera can sit at the front of
-//    a thousand tile lists): lane L walks bitmask words L, L+32, ... and adds
-//    whole rows 16 columns at a time, then a fixed shuffle tree adds the
-//    lanes.  The mode depends only on the range length, so the result is
-//    bitwise reproducible.
-template <int NP>
-__device__ __forceinline__ void reduce_rows_short(const GaussBwdArgs& b, uint32_t e0, uint32_t e1, int lane,
-                                                  float* acc) {
-  constexpr int NQ = (NP + 31) / 32;
-  const uint32_t w0 = e0 >> 5, w1 = (e1 - 1) >> 5;
-  for (uint32_t w = w0; w <= w1; ++w) {
-    uint32_t m = b.pflags[w];
-    const uint32_t lo = w << 5;
-    if (lo < e0) m &= ~0u << (e0 - lo);
-    if (e1 - lo < 32) m &= (1u << (e1 - lo)) - 1u;
-    while (m) {
-      uint32_t e[4];
-      bool v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        v[u] = m != 0u;
-        e[u] = lo + (v[u] ? (uint32_t)(__ffs(m) - 1) : 0u);
-        m = v[u] ? (m & (m - 1u)) : 0u;
-      }
-      float x[4][NQ];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float* row = b.partials + (size_t)e[u] * NP;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) x[u][q] = (v[u] && lane + 32 * q < NP) ? row[lane + 32 * q] : 0.0f;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int q = 0; q < NQ; ++q)
-          if (v[u]) acc[q] += x[u][q];
-    }
-  }
-}
-
-template <int NP>
-__device__ __forceinline__ void reduce_rows_long(const GaussBwdArgs& b, uint32_t e0, uint32_t e1, int lane,
-                                                 float* acc) {
-  const uint32_t w0 = e0 >> 5, w1 = (e1 - 1) >> 5;
-#pragma unroll 1
-  for (int c0 = 0; c0 < NP; c0 += 16) {
-    float part[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) part[i] = 0.0f;
-    for (uint32_t w = w0 + lane; w <= w1; w += 32) {
-      uint32_t m = b.pflags[w];
-      const uint32_t lo = w << 5;
-      if (lo < e0) m &= ~0u << (e0 - lo);
-      if (e1 - lo < 32) m &= (1u << (e1 - lo)) - 1u;
-      while (m) {
-        const uint32_t e = lo + (uint32_t)(__ffs(m) - 1);
-        m &= m - 1u;
-        const float4* row = reinterpret_cast<const float4*>(b.partials + (size_t)e * NP + c0);
-#pragma unroll
-        for (int i4 = 0; i4 < 4; ++i4) {
-          if (c0 + 4 * i4 < NP) {
-            const float4 v = row[i4];
-            part[4 * i4] += v.x; part[4 * i4 + 1] += v.y; part[4 * i4 + 2] += v.z; part[4 * i4 + 3] += v.w;
-          }
-        }
-      }
-    }
-    // Fixed-order tree over the 32 lanes; lane 0 ends with the sums.
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part[i] += __shfl_down_sync(0xFFFFFFFFu, part[i], o);
-    }
-    // Columns c0..c0+15 go to the lanes that own them in the column layout.
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const float v = __shfl_sync(0xFFFFFFFFu, part[i], 0);
-      const int col = c0 + i;
-      if (col < NP && (col & 31) == lane) acc[col >> 5] = v;
-    }
-  }
-}
+// Sum of each Gaussian's partial rows, writing d_feat[g] and the ten scalar
+// sums to psum[g].  The entries of consecutive depth ranks occupy
+// consecutive emission ranges, so one warp takes ranks_per_warp(D) consecutive
+// ranks: one coalesced load of their ranges, one of the bitmask words of
+// the whole range (read back by shuffle), then the written rows streamed RG
+// at a time (all RG rows' loads in flight before any is added), lane c
+// adding column c (and c + 32, ...).  Each Gaussian's rows are added one
+// after another in increasing emission order: a fixed order, so the result
+// is bitwise reproducible.
+// Ranks per warp: 8 for rows of at most 64 floats (D <= 52), else 4
+// (measured best at D = 32 and D = 128).
+__host__ __device__ constexpr int ranks_per_warp(int D) { return (partial_stride(D) + 31) / 32 <= 2 ? 8 : 4; }
 
 template <int D>
 __global__ void __launch_bounds__(kThreads) partial_reduce_kernel(const GaussBwdArgs b, int P) {
   constexpr int NP = partial_stride(D);
+  constexpr int NQ = (NP + 31) / 32;  // columns per lane
+  constexpr int RG = NQ <= 2 ? 16 : (NQ <= 4 ? 8 : 4);  // rows in flight
   const int lane = threadIdx.x & 31;
-  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (g >= P) return;
-  const uint32_t e0 = b.offs_by_gid[g];
-  const uint32_t e1 = (uint32_t)min((uint64_t)e0 + b.touched[g], (uint64_t)b.cap);  // e0 >= e1 past capacity
-  constexpr int NQ = (NP + 31) / 32;
-  float acc[NQ];  // columns lane, lane+32, ...
+  constexpr int GPW = ranks_per_warp(D);
+  const int64_t r0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * GPW;
+  if (r0 >= P) return;
+  const int nvalid = (int)min((int64_t)GPW, (int64_t)P - r0);
+  const uint64_t cap = (uint64_t)b.cap;
+  // Lane j < nvalid: the Gaussian of rank r0 + j and the end of its range.
+  const bool mine = lane < nvalid;
+  const uint32_t gid = mine ? b.order[r0 + lane] : 0u;
+  const uint32_t ebeg = mine ? (uint32_t)min((uint64_t)b.offs[r0 + lane], cap) : 0u;
+  const uint32_t eend = mine ? (uint32_t)min((uint64_t)b.offs[r0 + lane + 1], cap) : 0u;
+  const uint32_t E0 = __shfl_sync(0xFFFFFFFFu, ebeg, 0);
+  const uint32_t E1 = __shfl_sync(0xFFFFFFFFu, eend, nvalid - 1);
+  // Bitmask words of the range: word wbase + l in lane l (the rest, for a
+  // range of more than 32 words, read when reached).
+  const uint32_t wbase = E0 >> 5;
+  const uint32_t wlast = E0 < E1 ? (E1 - 1) >> 5 : wbase;
+  const uint32_t wl = (E0 < E1 && wbase + (uint32_t)lane <= wlast) ? __ldg(b.pflags + wbase + lane) : 0u;
+  auto word = [&](uint32_t w) -> uint32_t {
+    const uint32_t k = w - wbase;
+    const uint32_t v = __shfl_sync(0xFFFFFFFFu, wl, (int)(k & 31u));
+    return k < 32u ? v : __ldg(b.pflags + w);
+  };
+  float acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc[q] = 0.0f;
-  if (e0 < e1) {
-    if (e1 - e0 <= 64) reduce_rows_short<NP>(b, e0, e1, lane, acc);
-    else reduce_rows_long<NP>(b, e0, e1, lane, acc);
-  }
+  int j = 0;  // Gaussian (lane) whose rows are being added
+  uint32_t jend = __shfl_sync(0xFFFFFFFFu, eend, 0);
+  // Writes Gaussian j's sums and moves to the next one.
+  auto flush = [&]() {
+    const uint32_t g = __shfl_sync(0xFFFFFFFFu, gid, j);
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const int col = lane + 32 * q;
-    if (col < D) b.d_feat[g * D + col] = b.accumulate ? b.d_feat[g * D + col] + acc[q] : acc[q];
-    else if (col < NP) b.psum[g * 12 + (col - D)] = acc[q];
+    for (int q = 0; q < NQ; ++q) {
+      const int col = lane + 32 * q;
+      if (col < D) {
+        float* o = b.d_feat + (size_t)g * D + col;
+        *o = b.accumulate ? *o + acc[q] : acc[q];
+      } else if (col < NP) {
+        b.psum[(size_t)g * 12 + (col - D)] = acc[q];
+      }
+      acc[q] = 0.0f;
+    }
+    ++j;
+    jend = __shfl_sync(0xFFFFFFFFu, eend, j < nvalid ? j : nvalid - 1);
+  };
+  // Word w of the bitmask, m its bits not yet taken.
+  uint32_t w = wbase;
+  uint32_t m = E0 < E1 ? word(w) & (~0u << (E0 & 31u)) : 0u;
+  bool done = E0 >= E1;
+  while (!done) {
+    // The next RG written rows (warp-uniform; slot u holds one if has[u]).
+    uint32_t idx[RG];
+    bool has[RG];
+#pragma unroll
+    for (int u = 0; u < RG; ++u) {
+      while (!done && m == 0u) {
+        ++w;
+        if (w > wlast) done = true;
+        else m = word(w);
+      }
+      const uint32_t e = (w << 5) + (uint32_t)(__ffs(m) - 1);
+      has[u] = !done && e < E1;
+      if (!done && e >= E1) done = true;
+      idx[u] = has[u] ? e : 0u;
+      if (has[u]) m &= m - 1u;
+    }
+    float x[RG][NQ];
+#pragma unroll
+    for (int u = 0; u < RG; ++u) {
+      const float* row = b.partials + (size_t)idx[u] * NP;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) x[u][q] = (has[u] && lane + 32 * q < NP) ? __ldg(row + lane + 32 * q) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < RG; ++u) {
+      if (has[u]) {
+        while (idx[u] >= jend) flush();  // rows belong to the Gaussians in order
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] += x[u][q];
+      }
+    }
   }
+  while (j < nvalid) flush();  // the last Gaussian with rows, and any after it without
 }
 
 // ---------------------------------------------------------------------------
@@ -1166,7 +1140,8 @@ static cudaError_t launch_bwd_deform_t(const GaussArgs& a, const GaussBwdArgs& b
 
 cudaError_t launch_gauss_bwd(const GaussArgs& a, const GaussBwdArgs& b, cudaStream_t st, cudaEvent_t mid) {
   if (a.P <= 0) return mid ? cudaEventRecord(mid, st) : cudaSuccess;
-  const int64_t nthreads = (int64_t)a.P * 32;
+  const int gpw = ranks_per_warp(b.D);
+  const int64_t nthreads = ((int64_t)a.P + gpw - 1) / gpw * 32;  // a warp per gpw depth ranks
   const int nblk = (int)((nthreads + kThreads - 1) / kThreads);
   switch (b.D) {
     case 16: partial_reduce_kernel<16><<<nblk, kThreads, 0, st>>>(b, a.P); break;

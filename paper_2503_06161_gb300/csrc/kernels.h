@@ -37,6 +37,8 @@ struct GaussBwdArgs {
   int D;
   int64_t cap;
   const uint32_t *touched, *offs_by_gid;
+  const uint32_t* order;  // [P] Gaussian ids in depth order (the emission order of their entries)
+  const uint32_t* offs;   // [P + 1] first emission index of each depth rank
   const float* partials;
   const uint32_t* pflags;  // bit e set: partial row e was written
   float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh, *d_feat;
