@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,11 +26,37 @@ constexpr float kLn2 = 0.6931471805599453f;
 
 // Packed per-Gaussian render record (48 bytes, 16-byte aligned):
 //  [0] u  [1] v  [2] A  [3] B  [4] Cc  [5] opacity  [6] depth
-//  [7] r  [8] g  [9] b  [10] radius (float)  [11] 0
+//  [7] r  [8] g  [9] b  [10] radius (float)
+//  [11] half-widths (x, y) of a box holding every pixel centre the Gaussian
+//       may blend, two fp16 rounded up (negative: it blends nowhere;
+//       infinite: no box, the radius alone bounds it)
 // with power2 = A dx^2 + B dx dy + Cc dy^2 = log2(e) * power, i.e.
 // A = -0.5 log2(e) a, B = -log2(e) b, Cc = -0.5 log2(e) c for the conic
 // (a, b, c) = inverse of the dilated 2D covariance.
 constexpr int kRec = 12;
+
+// Record word 11 for the quadratic form q = qa dx^2 + qb dx dy + qc dy^2
+// (power2 = -q) and opacity o: alpha = o 2^-q >= 1/255 needs
+// q <= log2(255 o), an ellipse whose box has half-widths
+// sqrt(L qc / det), sqrt(L qa / det), det = qa qc - qb^2 / 4.  Widened by 1%
+// and half a pixel, with L raised by 0.01, the box leaves out only centres
+// whose alpha is below 1/255 by a margin far above the rounding of the
+// per-pixel evaluation.  Used only when det cancels less than a hundredfold.
+__device__ __forceinline__ float blend_box(float qa, float qb, float qc, float o) {
+  float hx, hy;
+  const float ac = qa * qc, det = fmaf(-0.25f * qb, qb, ac);
+  if (!(255.0f * o >= 0.99f)) {
+    hx = hy = -1.0f;  // alpha <= o < 1/255 everywhere
+  } else if (!(det > 0.01f * ac)) {
+    hx = hy = __int_as_float(0x7f800000);
+  } else {
+    const float L = fmaxf(log2f(255.0f * o), 0.0f) + 0.01f;
+    hx = fmaf(sqrtf(L * qc / det), 1.01f, 0.5f);
+    hy = fmaf(sqrtf(L * qa / det), 1.01f, 0.5f);
+  }
+  const __half2 h = __halves2half2(__float2half_ru(hx), __float2half_ru(hy));
+  return __uint_as_float(*reinterpret_cast<const uint32_t*>(&h));
+}
 
 // Device-side error bits, sticky within one call.
 enum : uint32_t { kErrOverflow = 1u, kErrTimeout = 2u, kErrNonFinite = 4u };

@@ -99,6 +99,22 @@ __device__ __forceinline__ void stage_drain(StageState& st, uint64_t* s_bar, uin
   st.arms[1] += issued / 2;
 }
 
+// True when no pixel centre of the rectangle [x0, x1] x [y0, y1] can blend
+// record `rec` (so a warp covering it may skip the entry without changing
+// anything): either the 3-sigma square misses the rectangle -- the per-pixel
+// test, at the rectangle's nearest centres, with the same subtractions -- or
+// the record's blend box (word 11) does.
+__device__ __forceinline__ bool block_misses(const float* rec, float x0, float x1, float y0, float y1) {
+  const float2 uv = *reinterpret_cast<const float2*>(rec);
+  const float2 rb = *reinterpret_cast<const float2*>(rec + 10);  // radius, packed box
+  const float u = uv.x, v = uv.y, r = rb.x;
+  if (__fsub_rn(x0, u) > r || __fsub_rn(u, x1) > r || __fsub_rn(y0, v) > r || __fsub_rn(v, y1) > r) return true;
+  const uint32_t hb = __float_as_uint(rb.y);
+  const __half2 h = *reinterpret_cast<const __half2*>(&hb);
+  const float hx = __low2float(h), hy = __high2float(h);
+  return hx < 0.0f || x0 - u > hx || u - x1 > hx || y0 - v > hy || v - y1 > hy;
+}
+
 // Forward compositing of one tile by the whole block (see the file comment).
 template <int D, int B, bool kCount>
 __device__ __forceinline__ void fwd_tile(const CompositeArgs& a, const int tile, unsigned char* smem, uint64_t* s_bar,
@@ -143,6 +159,9 @@ __device__ __forceinline__ void fwd_tile(const CompositeArgs& a, const int tile,
   const bool track = !kCount && a.cmask != nullptr && a.aux;
   const size_t cslot0 = (size_t)(rg.x >> 5) + (size_t)tile;
   const int lane = tid & 31, warp = tid >> 5;
+  // Pixel centres of this warp's 8 x 4 block.
+  const float bx0 = (float)(tx * a.tw + ((warp % (a.tw >> 3)) << 3)) + 0.5f;
+  const float by0 = (float)(ty * a.th + ((warp / (a.tw >> 3)) << 2)) + 0.5f;
   for (uint32_t k = 0; k < nbatch; ++k) {
     // Every thread is past batch k-1 here, so its buffer may be refilled.
     // A wait on batch k-1 that gave up (s_abort[(k-1) & 1], written before
@@ -173,6 +192,21 @@ __device__ __forceinline__ void fwd_tile(const CompositeArgs& a, const int tile,
       s_feat = s_wide;
     }
     uint32_t cur = 0u;  // blended entries of the current 32-entry group
+    // Entries of each 32-entry group that some pixel of this warp's block
+    // may blend (the others leave every pixel of the block unchanged).
+    uint32_t em0 = 0u, em1 = 0u, em2 = 0u, em3 = 0u;
+    if (!kCount && __any_sync(0xFFFFFFFFu, !done)) {
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const int j = 32 * g + lane;
+        const bool ev = j < nb && !block_misses(s_rec + j * kRec, bx0, bx0 + 7.0f, by0, by0 + 3.0f);
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, ev);
+        if (g == 0) em0 = m;
+        if (g == 1) em1 = m;
+        if (g == 2) em2 = m;
+        if (g == 3) em3 = m;
+      }
+    }
     // Blend entry j (pe: its evaluation); true once the pixel is done.
     auto blend = [&](int j, const PairEval& pe) -> bool {
       const float* rec = s_rec + j * kRec;
@@ -209,25 +243,29 @@ __device__ __forceinline__ void fwd_tile(const CompositeArgs& a, const int tile,
           if (eval_pair(s_rec + j * kRec, pxc, pyc, pe) && blend(j, pe)) break;
         }
       } else {
-        // Groups of 32 entries; within a group two entries are evaluated
-        // ahead of their (ordered) blending: the two evaluations are
-        // independent, only the blend carries T.
+        // Groups of 32 entries; the entries the warp's block may blend are
+        // taken in order, two at a time: both evaluated ahead of their
+        // (ordered) blending -- the two evaluations are independent, only
+        // the blend carries T.
         for (int g = 0; g < NG && !done; ++g) {
-          const int je = min(nb, 32 * g + 32);
-          int j = 32 * g;
+          uint32_t t = g == 0 ? em0 : g == 1 ? em1 : g == 2 ? em2 : em3;
           cur = 0u;
-          for (; j + 1 < je; j += 2) {
+          while (t) {
+            const int ja = 32 * g + __ffs(t) - 1;
+            t &= t - 1u;
             PairEval p0, p1;
-            // Both evaluations without early exits, so that they interleave
+            // Evaluations without early exits, so that they interleave
             // (identical arithmetic and decisions to eval_pair).
-            const bool h0 = eval_pair_flat(s_rec + j * kRec, pxc, pyc, p0);
-            const bool h1 = eval_pair_flat(s_rec + (j + 1) * kRec, pxc, pyc, p1);
-            if (h0 && blend(j, p0)) break;
-            if (h1 && blend(j + 1, p1)) break;
-          }
-          if (!done && j == je - 1) {
-            PairEval pe;
-            if (eval_pair(s_rec + j * kRec, pxc, pyc, pe)) blend(j, pe);
+            const bool h0 = eval_pair_flat(s_rec + ja * kRec, pxc, pyc, p0);
+            if (t) {
+              const int jb = 32 * g + __ffs(t) - 1;
+              t &= t - 1u;
+              const bool h1 = eval_pair_flat(s_rec + jb * kRec, pxc, pyc, p1);
+              if (h0 && blend(ja, p0)) break;
+              if (h1 && blend(jb, p1)) break;
+            } else if (h0 && blend(ja, p0)) {
+              break;
+            }
           }
           cm0 |= g == 0 ? cur : 0u;
           if (NG > 1) cm1 |= g == 1 ? cur : 0u;

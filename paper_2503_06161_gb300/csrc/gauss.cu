@@ -754,7 +754,8 @@ __global__ void __launch_bounds__(kThreads, 2) gauss_fwd_kernel(const GaussArgs 
         vis = true;
         r0 = make_float4(s.u, s.v, -0.5f * kLog2e * s.ca, -kLog2e * s.cb);
         r1 = make_float4(-0.5f * kLog2e * s.cc, s.o, s.p[2], fmaxf(s.rgb_raw[0], 0.0f));
-        r2 = make_float4(fmaxf(s.rgb_raw[1], 0.0f), fmaxf(s.rgb_raw[2], 0.0f), (float)s.radius, 0.0f);
+        r2 = make_float4(fmaxf(s.rgb_raw[1], 0.0f), fmaxf(s.rgb_raw[2], 0.0f), (float)s.radius,
+                         blend_box(0.5f * kLog2e * s.ca, kLog2e * s.cb, 0.5f * kLog2e * s.cc, s.o));
       }
     }
     float4* rec = a.rec + 3 * (size_t)g;
