@@ -494,7 +494,7 @@ fe_status fe_screen_grad_stats(const void* workspace, size_t workspace_bytes, in
   if (workspace_bytes < L.total) return FE_ERR_WORKSPACE;
   void* ws = const_cast<void*>(workspace);
   // psum[g][0..1] hold dL/du and dL/dv of the last fe_render_backward.
-  return cuda_status(launch_screen_stats(at<uint32_t>(ws, L.touched), at<float>(ws, L.psum), P, width, height, accum,
+  return cuda_status(launch_screen_stats(at<float4>(ws, L.rec), at<float>(ws, L.psum), P, width, height, accum,
                                          count, static_cast<cudaStream_t>(stream)));
 }
 

@@ -258,10 +258,11 @@ __global__ void reset_opacity_kernel(float* logits, int64_t P, float cap) {
     logits[i] = fminf(logits[i], cap);
 }
 
-__global__ void screen_stats_kernel(const uint32_t* __restrict__ touched, const float* __restrict__ psum, int P,
+// A Gaussian is in view when the projection wrote its record (radius > 0).
+__global__ void screen_stats_kernel(const float4* __restrict__ rec, const float* __restrict__ psum, int P,
                                     float sx, float sy, float* accum, int32_t* count) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= P || touched[g] == 0u) return;
+  if (g >= P || !(rec[3 * (size_t)g + 2].z > 0.0f)) return;
   const float du = psum[(size_t)g * 12] * sx, dv = psum[(size_t)g * 12 + 1] * sy;
   accum[g] += sqrtf(du * du + dv * dv);
   count[g] += 1;
@@ -272,10 +273,10 @@ size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 
-cudaError_t launch_screen_stats(const uint32_t* touched, const float* psum, int P, int W, int H, float* accum,
+cudaError_t launch_screen_stats(const float4* rec, const float* psum, int P, int W, int H, float* accum,
                                 int32_t* count, cudaStream_t st) {
   if (P <= 0) return cudaSuccess;
-  screen_stats_kernel<<<ceil_blocks(P, 256), 256, 0, st>>>(touched, psum, P, 0.5f * (float)W, 0.5f * (float)H,
+  screen_stats_kernel<<<ceil_blocks(P, 256), 256, 0, st>>>(rec, psum, P, 0.5f * (float)W, 0.5f * (float)H,
                                                            accum, count);
   return cudaGetLastError();
 }

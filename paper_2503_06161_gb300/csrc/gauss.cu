@@ -747,15 +747,35 @@ __global__ void __launch_bounds__(kThreads, 2) gauss_fwd_kernel(const GaussArgs 
     if (s.visible) {
       int x0, y0, x1, y1;
       if (pixel_rect(s.u, s.v, s.radius, a.W, a.H, x0, y0, x1, y1)) {
-        const int tx0 = x0 / a.tw, tx1 = x1 / a.tw, ty0 = y0 / a.th, ty1 = y1 / a.th;
-        rect = make_ushort4(tx0, ty0, tx1, ty1);
-        touched = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        // On screen: its record is written.  Its tiles are those of the
+        // pixel rect cut to the blend box (the pixels whose centres lie
+        // within the box's half-widths of the centre): outside it the
+        // Gaussian blends nowhere, so the lists lose only entries that no
+        // pixel would blend.
+        const float box = blend_box(0.5f * kLog2e * s.ca, kLog2e * s.cb, 0.5f * kLog2e * s.cc, s.o);
+        const uint32_t hb = __float_as_uint(box);
+        const __half2 h2 = *reinterpret_cast<const __half2*>(&hb);
+        const float hx = __low2float(h2), hy = __high2float(h2);
+        bool blends = hx >= 0.0f;
+        if (blends && hx < 1e30f) {
+          x0 = max(x0, (int)ceilf(s.u - hx - 0.5f));
+          x1 = min(x1, (int)floorf(s.u + hx - 0.5f));
+        }
+        if (blends && hy < 1e30f) {
+          y0 = max(y0, (int)ceilf(s.v - hy - 0.5f));
+          y1 = min(y1, (int)floorf(s.v + hy - 0.5f));
+        }
+        blends = blends && x0 <= x1 && y0 <= y1;
+        if (blends) {
+          const int tx0 = x0 / a.tw, tx1 = x1 / a.tw, ty0 = y0 / a.th, ty1 = y1 / a.th;
+          rect = make_ushort4(tx0, ty0, tx1, ty1);
+          touched = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        }
         key = __float_as_uint(s.p[2]);
         vis = true;
         r0 = make_float4(s.u, s.v, -0.5f * kLog2e * s.ca, -kLog2e * s.cb);
         r1 = make_float4(-0.5f * kLog2e * s.cc, s.o, s.p[2], fmaxf(s.rgb_raw[0], 0.0f));
-        r2 = make_float4(fmaxf(s.rgb_raw[1], 0.0f), fmaxf(s.rgb_raw[2], 0.0f), (float)s.radius,
-                         blend_box(0.5f * kLog2e * s.ca, kLog2e * s.cb, 0.5f * kLog2e * s.cc, s.o));
+        r2 = make_float4(fmaxf(s.rgb_raw[1], 0.0f), fmaxf(s.rgb_raw[2], 0.0f), (float)s.radius, box);
       }
     }
     float4* rec = a.rec + 3 * (size_t)g;

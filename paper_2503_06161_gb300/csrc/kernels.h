@@ -145,7 +145,7 @@ struct DumpArgs {
 cudaError_t launch_dump(const DumpArgs& d, cudaStream_t st);
 
 // Screen-space gradient statistics of adaptive density control (density.cu).
-cudaError_t launch_screen_stats(const uint32_t* touched, const float* psum, int P, int W, int H, float* accum,
+cudaError_t launch_screen_stats(const float4* rec, const float* psum, int P, int W, int H, float* accum,
                                 int32_t* count, cudaStream_t st);
 
 cudaError_t probe_fp32(int iters, double* flops, cudaStream_t st);

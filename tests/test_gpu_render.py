@@ -160,6 +160,11 @@ def test_needle_thin_gaussians_conic_and_radius():
 
 
 def test_tile_lists_match_oracle_rects():
+    # Each tile's list is the oracle's 3-sigma-square list in depth order,
+    # less only Gaussians that blend at no pixel centre of the tile (the
+    # projection cuts the square to the box of the alpha >= 1/255 ellipse):
+    # every Gaussian whose FP64 alpha reaches 1/255 (with 0.1% to spare) at
+    # some centre of the tile is listed, and nothing outside the square is.
     sc, cam, df = deformed_case()
     run = gpu_forward(sc, cam, df, t=0.3)
     d = run.rast.dump()
@@ -179,7 +184,9 @@ def test_tile_lists_match_oracle_rects():
     gauss = d["gauss"].cpu().numpy()
     ranges = d["ranges"].cpu().numpy()
     depth = g["depth"]
-    checked = 0
+    ca, cb, cc = g["conic"][:, 0], g["conic"][:, 1], g["conic"][:, 2]
+    op = g["opacity"]
+    checked = blending = dropped = 0
     for ty in range(ty_n):
         for tx in range(tx_n):
             t = ty * tx_n + tx
@@ -191,10 +198,23 @@ def test_tile_lists_match_oracle_rects():
             ref = sorted(np.nonzero(inside)[0].tolist(), key=lambda i: (depth[i], i))
             a = [i for i in got if not risky[i]]
             b = [i for i in ref if not risky[i]]
-            assert a == b, f"tile {t}"
+            listed = set(a)
+            assert listed <= set(b), f"tile {t}: listed outside the square"
+            assert a == [i for i in b if i in listed], f"tile {t}: order"
+            # Highest FP64 alpha over the tile's pixel centres of each square entry.
+            px, py = np.meshgrid(np.arange(x0, x1 + 1) + 0.5, np.arange(y0, y1 + 1) + 0.5)
+            for i in b:
+                dx, dy = px - u[i], py - v[i]
+                q = 0.5 * ca[i] * dx * dx + cb[i] * dx * dy + 0.5 * cc[i] * dy * dy
+                amax = op[i] * np.exp(-q.min())
+                if amax >= (1.0 + 1e-3) / 255.0:
+                    blending += 1
+                    assert i in listed, f"tile {t}: Gaussian {i} blends (alpha {amax:.4g}) but is not listed"
+            dropped += len(b) - len(a)
             assert np.all((keys[ranges[t, 0]:ranges[t, 1]] >> np.uint64(32)) == t)
             checked += len(a)
-    assert checked > 10000
+    print("listed", checked, "blending", blending, "dropped from the square", dropped)
+    assert checked > 5000 and blending > 5000
 
 
 def test_tile_shape_invariance_bitwise():
