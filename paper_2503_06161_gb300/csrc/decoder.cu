@@ -96,7 +96,15 @@ struct DecCfg {
   static constexpr uint32_t off_w = 0;
   static constexpr uint32_t off_f = off_w + w_bytes;                  // kFStages stages
   static constexpr uint32_t off_t = off_f + kFStages * f_stride;      // target boxes / S panels
-  static constexpr uint32_t off_ones = off_t + kTSlots * kBoxBytes;
+  // D <= 64: each epilogue warp stages its 32 rows x D/2 columns of dF in
+  // a swizzled box of its own (64-byte rows at D = 32, 128-byte at D = 64)
+  // and one tensor store writes it: 4 (8) whole-line writes of each row
+  // instead of one 16-byte piece of 32 rows per store instruction.  D = 128
+  // (no room) stores from registers.
+  static constexpr bool tma_df = D <= 64;
+  static constexpr uint32_t stage_warp = tma_df ? 32u * (D / 2) * 4u : 0u;
+  static constexpr uint32_t off_stage = off_t + kTSlots * kBoxBytes;
+  static constexpr uint32_t off_ones = off_stage + 8 * stage_warp;
   static constexpr uint32_t off_bias = off_ones + 512;  // one 16 x 16 all-ones operand
   static constexpr uint32_t off_bar = off_bias + kDecN * 4;
   static constexpr uint32_t bytes = off_bar + 320;
@@ -175,6 +183,18 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
+
+// Tensor store of one box from shared memory (bulk-group completion), and
+// the waits of this thread's bulk groups: until their shared-memory reads
+// are done, or until they are complete.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map),
+               "r"(smem_addr(src)), "r"(x), "r"(y)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(
@@ -280,7 +300,8 @@ __device__ __forceinline__ bool dec_spin(uint64_t* bar, uint32_t parity, volatil
 template <int D, int MODE>
 __global__ void __launch_bounds__(kDecThreads, 1)
     decoder_kernel(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_w,
-                   const __grid_constant__ CUtensorMap tm_t, const DecArgs a) {
+                   const __grid_constant__ CUtensorMap tm_t, const __grid_constant__ CUtensorMap tm_d,
+                   const DecArgs a) {
   using C = DecCfg<D>;
   constexpr bool kL1 = MODE != kDecForward;
   constexpr bool kTF32 = MODE == kDecL1F32;
@@ -478,26 +499,54 @@ __global__ void __launch_bounds__(kDecThreads, 1)
     auto store_df = [&](int j) {
       const int64_t pj = ((int64_t)blockIdx.x + (int64_t)j * gridDim.x) * kDecBM + r;
       const uint32_t col = C::col_df + (C::dfdb ? (j & 1) * D : 0);  // dF buffer of tile j
-      // This half's D/2 columns, 32 (or 16) at a time.
-#pragma unroll
-      for (int part = 0; part < (D >= 64 ? D / 64 : 1); ++part) {
+      if constexpr (C::tma_df) {
         uint32_t v[32];
-        const int c_lo = (D / 2) * h + 32 * part;  // first column of this part
-        if (D == 32) tmem_ld16(t_row + col + 16 * h, v);
+        const int c_lo = (D / 2) * h;  // first column of this half
+        if (D == 32) tmem_ld16(t_row + col + c_lo, v);
         else tmem_ld32(t_row + col + c_lo, v);
         tmem_wait_ld(v);
-        if (pj < a.HW && c_lo < a.d_real) {
-          float4* o = reinterpret_cast<float4*>(a.d_feat + pj * a.d_real + c_lo);
-          constexpr int NE = D == 32 ? 4 : 8;
+        const int64_t row0 = pj - lane;                 // first row of this warp's box
+        if (row0 < a.HW && c_lo < a.d_real) {  // else the box lies outside d_feat (warp-uniform)
+          unsigned char* stg = sm + C::off_stage + warp * C::stage_warp;
+          // This warp's previous tensor store has read the staging box.
+          if (lane == 0) bulk_wait_read();
+          __syncwarp();
+          // Row `lane` of the box, its 16-byte chunks placed as the tensor
+          // map's swizzle reads them: chunk e at e ^ ((lane / 2) mod 4) in
+          // 64-byte rows, at e ^ (lane mod 8) in 128-byte rows.
+          constexpr int NE = D / 8;
+          const int sw = D == 32 ? (lane >> 1) & 3 : lane & 7;
 #pragma unroll
-          for (int e = 0; e < NE; ++e) {
-            float4 x = make_float4(a.scale * __uint_as_float(v[4 * e]), a.scale * __uint_as_float(v[4 * e + 1]),
-                                   a.scale * __uint_as_float(v[4 * e + 2]), a.scale * __uint_as_float(v[4 * e + 3]));
-            if (a.df_add) {
-              const float4 y = o[e];
-              x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
+          for (int e = 0; e < NE; ++e)
+            *reinterpret_cast<float4*>(stg + lane * (NE * 16) + ((e ^ sw) << 4)) =
+                make_float4(a.scale * __uint_as_float(v[4 * e]), a.scale * __uint_as_float(v[4 * e + 1]),
+                            a.scale * __uint_as_float(v[4 * e + 2]), a.scale * __uint_as_float(v[4 * e + 3]));
+          fence_proxy_async();  // staging stores -> the tensor store's reads
+          __syncwarp();
+          // Rows past HW are clipped by the tensor map.
+          if (lane == 0) tma_store_2d(&tm_d, stg, c_lo, (int)row0);
+        }
+      } else {
+        // This half's D/2 columns, 32 at a time, from registers (the second
+        // launch adds to the first's dF).
+#pragma unroll
+        for (int part = 0; part < D / 64; ++part) {
+          uint32_t v[32];
+          const int c_lo = (D / 2) * h + 32 * part;  // first column of this part
+          tmem_ld32(t_row + col + c_lo, v);
+          tmem_wait_ld(v);
+          if (pj < a.HW && c_lo < a.d_real) {
+            float4* o = reinterpret_cast<float4*>(a.d_feat + pj * a.d_real + c_lo);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              float4 x = make_float4(a.scale * __uint_as_float(v[4 * e]), a.scale * __uint_as_float(v[4 * e + 1]),
+                                     a.scale * __uint_as_float(v[4 * e + 2]), a.scale * __uint_as_float(v[4 * e + 3]));
+              if (a.df_add) {
+                const float4 y = o[e];
+                x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
+              }
+              o[e] = x;
             }
-            o[e] = x;
           }
         }
       }
@@ -672,6 +721,8 @@ __global__ void __launch_bounds__(kDecThreads, 1)
         a.part_loss[blockIdx.x] = sum;
       }
     }
+    // Tensor stores of dF complete before the block leaves.
+    if (C::tma_df && kL1 && lane == 0) bulk_wait_all();
     tc_fence_before();
   }
   __syncthreads();
@@ -785,13 +836,13 @@ cudaError_t launch_pdl(void (*k)(Params...), int grid, int block, size_t smem, c
 }
 
 template <int D, int MODE>
-cudaError_t launch_dec(const CUtensorMap& mf, const CUtensorMap& mw, const CUtensorMap& mt, const DecArgs& a, int grid,
-                       cudaStream_t st) {
+cudaError_t launch_dec(const CUtensorMap& mf, const CUtensorMap& mw, const CUtensorMap& mt, const CUtensorMap& md,
+                       const DecArgs& a, int grid, cudaStream_t st) {
   auto k = decoder_kernel<D, MODE>;
   const size_t smem = DecCfg<D>::launch_bytes;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return launch_pdl(k, grid, kDecThreads, smem, st, mf, mw, mt, a);
+  return launch_pdl(k, grid, kDecThreads, smem, st, mf, mw, mt, md, a);
 }
 
 // Workspace: 256-byte header (error bits), then per-CTA partial loss, dW, db.
@@ -830,12 +881,12 @@ fe_status dec_check(const fe_decoder_args* a) {
 }
 
 template <int MODE>
-cudaError_t dispatch(int D, const CUtensorMap& mf, const CUtensorMap& mw, const CUtensorMap& mt, const DecArgs& a,
-                     int grid, cudaStream_t st) {
+cudaError_t dispatch(int D, const CUtensorMap& mf, const CUtensorMap& mw, const CUtensorMap& mt, const CUtensorMap& md,
+                     const DecArgs& a, int grid, cudaStream_t st) {
   switch (D) {
-    case 32: return launch_dec<32, MODE>(mf, mw, mt, a, grid, st);
-    case 64: return launch_dec<64, MODE>(mf, mw, mt, a, grid, st);
-    case 128: return launch_dec<128, MODE>(mf, mw, mt, a, grid, st);
+    case 32: return launch_dec<32, MODE>(mf, mw, mt, md, a, grid, st);
+    case 64: return launch_dec<64, MODE>(mf, mw, mt, md, a, grid, st);
+    case 128: return launch_dec<128, MODE>(mf, mw, mt, md, a, grid, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -886,7 +937,7 @@ fe_status fe_decode_forward(const fe_decoder_args* a, float* out, void* workspac
   d.err = static_cast<uint32_t*>(workspace);
   for (int pass = 0; pass < dec_passes(DW); ++pass) {
     d.c0 = 128 * pass;
-    if (dispatch<kDecForward>(DW, mf, mw, mw, d, L.ncta, st) != cudaSuccess) return FE_ERR_CUDA;
+    if (dispatch<kDecForward>(DW, mf, mw, mw, mw, d, L.ncta, st) != cudaSuccess) return FE_ERR_CUDA;
   }
   return FE_OK;
 }
@@ -911,11 +962,17 @@ fe_status fe_decode_l1(const fe_decoder_args* a, const void* target, int target_
       return FE_ERR_CUDA;
     return FE_OK;
   }
-  CUtensorMap mf, mw, mt;
+  CUtensorMap mf, mw, mt, md;
   const bool tb = target_bf16 != 0;
   if (!dec_maps(a, DW, &mf, &mw) ||
       !make_map(&mt, tb ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, tb ? 2 : 4, target,
                 kDecN, a->HW, tb ? 64 : 32, kDecBM, CU_TENSOR_MAP_SWIZZLE_128B))
+    return FE_ERR_CUDA;
+  // d_feat in boxes of 32 rows x DW/2 channels: the dF a warp stages at
+  // D <= 64 (D = 128 stores from registers and reads no map).
+  md = mw;
+  if (DW <= 64 && !make_map(&md, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d_feat, a->D, a->HW, DW / 2, 32,
+                            DW == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B))
     return FE_ERR_CUDA;
   DecArgs d{};
   d.HW = a->HW;
@@ -936,8 +993,8 @@ fe_status fe_decode_l1(const fe_decoder_args* a, const void* target, int target_
     dp.c0 = 128 * pass;
     dp.df_add = pass > 0 ? 1 : 0;
     dp.part_loss = d.part_loss + (size_t)pass * L.ncta;
-    const cudaError_t e = tb ? dispatch<kDecL1Bf16>(DW, mf, mw, mt, dp, L.ncta, st)
-                             : dispatch<kDecL1F32>(DW, mf, mw, mt, dp, L.ncta, st);
+    const cudaError_t e = tb ? dispatch<kDecL1Bf16>(DW, mf, mw, mt, md, dp, L.ncta, st)
+                             : dispatch<kDecL1F32>(DW, mf, mw, mt, md, dp, L.ncta, st);
     if (e != cudaSuccess) return FE_ERR_CUDA;
   }
   const int n = kDecN * a->D + kDecN + 1;
