@@ -147,25 +147,36 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint32_t* __re
     bcount += c;
   }
   // Publish the aggregate, look back for the exclusive prefix of this digit.
+  // Predecessors are read four at a time (independent loads, overlapping
+  // latencies), then taken in order until the first inclusive prefix.
   uint32_t excl = 0;
   if (b == 0) {
     st_vol(status + tid, kFlagPre | bcount);
   } else {
     st_vol(status + (size_t)b * 256 + tid, kFlagAgg | bcount);
-    for (int64_t j = (int64_t)b - 1; j >= 0; --j) {
-      uint32_t s = ld_vol(status + (size_t)j * 256 + tid);
-      int spins = 0;
-      while ((s & ~kValMask) == 0u) {
-        if (++spins > kSpinLimit) {
-          set_err(err, kErrTimeout);
-          s = kFlagPre;
-          break;
+    bool fin = false;
+    for (int64_t j = (int64_t)b - 1; !fin && j >= 0; j -= 4) {
+      uint32_t sv[4];
+#pragma unroll
+      for (int w = 0; w < 4; ++w) sv[w] = j - w >= 0 ? ld_vol(status + (size_t)(j - w) * 256 + tid) : 0u;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        if (!fin && j - w >= 0) {
+          uint32_t s = sv[w];
+          int spins = 0;
+          while ((s & ~kValMask) == 0u) {
+            if (++spins > kSpinLimit) {
+              set_err(err, kErrTimeout);
+              s = kFlagPre;
+              break;
+            }
+            __nanosleep(32);
+            s = ld_vol(status + (size_t)(j - w) * 256 + tid);
+          }
+          excl += s & kValMask;
+          if (s & kFlagPre) fin = true;
         }
-        __nanosleep(32);
-        s = ld_vol(status + (size_t)j * 256 + tid);
       }
-      excl += s & kValMask;
-      if (s & kFlagPre) break;
     }
     st_vol(status + (size_t)b * 256 + tid, kFlagPre | ((excl + bcount) & kValMask));
   }
@@ -195,7 +206,8 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint32_t* __re
 
 // ---------------------------------------------------------------------------
 // Decoupled look-back over a 64-bit running total: block b publishes its
-// aggregate, then sums its predecessors back to the first inclusive prefix.
+// aggregate, then sums its predecessors back to the first inclusive prefix,
+// reading them eight at a time.
 __device__ __forceinline__ uint64_t lookback64(uint64_t* status, uint32_t b, uint64_t aggregate, uint32_t* err) {
   if (b == 0) {
     st_vol64(status, kFlagPre64 | aggregate);
@@ -203,20 +215,29 @@ __device__ __forceinline__ uint64_t lookback64(uint64_t* status, uint32_t b, uin
   }
   st_vol64(status + b, kFlagAgg64 | aggregate);
   uint64_t excl = 0;
-  for (int64_t j = (int64_t)b - 1; j >= 0; --j) {
-    uint64_t s = ld_vol64(status + j);
-    int spins = 0;
-    while ((s & ~kValMask64) == 0ull) {
-      if (++spins > kSpinLimit) {
-        set_err(err, kErrTimeout);
-        s = kFlagPre64;
-        break;
+  bool fin = false;
+  for (int64_t j = (int64_t)b - 1; !fin && j >= 0; j -= 8) {
+    uint64_t sv[8];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sv[w] = j - w >= 0 ? ld_vol64(status + (j - w)) : 0ull;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      if (!fin && j - w >= 0) {
+        uint64_t s = sv[w];
+        int spins = 0;
+        while ((s & ~kValMask64) == 0ull) {
+          if (++spins > kSpinLimit) {
+            set_err(err, kErrTimeout);
+            s = kFlagPre64;
+            break;
+          }
+          __nanosleep(32);
+          s = ld_vol64(status + (j - w));
+        }
+        excl += s & kValMask64;
+        if (s & kFlagPre64) fin = true;
       }
-      __nanosleep(32);
-      s = ld_vol64(status + j);
     }
-    excl += s & kValMask64;
-    if (s & kFlagPre64) break;
   }
   st_vol64(status + b, kFlagPre64 | (excl + aggregate));
   return excl;
@@ -243,6 +264,7 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const CountArgs a) 
   __shared__ uint32_t s_ticket;
   __shared__ uint64_t s_prefix;
   __shared__ uint32_t s_c[kBinChunk];
+  __shared__ float s_iw[kBinChunk];  // 1 / (rect width in tiles), once per Gaussian
   __shared__ ushort4 s_rect[kBinChunk];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < a.ntiles; i += kThreads) s_cnt[i] = 0;
@@ -260,7 +282,9 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const CountArgs a) 
     gid[i] = r < a.P ? a.order[r] : 0u;
     cnt[i] = r < a.P ? a.touched[gid[i]] : 0u;
     s_c[li] = cnt[i];
-    s_rect[li] = cnt[i] ? a.rect[gid[i]] : make_ushort4(1, 1, 0, 0);
+    const ushort4 rc = cnt[i] ? a.rect[gid[i]] : make_ushort4(0, 0, 0, 0);
+    s_rect[li] = rc;
+    s_iw[li] = 1.0f / (float)(rc.z - rc.x + 1u);
     tsum += cnt[i];
   }
   uint32_t btot;
@@ -291,7 +315,7 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const CountArgs a) 
     if (!c) continue;
     const ushort4 rc = s_rect[i];
     const uint32_t wdt = rc.z - rc.x + 1u;
-    const float iw = 1.0f / (float)wdt;
+    const float iw = s_iw[i];
     for (uint32_t k = lane; k < c; k += 32) {
       const uint32_t dy = (uint32_t)(((float)k + 0.5f) * iw), dx = k - dy * wdt;  // exact for these sizes
       atomicAdd(&s_cnt[(rc.y + dy) * (uint32_t)a.tiles_x + rc.x + dx], 1u);
@@ -353,6 +377,7 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(const ScatterArgs
   uint32_t* s_base = s_dyn;                                        // [ntiles]
   uint16_t* s_wc = reinterpret_cast<uint16_t*>(s_dyn + a.ntiles);  // [8][ntiles]
   __shared__ uint32_t s_gid[kBinChunk], s_cnt[kBinChunk], s_off[kBinChunk];
+  __shared__ float s_iw[kBinChunk];  // 1 / (rect width in tiles), once per Gaussian
   __shared__ ushort4 s_rect[kBinChunk];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = blockIdx.x;
@@ -379,7 +404,9 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(const ScatterArgs
     s_gid[i] = g;
     s_cnt[i] = c;
     s_off[i] = a.offs[start + i];
-    s_rect[i] = c ? a.rect[g] : make_ushort4(1, 1, 0, 0);
+    const ushort4 rc = c ? a.rect[g] : make_ushort4(0, 0, 0, 0);
+    s_rect[i] = rc;
+    s_iw[i] = 1.0f / (float)(rc.z - rc.x + 1u);
   }
   __syncthreads();
   uint16_t* wc = s_wc + (size_t)warp * a.ntiles;
@@ -389,7 +416,7 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(const ScatterArgs
     if (!c) continue;
     const ushort4 rc = s_rect[i];
     const uint32_t wdt = rc.z - rc.x + 1u;
-    const float iw = 1.0f / (float)wdt;
+    const float iw = s_iw[i];
     for (uint32_t k = lane; k < c; k += 32) {
       const uint32_t dy = (uint32_t)(((float)k + 0.5f) * iw), dx = k - dy * wdt;  // exact for k < 2^20
       const uint32_t tile = (rc.y + dy) * (uint32_t)a.tiles_x + rc.x + dx;
@@ -413,7 +440,7 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(const ScatterArgs
     if (!c) continue;
     const ushort4 rc = s_rect[i];
     const uint32_t wdt = rc.z - rc.x + 1u;
-    const float iw = 1.0f / (float)wdt;
+    const float iw = s_iw[i];
     const uint32_t g = s_gid[i], e0 = s_off[i];
     for (uint32_t k = lane; k < c; k += 32) {
       const uint32_t dy = (uint32_t)(((float)k + 0.5f) * iw), dx = k - dy * wdt;
