@@ -340,7 +340,7 @@ __device__ __forceinline__ void stage_init(uint64_t* s_bar) {
 
 // One block per tile.
 template <int D, int B, bool kCount>
-__global__ void __launch_bounds__(kThreads, D <= 32 ? 3 : 1) composite_fwd_kernel(const CompositeArgs a) {
+__global__ void __launch_bounds__(kThreads, D <= 32 ? 3 : (D <= 64 ? 2 : 1)) composite_fwd_kernel(const CompositeArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ int s_abort[2];
@@ -362,7 +362,7 @@ __device__ __forceinline__ int batch_view(const BatchCompositeArgs& ba, int item
 // items from a device counter until the batch is exhausted (no block waits
 // for another: items are independent).
 template <int D, int B>
-__global__ void __launch_bounds__(kThreads, D <= 32 ? 3 : 1)
+__global__ void __launch_bounds__(kThreads, D <= 32 ? 3 : (D <= 64 ? 2 : 1))
     composite_fwd_batch_kernel(const __grid_constant__ BatchCompositeArgs ba) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_bar[2];
