@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfe4dgs.so")
-SOURCES = ["api.cu", "gauss.cu", "binning.cu", "composite.cu", "loss.cu", "decoder.cu", "optim.cu", "fst.cu", "density.cu"]
-HEADERS = ["common.cuh", "kernels.h"]
+SOURCES = ["api.cu", "gauss.cu", "binning.cu", "composite.cu", "loss.cu", "decoder.cu", "optim.cu", "fst.cu", "density.cu", "deform_mlp.cu"]
+HEADERS = ["common.cuh", "kernels.h", "tc.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -109,7 +109,8 @@ fe_status fill_gauss_args(const fe_gaussians* g, const fe_deform* df, const fe_c
   a.dkey = at<uint32_t>(ws, L.dkey[0]);
   a.err = &hdr->err;
   a.num_visible = &hdr->num_visible;
-  if (L.with_backward) a.dstate = at<float>(ws, L.dstate);
+  a.dstate = at<float>(ws, L.dstate);
+  a.fsplit = at<uint16_t>(ws, L.fsplit);
   return FE_OK;
 }
 

@@ -107,7 +107,7 @@ struct Layout {
   int64_t cap;
   bool with_backward;
   size_t hdr, rec, rect, touched, dkey[2], dval[2], offs, offs_by_gid, sorted, table;
-  size_t status, hist, ranges, tfinal, ncontrib, partials, pflags, cmask, dstate, ddstate, psum;
+  size_t status, hist, ranges, tfinal, ncontrib, partials, pflags, cmask, dstate, fsplit, ddstate, psum;
   size_t status_words, table_blocks;
   size_t total;
 };
@@ -151,13 +151,17 @@ inline Layout make_layout(int P, int D, int W, int H, int tw, int th, int64_t ca
   L.ranges = take((size_t)L.ntiles * 8);
   L.tfinal = take((size_t)W * H * 4);
   L.ncontrib = take((size_t)W * H * 4);
+  // Deformation state (offsets + MLP unit masks) and the HexPlane features
+  // as three BF16 terms (up to 64 channels) for the tensor-core MLP, with
+  // 128 rows of slack so a 128-row tile of any term stays in the region.
+  L.dstate = take(Pn * 16 * 4);
+  L.fsplit = take((Pn + 128) * 3 * 64 * 2);
   if (with_backward) {
     L.partials = take(Kn * (size_t)partial_stride(D) * 4);
     L.pflags = take((Kn + 31) / 32 * 4);
     // Per (tile, 32-entry group, warp): which entries blended in some pixel
     // of the warp; tile t's groups start at slot rg.x / 32 + t.
     L.cmask = take(((Kn + 31) / 32 + (size_t)L.ntiles + 1) * 8 * 4);
-    L.dstate = take(Pn * 16 * 4);
     L.ddstate = take(Pn * 12 * 4);
     L.psum = take(Pn * 12 * 4);
   }

@@ -1,12 +1,17 @@
 // Per-Gaussian kernels of the FE-4DGS pass (one thread per Gaussian):
-//   gauss_fwd: FST deformation query (Sec. 3.2, Eq. 4-6; Appendix A), EWA
-//              projection (Sec. 3.3), SH colour (Sec. 3.1), tile rect and
-//              depth key.  Writes the 48-byte render record.
+//   hexplane_split: HexPlane sample of the FST deformation query (Sec. 3.2,
+//              Eq. 5-6), written as three BF16 terms for the MLP (Eq. 4),
+//              which runs on the tensor cores (deform_mlp.cu);
+//   gauss_fwd: the offsets applied, EWA projection (Sec. 3.3), SH colour
+//              (Sec. 3.1), tile rect and depth key.  Writes the 48-byte
+//              render record.
 //   gauss_bwd: fixed-order sum of the per-(tile, Gaussian) partials, then
 //              the reverse of projection, colour, activations and the
-//              deformation query back to the canonical parameters.
-// The MLP weights sit in shared memory (uniform broadcast reads); each
-// thread keeps its 32/64-wide HexPlane feature and hidden layer in registers.
+//              deformation query back to the canonical parameters (the MLP
+//              reverse from the forward's unit masks, weights in shared
+//              memory as uniform broadcast reads).
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -252,86 +257,6 @@ __device__ __forceinline__ void load_mlp(const GaussArgs& a, float* sw) {
     sw[L::kWht + i * 12 + 11] = 0.0f;
   }
   if (threadIdx.x < 12) sw[L::kBh + threadIdx.x] = threadIdx.x < kHeads ? a.bh[threadIdx.x] : 0.0f;
-}
-
-// h2pre = W2 relu(W1 f + b1) + b2, streamed over the first-layer units so
-// only f and the 64 second-layer accumulators live in registers; m1 gets
-// bit i set where first-layer unit i is active.
-// Packed FP32 FMAs throughout: the first-layer dot keeps even and odd
-// channels in the two halves of a pair (two independent chains), the
-// second-layer accumulators are output pairs.
-template <int C>
-__device__ __forceinline__ void mlp_hidden2(const float* sw, const float f[C], float h2[kHidden], uint64_t& m1) {
-  using L = Mlp<C>;
-  float2 h2p[kHidden / 2];
-#pragma unroll
-  for (int o = 0; o < kHidden / 2; ++o) h2p[o] = make_float2(sw[L::kB2 + 2 * o], sw[L::kB2 + 2 * o + 1]);
-  m1 = 0;
-  // First-layer units G at a time: their dots are independent chains
-  // (each unit's own sequence of FMAs is unchanged), then the second-layer
-  // updates in unit order.  (C = 64 keeps one unit: more would spill.)
-  constexpr int G = C <= 32 ? 4 : 1;
-#pragma unroll 1
-  for (int o0 = 0; o0 < kHidden; o0 += G) {
-    float2 acc2[G];
-#pragma unroll
-    for (int u = 0; u < G; ++u) acc2[u] = make_float2(sw[L::kB1 + o0 + u], 0.0f);
-#pragma unroll
-    for (int c4 = 0; c4 < C / 4; ++c4) {
-#pragma unroll
-      for (int u = 0; u < G; ++u) {
-        const float4 w = reinterpret_cast<const float4*>(sw + L::kW1 + (o0 + u) * C)[c4];
-        acc2[u] = __ffma2_rn(make_float2(w.x, w.y), make_float2(f[4 * c4], f[4 * c4 + 1]), acc2[u]);
-        acc2[u] = __ffma2_rn(make_float2(w.z, w.w), make_float2(f[4 * c4 + 2], f[4 * c4 + 3]), acc2[u]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < G; ++u) {
-      const float acc = acc2[u].x + acc2[u].y;
-      m1 |= (uint64_t)(acc > 0.0f) << (o0 + u);
-      const float h = fmaxf(acc, 0.0f);
-      const float2 hh = make_float2(h, h);
-      const float4* w2r = reinterpret_cast<const float4*>(sw + L::kW2t + (o0 + u) * kHidden);
-#pragma unroll
-      for (int o4 = 0; o4 < kHidden / 4; ++o4) {
-        const float4 w = w2r[o4];
-        h2p[2 * o4] = __ffma2_rn(make_float2(w.x, w.y), hh, h2p[2 * o4]);
-        h2p[2 * o4 + 1] = __ffma2_rn(make_float2(w.z, w.w), hh, h2p[2 * o4 + 1]);
-      }
-    }
-  }
-#pragma unroll
-  for (int o = 0; o < kHidden / 2; ++o) {
-    h2[2 * o] = h2p[o].x;
-    h2[2 * o + 1] = h2p[o].y;
-  }
-}
-
-// delta = Wh relu(h2pre) + bh; m1 / m2: active units of the two layers.
-template <int C>
-__device__ __forceinline__ void mlp_forward(const float* sw, const float f[C], float delta[kHeads], uint64_t& m1,
-                                            uint64_t& m2) {
-  using L = Mlp<C>;
-  float h2[kHidden];
-  mlp_hidden2<C>(sw, f, h2, m1);
-  m2 = 0;
-#pragma unroll
-  for (int o = 0; o < kHidden; ++o) {
-    m2 |= (uint64_t)(h2[o] > 0.0f) << o;
-    h2[o] = fmaxf(h2[o], 0.0f);
-  }
-#pragma unroll
-  for (int k = 0; k < kHeads; ++k) {
-    const float4* wr = reinterpret_cast<const float4*>(sw + L::kWh + k * kHidden);
-    float2 acc2 = make_float2(sw[L::kBh + k], 0.0f);
-#pragma unroll
-    for (int o4 = 0; o4 < kHidden / 4; ++o4) {
-      const float4 w = wr[o4];
-      acc2 = __ffma2_rn(make_float2(w.x, w.y), make_float2(h2[4 * o4], h2[4 * o4 + 1]), acc2);
-      acc2 = __ffma2_rn(make_float2(w.z, w.w), make_float2(h2[4 * o4 + 2], h2[4 * o4 + 3]), acc2);
-    }
-    delta[k] = acc2.x + acc2.y;
-  }
 }
 
 // df = (d delta / d f)^T dd from the forward's unit masks: no activation is
@@ -694,48 +619,74 @@ __device__ __forceinline__ void project(const GaussArgs& a, int g, const float d
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Deformation offsets of Gaussian g (zero for a static scene).  When
-// dstate is given, the reverse pass's state is stored there: the offsets
-// (11 floats) and the two MLP unit masks (words 12..15).
+// HexPlane feature of every Gaussian for the tensor-core MLP: f (Eq. 4-6)
+// split into three BF16 terms f = hi + mid + lo, each the BF16 rounding of
+// what the previous terms leave, written as three [P][C] arrays (term t at
+// fsplit + t P C).
 template <int C>
-__device__ __forceinline__ void deform_delta(const GaussArgs& a, const float* sw, float* sfw, int g, bool active,
-                                             float delta[kHeads], float* dstate) {
-#pragma unroll
-  for (int k = 0; k < kHeads; ++k) delta[k] = 0.0f;
-  if (!a.has_deform) return;  // uniform over the launch
+__global__ void __launch_bounds__(kThreads) hexplane_split_kernel(const GaussArgs a) {
+  extern __shared__ __align__(16) float s_slices[];
+  float* sfw = s_slices + (threadIdx.x >> 5) * 32 * (C + 1);  // this warp's transpose slice
+  const int g = blockIdx.x * kThreads + threadIdx.x;
+  const bool active = g < a.P;
   float mu[3] = {0.f, 0.f, 0.f};
   if (active) { mu[0] = a.means[3 * g]; mu[1] = a.means[3 * g + 1]; mu[2] = a.means[3 * g + 2]; }
   float f[C];
   hexplane_sample_warp<C>(a, mu, active, sfw, f);
   if (!active) return;
-  uint64_t m1, m2;
-  mlp_forward<C>(sw, f, delta, m1, m2);
+  auto pack = [](float x, float y) -> uint32_t {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(x, y);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  };
+  const size_t term = (size_t)a.P * C;
+  uint4* hi = reinterpret_cast<uint4*>(a.fsplit + (size_t)g * C);
+  uint4* mid = reinterpret_cast<uint4*>(a.fsplit + term + (size_t)g * C);
+  uint4* lo = reinterpret_cast<uint4*>(a.fsplit + 2 * term + (size_t)g * C);
+#pragma unroll
+  for (int c8 = 0; c8 < C / 8; ++c8) {
+    uint32_t h[4], m[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float x = f[8 * c8 + 2 * i], y = f[8 * c8 + 2 * i + 1];
+      h[i] = pack(x, y);
+      x -= __uint_as_float(h[i] << 16);
+      y -= __uint_as_float(h[i] & 0xFFFF0000u);
+      m[i] = pack(x, y);
+      x -= __uint_as_float(m[i] << 16);
+      y -= __uint_as_float(m[i] & 0xFFFF0000u);
+      l[i] = pack(x, y);
+    }
+    hi[c8] = make_uint4(h[0], h[1], h[2], h[3]);
+    mid[c8] = make_uint4(m[0], m[1], m[2], m[3]);
+    lo[c8] = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// Deformation offsets of Gaussian g (zero for a static scene): the MLP's
+// output in dstate, plus the optional positional noise, which is stored
+// back so that the reverse pass sees the offsets that were applied.
+__device__ __forceinline__ void deform_delta(const GaussArgs& a, int g, float delta[kHeads]) {
+#pragma unroll
+  for (int k = 0; k < kHeads; ++k) delta[k] = 0.0f;
+  if (!a.has_deform) return;  // uniform over the launch
+  float4* d = reinterpret_cast<float4*>(a.dstate + (size_t)g * kDStride);
+  const float4 q0 = d[0], q1 = d[1], q2 = d[2];
+  delta[0] = q0.x; delta[1] = q0.y; delta[2] = q0.z; delta[3] = q0.w; delta[4] = q1.x; delta[5] = q1.y;
+  delta[6] = q1.z; delta[7] = q1.w; delta[8] = q2.x; delta[9] = q2.y; delta[10] = q2.z;
   if (a.noise) {
     const float nt = a.noise_scale * a.t;
 #pragma unroll
     for (int k = 0; k < 3; ++k) delta[k] = fmaf(nt, a.noise[3 * g + k], delta[k]);
-  }
-  if (dstate) {
-    float4* d = reinterpret_cast<float4*>(dstate);
     d[0] = make_float4(delta[0], delta[1], delta[2], delta[3]);
-    d[1] = make_float4(delta[4], delta[5], delta[6], delta[7]);
-    d[2] = make_float4(delta[8], delta[9], delta[10], 0.0f);
-    reinterpret_cast<uint4*>(dstate)[3] = make_uint4((uint32_t)m1, (uint32_t)(m1 >> 32), (uint32_t)m2,
-                                                     (uint32_t)(m2 >> 32));
   }
 }
 
-template <int C>
 __global__ void __launch_bounds__(kThreads, 2) gauss_fwd_kernel(const GaussArgs a) {
-  extern __shared__ __align__(16) float sw[];
-  float* sfw = sw + mlp_floats<C>() + (threadIdx.x >> 5) * 32 * (C + 1);  // this warp's transpose slice
-  if (a.has_deform) load_mlp<C>(a, sw);
-  __syncthreads();
   const int g = blockIdx.x * kThreads + threadIdx.x;
   bool vis = false;
-  float delta[kHeads];
-  deform_delta<C>(a, sw, sfw, g, g < a.P, delta, (a.dstate && g < a.P) ? a.dstate + (size_t)g * kDStride : nullptr);
   if (g < a.P) {
+    float delta[kHeads];
+    deform_delta(a, g, delta);
     float sh[48];
     load_sh(a.sh, a.sh_bf16, g, sh);
     Proj s;
@@ -1133,21 +1084,26 @@ __global__ void __launch_bounds__(kThreads, 2) gauss_bwd_deform_kernel(const Gau
 // Launchers
 // ---------------------------------------------------------------------------
 template <int C>
-static cudaError_t launch_fwd_t(const GaussArgs& a, cudaStream_t st) {
-  const size_t full = (mlp_floats<C>() + (size_t)8 * 32 * (C + 1)) * sizeof(float);
-  const size_t smem = a.has_deform ? full : 0;
-  auto k = gauss_fwd_kernel<C>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
+static cudaError_t launch_split_t(const GaussArgs& a, cudaStream_t st) {
+  const size_t smem = (size_t)8 * 32 * (C + 1) * sizeof(float);  // 66.5 KB at C = 64
+  auto k = hexplane_split_kernel<C>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   k<<<ceil_div(a.P, kThreads), kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
+// Deformed scenes: HexPlane features (split), the MLP on the tensor cores,
+// then the projection; static scenes: the projection alone.
 cudaError_t launch_gauss_fwd(const GaussArgs& a, cudaStream_t st) {
   if (a.P <= 0) return cudaSuccess;
-  const int C = a.has_deform ? a.C : 32;
-  if (C == 32) return launch_fwd_t<32>(a, st);
-  if (C == 64) return launch_fwd_t<64>(a, st);
-  return cudaErrorInvalidValue;
+  if (a.has_deform) {
+    cudaError_t e = a.C == 32 ? launch_split_t<32>(a, st) : (a.C == 64 ? launch_split_t<64>(a, st) : cudaErrorInvalidValue);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_deform_mlp(a, st)) != cudaSuccess) return e;
+  }
+  gauss_fwd_kernel<<<ceil_div(a.P, kThreads), kThreads, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 template <int C>

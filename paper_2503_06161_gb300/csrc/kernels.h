@@ -23,9 +23,11 @@ struct GaussArgs {
   float fx, fy, cx, cy, znear, limx, limy;
   float V[12];
   float campos[3];
-  // state kept for the reverse pass (NULL when the workspace has none):
-  // [P][kDStride] deformation offsets and MLP unit masks
+  // [P][kDStride] deformation offsets and MLP unit masks (written by the
+  // MLP kernel, read by the projection and the reverse pass)
   float* dstate;
+  // three [P][C] BF16 arrays: the HexPlane features split hi + mid + lo
+  uint16_t* fsplit;
   // outputs
   float4* rec;
   ushort4* rect;
@@ -48,6 +50,8 @@ struct GaussBwdArgs {
 };
 
 cudaError_t launch_gauss_fwd(const GaussArgs& a, cudaStream_t st);
+// Deformation MLP on the tensor cores: a.fsplit -> a.dstate (deform_mlp.cu).
+cudaError_t launch_deform_mlp(const GaussArgs& a, cudaStream_t st);
 cudaError_t launch_gauss_bwd(const GaussArgs& a, const GaussBwdArgs& b, cudaStream_t st, cudaEvent_t mid);
 
 // Integer stage: binning of projected Gaussians into tile lists.
