@@ -146,25 +146,27 @@ __global__ void __launch_bounds__(kMlpThreads, 2)
   if (warp < kMlpEpiWarps) {
     // Weights as three BF16 terms in the operand layouts, one 16-byte chunk
     // (8 consecutive inputs of one output row) at a time; bias in FP32.
+    // All of a thread's loads are issued before its first split.
     constexpr int n1 = kHidden * C / 8, n2 = kHidden * 64 / 8, nh = 16 * 64 / 8;
-    for (int q = tid; q < n1 + n2 + nh; q += 32 * kMlpEpiWarps) {
-      float x[8];
-      if (q < n1) {
-        const int r = q / (C / 8), c = q % (C / 8);
+    constexpr int kPer = (n1 + n2 + nh + 32 * kMlpEpiWarps - 1) / (32 * kMlpEpiWarps);
+    float xs[kPer][8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = a.w1[r * C + 8 * c + i];
-        store_split8(sm + K::off_w1, K::w1_term, chunk_off(r, c, K::row1), x);
-      } else if (q < n1 + n2) {
-        const int r = (q - n1) / 8, c = (q - n1) % 8;  // W2[r][in]: output r, inputs 8c..8c+7
+    for (int j = 0; j < kPer; ++j) {
+      const int q = tid + j * 32 * kMlpEpiWarps;
+      const float* src = nullptr;
+      if (q < n1) src = a.w1 + (q / (C / 8)) * C + 8 * (q % (C / 8));
+      else if (q < n1 + n2) src = a.w2 + ((q - n1) / 8) * kHidden + 8 * ((q - n1) % 8);  // W2[out][in]
+      else if (q < n1 + n2 + nh && (q - n1 - n2) / 8 < kHeads) src = a.wh + ((q - n1 - n2) / 8) * kHidden + 8 * ((q - n1 - n2) % 8);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = a.w2[r * kHidden + 8 * c + i];
-        store_split8(sm + K::off_w2, K::w2_term, chunk_off(r, c, 128), x);
-      } else {
-        const int r = (q - n1 - n2) / 8, c = (q - n1 - n2) % 8;  // rows 11-15 zero
+      for (int i = 0; i < 8; ++i) xs[j][i] = src ? __ldg(src + i) : 0.0f;  // Wh rows 11-15: zero
+    }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = r < kHeads ? a.wh[r * kHidden + 8 * c + i] : 0.0f;
-        store_split8(sm + K::off_wh, K::wh_term, chunk_off(r, c, 128), x);
-      }
+    for (int j = 0; j < kPer; ++j) {
+      const int q = tid + j * 32 * kMlpEpiWarps;
+      if (q < n1) store_split8(sm + K::off_w1, K::w1_term, chunk_off(q / (C / 8), q % (C / 8), K::row1), xs[j]);
+      else if (q < n1 + n2) store_split8(sm + K::off_w2, K::w2_term, chunk_off((q - n1) / 8, (q - n1) % 8, 128), xs[j]);
+      else if (q < n1 + n2 + nh)
+        store_split8(sm + K::off_wh, K::wh_term, chunk_off((q - n1 - n2) / 8, (q - n1 - n2) % 8, 128), xs[j]);
     }
     for (int i = tid; i < 144; i += 32 * kMlpEpiWarps)
       s_bias[i] = i < 64 ? a.b1[i] : (i < 128 ? a.b2[i - 64] : (i - 128 < kHeads ? a.bh[i - 128] : 0.0f));
