@@ -309,6 +309,253 @@ __global__ void __launch_bounds__(kMlpThreads, 2)
   }
 }
 
+// Reverse of the MLP for the mean gradient (the offsets' gradient dd, 11
+// values, back to the HexPlane feature): with the forward's unit masks m1,
+// m2,
+//   g2 = m2 . (Wh^T dd),  d1 = m1 . (W2^T g2),  df = W1^T d1,
+// as three tensor-core layers of the same three-term form (K = 16 padded to
+// 32, then 64 and 64; N = 64, 64 and C).  The epilogue warps write each
+// tile's dd terms themselves (no TMA) and apply the masks between layers;
+// df goes to a [P][C] FP32 array for the HexPlane reverse.
+struct MlpBwdArgs {
+  int P, ntiles;
+  const float *w1, *w2, *wh;
+  const float* ddstate;  // [P][12]: dd (11), active flag
+  const float* dstate;   // [P][kDStride]: the masks in words 12-15
+  float* df;             // [P][C]
+  uint32_t* err;
+};
+
+template <int C>
+struct MlpBwdCfg {
+  static constexpr uint32_t b1_term = kHidden * 64;   // Wh^T [64][32] (K padded to 32: 64-byte rows)
+  static constexpr uint32_t b2_term = kHidden * 128;  // W2^T [64][64]
+  static constexpr uint32_t b3_term = C * 128;        // W1^T [C][64]
+  static constexpr uint32_t a_term = kMlpBM * 128;
+  static constexpr uint32_t off_b1 = 0;
+  static constexpr uint32_t off_b2 = off_b1 + kNTerms * b1_term;
+  static constexpr uint32_t off_b3 = off_b2 + kNTerms * b2_term;
+  static constexpr uint32_t off_a = off_b3 + kNTerms * b3_term;
+  static constexpr uint32_t off_bar = off_a + kNTerms * a_term;
+  static constexpr uint32_t bytes = off_bar + 128;
+  static constexpr size_t launch_bytes = bytes + 1024;
+  static_assert(off_b2 % 1024 == 0 && off_b3 % 1024 == 0 && off_a % 1024 == 0, "1024-byte aligned operands");
+  static_assert(2 * (launch_bytes + 1024) <= 233472, "two CTAs per SM");
+};
+
+enum : int { kBwA0 = 0, kBwD1, kBwA2, kBwD2, kBwA3, kBwD3, kBwDrain, kBwBars };
+constexpr int kMlpBwdThreads = 32 * 5;  // 4 epilogue warps + the MMA warp
+
+template <int C>
+__global__ void __launch_bounds__(kMlpBwdThreads, 2) deform_mlp_bwd_kernel(const MlpBwdArgs a) {
+  using K = MlpBwdCfg<C>;
+  extern __shared__ unsigned char dsmem_raw[];
+  const uint32_t raw_addr = smem_addr(dsmem_raw);
+  unsigned char* sm = dsmem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
+  const uint32_t sb = smem_addr(sm);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + K::off_bar);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + K::off_bar + kBwBars * 8);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(sm + K::off_bar + kBwBars * 8 + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_mine = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (tid == 0) {
+    for (int i = 0; i < kBwBars; ++i) mbar_init(&bars[i], (i == kBwA0 || i == kBwA2 || i == kBwA3) ? kMlpEpiWarps : 1);
+    *s_abort = 0;
+    mbar_init_fence();
+  }
+  if (warp < kMlpEpiWarps) {
+    // Transposed weights as three BF16 terms, one 16-byte chunk (8
+    // consecutive K values of one output row) at a time; all of a thread's
+    // loads issued before its first split.
+    constexpr int n1 = kHidden * 4, n2 = kHidden * 8, n3 = C * 8;
+    constexpr int kPer = (n1 + n2 + n3 + 32 * kMlpEpiWarps - 1) / (32 * kMlpEpiWarps);
+    float xs[kPer][8];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int q = tid + j * 32 * kMlpEpiWarps;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float x = 0.0f;
+        if (q < n1) {
+          const int o = q / 4, k = 8 * (q % 4) + i;  // Wh^T[o][k] = Wh[k][o], k < 11
+          if (k < kHeads) x = __ldg(a.wh + k * kHidden + o);
+        } else if (q < n1 + n2) {
+          const int o1 = (q - n1) / 8, o = 8 * ((q - n1) % 8) + i;  // W2^T[o1][o] = W2[o][o1]
+          x = __ldg(a.w2 + o * kHidden + o1);
+        } else if (q < n1 + n2 + n3) {
+          const int c = (q - n1 - n2) / 8, o1 = 8 * ((q - n1 - n2) % 8) + i;  // W1^T[c][o1] = W1[o1][c]
+          x = __ldg(a.w1 + o1 * C + c);
+        }
+        xs[j][i] = x;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int q = tid + j * 32 * kMlpEpiWarps;
+      if (q < n1) store_split8(sm + K::off_b1, K::b1_term, chunk_off(q / 4, q % 4, 64), xs[j]);
+      else if (q < n1 + n2) store_split8(sm + K::off_b2, K::b2_term, chunk_off((q - n1) / 8, (q - n1) % 8, 128), xs[j]);
+      else if (q < n1 + n2 + n3)
+        store_split8(sm + K::off_b3, K::b3_term, chunk_off((q - n1 - n2) / 8, (q - n1 - n2) % 8, 128), xs[j]);
+    }
+    fence_proxy_async();
+  }
+  if (warp == kMlpEpiWarps) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
+                 "r"(kMlpTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+
+  if (warp == kMlpEpiWarps) {
+    // ---------------- tensor-core issue ----------------
+    if (lane == 0) {
+      const uint32_t s_a = sb + K::off_a;
+      constexpr uint32_t id64 = mma_idesc(128, 64, 0, 0), idc = mma_idesc(128, C, 0, 0);
+      auto layer = [&](uint32_t col, uint32_t b_base, uint32_t b_term, uint32_t row_bytes, uint64_t layout, int ksteps,
+                       uint32_t idesc) {
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+          for (int k = 0; k < ksteps; ++k)
+            mma_bf16(tmem + col, smem_desc(s_a + kPairA[p] * K::a_term + 32u * k, 16, 8 * row_bytes, layout),
+                     smem_desc(b_base + kPairW[p] * b_term + 32u * k, 16, 8 * row_bytes, layout), idesc,
+                     (p > 0 || k > 0) ? 1u : 0u);
+      };
+      for (int i = 0; i < n_mine; ++i) {
+        const uint32_t ph = i & 1;
+        if (!mlp_wait(&bars[kBwA0], ph, s_abort, a.err)) break;
+        tc_fence_after();
+        layer(kColD1, sb + K::off_b1, K::b1_term, 64, kLayout64B, 2, id64);
+        mma_commit(&bars[kBwD1]);
+        if (!mlp_wait(&bars[kBwA2], ph, s_abort, a.err)) break;
+        tc_fence_after();
+        layer(kColD2, sb + K::off_b2, K::b2_term, 128, kLayout128B, 4, id64);
+        mma_commit(&bars[kBwD2]);
+        if (!mlp_wait(&bars[kBwA3], ph, s_abort, a.err)) break;
+        tc_fence_after();
+        layer(kColD3, sb + K::off_b3, K::b3_term, 128, kLayout128B, 4, idc);
+        mma_commit(&bars[kBwD3]);
+      }
+      mma_commit(&bars[kBwDrain]);
+      if (!mbar_wait(&bars[kBwDrain], 0)) set_err(a.err, kErrTimeout);
+    }
+  } else {
+    // ---------------- epilogue: one Gaussian per thread ----------------
+    const int r = warp * 32 + lane;
+    const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+    unsigned char* s_a = sm + K::off_a;
+    // A masked 64-wide layer output as the three terms of the next input.
+    auto masked = [&](uint32_t col, uint64_t mask) {
+      uint32_t v[32];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        tmem_ld32(t_row + col + 32 * half, v);
+        tmem_wait_ld(v);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float x[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int o = 32 * half + 8 * c + j;
+            x[j] = ((mask >> o) & 1ull) ? __uint_as_float(v[8 * c + j]) : 0.0f;
+          }
+          store_split8(s_a, K::a_term, chunk_off(r, 4 * half + c, 128), x);
+        }
+      }
+    };
+    bool ok = true;
+    for (int i = 0; ok && i < n_mine; ++i) {
+      const uint32_t ph = i & 1;
+      const int64_t g = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * kMlpBM + r;
+      // dd of this row (zero for an inactive Gaussian or a row past P) as
+      // the first layer's input; the masks for the later layers.  Row g of
+      // the previous tile's products is complete (its D3 was waited for).
+      float x[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) x[k] = 0.0f;
+      uint64_t m1 = 0, m2 = 0;
+      if (g < a.P) {
+        const float4* dd4 = reinterpret_cast<const float4*>(a.ddstate + g * 12);
+        const float4 q0 = dd4[0], q1 = dd4[1], q2 = dd4[2];
+        if (q2.w != 0.0f) {
+          x[0] = q0.x; x[1] = q0.y; x[2] = q0.z; x[3] = q0.w; x[4] = q1.x; x[5] = q1.y;
+          x[6] = q1.z; x[7] = q1.w; x[8] = q2.x; x[9] = q2.y; x[10] = q2.z;
+          const uint4 mk = reinterpret_cast<const uint4*>(a.dstate + g * kDStride)[3];
+          m1 = (uint64_t)mk.x | ((uint64_t)mk.y << 32);
+          m2 = (uint64_t)mk.z | ((uint64_t)mk.w << 32);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) store_split8(s_a, K::a_term, chunk_off(r, c, 64), x + 8 * c);
+      fence_proxy_async();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars[kBwA0]);
+      if (!mlp_wait(&bars[kBwD1], ph, s_abort, a.err)) break;
+      tc_fence_after();
+      masked(kColD1, m2);  // g2
+      fence_proxy_async();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars[kBwA2]);
+      if (!mlp_wait(&bars[kBwD2], ph, s_abort, a.err)) break;
+      tc_fence_after();
+      masked(kColD2, m1);  // d1
+      fence_proxy_async();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars[kBwA3]);
+      if (!mlp_wait(&bars[kBwD3], ph, s_abort, a.err)) break;
+      tc_fence_after();
+#pragma unroll
+      for (int part = 0; part < C / 32; ++part) {
+        uint32_t v[32];
+        tmem_ld32(t_row + kColD3 + 32 * part, v);
+        tmem_wait_ld(v);
+        if (g < a.P) {
+          float4* o = reinterpret_cast<float4*>(a.df + g * C + 32 * part);
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            o[e] = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                               __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
+        }
+      }
+      tc_fence_before();
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == kMlpEpiWarps) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMlpTmemCols) : "memory");
+  }
+}
+
+template <int C>
+cudaError_t launch_mlp_bwd_t(const GaussArgs& g, const GaussBwdArgs& b, float* df, cudaStream_t st) {
+  using K = MlpBwdCfg<C>;
+  MlpBwdArgs a{};
+  a.P = g.P;
+  a.ntiles = (g.P + kMlpBM - 1) / kMlpBM;
+  a.w1 = g.w1; a.w2 = g.w2; a.wh = g.wh;
+  a.ddstate = b.ddstate;
+  a.dstate = g.dstate;
+  a.df = df;
+  a.err = g.err;
+  const int sms = num_sms();
+  int grid = 2 * (sms > 0 ? sms : 1);
+  if (grid > a.ntiles) grid = a.ntiles;
+  auto k = deform_mlp_bwd_kernel<C>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::launch_bytes);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kMlpBwdThreads, K::launch_bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int C>
 cudaError_t launch_mlp_t(const GaussArgs& g, cudaStream_t st) {
   using K = MlpCfg<C>;
@@ -338,6 +585,14 @@ cudaError_t launch_mlp_t(const GaussArgs& g, cudaStream_t st) {
 }
 
 }  // namespace
+
+cudaError_t launch_deform_mlp_bwd(const GaussArgs& g, const GaussBwdArgs& b, float* df, cudaStream_t st) {
+  if (g.P <= 0 || !g.has_deform) return cudaSuccess;
+  if (!df || !g.dstate || !b.ddstate) return cudaErrorInvalidValue;
+  if (g.C == 32) return launch_mlp_bwd_t<32>(g, b, df, st);
+  if (g.C == 64) return launch_mlp_bwd_t<64>(g, b, df, st);
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_deform_mlp(const GaussArgs& g, cudaStream_t st) {
   if (g.P <= 0 || !g.has_deform) return cudaSuccess;

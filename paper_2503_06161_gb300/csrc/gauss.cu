@@ -8,8 +8,8 @@
 //   gauss_bwd: fixed-order sum of the per-(tile, Gaussian) partials, then
 //              the reverse of projection, colour, activations and the
 //              deformation query back to the canonical parameters (the MLP
-//              reverse from the forward's unit masks, weights in shared
-//              memory as uniform broadcast reads).
+//              reverse, from the forward's unit masks, on the tensor cores:
+//              deform_mlp.cu).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -224,88 +224,6 @@ __device__ __forceinline__ void hexplane_sample_warp(const GaussArgs& a, const f
     for (int c = 0; c < C; ++c) f[c] = sfw[lane * (C + 1) + c];
   }
   __syncwarp();
-}
-
-// Shared-memory weights, laid out so every inner loop reads 16-byte
-// broadcast rows: w1[64][C], b1[64], w2t[64][64] with w2t[i][o] = W2[o][i],
-// b2[64], wh[11][64], wht[64][12] with wht[o][k] = Wh[k][o], bh[12].
-template <int C>
-struct Mlp {
-  static constexpr int kW1 = 0, kB1 = kHidden * C, kW2t = kB1 + kHidden, kB2 = kW2t + kHidden * kHidden,
-                       kWh = kB2 + kHidden, kWht = kWh + kHeads * kHidden, kBh = kWht + kHidden * 12,
-                       kFloats = kBh + 12;
-};
-template <int C>
-constexpr int mlp_floats() { return Mlp<C>::kFloats; }
-
-template <int C>
-__device__ __forceinline__ void load_mlp(const GaussArgs& a, float* sw) {
-  using L = Mlp<C>;
-  for (int i = threadIdx.x; i < kHidden * C; i += blockDim.x) sw[L::kW1 + i] = a.w1[i];
-  for (int i = threadIdx.x; i < kHidden * kHidden; i += blockDim.x) {
-    const int o = i / kHidden, in = i % kHidden;  // W2[o][in]
-    sw[L::kW2t + in * kHidden + o] = a.w2[i];
-  }
-  for (int i = threadIdx.x; i < kHeads * kHidden; i += blockDim.x) {
-    const int k = i / kHidden, o = i % kHidden;   // Wh[k][o]
-    sw[L::kWh + i] = a.wh[i];
-    sw[L::kWht + o * 12 + k] = a.wh[i];
-  }
-  for (int i = threadIdx.x; i < kHidden; i += blockDim.x) {
-    sw[L::kB1 + i] = a.b1[i];
-    sw[L::kB2 + i] = a.b2[i];
-    sw[L::kWht + i * 12 + 11] = 0.0f;
-  }
-  if (threadIdx.x < 12) sw[L::kBh + threadIdx.x] = threadIdx.x < kHeads ? a.bh[threadIdx.x] : 0.0f;
-}
-
-// df = (d delta / d f)^T dd from the forward's unit masks: no activation is
-// recomputed.  g2 = m2 (Wh^T dd), d1 = m1 (W2^T g2), df = W1^T d1.
-template <int C>
-__device__ __forceinline__ void mlp_backward(const float* sw, uint64_t m1, uint64_t m2, const float dd[kHeads],
-                                             float df[C]) {
-  using L = Mlp<C>;
-  float g2[kHidden];
-#pragma unroll
-  for (int o = 0; o < kHidden; ++o) {
-    const float4* wr = reinterpret_cast<const float4*>(sw + L::kWht + o * 12);
-    const float4 a0 = wr[0], a1 = wr[1], a2 = wr[2];
-    float acc = a0.x * dd[0];
-    acc = fmaf(a0.y, dd[1], acc); acc = fmaf(a0.z, dd[2], acc); acc = fmaf(a0.w, dd[3], acc);
-    acc = fmaf(a1.x, dd[4], acc); acc = fmaf(a1.y, dd[5], acc); acc = fmaf(a1.z, dd[6], acc);
-    acc = fmaf(a1.w, dd[7], acc); acc = fmaf(a2.x, dd[8], acc); acc = fmaf(a2.y, dd[9], acc);
-    acc = fmaf(a2.z, dd[10], acc);
-    g2[o] = ((m2 >> o) & 1ull) ? acc : 0.0f;
-  }
-  float2 dfp[C / 2];
-#pragma unroll
-  for (int c = 0; c < C / 2; ++c) dfp[c] = make_float2(0.0f, 0.0f);
-#pragma unroll 1
-  for (int o1 = 0; o1 < kHidden; ++o1) {
-    if (!((m1 >> o1) & 1ull)) continue;
-    const float4* w2r = reinterpret_cast<const float4*>(sw + L::kW2t + o1 * kHidden);
-    float2 d2 = make_float2(0.0f, 0.0f);
-#pragma unroll
-    for (int o4 = 0; o4 < kHidden / 4; ++o4) {
-      const float4 w = w2r[o4];
-      d2 = __ffma2_rn(make_float2(w.x, w.y), make_float2(g2[4 * o4], g2[4 * o4 + 1]), d2);
-      d2 = __ffma2_rn(make_float2(w.z, w.w), make_float2(g2[4 * o4 + 2], g2[4 * o4 + 3]), d2);
-    }
-    const float d1 = d2.x + d2.y;
-    const float2 dd1 = make_float2(d1, d1);
-    const float4* w1r = reinterpret_cast<const float4*>(sw + L::kW1 + o1 * C);
-#pragma unroll
-    for (int c4 = 0; c4 < C / 4; ++c4) {
-      const float4 w = w1r[c4];
-      dfp[2 * c4] = __ffma2_rn(make_float2(w.x, w.y), dd1, dfp[2 * c4]);
-      dfp[2 * c4 + 1] = __ffma2_rn(make_float2(w.z, w.w), dd1, dfp[2 * c4 + 1]);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < C / 2; ++c) {
-    df[2 * c] = dfp[c].x;
-    df[2 * c + 1] = dfp[c].y;
-  }
 }
 
 // dmu from df (thread-private slice of shared memory, C floats) through the
@@ -1034,34 +952,27 @@ __global__ void __launch_bounds__(kThreads) gauss_bwd_proj_kernel(const GaussArg
 // Mean gradient through the deformation: MLP reverse from the stored
 // HexPlane feature, then the six bilinear samples (Sec. 3.2, Eq. 4-6).
 template <int C>
-__global__ void __launch_bounds__(kThreads, 2) gauss_bwd_deform_kernel(const GaussArgs a, const GaussBwdArgs b) {
+__global__ void __launch_bounds__(kThreads, 2) gauss_bwd_deform_kernel(const GaussArgs a, const GaussBwdArgs b,
+                                                                     const float* __restrict__ df_all) {
   extern __shared__ __align__(16) float sw[];
-  float* s_df = sw + mlp_floats<C>();                               // [kThreads][C]
+  float* s_df = sw;                                                  // [kThreads][C]
   float* s_red = s_df + (size_t)kThreads * C + (threadIdx.x >> 5) * 32 * 12;  // this warp's [32][12]
-  load_mlp<C>(a, sw);
-  __syncthreads();
   const int g = blockIdx.x * kThreads + threadIdx.x;
   bool active = false;
   float dd[kHeads];
-  uint64_t m1 = 0, m2 = 0;
   if (g < a.P) {
     const float4* dd4 = reinterpret_cast<const float4*>(b.ddstate + (size_t)g * 12);
     const float4 q0 = dd4[0], q1 = dd4[1], q2 = dd4[2];
     active = q2.w != 0.0f;
-    dd[0] = q0.x; dd[1] = q0.y; dd[2] = q0.z; dd[3] = q0.w; dd[4] = q1.x; dd[5] = q1.y;
-    dd[6] = q1.z; dd[7] = q1.w; dd[8] = q2.x; dd[9] = q2.y; dd[10] = q2.z;
-    const uint4 mk = reinterpret_cast<const uint4*>(a.dstate + (size_t)g * kDStride)[3];
-    m1 = (uint64_t)mk.x | ((uint64_t)mk.y << 32);
-    m2 = (uint64_t)mk.z | ((uint64_t)mk.w << 32);
+    dd[0] = q0.x; dd[1] = q0.y; dd[2] = q0.z;
   }
   if (!__any_sync(0xFFFFFFFFu, active)) return;  // whole warp idle
+  // dL/df of this Gaussian: the MLP reverse on the tensor cores wrote it.
   float* my_df = s_df + (size_t)threadIdx.x * C;
   if (active) {
-    float df[C];
-    mlp_backward<C>(sw, m1, m2, dd, df);
+    const float4* src = reinterpret_cast<const float4*>(df_all + (size_t)g * C);
 #pragma unroll
-    for (int c4 = 0; c4 < C / 4; ++c4)
-      reinterpret_cast<float4*>(my_df)[c4] = make_float4(df[4 * c4], df[4 * c4 + 1], df[4 * c4 + 2], df[4 * c4 + 3]);
+    for (int c4 = 0; c4 < C / 4; ++c4) reinterpret_cast<float4*>(my_df)[c4] = src[c4];
   }
   __syncwarp();
   float mu0[3] = {0.f, 0.f, 0.f};
@@ -1106,12 +1017,18 @@ cudaError_t launch_gauss_fwd(const GaussArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// The MLP reverse on the tensor cores writes dL/df into the region of the
+// split features (free once the forward's MLP has read them), then the
+// HexPlane reverse takes it from there.
 template <int C>
 static cudaError_t launch_bwd_deform_t(const GaussArgs& a, const GaussBwdArgs& b, cudaStream_t st) {
-  const size_t smem = (mlp_floats<C>() + (size_t)kThreads * C + (size_t)8 * 32 * 12) * sizeof(float);
+  float* df = reinterpret_cast<float*>(a.fsplit);
+  cudaError_t e = launch_deform_mlp_bwd(a, b, df, st);
+  if (e != cudaSuccess) return e;
+  const size_t smem = ((size_t)kThreads * C + (size_t)8 * 32 * 12) * sizeof(float);
   auto k = gauss_bwd_deform_kernel<C>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k<<<ceil_div(a.P, kThreads), kThreads, smem, st>>>(a, b);
+  if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  k<<<ceil_div(a.P, kThreads), kThreads, smem, st>>>(a, b, df);
   return cudaGetLastError();
 }
 

@@ -53,6 +53,9 @@ cudaError_t launch_gauss_fwd(const GaussArgs& a, cudaStream_t st);
 // Deformation MLP on the tensor cores: a.fsplit -> a.dstate (deform_mlp.cu).
 cudaError_t launch_deform_mlp(const GaussArgs& a, cudaStream_t st);
 cudaError_t launch_gauss_bwd(const GaussArgs& a, const GaussBwdArgs& b, cudaStream_t st, cudaEvent_t mid);
+// Reverse of the deformation MLP on the tensor cores: b.ddstate -> df [P][C]
+// (deform_mlp.cu).
+cudaError_t launch_deform_mlp_bwd(const GaussArgs& a, const GaussBwdArgs& b, float* df, cudaStream_t st);
 
 // Integer stage: binning of projected Gaussians into tile lists.
 struct BinArgs {
