@@ -141,10 +141,14 @@ def flops_gauss_fwd(P, C, deform=True):
 
 
 def flops_gauss_bwd(Pvis, P, C, deform=True):
-    recompute = flops_gauss_fwd(1, C, deform)
-    mlp_b = 2 * (64 * C + 64 * 64 + 11 * 64 + 64 * 64 + 64 * C) if deform else 0
-    grid_b = 6 * C * 24 if deform else 0
-    return Pvis * (recompute + mlp_b + grid_b + 600)
+    # Per visible Gaussian: the projection / colour / activation reverse
+    # (~600 + the SH degree-3 basis 450), and with a deformation the MLP
+    # reverse from the stored unit masks (FP32-equivalent; on the tensor
+    # cores) and the HexPlane reverse (samples recomputed, 24 per plane corner
+    # derivative term).
+    mlp_b = 2 * (11 * 64 + 64 * 64 + 64 * C) if deform else 0
+    grid_b = 6 * C * (9 + 24) if deform else 0
+    return Pvis * (mlp_b + grid_b + 600 + 450)
 
 
 def flops_composite_fwd(visits, contribs, D):
@@ -438,6 +442,9 @@ def run_ours(args, world, rank, local):
         kern["deform_project"].pop("frac_of_alu_peak")
         kern["deform_project"]["note"] = ("FP32-equivalent algorithmic flops over the gather, the tensor-core "
                                           "MLP and the projection")
+        kern["gauss_bwd"].pop("frac_of_alu_peak")
+        kern["gauss_bwd"]["note"] = ("FP32-equivalent algorithmic flops over the projection reverse, the "
+                                     "tensor-core MLP reverse and the HexPlane reverse")
     for n in ("binning", "loss", "feat_grad"):
         kern[n] = {"ms": round(stages[n], 4)}
     hbm, hbm_basis = hbm_peak()
