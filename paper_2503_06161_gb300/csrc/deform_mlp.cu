@@ -467,27 +467,40 @@ __global__ void __launch_bounds__(kMlpBwdThreads, 2) deform_mlp_bwd_kernel(const
         }
       }
     };
+    // This row's dd (zero for an inactive Gaussian or a row past P) and unit
+    // masks of tile i, loaded one tile ahead so that their latency overlaps
+    // the previous tile's layers.
+    float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, n2 = n0;
+    uint4 nmk = make_uint4(0u, 0u, 0u, 0u);
+    auto load_in = [&](int i) {
+      const int64_t g = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * kMlpBM + r;
+      n0 = n1 = n2 = make_float4(0.f, 0.f, 0.f, 0.f);
+      nmk = make_uint4(0u, 0u, 0u, 0u);
+      if (g < a.P) {
+        const float4* dd4 = reinterpret_cast<const float4*>(a.ddstate + g * 12);
+        n0 = dd4[0]; n1 = dd4[1]; n2 = dd4[2];
+        nmk = reinterpret_cast<const uint4*>(a.dstate + g * kDStride)[3];
+      }
+    };
+    if (n_mine > 0) load_in(0);
     bool ok = true;
     for (int i = 0; ok && i < n_mine; ++i) {
       const uint32_t ph = i & 1;
       const int64_t g = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * kMlpBM + r;
-      // dd of this row (zero for an inactive Gaussian or a row past P) as
-      // the first layer's input; the masks for the later layers.  Row g of
-      // the previous tile's products is complete (its D3 was waited for).
+      const float4 q0 = n0, q1 = n1, q2 = n2;
+      const uint4 mk = nmk;
+      if (i + 1 < n_mine) load_in(i + 1);
+      // dd as the first layer's input (the previous tile's products are
+      // complete: its D3 was waited for), the masks for the later layers.
       float x[32];
 #pragma unroll
       for (int k = 0; k < 32; ++k) x[k] = 0.0f;
       uint64_t m1 = 0, m2 = 0;
-      if (g < a.P) {
-        const float4* dd4 = reinterpret_cast<const float4*>(a.ddstate + g * 12);
-        const float4 q0 = dd4[0], q1 = dd4[1], q2 = dd4[2];
-        if (q2.w != 0.0f) {
-          x[0] = q0.x; x[1] = q0.y; x[2] = q0.z; x[3] = q0.w; x[4] = q1.x; x[5] = q1.y;
-          x[6] = q1.z; x[7] = q1.w; x[8] = q2.x; x[9] = q2.y; x[10] = q2.z;
-          const uint4 mk = reinterpret_cast<const uint4*>(a.dstate + g * kDStride)[3];
-          m1 = (uint64_t)mk.x | ((uint64_t)mk.y << 32);
-          m2 = (uint64_t)mk.z | ((uint64_t)mk.w << 32);
-        }
+      if (q2.w != 0.0f) {
+        x[0] = q0.x; x[1] = q0.y; x[2] = q0.z; x[3] = q0.w; x[4] = q1.x; x[5] = q1.y;
+        x[6] = q1.z; x[7] = q1.w; x[8] = q2.x; x[9] = q2.y; x[10] = q2.z;
+        m1 = (uint64_t)mk.x | ((uint64_t)mk.y << 32);
+        m2 = (uint64_t)mk.z | ((uint64_t)mk.w << 32);
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) store_split8(s_a, K::a_term, chunk_off(r, c, 64), x + 8 * c);
