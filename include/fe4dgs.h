@@ -80,7 +80,9 @@ typedef struct {
  * h1 = relu(W1 f + b1), h2 = relu(W2 h1 + b2), delta = Wh h2 + bh with
  * delta = (d_mu[3], d_q[4], d_s[3], d_o[1]) applied as
  * mu + d_mu (+ noise_scale * t * noise), normalise(q + d_q), log_s + d_s,
- * logit + d_o. */
+ * logit + d_o.  The MLP and its reverse run on the tensor cores with FP32
+ * accuracy: each operand as three BF16 terms, six term products per layer
+ * accumulated in FP32. */
 typedef struct {
   int C;                    /* plane channels: 32 or 64 */
   int R;                    /* plane resolution (R x R), >= 2 */
@@ -152,8 +154,12 @@ typedef struct {
 } fe_stats;
 
 /* Bytes of workspace for P Gaussians, D channels, a width x height image
- * and opts (NULL = defaults).  Returns FE_ERR_UNSUPPORTED for a tile shape
- * or D that is not compiled in, or for more than 8192 tiles. */
+ * and opts (NULL = defaults).  It includes, for any deformation field the
+ * forward may be given (HexPlane channels C <= 64), the deformation state
+ * (64 B per Gaussian) and the HexPlane features split into three BF16
+ * terms for the tensor-core MLP (384 B per Gaussian).  Returns
+ * FE_ERR_UNSUPPORTED for a tile shape or D that is not compiled in, or for
+ * more than 8192 tiles. */
 fe_status fe_workspace_size(int P, int D, int width, int height, const fe_opts *opts, size_t *bytes);
 
 /* Forward pass (Sec. 3.2-3.3): deform (deform may be NULL: static scene)
