@@ -83,7 +83,7 @@ static_assert(sizeof(Header) == 256, "header is 256 bytes");
 // all SMs).
 constexpr int kSortItems = 16;
 constexpr int kSortChunk = kThreads * kSortItems;
-constexpr int kPItems = 4;
+constexpr int kPItems = 8;
 constexpr int kPChunk = kThreads * kPItems;
 // Depth-ordered Gaussians per block of the tile count / scatter kernels
 // (each of the 8 warps walks 64 of them in order).
