@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(kThreads) partial_reduce_kernel(const GaussBwd
 // gradients of log-scale, quaternion, opacity logit and SH; the mean's
 // path through the HexPlane grid is added by gauss_bwd_deform_kernel from
 // dd = d L / d delta stored per Gaussian.
-__global__ void __launch_bounds__(kThreads) gauss_bwd_proj_kernel(const GaussArgs a, const GaussBwdArgs b) {
+__global__ void __launch_bounds__(kThreads, 2) gauss_bwd_proj_kernel(const GaussArgs a, const GaussBwdArgs b) {
   const int g = blockIdx.x * kThreads + threadIdx.x;
   if (g >= a.P) return;
   float acc[kPartialScalars + 2];
