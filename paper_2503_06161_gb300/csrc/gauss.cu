@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(kThreads, 2) gauss_fwd_kernel(const GaussArgs 
 __host__ __device__ constexpr int ranks_per_warp(int D) { return (partial_stride(D) + 31) / 32 <= 2 ? 8 : 4; }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads) partial_reduce_kernel(const GaussBwdArgs b, int P) {
+__global__ void __launch_bounds__(kThreads, 3) partial_reduce_kernel(const GaussBwdArgs b, int P) {
   constexpr int NP = partial_stride(D);
   constexpr int NQ = (NP + 31) / 32;  // columns per lane
   constexpr int RG = NQ <= 2 ? 16 : (NQ <= 4 ? 8 : 4);  // rows in flight
