@@ -815,7 +815,6 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
       jm[w8] = s_jact[w8];
       bm |= jm[w8];
     }
-    const int nact = __popc(bm);
     // One item = four consecutive columns of an active entry's partial row
     // [features | du dv dA dB dCc dopacity | r g b | depth | 0 0]: the warp
     // partials (feature columns from the warp slices, the rest from the
@@ -823,11 +822,13 @@ __device__ __forceinline__ void bwd_tile(const CompositeArgs& a, const int tile,
     // 16-byte store.  A channel-split pass that is not the first adds its
     // geometric terms (du .. dopacity) to the row the first pass wrote and
     // leaves colour and depth alone.
+    // Items over every entry slot (a compile-time count of column groups):
+    // slots no pixel blended, and the last group outside the first pass,
+    // are skipped.
     constexpr int NQ = D / 4 + 3;
-    const int nq = a.aux ? NQ : NQ - 1;
-    for (int item = tid; item < nact * nq; item += kThreads) {
-      const int ja = item / nq, q4 = item - ja * nq;
-      const int j = (int)__fns(bm, 0, ja + 1);  // the ja-th active entry
+    for (int item = tid; item < B * NQ; item += kThreads) {
+      const int j = item / NQ, q4 = item - j * NQ;
+      if (!((bm >> j) & 1u) || (!a.aux && q4 == NQ - 1)) continue;
       const bool fcol = q4 < D / 4;
       const float* src = fcol ? s_slice + j * NC + 4 + 4 * q4 : s_geo + j * K::GR + 4 * (q4 - D / 4);
       const int wstride = fcol ? K::SLICE : (B + 1) * K::GR;
