@@ -283,6 +283,23 @@ def test_backward_matches_oracle(D, deform, flagged_max):
     check_grads(errs, grep, near_max=2)
 
 
+@pytest.mark.parametrize("P,C", [(37, 32), (100, 64), (129, 32)])
+def test_deformed_few_gaussians_forward_and_backward(P, C):
+    # Fewer Gaussians than one 128-row tile of the deformation MLP (its
+    # feature rows are read as whole tiles), and one past a tile: forward
+    # and reverse against the oracle.
+    sc, cam, df = deformed_case(P=P, W=64, H=48, D=16, C=C, R=8, seed=11)
+    t, bg = 0.6, (0.1, 0.1, 0.1)
+    run = gpu_forward(sc, cam, df, t=t, bg=bg)
+    pix = O.all_pixels(cam.width, cam.height)
+    e, rep, flip = forward_parity(run, sc, cam, df, t=t, bg=bg)
+    check_forward(e, rep, flagged_max=8)
+    G = _upstream(len(pix), 16)
+    got = gpu_backward(run, t, G["rgb"], G["depth"], G["alpha"], G["feat"])
+    errs, grep = grad_parity(got, sc, cam, df, t, bg, pix, G, flip)
+    check_grads(errs, grep, near_max=2)
+
+
 def test_backward_matches_central_differences():
     # Tiny scene: GPU gradients vs central differences of the FP64 oracle forward.
     rng = np.random.default_rng(2)
