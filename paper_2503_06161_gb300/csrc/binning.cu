@@ -146,14 +146,18 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint32_t* __re
     sm.wcnt[w][tid] = bcount;
     bcount += c;
   }
-  // Publish the aggregate, look back for the exclusive prefix of this digit.
-  // Predecessors are read four at a time (independent loads, overlapping
-  // latencies), then taken in order until the first inclusive prefix.
+  // Publish the aggregate; the two block scans, which do not need the
+  // prefix, run before the look-back for the exclusive prefix of this digit,
+  // so predecessors have more time to resolve theirs.  Predecessors are read
+  // four at a time (independent loads, overlapping latencies), then taken in
+  // order until the first inclusive prefix.
+  st_vol(status + (size_t)b * 256 + tid, (b == 0 ? kFlagPre : kFlagAgg) | bcount);
+  uint32_t tot;
+  const uint32_t gexcl = block_excl_scan(hist[tid], sm.scan, tot);
+  const uint32_t bst = block_excl_scan(bcount, sm.scan, tot);
+  sm.bstart[tid] = bst;
   uint32_t excl = 0;
-  if (b == 0) {
-    st_vol(status + tid, kFlagPre | bcount);
-  } else {
-    st_vol(status + (size_t)b * 256 + tid, kFlagAgg | bcount);
+  if (b > 0) {
     bool fin = false;
     for (int64_t j = (int64_t)b - 1; !fin && j >= 0; j -= 4) {
       uint32_t sv[4];
@@ -180,11 +184,7 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint32_t* __re
     }
     st_vol(status + (size_t)b * 256 + tid, kFlagPre | ((excl + bcount) & kValMask));
   }
-  uint32_t tot;
-  const uint32_t gexcl = block_excl_scan(hist[tid], sm.scan, tot);
   sm.gbase[tid] = gexcl + excl;
-  const uint32_t bst = block_excl_scan(bcount, sm.scan, tot);
-  sm.bstart[tid] = bst;
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
@@ -208,12 +208,15 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint32_t* __re
 // Decoupled look-back over a 64-bit running total: block b publishes its
 // aggregate, then sums its predecessors back to the first inclusive prefix,
 // reading them eight at a time.
-__device__ __forceinline__ uint64_t lookback64(uint64_t* status, uint32_t b, uint64_t aggregate, uint32_t* err) {
-  if (b == 0) {
-    st_vol64(status, kFlagPre64 | aggregate);
-    return 0;
-  }
-  st_vol64(status + b, kFlagAgg64 | aggregate);
+// In two halves, so a block can do independent work between them: publish
+// the aggregate (block 0: its inclusive prefix), then resolve the exclusive
+// prefix from the predecessors.
+__device__ __forceinline__ void lookback64_publish(uint64_t* status, uint32_t b, uint64_t aggregate) {
+  st_vol64(status + b, (b == 0 ? kFlagPre64 : kFlagAgg64) | aggregate);
+}
+
+__device__ __forceinline__ uint64_t lookback64_resolve(uint64_t* status, uint32_t b, uint64_t aggregate, uint32_t* err) {
+  if (b == 0) return 0;
   uint64_t excl = 0;
   bool fin = false;
   for (int64_t j = (int64_t)b - 1; !fin && j >= 0; j -= 8) {
@@ -241,6 +244,11 @@ __device__ __forceinline__ uint64_t lookback64(uint64_t* status, uint32_t b, uin
   }
   st_vol64(status + b, kFlagPre64 | (excl + aggregate));
   return excl;
+}
+
+__device__ __forceinline__ uint64_t lookback64(uint64_t* status, uint32_t b, uint64_t aggregate, uint32_t* err) {
+  lookback64_publish(status, b, aggregate);
+  return lookback64_resolve(status, b, aggregate, err);
 }
 
 // Step 2: block b (ticket) owns depth ranks [512 b, 512 b + 512); thread t
@@ -289,7 +297,24 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const CountArgs a) 
   }
   uint32_t btot;
   const uint32_t texcl = block_excl_scan(tsum, s_scan, btot);
-  if (tid == 0) s_prefix = lookback64(a.status, b, btot, &a.hdr->err);
+  // The block's total goes out at once; its tile counts, which do not need
+  // the prefix, are taken while the predecessors resolve theirs.
+  if (tid == 0) lookback64_publish(a.status, b, btot);
+  // Tile counts: each warp walks its Gaussians, lanes over one rect's tiles.
+  const int nloc = (int)min((int64_t)kBinChunk, (int64_t)a.P - start);
+  const int i0 = warp * (kBinChunk / 8), i1 = min(nloc, i0 + kBinChunk / 8);
+  for (int i = i0; i < i1; ++i) {
+    const uint32_t c = s_c[i];
+    if (!c) continue;
+    const ushort4 rc = s_rect[i];
+    const uint32_t wdt = rc.z - rc.x + 1u;
+    const float iw = s_iw[i];
+    for (uint32_t k = lane; k < c; k += 32) {
+      const uint32_t dy = (uint32_t)(((float)k + 0.5f) * iw), dx = k - dy * wdt;  // exact for these sizes
+      atomicAdd(&s_cnt[(rc.y + dy) * (uint32_t)a.tiles_x + rc.x + dx], 1u);
+    }
+  }
+  if (tid == 0) s_prefix = lookback64_resolve(a.status, b, btot, &a.hdr->err);
   __syncthreads();
   uint64_t run = s_prefix + texcl;
 #pragma unroll
@@ -306,20 +331,6 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const CountArgs a) 
     a.offs[a.P] = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
     a.hdr->num_dups = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
     if (run > (uint64_t)a.cap) set_err(&a.hdr->err, kErrOverflow);
-  }
-  // Tile counts: each warp walks its Gaussians, lanes over one rect's tiles.
-  const int nloc = (int)min((int64_t)kBinChunk, (int64_t)a.P - start);
-  const int i0 = warp * (kBinChunk / 8), i1 = min(nloc, i0 + kBinChunk / 8);
-  for (int i = i0; i < i1; ++i) {
-    const uint32_t c = s_c[i];
-    if (!c) continue;
-    const ushort4 rc = s_rect[i];
-    const uint32_t wdt = rc.z - rc.x + 1u;
-    const float iw = s_iw[i];
-    for (uint32_t k = lane; k < c; k += 32) {
-      const uint32_t dy = (uint32_t)(((float)k + 0.5f) * iw), dx = k - dy * wdt;  // exact for these sizes
-      atomicAdd(&s_cnt[(rc.y + dy) * (uint32_t)a.tiles_x + rc.x + dx], 1u);
-    }
   }
   __syncthreads();
   for (int t = tid; t < a.ntiles; t += kThreads) a.table[(size_t)t * a.nblocks + b] = s_cnt[t];
