@@ -463,7 +463,9 @@ def run_ours(args, world, rank, local):
     dom = max(work, key=lambda n: stages[n])
     ach = work[dom] / (stages[dom] * 1e-3) / 1e12
     roofline = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
-                "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4), "traffic": kernel_traffic(dom, args.workload),
+                "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4),
+                # The recorded capture is of the workload at its own D: none for a D override.
+                "traffic": kernel_traffic(dom, args.workload) if args.D is None else None,
                 "peak_basis": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz "
                               f"(median SM clock sampled in the timed region; {alu_peak_max:.1f} at 2070 MHz max)",
                 "fma_probe_tflops": round(probe_tflops, 2)}
